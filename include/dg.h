@@ -1,0 +1,154 @@
+/*
+ * dg.h -- C ABI of a GB300-native (sm_103a) library for the right-hand side of entropy-stable,
+ * kinetic-energy-preserving flux-differencing LGL-DGSEM for the compressible Euler equations
+ * (Ranocha, Schlottke-Lakemper, Chan, Rueda-Ramirez, Winters, Hindenlang, Gassner, arXiv:2112.10517).
+ *
+ * The semidiscretization (Sec. 2, Eq. fluxdiff-SBP-opDsplit, curvilinear via Eq. curvilinear-rearrange):
+ *
+ *   du_i = -(1/J_i) [ sum_n sum_k Dt_{i_n k_n} f(u_i, u_k, (Ja^n_i + Ja^n_k)/2)            (volume)
+ *                   + sum_n ( [i_n = p] f*_{upper face} - [i_n = 0] f*_{lower face} ) / w_0 ] (surface)
+ *
+ * with Dt = 2D - M^{-1} B the flux-differencing operator (Eq. opDsplit), f Ranocha's EC/KEP two-point flux
+ * (Eq. flux_ranocha) in directional form, f* the same flux plus optional local Lax-Friedrichs dissipation at
+ * each interface, Ja the contravariant metric terms and J the Jacobian (Sec. 2.3).
+ *
+ * CONVENTIONS (all entry points)
+ *   Layout.   A state u (and du, and RK scratch) is a C-order array of doubles u[E][nvar][Nd]:
+ *             E elements in lexicographic order (e = e1 + n1*(e2 + n2*e3), e1 fastest), nvar = ndims+2
+ *             conserved variables (rho, rho v_1..rho v_d, rho e), Nd = (p+1)^ndims LGL nodes per element
+ *             with node index i = i1 + N*i2 + N*N*i3 (i1 along xi_1 fastest, N = p+1).
+ *   Memory.   Pointers named *_host are host memory; all other state pointers are DEVICE memory on the
+ *             device that was current at dg_init, 8-byte aligned. The caller owns u, du and scratch and
+ *             keeps them valid until the work queued on `stream` has completed. The library owns its
+ *             context (metrics, tables, workspaces) and frees it in dg_free.
+ *   Streams.  Work is queued on `stream` (NULL: the legacy default stream). Entry points do not
+ *             synchronize the host except where stated (dg_entropy_rate, dg_check_status, the getters).
+ *             Calls that share one context must not run concurrently on different streams (they share
+ *             the context's workspaces).
+ *   Errors.   Every entry point returns a dg_status and never throws or aborts. Argument errors are
+ *             detected before any work is queued. Non-physical states (rho <= 0, p <= 0 or NaN) met by a
+ *             kernel set an asynchronous flag that dg_check_status reports as DG_ERR_NONPHYSICAL.
+ *   Boundary. Every direction is periodic (the paper treats volume terms and interior interfaces only,
+ *             Sec. 2); meshes are conforming, structured boxes of hexahedra (3D) or quadrilaterals (2D).
+ *   Degree.   1 <= polydeg <= 7.
+ */
+#ifndef DG_H
+#define DG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dg_ctx dg_ctx;             /* opaque; created by dg_init, destroyed by dg_free */
+typedef struct CUstream_st* dg_stream_t;  /* identical to cudaStream_t */
+
+typedef enum dg_status {
+  DG_OK = 0,
+  DG_ERR_ARG = 1,          /* invalid argument (null pointer, bad size, unsupported combination) */
+  DG_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  DG_ERR_OOM = 3,          /* device allocation failed */
+  DG_ERR_UNSUPPORTED = 4,  /* valid request the library does not implement (e.g. polydeg > 7) */
+  DG_ERR_NONPHYSICAL = 5,  /* a kernel met rho <= 0, p <= 0 or NaN since the last dg_check_status */
+  DG_ERR_TIMEOUT = 6       /* a bounded host wait gave up */
+} dg_status;
+
+enum { DG_MAP_AFFINE = 0, DG_MAP_SINE = 1, DG_MAP_NODES = 2 };
+enum { DG_SURF_EC = 0, DG_SURF_EC_LLF = 1 };
+enum { DG_FP64 = 0, DG_FP32 = 1 };
+enum { DG_VOL_RANOCHA = 0 };
+enum { DG_RK4_CLASSIC = 0, DG_LSRK45_CK = 1 };
+
+/* Periodic box [lo, hi] with nelem[m] elements per direction (nelem[2], lo[2], hi[2] ignored in 2D).
+   mapping: DG_MAP_AFFINE  x = xi;
+            DG_MAP_SINE    x_m = xi_m + map_amp (L_m/2pi) prod_k sin(2pi (xi_k - c_k)/L_k), L = hi - lo,
+                           c = (lo + hi)/2; on [-pi, pi]^3 this is x_m = xi_m + a sin(xi_1) sin(xi_2) sin(xi_3);
+            DG_MAP_NODES   node_xyz (host, [E][ndims][Nd]) gives the physical node coordinates. */
+typedef struct dg_mesh {
+  int ndims;
+  int nelem[3];
+  double lo[3];
+  double hi[3];
+  int mapping;
+  double map_amp;
+  const double* node_xyz_host;
+} dg_mesh;
+
+/* Optional override of the metric terms (host memory, copied at dg_init):
+   Ja_host [E][ndims][ndims][Nd], Ja[e][n][j][i] = (Ja^n)_j at node i (reference direction n, Cartesian
+   component j); J_host [E][Nd]. When NULL, dg_init computes them from the node coordinates: 2D with the
+   cross-product form and 3D with the conservative curl form (Sec. 2.3, free-stream preservation). */
+typedef struct dg_metrics {
+  const double* Ja_host;
+  const double* J_host;
+} dg_metrics;
+
+/* gamma: ratio of specific heats (> 1). volume_flux: DG_VOL_RANOCHA (Eq. flux_ranocha).
+   surface_flux: DG_SURF_EC (Ranocha flux) or DG_SURF_EC_LLF (plus local Lax-Friedrichs dissipation).
+   precision: DG_FP64, or DG_FP32 (two-point fluxes and line sums in FP32; metric terms computed in
+   FP64 and rounded once; state, du, RK accumulation and the entropy diagnostic in FP64). */
+typedef struct dg_opts {
+  double gamma;
+  int volume_flux;
+  int surface_flux;
+  int precision;
+  int reserved[5]; /* must be zero */
+} dg_opts;
+
+/* Sizes of a context. */
+typedef struct dg_info {
+  int ndims, polydeg, nvar, nodes_per_elem;
+  long long nelem_total;   /* E */
+  long long ndofs;         /* E * Nd: the DOF count of the performance index (Sec. 4.1, Def. PID) */
+  long long state_len;     /* E * nvar * Nd doubles in u, du */
+  int precision, surface_flux;
+} dg_info;
+
+/* Build a context: LGL tables (Sec. 2), node coordinates, metric terms and Jacobian (Sec. 2.3) in FP64
+   on the host, uploaded to the current device. Allocates device memory (about 100 bytes per DOF).
+   Returns DG_ERR_ARG for a bad mesh/options, DG_ERR_UNSUPPORTED for polydeg outside 1..7, DG_ERR_OOM. */
+dg_status dg_init(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metrics* metrics, const dg_opts* opts);
+
+/* du = RHS(u) (Eq. fluxdiff-SBP-opDsplit). u, du: device [E][nvar][Nd], distinct, not overlapping.
+   t is accepted for interface completeness and unused (autonomous, periodic problem). u is not modified.
+   Queues 2 kernels (interface flux, then volume + surface lift + Jacobian) on `stream`. */
+dg_status dg_rhs(dg_ctx* ctx, const double* u, double* du, double t, dg_stream_t stream);
+
+/* One explicit time step u <- u + dt * (...) of the low-storage Runge-Kutta method `scheme` (Sec. 4.1):
+   DG_RK4_CLASSIC  classical four-stage RK4 in low-storage form; scratch = 2 state arrays (2*state_len);
+   DG_LSRK45_CK    five-stage fourth-order 2N method of Carpenter and Kennedy; scratch = 1 state array.
+   u and scratch are device memory; scratch contents on entry are ignored. RK accumulation is FP64. */
+dg_status dg_step(dg_ctx* ctx, double* u, double* scratch, double t, double dt, int scheme, dg_stream_t stream);
+
+/* Entropy rate dS/dt = sum_e sum_i J_i W_i w(u_i) . du_i (Sec. 2: EC/ED semidiscretizations; W the tensor
+   LGL weights, w the entropy variables of U = -rho s/(gamma-1)). FP64, deterministic order. Writes the value
+   to *out_host and, when abs_out_host is not NULL, sum |J W w.du| to *abs_out_host. Synchronizes `stream`. */
+dg_status dg_entropy_rate(dg_ctx* ctx, const double* u, const double* du, double* out_host, double* abs_out_host,
+                          dg_stream_t stream);
+
+/* Reads and clears the asynchronous flag of non-physical states. Waits (bounded, 60 s) for the work queued
+   on the stream of the last call; returns DG_OK, DG_ERR_NONPHYSICAL or DG_ERR_TIMEOUT. */
+dg_status dg_check_status(dg_ctx* ctx);
+
+/* Getters (host copies; synchronize the device). */
+dg_status dg_get_info(const dg_ctx* ctx, dg_info* info);
+dg_status dg_get_node_coords(const dg_ctx* ctx, double* xyz_host /* [E][ndims][Nd] */);
+dg_status dg_get_metrics(const dg_ctx* ctx, double* Ja_host /* [E][d][d][Nd] */, double* J_host /* [E][Nd] */);
+
+/* Kernel timing with CUDA events recorded on the launching stream around every launch of kernel `which`
+   (0 = volume, 1 = interface, 2 = RK update) while enabled. dg_profile_read returns the summed milliseconds
+   and the launch count since the last enable, and synchronizes. dg_launch_count counts every kernel the
+   context has launched since dg_init. */
+dg_status dg_profile_enable(dg_ctx* ctx, int on);
+dg_status dg_profile_read(dg_ctx* ctx, int which, double* total_ms, long long* launches);
+long long dg_launch_count(const dg_ctx* ctx);
+
+void dg_free(dg_ctx* ctx);
+const char* dg_status_string(dg_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DG_H */

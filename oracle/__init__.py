@@ -198,15 +198,17 @@ def metrics(ndims: int, p: int, xyz, curl_form: bool = True):
 def rhs(ndims: int, p: int, nelem, Ja, J, u, gamma: float = 1.4, llf: bool = True,
         elem_range=None) -> np.ndarray:
     """du/dt of the flux-differencing LGL-DGSEM (Eq. strong-form-SBP with Eq. fluxdiff-SBP,
-    curvilinear via Eq. curvilinear-rewrite). elem_range=(b, e) computes only elements [b, e)."""
+    curvilinear via Eq. curvilinear-rewrite). elem_range=(b, e) computes only elements [b, e) and returns
+    that slice [e-b, nvar, Nd]."""
     lib = _load()
     Ja = _f64(Ja)
     J = _f64(J)
     u = _f64(u)
     E = num_elements(ndims, nelem)
     assert u.shape == (E, ndims + 2, (p + 1) ** ndims), u.shape
-    du = np.zeros_like(u)
     b, e = (0, E) if elem_range is None else elem_range
+    assert 0 <= b <= e <= E
+    du = np.zeros((e - b,) + u.shape[1:])
     _check(lib.orc_rhs(ndims, p, _ivec(nelem), _ptr(Ja), _ptr(J), _ptr(u), ctypes.c_double(gamma),
                        int(bool(llf)), int(b), int(e), _ptr(du)), "rhs")
     return du

@@ -404,7 +404,7 @@ int orc_metrics(int nd, int p, int nelem_total, const double* xyz, int curl_form
 /* (D_n)_{ik}, alpha the averaged contravariant vector (Sec. 2.3); the surface term is               */
 /* M^{-1} R^T B (f* - sum_j N_j R f^j) with the outward scaled normal +-Ja^n on face xi_n = +-1.     */
 /* u_nbr is the coincident node of the neighbour across the face (periodic). Elements                */
-/* [elem_begin, elem_end) are computed; the others of du are left untouched.                         */
+/* [elem_begin, elem_end) are computed and stored in du as elements 0 .. elem_end-elem_begin-1.      */
 /* ------------------------------------------------------------------------------------------------ */
 
 int orc_rhs(int nd, int p, const int* nelem, const double* Ja, const double* J, const double* u, double gamma,
@@ -457,7 +457,8 @@ int orc_rhs(int nd, int p, const int* nelem, const double* Ja, const double* J, 
           for (int c = 0; c < nv; ++c) acc[c] += winv * (fstar[c] - fn[c]);
         }
       }
-      for (int c = 0; c < nv; ++c) du[((size_t)e * nv + c) * Nd + i] = -acc[c] / J[(size_t)e * Nd + i];
+      for (int c = 0; c < nv; ++c)
+        du[((size_t)(e - elem_begin) * nv + c) * Nd + i] = -acc[c] / J[(size_t)e * Nd + i];
     }
   }
   return 0;

@@ -1,0 +1,562 @@
+// Host side of the library: reference element, mesh geometry, metric terms, context management and the
+// C-ABI entry points. Arithmetic here is FP64 (long double for the LGL tables) and runs once per dg_init.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#include <time.h>
+
+#include <new>
+#include <vector>
+
+#include "dg_internal.h"
+
+namespace {
+
+// ---------------------------------------------------------------------------------------------------
+// Reference element (Sec. 2, LGL example): LGL nodes are +-1 and the roots of P_p'. They are the roots of
+// q = P_{p+1} - P_{p-1} = (2p+1)(x^2-1)P_p'/(p(p+1)), and q' = (2p+1) P_p, which gives a Newton step that
+// needs only Legendre values. Weights 2/(p(p+1) P_p(x)^2). The derivative matrix uses the closed form for
+// LGL nodes: D_ik = P_p(x_i) / (P_p(x_k) (x_i - x_k)) off the diagonal, D_00 = -p(p+1)/4, D_pp = p(p+1)/4.
+// ---------------------------------------------------------------------------------------------------
+
+void legendre_upto(long double x, int n, long double* P /* P[0..n] */) {
+  P[0] = 1.0L;
+  if (n >= 1) P[1] = x;
+  for (int k = 2; k <= n; ++k) P[k] = ((2 * k - 1) * x * P[k - 1] - (k - 1) * P[k - 2]) / k;
+}
+
+void build_ref_tables(int p, dgk::RefTables* t) {
+  const int N = p + 1;
+  long double X[DG_MAXN], Pp[DG_MAXN];
+  long double P[DG_MAXN + 2];
+  for (int i = 0; i < N; ++i) {
+    long double xi;
+    if (i == 0) {
+      xi = -1.0L;
+    } else if (i == p) {
+      xi = 1.0L;
+    } else {
+      xi = -cosl(3.141592653589793238462643383279502884L * (long double)i / (long double)p);
+      for (int it = 0; it < 100; ++it) {
+        legendre_upto(xi, p + 1, P);
+        const long double step = (P[p + 1] - P[p - 1]) / ((2.0L * p + 1.0L) * P[p]);
+        xi -= step;
+        if (fabsl(step) <= 1e-19L) break;
+      }
+    }
+    X[i] = xi;
+    legendre_upto(xi, p, P);
+    Pp[i] = P[p];
+  }
+  memset(t, 0, sizeof(*t));
+  for (int i = 0; i < N; ++i) {
+    t->x[i] = (double)X[i];
+    t->w[i] = (double)(2.0L / ((long double)p * (p + 1) * Pp[i] * Pp[i]));
+  }
+  for (int i = 0; i < N; ++i)
+    for (int k = 0; k < N; ++k) {
+      long double d;
+      if (i != k)
+        d = Pp[i] / (Pp[k] * (X[i] - X[k]));
+      else if (i == 0)
+        d = -(long double)p * (p + 1) / 4.0L;
+      else if (i == p)
+        d = (long double)p * (p + 1) / 4.0L;
+      else
+        d = 0.0L;
+      t->D[i * N + k] = (double)d;
+      // flux-differencing operator Dt = 2D - M^{-1} B (Eq. opDsplit): M^{-1}B = diag(-1/w_0, 0, .., 1/w_p);
+      // its diagonal vanishes (Sec. 2.2: M Dt is skew-symmetric), so it is set to exactly zero.
+      t->Dt[i * N + k] = (i == k) ? 0.0 : (double)(2.0L * d);
+    }
+}
+
+
+int ipow(int b, int e) {
+  int r = 1;
+  while (e-- > 0) r *= b;
+  return r;
+}
+
+// ---------------------------------------------------------------------------------------------------
+// Geometry (Sec. 2.3)
+// ---------------------------------------------------------------------------------------------------
+
+void node_coords(const dg_mesh* m, int p, const dgk::RefTables& t, double* xyz) {
+  const int nd = m->ndims, N = p + 1, Nd = ipow(N, nd);
+  const int n1 = m->nelem[0], n2 = m->nelem[1], n3 = nd == 3 ? m->nelem[2] : 1;
+  const double twopi = 6.283185307179586476925286766559;
+  for (int e = 0; e < n1 * n2 * n3; ++e) {
+    const int ei[3] = {e % n1, (e / n1) % n2, e / (n1 * n2)};
+    for (int i = 0; i < Nd; ++i) {
+      const int ii[3] = {i % N, (i / N) % N, i / (N * N)};
+      double xi[3];
+      for (int d = 0; d < nd; ++d) {
+        const double h = (m->hi[d] - m->lo[d]) / m->nelem[d];
+        xi[d] = m->lo[d] + h * (ei[d] + 0.5 * (t.x[ii[d]] + 1.0));
+      }
+      double s = 1.0;
+      if (m->mapping == DG_MAP_SINE)
+        for (int d = 0; d < nd; ++d) {
+          const double L = m->hi[d] - m->lo[d];
+          s *= sin(twopi * (xi[d] - 0.5 * (m->lo[d] + m->hi[d])) / L);
+        }
+      for (int d = 0; d < nd; ++d) {
+        const double L = m->hi[d] - m->lo[d];
+        const double pert = m->mapping == DG_MAP_SINE ? m->map_amp * (L / twopi) * s : 0.0;
+        xyz[((size_t)e * nd + d) * Nd + i] = xi[d] + pert;
+      }
+    }
+  }
+}
+
+// out = (D along reference direction `dir`) g, for one element's nodal field (Nd values)
+void deriv(int nd, int N, const double* D, int dir, const double* g, double* out) {
+  const int Nd = ipow(N, nd), st = ipow(N, dir);
+  for (int i = 0; i < Nd; ++i) {
+    const int a = (i / st) % N;
+    const double* line = g + (i - a * st);
+    double acc = 0.0;
+    for (int k = 0; k < N; ++k) acc += D[a * N + k] * line[k * st];
+    out[i] = acc;
+  }
+}
+
+// Metric terms: 2D cross-product form (Sec. 2.3); 3D conservative curl form (Ja^n)_j =
+// -[curl_xi I^N(X_l grad_xi X_m)]_n, (j, m, l) cyclic, which satisfies the discrete metric identities
+// sum_n D_n (Ja^n)_j = 0 and so preserves free streams (Sec. 2.3). J = det(dx/dxi).
+bool compute_metrics(int nd, int p, long long E, const double* xyz, const dgk::RefTables& t, double* Ja, double* J) {
+  const int N = p + 1, Nd = ipow(N, nd);
+  std::vector<double> g(9 * Nd), V(3 * Nd), a(Nd), b(Nd);
+  for (long long e = 0; e < E; ++e) {
+    const double* X = xyz + (size_t)e * nd * Nd;
+    double* Jae = Ja + (size_t)e * nd * nd * Nd;
+    double* Je = J + (size_t)e * Nd;
+    // g[(k*nd + m)*Nd + i] = d x_m / d xi_k
+    for (int k = 0; k < nd; ++k)
+      for (int m = 0; m < nd; ++m) deriv(nd, N, t.D, k, X + (size_t)m * Nd, &g[(k * nd + m) * Nd]);
+    if (nd == 2) {
+      for (int i = 0; i < Nd; ++i) {
+        const double x_1 = g[0 * Nd + i], y_1 = g[1 * Nd + i], x_2 = g[2 * Nd + i], y_2 = g[3 * Nd + i];
+        Jae[0 * Nd + i] = y_2;   // (Ja^1)_1
+        Jae[1 * Nd + i] = -x_2;  // (Ja^1)_2
+        Jae[2 * Nd + i] = -y_1;  // (Ja^2)_1
+        Jae[3 * Nd + i] = x_1;   // (Ja^2)_2
+        Je[i] = x_1 * y_2 - x_2 * y_1;
+      }
+    } else {
+      for (int i = 0; i < Nd; ++i) {
+        double c[3][3];
+        for (int k = 0; k < 3; ++k)
+          for (int m = 0; m < 3; ++m) c[k][m] = g[(k * 3 + m) * Nd + i];
+        Je[i] = c[0][0] * (c[1][1] * c[2][2] - c[2][1] * c[1][2]) + c[0][1] * (c[1][2] * c[2][0] - c[1][0] * c[2][2]) +
+                c[0][2] * (c[1][0] * c[2][1] - c[1][1] * c[2][0]);
+      }
+      for (int j = 0; j < 3; ++j) {
+        const int m = (j + 1) % 3, l = (j + 2) % 3;
+        for (int k = 0; k < 3; ++k)
+          for (int i = 0; i < Nd; ++i) V[k * Nd + i] = X[(size_t)l * Nd + i] * g[(k * 3 + m) * Nd + i];
+        for (int n = 0; n < 3; ++n) {
+          const int n1 = (n + 1) % 3, n2 = (n + 2) % 3;
+          deriv(3, N, t.D, n1, &V[n2 * Nd], a.data());
+          deriv(3, N, t.D, n2, &V[n1 * Nd], b.data());
+          for (int i = 0; i < Nd; ++i) Jae[(n * 3 + j) * Nd + i] = b[i] - a[i];
+        }
+      }
+    }
+    for (int i = 0; i < Nd; ++i)
+      if (!(Je[i] > 0.0)) return false;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------------------------------
+// Context helpers
+// ---------------------------------------------------------------------------------------------------
+
+dg_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return DG_OK;
+  if (e == cudaErrorMemoryAllocation) return DG_ERR_OOM;
+  return DG_ERR_CUDA;
+}
+
+template <typename T>
+cudaError_t dev_alloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, count * sizeof(T) + 16);
+}
+
+void release(dg_ctx* c) {
+  if (!c) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(c->device);
+  cudaFree(c->d_Ja);
+  cudaFree(c->d_Ja32);
+  cudaFree(c->d_invJ);
+  cudaFree(c->d_JW);
+  cudaFree(c->d_face);
+  cudaFree(c->d_du);
+  cudaFree(c->d_red);
+  cudaFree(c->d_flag);
+  if (c->prof_ev) {
+    for (int i = 0; i < 2 * c->prof_cap; ++i) cudaEventDestroy(c->prof_ev[i]);
+    free(c->prof_ev);
+  }
+  free(c->prof_kid);
+  free(c->h_xyz);
+  free(c->h_Ja);
+  free(c->h_J);
+  if (prev >= 0) cudaSetDevice(prev);
+  delete c;
+}
+
+// Bounded wait on `s`: poll an event for up to `seconds`.
+dg_status bounded_sync(cudaStream_t s, double seconds) {
+  cudaEvent_t ev;
+  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaEventRecord(ev, s);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(ev);
+    return cuda_status(e);
+  }
+  dg_status st = DG_ERR_TIMEOUT;
+  const long long max_polls = (long long)(seconds * 1e4);
+  for (long long i = 0; i < max_polls; ++i) {
+    e = cudaEventQuery(ev);
+    if (e == cudaSuccess) {
+      st = DG_OK;
+      break;
+    }
+    if (e != cudaErrorNotReady) {
+      st = cuda_status(e);
+      break;
+    }
+    struct timespec ts = {0, 100000};  // 100 us
+    nanosleep(&ts, nullptr);
+  }
+  cudaEventDestroy(ev);
+  return st;
+}
+
+}  // namespace
+
+namespace dgk {
+const RefTables& ref_tables(int p) {
+  struct All {
+    RefTables t[DG_MAXN];
+    All() {
+      for (int q = 1; q < DG_MAXN; ++q) build_ref_tables(q, &t[q]);
+    }
+  };
+  static const All all;  // thread-safe one-time initialisation
+  return all.t[p];
+}
+}  // namespace dgk
+
+// ---------------------------------------------------------------------------------------------------
+// Profiling hooks used by the launch wrappers
+// ---------------------------------------------------------------------------------------------------
+namespace dgk {
+void prof_begin(dg_ctx* c, int kid, cudaStream_t s, int* slot) {
+  *slot = -1;
+  c->launches++;
+  if (!c->prof_on || c->prof_used >= c->prof_cap) return;
+  *slot = c->prof_used++;
+  c->prof_kid[*slot] = kid;
+  cudaEventRecord(c->prof_ev[2 * *slot], s);
+}
+void prof_end(dg_ctx* c, cudaStream_t s, int slot) {
+  if (slot >= 0) cudaEventRecord(c->prof_ev[2 * slot + 1], s);
+}
+}  // namespace dgk
+
+// ---------------------------------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------------------------------
+extern "C" {
+
+const char* dg_status_string(dg_status s) {
+  switch (s) {
+    case DG_OK: return "ok";
+    case DG_ERR_ARG: return "invalid argument";
+    case DG_ERR_CUDA: return "CUDA runtime error";
+    case DG_ERR_OOM: return "device out of memory";
+    case DG_ERR_UNSUPPORTED: return "unsupported";
+    case DG_ERR_NONPHYSICAL: return "non-physical state (rho <= 0, p <= 0 or NaN)";
+    case DG_ERR_TIMEOUT: return "timeout";
+  }
+  return "unknown status";
+}
+
+dg_status dg_init(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metrics* metrics, const dg_opts* opts) {
+  if (!out || !mesh || !opts) return DG_ERR_ARG;
+  *out = nullptr;
+  const int nd = mesh->ndims;
+  if (nd != 2 && nd != 3) return DG_ERR_ARG;
+  if (polydeg < 1 || polydeg >= DG_MAXN) return DG_ERR_UNSUPPORTED;
+  for (int d = 0; d < nd; ++d) {
+    if (mesh->nelem[d] < 1 || mesh->nelem[d] > (1 << 20)) return DG_ERR_ARG;
+    if (!(mesh->hi[d] > mesh->lo[d])) return DG_ERR_ARG;
+  }
+  if (mesh->mapping < DG_MAP_AFFINE || mesh->mapping > DG_MAP_NODES) return DG_ERR_ARG;
+  if (mesh->mapping == DG_MAP_NODES && !mesh->node_xyz_host) return DG_ERR_ARG;
+  if (!(opts->gamma > 1.0)) return DG_ERR_ARG;
+  if (opts->volume_flux != DG_VOL_RANOCHA) return DG_ERR_UNSUPPORTED;
+  if (opts->surface_flux != DG_SURF_EC && opts->surface_flux != DG_SURF_EC_LLF) return DG_ERR_ARG;
+  if (opts->precision != DG_FP64 && opts->precision != DG_FP32) return DG_ERR_ARG;
+  for (int r = 0; r < 5; ++r)
+    if (opts->reserved[r] != 0) return DG_ERR_ARG;
+  if (metrics && ((metrics->Ja_host == nullptr) != (metrics->J_host == nullptr))) return DG_ERR_ARG;
+  const long long n3 = nd == 3 ? mesh->nelem[2] : 1;
+  const long long E = (long long)mesh->nelem[0] * mesh->nelem[1] * n3;
+  const int N = polydeg + 1, Nd = ipow(N, nd), nv = nd + 2;
+  if (E * Nd * nv > (1LL << 31) - 1) return DG_ERR_UNSUPPORTED;  // 32-bit node offsets in the kernels
+
+  dg_ctx* c = new (std::nothrow) dg_ctx();
+  if (!c) return DG_ERR_OOM;
+  memset(c, 0, sizeof(*c));
+  cudaError_t ce = cudaGetDevice(&c->device);
+  if (ce != cudaSuccess) {
+    delete c;
+    return cuda_status(ce);
+  }
+  c->nd = nd;
+  c->p = polydeg;
+  c->N = N;
+  c->Nd = Nd;
+  c->nv = nv;
+  c->md.n1 = mesh->nelem[0];
+  c->md.n2 = mesh->nelem[1];
+  c->md.n3 = (int)n3;
+  c->md.E = (int)E;
+  c->E = E;
+  c->ndofs = E * Nd;
+  c->state_len = E * Nd * nv;
+  c->gamma = opts->gamma;
+  c->precision = opts->precision;
+  c->surface_flux = opts->surface_flux;
+  c->volume_flux = opts->volume_flux;
+
+  const dgk::RefTables& t = dgk::ref_tables(polydeg);
+  const size_t nx = (size_t)E * nd * Nd, nja = (size_t)E * nd * nd * Nd, nj = (size_t)E * Nd;
+  c->h_xyz = (double*)malloc(nx * sizeof(double));
+  c->h_Ja = (double*)malloc(nja * sizeof(double));
+  c->h_J = (double*)malloc(nj * sizeof(double));
+  if (!c->h_xyz || !c->h_Ja || !c->h_J) {
+    release(c);
+    return DG_ERR_OOM;
+  }
+  if (mesh->mapping == DG_MAP_NODES)
+    memcpy(c->h_xyz, mesh->node_xyz_host, nx * sizeof(double));
+  else
+    node_coords(mesh, polydeg, t, c->h_xyz);
+  if (metrics && metrics->Ja_host) {
+    memcpy(c->h_Ja, metrics->Ja_host, nja * sizeof(double));
+    memcpy(c->h_J, metrics->J_host, nj * sizeof(double));
+    for (size_t i = 0; i < nj; ++i)
+      if (!(c->h_J[i] > 0.0)) {
+        release(c);
+        return DG_ERR_ARG;
+      }
+  } else if (!compute_metrics(nd, polydeg, E, c->h_xyz, t, c->h_Ja, c->h_J)) {
+    release(c);
+    return DG_ERR_ARG;  // inverted or degenerate element
+  }
+
+  // device copies: Ja (FP64, plus an FP32 rounding for the FP32 flux path), 1/J, J*W
+  std::vector<double> invJ(nj), JW(nj);
+  for (long long e = 0; e < E; ++e)
+    for (int i = 0; i < Nd; ++i) {
+      double W = 1.0;
+      int r = i;
+      for (int d = 0; d < nd; ++d) {
+        W *= t.w[r % N];
+        r /= N;
+      }
+      invJ[(size_t)e * Nd + i] = 1.0 / c->h_J[(size_t)e * Nd + i];
+      JW[(size_t)e * Nd + i] = c->h_J[(size_t)e * Nd + i] * W;
+    }
+  const size_t nface = (size_t)nd * E * nv * ipow(N, nd - 1);
+  const size_t face_bytes = nface * (c->precision == DG_FP32 ? sizeof(float) : sizeof(double));
+  ce = dev_alloc(&c->d_Ja, nja);
+  if (ce == cudaSuccess) ce = dev_alloc(&c->d_invJ, nj);
+  if (ce == cudaSuccess) ce = dev_alloc(&c->d_JW, nj);
+  if (ce == cudaSuccess) ce = cudaMalloc(&c->d_face, face_bytes + 16);
+  if (ce == cudaSuccess) ce = dev_alloc(&c->d_red, (size_t)2 * dgk::entropy_rate_blocks() + 2);
+  if (ce == cudaSuccess) ce = dev_alloc(&c->d_flag, 1);
+  if (ce == cudaSuccess && c->precision == DG_FP32) ce = dev_alloc(&c->d_Ja32, nja);
+  if (ce == cudaSuccess) ce = cudaMemcpy(c->d_Ja, c->h_Ja, nja * sizeof(double), cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) ce = cudaMemcpy(c->d_invJ, invJ.data(), nj * sizeof(double), cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) ce = cudaMemcpy(c->d_JW, JW.data(), nj * sizeof(double), cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) ce = cudaMemset(c->d_flag, 0, sizeof(int));
+  if (ce == cudaSuccess && c->precision == DG_FP32) {
+    std::vector<float> ja32(nja);
+    for (size_t i = 0; i < nja; ++i) ja32[i] = (float)c->h_Ja[i];
+    ce = cudaMemcpy(c->d_Ja32, ja32.data(), nja * sizeof(float), cudaMemcpyHostToDevice);
+  }
+  if (ce != cudaSuccess) {
+    release(c);
+    return cuda_status(ce);
+  }
+  c->prof_cap = 1 << 14;
+  c->prof_ev = (cudaEvent_t*)calloc(2 * c->prof_cap, sizeof(cudaEvent_t));
+  c->prof_kid = (int*)calloc(c->prof_cap, sizeof(int));
+  if (!c->prof_ev || !c->prof_kid) {
+    release(c);
+    return DG_ERR_OOM;
+  }
+  for (int i = 0; i < 2 * c->prof_cap; ++i) {
+    ce = cudaEventCreate(&c->prof_ev[i]);
+    if (ce != cudaSuccess) {
+      c->prof_cap = i / 2;
+      break;
+    }
+  }
+  *out = c;
+  return DG_OK;
+}
+
+void dg_free(dg_ctx* ctx) { release(ctx); }
+
+dg_status dg_rhs(dg_ctx* c, const double* u, double* du, double t, dg_stream_t stream) {
+  (void)t;
+  if (!c || !u || !du) return DG_ERR_ARG;
+  const size_t bytes = (size_t)c->state_len * sizeof(double);
+  const char *ub = (const char*)u, *db = (const char*)du;
+  if (ub < db + bytes && db < ub + bytes) return DG_ERR_ARG;  // u and du overlap
+  if (((uintptr_t)u | (uintptr_t)du) & 7) return DG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  int slot;
+  dgk::prof_begin(c, dgk::KID_INTERFACE, s, &slot);
+  const void* ja = c->precision == DG_FP32 ? (const void*)c->d_Ja32 : (const void*)c->d_Ja;
+  cudaError_t e = dgk::launch_interface(c->nd, c->p, c->precision, c->surface_flux == DG_SURF_EC_LLF, c->md, u, ja,
+                                        c->d_face, c->gamma, c->d_flag, s);
+  dgk::prof_end(c, s, slot);
+  if (e != cudaSuccess) return cuda_status(e);
+  dgk::prof_begin(c, dgk::KID_VOLUME, s, &slot);
+  e = dgk::launch_volume(c->nd, c->p, c->precision, c->md, u, ja, c->d_invJ, c->d_face, du, c->gamma, c->d_flag, s);
+  dgk::prof_end(c, s, slot);
+  return cuda_status(e);
+}
+
+dg_status dg_step(dg_ctx* c, double* u, double* scratch, double t, double dt, int scheme, dg_stream_t stream) {
+  if (!c || !u || !scratch) return DG_ERR_ARG;
+  if (scheme != DG_RK4_CLASSIC && scheme != DG_LSRK45_CK) return DG_ERR_ARG;
+  if (!(dt == dt)) return DG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  if (!c->d_du) {
+    cudaError_t e = dev_alloc(&c->d_du, (size_t)c->state_len);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  const size_t n = (size_t)c->state_len;
+  const int stages = scheme == DG_RK4_CLASSIC ? 4 : 5;
+  double* y = scratch;
+  double* acc = scheme == DG_RK4_CLASSIC ? scratch + n : nullptr;
+  for (int st = 0; st < stages; ++st) {
+    const double* in = (scheme == DG_RK4_CLASSIC && st > 0) ? y : u;
+    dg_status r = dg_rhs(c, in, c->d_du, t, stream);
+    if (r != DG_OK) return r;
+    int slot;
+    dgk::prof_begin(c, dgk::KID_UPDATE, s, &slot);
+    cudaError_t e = dgk::launch_rk_update(scheme, st, n, dt, u, y, acc, c->d_du, s);
+    dgk::prof_end(c, s, slot);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return DG_OK;
+}
+
+dg_status dg_entropy_rate(dg_ctx* c, const double* u, const double* du, double* out_host, double* abs_out_host,
+                          dg_stream_t stream) {
+  if (!c || !u || !du || !out_host) return DG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  const int nb = dgk::entropy_rate_blocks();
+  c->launches += 2;
+  cudaError_t e = dgk::launch_entropy_rate(c->nd, c->p, c->md, u, du, c->d_JW, c->gamma, c->d_red, nb,
+                                           c->d_red + 2 * nb, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  double res[2];
+  e = cudaMemcpyAsync(res, c->d_red + 2 * nb, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  dg_status st = bounded_sync(s, 60.0);
+  if (st != DG_OK) return st;
+  *out_host = res[0];
+  if (abs_out_host) *abs_out_host = res[1];
+  return DG_OK;
+}
+
+dg_status dg_check_status(dg_ctx* c) {
+  if (!c) return DG_ERR_ARG;
+  dg_status st = bounded_sync(c->last_stream, 60.0);
+  if (st != DG_OK) return st;
+  int flag = 0;
+  cudaError_t e = cudaMemcpy(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (flag) {
+    e = cudaMemset(c->d_flag, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_status(e);
+    return DG_ERR_NONPHYSICAL;
+  }
+  return DG_OK;
+}
+
+dg_status dg_get_info(const dg_ctx* c, dg_info* info) {
+  if (!c || !info) return DG_ERR_ARG;
+  info->ndims = c->nd;
+  info->polydeg = c->p;
+  info->nvar = c->nv;
+  info->nodes_per_elem = c->Nd;
+  info->nelem_total = c->E;
+  info->ndofs = c->ndofs;
+  info->state_len = c->state_len;
+  info->precision = c->precision;
+  info->surface_flux = c->surface_flux;
+  return DG_OK;
+}
+
+dg_status dg_get_node_coords(const dg_ctx* c, double* xyz) {
+  if (!c || !xyz) return DG_ERR_ARG;
+  memcpy(xyz, c->h_xyz, (size_t)c->E * c->nd * c->Nd * sizeof(double));
+  return DG_OK;
+}
+
+dg_status dg_get_metrics(const dg_ctx* c, double* Ja, double* J) {
+  if (!c || (!Ja && !J)) return DG_ERR_ARG;
+  if (Ja) memcpy(Ja, c->h_Ja, (size_t)c->E * c->nd * c->nd * c->Nd * sizeof(double));
+  if (J) memcpy(J, c->h_J, (size_t)c->E * c->Nd * sizeof(double));
+  return DG_OK;
+}
+
+dg_status dg_profile_enable(dg_ctx* c, int on) {
+  if (!c) return DG_ERR_ARG;
+  c->prof_on = on ? 1 : 0;
+  c->prof_used = 0;
+  return DG_OK;
+}
+
+dg_status dg_profile_read(dg_ctx* c, int which, double* total_ms, long long* launches) {
+  if (!c || which < 0 || which >= dgk::KID_COUNT || !total_ms) return DG_ERR_ARG;
+  double tot = 0.0;
+  long long n = 0;
+  for (int i = 0; i < c->prof_used; ++i) {
+    if (c->prof_kid[i] != which) continue;
+    cudaError_t e = cudaEventSynchronize(c->prof_ev[2 * i + 1]);
+    if (e != cudaSuccess) return cuda_status(e);
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]);
+    if (e != cudaSuccess) return cuda_status(e);
+    tot += ms;
+    ++n;
+  }
+  *total_ms = tot;
+  if (launches) *launches = n;
+  return DG_OK;
+}
+
+long long dg_launch_count(const dg_ctx* c) { return c ? c->launches : -1; }
+
+}  // extern "C"

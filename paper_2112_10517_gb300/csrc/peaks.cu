@@ -1,0 +1,150 @@
+// ALU throughput microbenchmarks for the roofline denominators of the RHS kernels.
+//
+// The volume term of flux-differencing DGSEM (Sec. 2.1-2.3, Eq. fluxdiff-SBP-opDsplit) is bound by
+// floating-point arithmetic, not by memory, so its roofline needs the device's FP64 and FP32 FMA rates
+// and the rates of the special operations the two-point flux uses (division, logarithm; Sec. 3.1).
+// Each kernel runs many independent dependency chains per thread so that the pipe, not latency, limits it.
+// Exported with a C ABI (plain pointers and sizes); the caller reads ops/second.
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace {
+
+constexpr int kChains = 8;
+
+enum Kind : int {
+  K_DFMA = 0,      // fp64 fused multiply-add (2 flop)
+  K_FFMA = 1,      // fp32 fused multiply-add (2 flop)
+  K_DDIV = 2,      // fp64 IEEE division a/b
+  K_DLOG = 3,      // fp64 log()
+  K_FLOG = 4,      // fp32 logf()
+  K_MUFU_LG2 = 5,  // fp32 lg2.approx (special-function unit)
+  K_MUFU_RCP = 6,  // fp32 rcp.approx (special-function unit)
+  K_FDIV = 7,      // fp32 IEEE division
+  K_DRCP = 8,      // fp64 reciprocal, round to nearest
+  K_NKINDS = 9
+};
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float r;
+  asm volatile("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+template <int KIND>
+__global__ void chain_kernel(double* sink, int iters, double seed) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  double d[kChains];
+  float f[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) {
+    d[c] = 1.0 + 1e-3 * (double)((tid + c) & 15);
+    f[c] = 1.0f + 1e-3f * (float)((tid + c) & 15);
+  }
+  const double b = 0.999999 * seed, a = 1e-7 * seed;
+  const float bf = (float)b, af = (float)a;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) {
+      if (KIND == K_DFMA) d[c] = fma(d[c], b, a);
+      if (KIND == K_FFMA) {
+        f[c] = fmaf(f[c], bf, af);
+        f[c + 0] = fmaf(f[c], bf, af);  // two per chain step keep fp32 issue dense
+      }
+      if (KIND == K_DDIV) d[c] = 2.0 + b / d[c];
+      if (KIND == K_DLOG) d[c] = 1.0 + log(d[c] + b);
+      if (KIND == K_FLOG) f[c] = 1.0f + logf(f[c] + bf);
+      if (KIND == K_MUFU_LG2) f[c] = lg2_approx(f[c] + bf);
+      if (KIND == K_MUFU_RCP) f[c] = rcp_approx(f[c] + af);
+      if (KIND == K_FDIV) f[c] = 2.0f + bf / f[c];
+      if (KIND == K_DRCP) d[c] = 2.0 + __drcp_rn(d[c]);
+    }
+  }
+  double acc = 0.0;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) acc += d[c] + (double)f[c];
+  if (acc == seed * 12345.678) sink[tid] = acc;  // never true for the seeds used; keeps the chains live
+}
+
+// operations counted per chain step (FFMA does two dependent FMAs per chain step)
+__host__ int ops_per_step(int kind) { return kind == K_FFMA ? 2 : 1; }
+
+template <int KIND>
+cudaError_t launch(int blocks, int threads, double* sink, int iters, cudaStream_t s) {
+  chain_kernel<KIND><<<blocks, threads, 0, s>>>(sink, iters, 1.0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kind(int kind, int blocks, int threads, double* sink, int iters, cudaStream_t s) {
+  switch (kind) {
+    case K_DFMA: return launch<K_DFMA>(blocks, threads, sink, iters, s);
+    case K_FFMA: return launch<K_FFMA>(blocks, threads, sink, iters, s);
+    case K_DDIV: return launch<K_DDIV>(blocks, threads, sink, iters, s);
+    case K_DLOG: return launch<K_DLOG>(blocks, threads, sink, iters, s);
+    case K_FLOG: return launch<K_FLOG>(blocks, threads, sink, iters, s);
+    case K_MUFU_LG2: return launch<K_MUFU_LG2>(blocks, threads, sink, iters, s);
+    case K_MUFU_RCP: return launch<K_MUFU_RCP>(blocks, threads, sink, iters, s);
+    case K_FDIV: return launch<K_FDIV>(blocks, threads, sink, iters, s);
+    case K_DRCP: return launch<K_DRCP>(blocks, threads, sink, iters, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+// Number of benchmark kinds; kind ids are listed in include/dg_peaks.h.
+int dgpk_num_kinds(void) { return K_NKINDS; }
+
+// Runs benchmark `kind` on the current device and returns operations per second in *ops_per_s
+// (an FMA counts as one operation; multiply by 2 for flop/s). The iteration count is grown until one
+// launch takes at least `min_seconds`. Returns 0 on success, else a cudaError_t value.
+int dgpk_measure(int kind, double min_seconds, double* ops_per_s, double* seconds) {
+  if (kind < 0 || kind >= K_NKINDS || !ops_per_s) return (int)cudaErrorInvalidValue;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return (int)e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return (int)e;
+  const int threads = 256, blocks = sms * 8;
+  double* sink = nullptr;
+  e = cudaMalloc(&sink, sizeof(double) * (size_t)threads * blocks);
+  if (e != cudaSuccess) return (int)e;
+  cudaEvent_t t0, t1;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  int iters = 64;
+  float ms = 0.f;
+  // warm-up launch
+  e = launch_kind(kind, blocks, threads, sink, iters, 0);
+  for (int attempt = 0; attempt < 24 && e == cudaSuccess; ++attempt) {
+    cudaEventRecord(t0, 0);
+    e = launch_kind(kind, blocks, threads, sink, iters, 0);
+    cudaEventRecord(t1, 0);
+    if (e != cudaSuccess) break;
+    e = cudaEventSynchronize(t1);
+    if (e != cudaSuccess) break;
+    cudaEventElapsedTime(&ms, t0, t1);
+    if (ms * 1e-3 >= min_seconds || iters > (1 << 26)) break;
+    const double grow = ms > 0.5f ? (min_seconds * 1e3 / ms) * 1.2 : 16.0;
+    iters = (int)(iters * (grow > 16.0 ? 16.0 : (grow < 2.0 ? 2.0 : grow)));
+  }
+  if (e == cudaSuccess) {
+    const double ops = (double)blocks * threads * kChains * (double)iters * ops_per_step(kind);
+    *ops_per_s = ops / (ms * 1e-3);
+    if (seconds) *seconds = ms * 1e-3;
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  cudaFree(sink);
+  return (int)e;
+}
+
+}  // extern "C"

@@ -1,0 +1,228 @@
+"""ctypes binding of libdg.so (include/dg.h): argument marshalling only; every step of the RHS runs in the
+library's CUDA kernels. PyTorch provides device memory and streams.
+
+The module-level functions mirror the C entry points one to one (dg_init, dg_rhs, dg_step, dg_entropy_rate,
+dg_check_status, dg_free, ...) and take raw pointers; the class ``DG`` wraps one context for torch tensors.
+Importing this module loads libdg.so and raises if it has not been built (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdg.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libdg.so not found at %s: build it with `python -m paper_2112_10517_gb300.build` "
+                      "(needs nvcc); there is no CPU fallback" % LIB_PATH)
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# ---- status codes and enums (include/dg.h) ----
+DG_OK, DG_ERR_ARG, DG_ERR_CUDA, DG_ERR_OOM, DG_ERR_UNSUPPORTED, DG_ERR_NONPHYSICAL, DG_ERR_TIMEOUT = range(7)
+DG_MAP_AFFINE, DG_MAP_SINE, DG_MAP_NODES = 0, 1, 2
+DG_SURF_EC, DG_SURF_EC_LLF = 0, 1
+DG_FP64, DG_FP32 = 0, 1
+DG_VOL_RANOCHA = 0
+DG_RK4_CLASSIC, DG_LSRK45_CK = 0, 1
+KERNEL_VOLUME, KERNEL_INTERFACE, KERNEL_UPDATE = 0, 1, 2
+
+EXPORTED = ["dg_init", "dg_rhs", "dg_step", "dg_entropy_rate", "dg_check_status", "dg_get_info",
+            "dg_get_node_coords", "dg_get_metrics", "dg_profile_enable", "dg_profile_read", "dg_launch_count",
+            "dg_free", "dg_status_string"]
+
+
+class DgMesh(ctypes.Structure):
+    _fields_ = [("ndims", ctypes.c_int), ("nelem", ctypes.c_int * 3), ("lo", ctypes.c_double * 3),
+                ("hi", ctypes.c_double * 3), ("mapping", ctypes.c_int), ("map_amp", ctypes.c_double),
+                ("node_xyz_host", ctypes.POINTER(ctypes.c_double))]
+
+
+class DgMetrics(ctypes.Structure):
+    _fields_ = [("Ja_host", ctypes.POINTER(ctypes.c_double)), ("J_host", ctypes.POINTER(ctypes.c_double))]
+
+
+class DgOpts(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("volume_flux", ctypes.c_int), ("surface_flux", ctypes.c_int),
+                ("precision", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+
+
+class DgInfo(ctypes.Structure):
+    _fields_ = [("ndims", ctypes.c_int), ("polydeg", ctypes.c_int), ("nvar", ctypes.c_int),
+                ("nodes_per_elem", ctypes.c_int), ("nelem_total", ctypes.c_longlong), ("ndofs", ctypes.c_longlong),
+                ("state_len", ctypes.c_longlong), ("precision", ctypes.c_int), ("surface_flux", ctypes.c_int)]
+
+
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_sig = {
+    "dg_init": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(DgMesh), ctypes.c_int, ctypes.POINTER(DgMetrics),
+                               ctypes.POINTER(DgOpts)]),
+    "dg_rhs": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, _vp]),
+    "dg_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, _vp]),
+    "dg_entropy_rate": (ctypes.c_int, [_vp, _vp, _vp, _dp, _dp, _vp]),
+    "dg_check_status": (ctypes.c_int, [_vp]),
+    "dg_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(DgInfo)]),
+    "dg_get_node_coords": (ctypes.c_int, [_vp, _dp]),
+    "dg_get_metrics": (ctypes.c_int, [_vp, _dp, _dp]),
+    "dg_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "dg_profile_read": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_longlong)]),
+    "dg_launch_count": (ctypes.c_longlong, [_vp]),
+    "dg_free": (None, [_vp]),
+    "dg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+    globals()[_name] = _f
+
+
+class DGError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (what, dg_status_string(status).decode(), status))
+
+
+def check(status: int, what: str):
+    if status != DG_OK:
+        raise DGError(status, what)
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class DG:
+    """One context of the flux-differencing LGL-DGSEM RHS on the current CUDA device.
+
+    mapping: "affine", "sine" (x = xi + amp prod sin) or "nodes" (node_xyz [E, d, Nd] given).
+    surface: "ec" or "llf"; precision: "fp64" or "fp32".
+    """
+
+    def __init__(self, ndims: int, nelem, polydeg: int, lo=None, hi=None, mapping: str = "affine", amp: float = 0.0,
+                 node_xyz=None, Ja=None, J=None, gamma: float = 1.4, surface: str = "llf",
+                 precision: str = "fp64"):
+        mesh = DgMesh()
+        mesh.ndims = ndims
+        ne = list(nelem) + [1] * (3 - len(nelem))
+        lo = list(lo) if lo is not None else [-1.0] * ndims
+        hi = list(hi) if hi is not None else [1.0] * ndims
+        for i in range(3):
+            mesh.nelem[i] = int(ne[i])
+            mesh.lo[i] = float(lo[i]) if i < len(lo) else 0.0
+            mesh.hi[i] = float(hi[i]) if i < len(hi) else 1.0
+        mesh.mapping = {"affine": DG_MAP_AFFINE, "sine": DG_MAP_SINE, "nodes": DG_MAP_NODES}[mapping]
+        mesh.map_amp = float(amp)
+        self._keep = []
+        if node_xyz is not None:
+            xyz = np.ascontiguousarray(node_xyz, dtype=np.float64)
+            self._keep.append(xyz)
+            mesh.node_xyz_host = _dptr(xyz)
+        met = None
+        if Ja is not None:
+            Ja = np.ascontiguousarray(Ja, dtype=np.float64)
+            J = np.ascontiguousarray(J, dtype=np.float64)
+            self._keep += [Ja, J]
+            met = DgMetrics(_dptr(Ja), _dptr(J))
+        opts = DgOpts()
+        opts.gamma = gamma
+        opts.volume_flux = DG_VOL_RANOCHA
+        opts.surface_flux = {"ec": DG_SURF_EC, "llf": DG_SURF_EC_LLF}[surface]
+        opts.precision = {"fp64": DG_FP64, "fp32": DG_FP32}[precision]
+        ctx = ctypes.c_void_p()
+        check(dg_init(ctypes.byref(ctx), ctypes.byref(mesh), int(polydeg),
+                      ctypes.byref(met) if met is not None else None, ctypes.byref(opts)), "dg_init")
+        self.ctx = ctx
+        info = DgInfo()
+        check(dg_get_info(ctx, ctypes.byref(info)), "dg_get_info")
+        self.ndims, self.polydeg, self.nvar = info.ndims, info.polydeg, info.nvar
+        self.nodes_per_elem, self.nelem_total = info.nodes_per_elem, info.nelem_total
+        self.ndofs, self.state_len = info.ndofs, info.state_len
+        self.shape = (self.nelem_total, self.nvar, self.nodes_per_elem)
+        self.precision = precision
+        import torch
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    # ---- lifetime ----
+    def close(self):
+        if getattr(self, "ctx", None):
+            dg_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- argument checks ----
+    def _state(self, t, name):
+        import torch
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda:
+            raise TypeError("%s must be a CUDA float64 tensor" % name)
+        if tuple(t.shape) != self.shape or not t.is_contiguous():
+            raise ValueError("%s must be contiguous with shape %s, got %s" % (name, self.shape, tuple(t.shape)))
+        return ctypes.c_void_p(t.data_ptr())
+
+    # ---- entry points ----
+    def rhs(self, u, du=None, stream=None):
+        import torch
+        if du is None:
+            du = torch.empty_like(u)
+        check(dg_rhs(self.ctx, self._state(u, "u"), self._state(du, "du"), 0.0, _stream_handle(stream)), "dg_rhs")
+        return du
+
+    def step(self, u, dt: float, scheme: int = DG_RK4_CLASSIC, scratch=None, stream=None):
+        import torch
+        nreg = 2 if scheme == DG_RK4_CLASSIC else 1
+        if scratch is None:
+            scratch = torch.empty((nreg,) + self.shape, dtype=torch.float64, device=u.device)
+        if scratch.numel() < nreg * self.state_len or scratch.dtype != torch.float64 or not scratch.is_contiguous():
+            raise ValueError("scratch must be contiguous float64 with %d elements" % (nreg * self.state_len))
+        check(dg_step(self.ctx, self._state(u, "u"), ctypes.c_void_p(scratch.data_ptr()), 0.0, float(dt), int(scheme),
+                      _stream_handle(stream)), "dg_step")
+        return u
+
+    def entropy_rate(self, u, du, stream=None):
+        out = ctypes.c_double()
+        ab = ctypes.c_double()
+        check(dg_entropy_rate(self.ctx, self._state(u, "u"), self._state(du, "du"), ctypes.byref(out),
+                              ctypes.byref(ab), _stream_handle(stream)), "dg_entropy_rate")
+        return out.value, ab.value
+
+    def check_status(self) -> int:
+        return dg_check_status(self.ctx)
+
+    def node_coords(self) -> np.ndarray:
+        xyz = np.zeros((self.nelem_total, self.ndims, self.nodes_per_elem))
+        check(dg_get_node_coords(self.ctx, _dptr(xyz)), "dg_get_node_coords")
+        return xyz
+
+    def metrics(self):
+        Ja = np.zeros((self.nelem_total, self.ndims, self.ndims, self.nodes_per_elem))
+        J = np.zeros((self.nelem_total, self.nodes_per_elem))
+        check(dg_get_metrics(self.ctx, _dptr(Ja), _dptr(J)), "dg_get_metrics")
+        return Ja, J
+
+    def profile(self, on: bool):
+        check(dg_profile_enable(self.ctx, int(bool(on))), "dg_profile_enable")
+
+    def profile_read(self, kernel: int = KERNEL_VOLUME):
+        ms = ctypes.c_double()
+        n = ctypes.c_longlong()
+        check(dg_profile_read(self.ctx, int(kernel), ctypes.byref(ms), ctypes.byref(n)), "dg_profile_read")
+        return ms.value, n.value
+
+    def launch_count(self) -> int:
+        return int(dg_launch_count(self.ctx))

@@ -1,0 +1,90 @@
+"""Shared set-up for tests: seeded scenarios evaluated by the oracle (CPU) and, in GPU tests, by the library.
+
+Only the tests import this module. It builds oracle references; it never feeds a library result to the oracle.
+"""
+import math
+
+import numpy as np
+
+import oracle as orc
+from paper_2112_10517_gb300 import inputs
+
+PI = math.pi
+
+
+def twisted_coords(nd, nelem, p, amp=0.1):
+    """Affine nodes on [-pi, pi]^d moved by a smooth periodic map with a different perturbation per component."""
+    xyz = orc.coords(nd, nelem, [-PI] * nd, [PI] * nd, p)
+    X = [xyz[:, m].copy() for m in range(nd)]
+    out = np.empty_like(xyz)
+    for m in range(nd):
+        a, b = X[(m + 1) % nd], X[(m + 2) % nd] if nd == 3 else X[m]
+        out[:, m] = X[m] + amp * np.sin(a) * np.cos(b + 0.3 * m)
+    return out
+
+
+class Scenario:
+    """A mesh + state, with the oracle's metrics and (lazily) its RHS."""
+
+    def __init__(self, nd, nelem, p, mapping="sine", amp=0.1, box=None, ic="smooth", llf=True, seed=0):
+        self.nd, self.nelem, self.p = nd, list(nelem), p
+        self.mapping, self.amp, self.llf = mapping, amp, llf
+        self.lo, self.hi = box if box is not None else ([-PI] * nd, [PI] * nd)
+        if mapping == "twisted":
+            self.xyz = twisted_coords(nd, nelem, p, amp)
+        else:
+            self.xyz = orc.coords(nd, nelem, self.lo, self.hi, p, mapping=1 if mapping == "sine" else 0,
+                                  amp=amp if mapping == "sine" else 0.0)
+        self.Ja, self.J = orc.metrics(nd, p, self.xyz)
+        L = [h - l for l, h in zip(self.lo, self.hi)]
+        if ic == "smooth":
+            self.u = inputs.smooth_random(self.xyz, seed=seed, lengths=L)
+        elif ic == "rough":
+            self.u = inputs.smooth_random(self.xyz, seed=seed, lengths=L) + 0.05 * inputs.random_state(self.xyz, seed + 1)
+        elif ic == "random":
+            self.u = inputs.random_state(self.xyz, seed=seed)
+        elif ic == "tgv":
+            self.u = inputs.taylor_green(self.xyz)
+        elif ic == "noisy_sine":
+            self.u = inputs.noisy_sine_2d(self.xyz, seed=seed)
+        elif ic == "vortex":
+            self.u = inputs.isentropic_vortex(self.xyz, eps=20.0)
+        elif ic == "free_stream":
+            self.u = inputs.free_stream(self.xyz)
+        elif ic == "pressure_eq":
+            self.u = inputs.pressure_equilibrium(self.xyz, seed=seed)
+        else:
+            raise ValueError(ic)
+        self._du = None
+
+    @property
+    def E(self):
+        return self.u.shape[0]
+
+    def du_ref(self):
+        if self._du is None:
+            self._du = orc.rhs(self.nd, self.p, self.nelem, self.Ja, self.J, self.u, llf=self.llf)
+        return self._du
+
+    def dg_kwargs(self):
+        kw = dict(ndims=self.nd, nelem=self.nelem, polydeg=self.p, lo=self.lo, hi=self.hi,
+                  surface="llf" if self.llf else "ec")
+        if self.mapping == "twisted":
+            kw.update(mapping="nodes", node_xyz=self.xyz)
+        elif self.mapping == "sine":
+            kw.update(mapping="sine", amp=self.amp)
+        else:
+            kw.update(mapping="affine")
+        return kw
+
+
+def rel_err_per_var(got, ref):
+    """max_i |got - ref| / max_i |ref| for each variable (normwise, per variable)."""
+    got = np.asarray(got)
+    ref = np.asarray(ref)
+    nv = ref.shape[1]
+    out = []
+    for c in range(nv):
+        scale = np.max(np.abs(ref[:, c]))
+        out.append(np.max(np.abs(got[:, c] - ref[:, c])) / (scale if scale > 0 else 1.0))
+    return np.array(out)

@@ -1,0 +1,69 @@
+"""CPU checks of the C ABI: the library builds, loads, exports every entry point declared in include/dg.h,
+and rejects bad arguments before touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions(header):
+    text = open(os.path.join(ROOT, "include", header)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dg\w*)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2112_10517_gb300 import build
+    return build.build()
+
+
+def test_library_exports_every_declared_entry_point(built):
+    lib = ctypes.CDLL(built["libdg.so"])
+    names = declared_functions("dg.h")
+    assert "dg_init" in names and "dg_rhs" in names and "dg_step" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_peaks_library_exports(built):
+    lib = ctypes.CDLL(built["libdgpeaks.so"])
+    for n in declared_functions("dg_peaks.h"):
+        assert hasattr(lib, n), n
+
+
+def test_argument_errors_without_gpu(built):
+    from paper_2112_10517_gb300 import dg
+    assert dg.dg_status_string(dg.DG_ERR_ARG) == b"invalid argument"
+    ctx = ctypes.c_void_p()
+    mesh = dg.DgMesh()
+    opts = dg.DgOpts()
+    opts.gamma = 1.4
+    mesh.ndims = 4  # invalid
+    assert dg.dg_init(ctypes.byref(ctx), ctypes.byref(mesh), 3, None, ctypes.byref(opts)) == dg.DG_ERR_ARG
+    mesh.ndims = 3
+    for i in range(3):
+        mesh.nelem[i] = 2
+        mesh.lo[i] = -1.0
+        mesh.hi[i] = 1.0
+    assert dg.dg_init(ctypes.byref(ctx), ctypes.byref(mesh), 9, None, ctypes.byref(opts)) == dg.DG_ERR_UNSUPPORTED
+    assert dg.dg_init(ctypes.byref(ctx), ctypes.byref(mesh), 0, None, ctypes.byref(opts)) == dg.DG_ERR_UNSUPPORTED
+    opts.gamma = 1.0
+    assert dg.dg_init(ctypes.byref(ctx), ctypes.byref(mesh), 3, None, ctypes.byref(opts)) == dg.DG_ERR_ARG
+    opts.gamma = 1.4
+    opts.reserved[0] = 1
+    assert dg.dg_init(ctypes.byref(ctx), ctypes.byref(mesh), 3, None, ctypes.byref(opts)) == dg.DG_ERR_ARG
+    opts.reserved[0] = 0
+    mesh.hi[1] = -2.0  # empty box
+    assert dg.dg_init(ctypes.byref(ctx), ctypes.byref(mesh), 3, None, ctypes.byref(opts)) == dg.DG_ERR_ARG
+    mesh.hi[1] = 1.0
+    mesh.nelem[2] = 0  # no elements
+    assert dg.dg_init(ctypes.byref(ctx), ctypes.byref(mesh), 3, None, ctypes.byref(opts)) == dg.DG_ERR_ARG
+    assert dg.dg_rhs(None, None, None, 0.0, None) == dg.DG_ERR_ARG
+    assert dg.dg_step(None, None, None, 0.0, 0.1, 0, None) == dg.DG_ERR_ARG
+    assert dg.dg_check_status(None) == dg.DG_ERR_ARG
+    assert dg.dg_launch_count(None) == -1
+    dg.dg_free(None)  # no-op
