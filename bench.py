@@ -1,0 +1,423 @@
+#!/usr/bin/env python3
+"""Benchmark: performance index PID (Sec. 4.1, Def. PID: time of one RHS evaluation / #DOF, in ns) of the
+flux-differencing LGL-DGSEM RHS on GB300, FP64 (headline) and FP32-flux mode.
+
+Workload: 3D compressible Euler, inviscid Taylor-Green vortex at Mach 0.1 on the periodic curvilinear mesh
+[-pi, pi]^3 with x_i = xi_i + 0.1 sin(xi_1) sin(xi_2) sin(xi_3), 16^3 elements, polydeg 3 (262,144 DOF),
+Ranocha volume flux, Ranocha + local Lax-Friedrichs surface flux. One step = one dg_step of the four-stage
+low-storage RK4 (4 RHS evaluations + 4 fused stage updates); PID = step time / (4 * #DOF).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 launch with torchrun: every rank advances its own independent copy of the workload (weak
+scaling, no data-path collective); the step time is the max over ranks.
+--impl reference times the CPU oracle (plain C, FP64, one core) on a bounded element sample of the same
+workload, one oracle RHS evaluation per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NELEM = [16, 16, 16]
+POLYDEG = 3
+MACH = 0.1
+AMP = 0.1
+STAGES = 4  # classical RK4, low-storage form
+METRIC = "PID (ns per DOF per RHS eval), FP64 vs FP32, 1xGB300, with roofline fraction"
+WORKLOAD = "3D Euler inviscid Taylor-Green vortex M=0.1, curvilinear periodic [-pi,pi]^3 16^3 hex, p=3 (262,144 DOF)"
+L2_FLUSH_BYTES = 512 << 20
+
+# Algorithmic FLOPs of the volume kernel per DOF (3D, p = 3, series branch of both logarithmic means, a
+# division or reciprocal counted as one flop, an FMA as two): 4.5 node pairs per DOF x 98 flops per pair
+# (directional Ranocha flux 72 + averaged normal 6 + two-sided accumulation 20), plus 13 flops of primitive
+# variables and 30 flops of direction sums, surface lift and Jacobian scaling per node.
+VOLUME_FLOPS_PER_DOF = 4.5 * 98 + 13 + 30
+# Algorithmic HBM bytes of the volume kernel per DOF: u 40 (FP64) + Ja 72 (FP64; 36 as the FP32 copy) + 1/J 8
+# + du 40 (FP64) + interface fluxes 2d/(p+1) = 1.5 face nodes per DOF x 5 values (8 B FP64, 4 B FP32).
+VOLUME_BYTES_PER_DOF_F64 = 40 + 72 + 8 + 40 + 1.5 * 5 * 8
+VOLUME_BYTES_PER_DOF_F32 = 40 + 36 + 8 + 40 + 1.5 * 5 * 4
+NELEM_LARGE = [32, 32, 32]  # the precision workload: 2,097,152 DOF, inputs larger than L2
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (debug runs)")
+    ap.add_argument("--only", default="", help="comma-separated subset of fp64_16,fp32_16,fp64_32,fp32_32 "
+                    "(profiling runs; prints one line per configuration instead of the contract line)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------------
+def source_digest() -> str:
+    h = hashlib.sha256()
+    for f in ("kernels.cuh", "volume.cu"):
+        with open(os.path.join(ROOT, "paper_2112_10517_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(precision: str):
+    """DRAM bytes per volume-kernel launch from the committed ncu summary, if it was taken on the current
+    kernel source (same digest); else None."""
+    path = os.path.join(ROOT, "profiles", "volume_kernel_tgv16_p3.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch_%s:\s*([0-9.eE+]+)\s+source_digest:\s*([0-9a-f]+)" % precision, text)
+    if not m or m.group(2) != source_digest():
+        return None
+    return float(m.group(1))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            return json.load(open(path))
+        except ValueError:
+            pass
+    return {}
+
+
+def alu_peaks():
+    """FP64 and FP32 FMA rates measured live with libdgpeaks (flop/s, FMA = 2 flop)."""
+    import ctypes
+    from paper_2112_10517_gb300 import build as _b
+    lib = ctypes.CDLL(_b.lib_path("libdgpeaks.so"))
+    out = {}
+    for kind, name in ((0, "fp64"), (1, "fp32")):
+        ops = ctypes.c_double()
+        rc = lib.dgpk_measure(kind, ctypes.c_double(0.05), ctypes.byref(ops), None)
+        out[name] = 2.0 * ops.value if rc == 0 else None
+    return out
+
+
+def make_state(ctx):
+    from paper_2112_10517_gb300 import inputs
+    return inputs.taylor_green(ctx.node_coords(), mach=MACH)
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_2112_10517_gb300 import build as _b
+    if rank == 0 or world == 1:
+        _b.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2112_10517_gb300 import dg
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    lo, hi = [-math.pi] * 3, [math.pi] * 3
+    only = [x for x in args.only.split(",") if x]
+    peaks_alu = alu_peaks() if rank == 0 and not only else {}
+    results = {}
+    runs = [("fp64_16", NELEM, "fp64", True), ("fp32_16", NELEM, "fp32", False),
+            ("fp64_32", NELEM_LARGE, "fp64", False), ("fp32_32", NELEM_LARGE, "fp32", False)]
+    if only:
+        runs = [(lab, ne, pr, False) for lab, ne, pr, _ in runs if lab in only]
+    for label, nelem, precision, main in runs:
+        ctx = dg.DG(3, nelem, POLYDEG, lo=lo, hi=hi, mapping="sine", amp=AMP, surface="llf", precision=precision)
+        u0 = make_state(ctx)
+        u = torch.from_numpy(u0).to(dev)
+        scratch = torch.empty((2,) + ctx.shape, dtype=torch.float64, device=dev)
+        # time step: CFL 0.5 on the smallest node spacing (TGV speed |v| + c <= 1 + 1/M)
+        dt = 0.5 * (2 * math.pi / nelem[0]) / (POLYDEG + 1) ** 2 / (1.0 + 1.0 / MACH)
+        for _ in range(args.warmup):
+            ctx.step(u, dt, dg.DG_RK4_CLASSIC, scratch=scratch)
+        torch.cuda.synchronize()
+        if ctx.check_status() != dg.DG_OK:
+            raise RuntimeError("non-physical state during warm-up")
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        clocks = ClockSampler(local_rank) if main else None
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        ctx.profile(True)
+        launches0 = ctx.launch_count()
+        for k in range(args.steps):
+            flush.zero_()  # evict L2 (larger than the 126 MB L2) between timed steps
+            starts[k].record(stream)
+            ctx.step(u, dt, dg.DG_RK4_CLASSIC, scratch=scratch)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        launches = ctx.launch_count() - launches0
+        if world > 1:
+            torch.distributed.barrier()
+        clk = clocks.stop() if clocks else None
+        vol_ms, vol_n = ctx.profile_read(dg.KERNEL_VOLUME)
+        ifc_ms, ifc_n = ctx.profile_read(dg.KERNEL_INTERFACE)
+        upd_ms, upd_n = ctx.profile_read(dg.KERNEL_UPDATE)
+        ctx.profile(False)
+        ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
+        if world > 1:
+            t = torch.tensor([ms], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        status = ctx.check_status()
+        if status != dg.DG_OK:
+            raise RuntimeError("non-physical state during the timed steps")
+        ndofs = ctx.ndofs
+        pid = ms * 1e6 / (STAGES * ndofs * world)
+        vol_avg_s = vol_ms / max(vol_n, 1) * 1e-3
+        res = {"ms_per_step": ms, "pid_ns": pid, "launches": launches, "clocks": clk,
+               "volume_ms_avg": vol_avg_s * 1e3, "interface_ms_avg": ifc_ms / max(ifc_n, 1),
+               "update_ms_avg": upd_ms / max(upd_n, 1),
+               "volume_share_of_step": vol_ms / (ms * args.steps) if ms > 0 else None}
+        # e2e: the same step through the public API with the state in pinned host memory, copies timed
+        if main:
+            u_host = torch.from_numpy(u0).pin_memory()
+            u_out = torch.empty_like(u_host).pin_memory()
+            ud = torch.empty_like(u)
+            e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+            e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+            for k in range(args.warmup):
+                ud.copy_(u_host, non_blocking=True)
+                ctx.step(ud, dt, dg.DG_RK4_CLASSIC, scratch=scratch)
+                u_out.copy_(ud, non_blocking=True)
+            torch.cuda.synchronize()
+            for k in range(args.steps):
+                flush.zero_()
+                e0[k].record(stream)
+                ud.copy_(u_host, non_blocking=True)
+                ctx.step(ud, dt, dg.DG_RK4_CLASSIC, scratch=scratch)
+                u_out.copy_(ud, non_blocking=True)
+                e1[k].record(stream)
+            torch.cuda.synchronize()
+            ems = sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / args.steps
+            if world > 1:
+                t = torch.tensor([ems], dtype=torch.float64, device=dev)
+                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+                ems = float(t.item())
+            res["e2e_pid_ns"] = ems * 1e6 / (STAGES * ndofs * world)
+            res["e2e_bytes"] = int(u_host.numel() * 8)
+        # roofline of the dominant kernel (volume): FP64 is bound by the FP64 pipe, FP32 by HBM
+        vflops = VOLUME_FLOPS_PER_DOF * ndofs
+        if precision == "fp64":
+            peak = peaks_alu.get("fp64")
+            achieved = vflops / vol_avg_s / 1e12
+            res["roofline"] = {"bound": "alu", "achieved": achieved,
+                               "peak": peak / 1e12 if peak else None, "unit": "TFLOP/s",
+                               "frac": achieved / (peak / 1e12) if peak else None,
+                               "traffic": committed_traffic("fp64"),
+                               "peak_source": "measured live: libdgpeaks fp64 FMA chain x 2 flop",
+                               "algorithmic_flops_per_launch": vflops}
+        else:
+            hbm = measured_peaks().get("hbm_gbs", 6800.0)
+            vbytes = VOLUME_BYTES_PER_DOF_F32 * ndofs
+            achieved = vbytes / vol_avg_s / 1e9
+            peak32 = peaks_alu.get("fp32")
+            res["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                               "frac": achieved / hbm, "traffic": committed_traffic("fp32"),
+                               "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                               "algorithmic_bytes_per_launch": vbytes,
+                               "alu_frac_of_fp32_peak": (vflops / vol_avg_s) / peak32 if peak32 else None}
+        res["ndofs"] = ndofs
+        results[label] = res
+        del ctx, u, scratch
+    return results, peaks_alu
+
+
+def oracle_pid(seconds_target: float, elements=None):
+    """Time the CPU oracle RHS on the same workload; returns (pid_ns, sample description, reps)."""
+    import numpy as np
+    import oracle as orc
+    from paper_2112_10517_gb300 import inputs
+    lo, hi = [-math.pi] * 3, [math.pi] * 3
+    xyz = orc.coords(3, NELEM, lo, hi, POLYDEG, mapping=1, amp=AMP)
+    Ja, J = orc.metrics(3, POLYDEG, xyz)
+    u = inputs.taylor_green(xyz, mach=MACH)
+    E = u.shape[0]
+    b, e = (0, E) if elements is None else elements
+    nd = (e - b) * u.shape[2]
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        orc.rhs(3, POLYDEG, NELEM, Ja, J, u, llf=True, elem_range=(b, e))
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds_target and reps >= 2:
+            break
+    return el / (reps * nd) * 1e9, reps, nd
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle as orc
+    orc.build()
+    # each step: one oracle RHS evaluation on a fixed sample of 512 elements (1/8 of the mesh, 32,768 DOF)
+    import numpy as np
+    from paper_2112_10517_gb300 import inputs
+    lo, hi = [-math.pi] * 3, [math.pi] * 3
+    xyz = orc.coords(3, NELEM, lo, hi, POLYDEG, mapping=1, amp=AMP)
+    Ja, J = orc.metrics(3, POLYDEG, xyz)
+    u = inputs.taylor_green(xyz, mach=MACH)
+    sample = (1536, 2048)
+    nd = (sample[1] - sample[0]) * u.shape[2]
+    for _ in range(args.warmup):
+        orc.rhs(3, POLYDEG, NELEM, Ja, J, u, llf=True, elem_range=sample)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        orc.rhs(3, POLYDEG, NELEM, Ja, J, u, llf=True, elem_range=sample)
+        times.append(time.perf_counter() - t0)
+    ms = sum(times) / len(times) * 1e3
+    pid = ms * 1e6 / nd
+    line = {"metric": METRIC, "value": pid, "unit": "ns/DOF/RHS", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": "elements 1536-2047 (512 of 4096)", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": pid, "unit": "ns/DOF/RHS", "cores": 1, "kind": "oracle",
+                             "sample": "one oracle RHS evaluation per step on 512 of the 4096 elements"},
+            "e2e": {"value": pid, "unit": "ns/DOF/RHS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    if world > 1:
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    results, peaks_alu = run_ours(args, rank, world, local_rank)
+    if rank == 0 and args.only:
+        for label, res in results.items():
+            print(json.dumps({"configuration": label, "pid_ns": res["pid_ns"], "ms_per_step": res["ms_per_step"],
+                              "volume_ms": res["volume_ms_avg"], "interface_ms": res["interface_ms_avg"],
+                              "update_ms": res["update_ms_avg"]}), flush=True)
+    elif rank == 0:
+        r64, r32 = results["fp64_16"], results["fp32_16"]
+        b64, b32 = results["fp64_32"], results["fp32_32"]
+        cpu = None
+        if not args.no_cpu_baseline:
+            pid_cpu, reps, nd = oracle_pid(10.0)
+            cpu = {"value": pid_cpu, "unit": "ns/DOF/RHS", "cores": 1, "kind": "oracle",
+                   "sample": "%d oracle RHS evaluations of the full 16^3 p=3 mesh (%d DOF each), 1 core" % (reps, nd)}
+        line = {
+            "metric": METRIC, "value": r64["pid_ns"], "unit": "ns/DOF/RHS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r64["ms_per_step"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "time_step": "4-stage low-storage RK4 (4 RHS + 4 stage updates)",
+                       "pid_per": "RHS evaluation", "surface_flux": "Ranocha + LLF", "volume_flux": "Ranocha",
+                       "l2": "flushed (512 MB write) before every timed step",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": r64["roofline"],
+            "cpu_baseline": cpu,
+            "e2e": {"value": r64.get("e2e_pid_ns"), "unit": "ns/DOF/RHS",
+                    "h2d_bytes_per_step": r64.get("e2e_bytes"), "d2h_bytes_per_step": r64.get("e2e_bytes")},
+            "gpu_launches": r64["launches"],
+            "clocks": r64["clocks"],
+            "kernels_ms": {"volume": r64["volume_ms_avg"], "interface": r64["interface_ms_avg"],
+                           "update": r64["update_ms_avg"], "volume_share_of_step": r64["volume_share_of_step"]},
+            "fp32": {"value": r32["pid_ns"], "unit": "ns/DOF/RHS", "ms_per_step": r32["ms_per_step"],
+                     "workload": "same as value (16^3, p=3)", "dtype": "f32 flux + line sums; f64 state, RK",
+                     "speedup_vs_fp64": r64["pid_ns"] / r32["pid_ns"], "gpu_launches": r32["launches"],
+                     "kernels_ms": {"volume": r32["volume_ms_avg"], "interface": r32["interface_ms_avg"],
+                                    "update": r32["update_ms_avg"]}},
+            "precision_workload_32cubed": {
+                "workload": "same TGV on 32^3 elements, p=3 (2,097,152 DOF; inputs larger than L2)",
+                "fp64": {"value": b64["pid_ns"], "ms_per_step": b64["ms_per_step"], "roofline": b64["roofline"],
+                         "kernels_ms": {"volume": b64["volume_ms_avg"], "interface": b64["interface_ms_avg"],
+                                        "update": b64["update_ms_avg"]}},
+                "fp32": {"value": b32["pid_ns"], "ms_per_step": b32["ms_per_step"], "roofline": b32["roofline"],
+                         "kernels_ms": {"volume": b32["volume_ms_avg"], "interface": b32["interface_ms_avg"],
+                                        "update": b32["update_ms_avg"]}},
+                "speedup_fp32_vs_fp64": b64["pid_ns"] / b32["pid_ns"]},
+            "alu_peaks_measured_tflops": {k: (v / 1e12 if v else None) for k, v in peaks_alu.items()},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

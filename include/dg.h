@@ -123,7 +123,8 @@ dg_status dg_step(dg_ctx* ctx, double* u, double* scratch, double t, double dt, 
 
 /* Entropy rate dS/dt = sum_e sum_i J_i W_i w(u_i) . du_i (Sec. 2: EC/ED semidiscretizations; W the tensor
    LGL weights, w the entropy variables of U = -rho s/(gamma-1)). FP64, deterministic order. Writes the value
-   to *out_host and, when abs_out_host is not NULL, sum |J W w.du| to *abs_out_host. Synchronizes `stream`. */
+   to *out_host and, when abs_out_host is not NULL, the magnitude sum_e sum_i sum_c |J_i W_i w_c(u_i) du_c,i| to
+   *abs_out_host (the scale for judging dS/dt = 0). Synchronizes `stream`. */
 dg_status dg_entropy_rate(dg_ctx* ctx, const double* u, const double* du, double* out_host, double* abs_out_host,
                           dg_stream_t stream);
 

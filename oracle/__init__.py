@@ -196,10 +196,11 @@ def metrics(ndims: int, p: int, xyz, curl_form: bool = True):
 
 
 def rhs(ndims: int, p: int, nelem, Ja, J, u, gamma: float = 1.4, llf: bool = True,
-        elem_range=None) -> np.ndarray:
+        elem_range=None, scale: bool = False) -> np.ndarray:
     """du/dt of the flux-differencing LGL-DGSEM (Eq. strong-form-SBP with Eq. fluxdiff-SBP,
     curvilinear via Eq. curvilinear-rewrite). elem_range=(b, e) computes only elements [b, e) and returns
-    that slice [e-b, nvar, Nd]."""
+    that slice [e-b, nvar, Nd]. scale=True returns instead (1/J) x the sum of |terms| of that sum, the
+    magnitude that the rounding of any evaluation of it scales with."""
     lib = _load()
     Ja = _f64(Ja)
     J = _f64(J)
@@ -210,7 +211,7 @@ def rhs(ndims: int, p: int, nelem, Ja, J, u, gamma: float = 1.4, llf: bool = Tru
     assert 0 <= b <= e <= E
     du = np.zeros((e - b,) + u.shape[1:])
     _check(lib.orc_rhs(ndims, p, _ivec(nelem), _ptr(Ja), _ptr(J), _ptr(u), ctypes.c_double(gamma),
-                       int(bool(llf)), int(b), int(e), _ptr(du)), "rhs")
+                       int(bool(llf)), int(b), int(e), int(bool(scale)), _ptr(du)), "rhs")
     return du
 
 

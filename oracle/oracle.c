@@ -371,9 +371,12 @@ int orc_metrics(int nd, int p, int nelem_total, const double* xyz, int curl_form
         }
         continue;
       }
-      /* V_k = X_l * D_k X_m at the nodes (k = 0,1,2) */
+      /* V_k = X_l * D_k X_m at the nodes (k = 0,1,2), with X_l taken relative to the element's first node.
+         The curl of c grad X_m vanishes for a constant c (tensor-product D's commute), so the metric is the
+         same; relative coordinates keep the rounding of the products proportional to the element size h
+         instead of to |x| (absolute coordinates make it grow like |x|/h and jump across periodic boundaries). */
       for (int k = 0; k < 3; ++k)
-        for (int i = 0; i < Nd; ++i) V[k * Nd + i] = X[l * Nd + i] * dx[(k * 3 + m) * Nd + i];
+        for (int i = 0; i < Nd; ++i) V[k * Nd + i] = (X[l * Nd + i] - X[l * Nd]) * dx[(k * 3 + m) * Nd + i];
       /* (Ja^n)_j = -(curl V)_n: (curl V)_0 = D_1 V_2 - D_2 V_1, (curl V)_1 = D_2 V_0 - D_0 V_2,
          (curl V)_2 = D_0 V_1 - D_1 V_0 */
       for (int n = 0; n < 3; ++n) {
@@ -398,17 +401,23 @@ int orc_metrics(int nd, int p, int nelem_total, const double* xyz, int curl_form
 /*  du_i = -(1/J_i) [ sum_n sum_{k on i's line along xi_n} D_{i_n k_n} sum_j (Ja^n_j(i) + Ja^n_j(k))  */
 /*                                                              F_j(u_i, u_k)                        */
 /*                  + sum_n [i_n = p] (1/w_p) ( f*(u_i, u_nbr, Ja^n(i)) - sum_j Ja^n_j(i) f^j(u_i) )  */
-/*                  + sum_n [i_n = 0] (1/w_0) ( f*(u_i, u_nbr, -Ja^n(i)) + sum_j Ja^n_j(i) f^j(u_i) ) ] */
+/*                  + sum_n [i_n = 0] (1/w_0) ( f*(u_i, u_nbr, -Ja^n(nbr)) + sum_j Ja^n_j(i) f^j(u_i) ) ] */
 /*                                                                                                   */
 /* The volume term is 2 sum_j sum_k (D_j)_{ik} F_j with (D_j)_{ik} = (1/J_i) sum_n alpha^{j,n}_{ik}   */
 /* (D_n)_{ik}, alpha the averaged contravariant vector (Sec. 2.3); the surface term is               */
 /* M^{-1} R^T B (f* - sum_j N_j R f^j) with the outward scaled normal +-Ja^n on face xi_n = +-1.     */
+/* The paper does not print the curvilinear surface flux; here f* takes ONE normal per interface node,  */
+/* Ja^n of the element below the interface along xi_n (curl-form metrics agree on both sides up to      */
+/* rounding), which keeps the discrete scheme exactly conservative across every interface.             */
 /* u_nbr is the coincident node of the neighbour across the face (periodic). Elements                */
 /* [elem_begin, elem_end) are computed and stored in du as elements 0 .. elem_end-elem_begin-1.      */
+/* scale_mode != 0 returns instead (1/J_i) times the sum of the absolute values of every term above   */
+/* (each volume product and both surface products): the magnitude that rounding errors of any         */
+/* evaluation of the sum scale with.                                                                  */
 /* ------------------------------------------------------------------------------------------------ */
 
 int orc_rhs(int nd, int p, const int* nelem, const double* Ja, const double* J, const double* u, double gamma,
-            int llf, int elem_begin, int elem_end, double* du) {
+            int llf, int elem_begin, int elem_end, int scale_mode, double* du) {
   if (nd < 2 || nd > 3 || p < 1 || p >= ORC_MAXN) return -1;
   const int N = p + 1, Nd = orc_ipow(N, nd), nv = nd + 2;
   const int n1 = nelem[0], n2 = nelem[1], n3 = nd == 3 ? nelem[2] : 1;
@@ -433,7 +442,10 @@ int orc_rhs(int nd, int p, const int* nelem, const double* Ja, const double* J, 
             const double a = Ja[(((size_t)e * nd + n) * nd + j) * Nd + i] +
                              Ja[(((size_t)e * nd + n) * nd + j) * Nd + k];
             orc_flux_ranocha_cart(ui, uk, nd, gamma, j, F);
-            for (int c = 0; c < nv; ++c) acc[c] += D[ii[n] * N + kn] * a * F[c];
+            for (int c = 0; c < nv; ++c) {
+              const double term = D[ii[n] * N + kn] * a * F[c];
+              acc[c] += scale_mode ? fabs(term) : term;
+            }
           }
         }
         /* surface: faces xi_n = +1 (i_n = p) and xi_n = -1 (i_n = 0) */
@@ -445,20 +457,27 @@ int orc_rhs(int nd, int p, const int* nelem, const double* Ja, const double* J, 
           nb[n] = (nb[n] + (side == 0 ? 1 : ne[n] - 1)) % ne[n];
           const int enb = nb[0] + n1 * (nb[1] + n2 * nb[2]);
           const int inb = i + ((side == 0 ? 0 : p) - ii[n]) * stride;
-          double unb[5], m[3], fstar[5], fj[5], fn[5] = {0, 0, 0, 0, 0};
+          double unb[5], m[3], mf[3], fstar[5], fj[5], fn[5] = {0, 0, 0, 0, 0};
           for (int c = 0; c < nv; ++c) unb[c] = u[((size_t)enb * nv + c) * Nd + inb];
-          for (int j = 0; j < nd; ++j) m[j] = sgn * Ja[(((size_t)e * nd + n) * nd + j) * Nd + i];
-          orc_surface_flux(ui, unb, nd, gamma, m, llf, fstar); /* outward scaled normal m */
+          /* m: outward scaled normal of this element at node i (its own metric); mf: the normal of the
+             interface, one per interface node, taken from the element below it along xi_n (the same value
+             on both sides, so each interface flux enters the two elements with opposite signs). */
+          for (int j = 0; j < nd; ++j) {
+            m[j] = sgn * Ja[(((size_t)e * nd + n) * nd + j) * Nd + i];
+            mf[j] = side == 0 ? m[j] : -Ja[(((size_t)enb * nd + n) * nd + j) * Nd + inb];
+          }
+          orc_surface_flux(ui, unb, nd, gamma, mf, llf, fstar);
           for (int j = 0; j < nd; ++j) {
             orc_euler_flux(ui, nd, gamma, j, fj);
             for (int c = 0; c < nv; ++c) fn[c] += m[j] * fj[c];
           }
           const double winv = 1.0 / wg[side == 0 ? p : 0];
-          for (int c = 0; c < nv; ++c) acc[c] += winv * (fstar[c] - fn[c]);
+          for (int c = 0; c < nv; ++c)
+            acc[c] += scale_mode ? winv * (fabs(fstar[c]) + fabs(fn[c])) : winv * (fstar[c] - fn[c]);
         }
       }
       for (int c = 0; c < nv; ++c)
-        du[((size_t)(e - elem_begin) * nv + c) * Nd + i] = -acc[c] / J[(size_t)e * Nd + i];
+        du[((size_t)(e - elem_begin) * nv + c) * Nd + i] = (scale_mode ? acc[c] : -acc[c]) / J[(size_t)e * Nd + i];
     }
   }
   return 0;
@@ -547,13 +566,13 @@ int orc_rk_step(int scheme, int nd, int p, const int* nelem, const double* Ja, c
     double* k[4];
     double* y = (double*)malloc(sizeof(double) * n);
     for (int s = 0; s < 4; ++s) k[s] = (double*)malloc(sizeof(double) * n);
-    orc_rhs(nd, p, nelem, Ja, J, u, gamma, llf, 0, E, k[0]);
+    orc_rhs(nd, p, nelem, Ja, J, u, gamma, llf, 0, E, 0, k[0]);
     for (size_t q = 0; q < n; ++q) y[q] = u[q] + 0.5 * dt * k[0][q];
-    orc_rhs(nd, p, nelem, Ja, J, y, gamma, llf, 0, E, k[1]);
+    orc_rhs(nd, p, nelem, Ja, J, y, gamma, llf, 0, E, 0, k[1]);
     for (size_t q = 0; q < n; ++q) y[q] = u[q] + 0.5 * dt * k[1][q];
-    orc_rhs(nd, p, nelem, Ja, J, y, gamma, llf, 0, E, k[2]);
+    orc_rhs(nd, p, nelem, Ja, J, y, gamma, llf, 0, E, 0, k[2]);
     for (size_t q = 0; q < n; ++q) y[q] = u[q] + dt * k[2][q];
-    orc_rhs(nd, p, nelem, Ja, J, y, gamma, llf, 0, E, k[3]);
+    orc_rhs(nd, p, nelem, Ja, J, y, gamma, llf, 0, E, 0, k[3]);
     for (size_t q = 0; q < n; ++q) u[q] += dt / 6.0 * (k[0][q] + 2.0 * k[1][q] + 2.0 * k[2][q] + k[3][q]);
     free(y);
     for (int s = 0; s < 4; ++s) free(k[s]);
@@ -563,7 +582,7 @@ int orc_rk_step(int scheme, int nd, int p, const int* nelem, const double* Ja, c
     double* K = (double*)calloc(n, sizeof(double));
     double* f = (double*)malloc(sizeof(double) * n);
     for (int s = 0; s < 5; ++s) {
-      orc_rhs(nd, p, nelem, Ja, J, u, gamma, llf, 0, E, f);
+      orc_rhs(nd, p, nelem, Ja, J, u, gamma, llf, 0, E, 0, f);
       for (size_t q = 0; q < n; ++q) {
         K[q] = ORC_CK_A[s] * K[q] + dt * f[q];
         u[q] += ORC_CK_B[s] * K[q];

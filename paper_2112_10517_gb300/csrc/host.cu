@@ -155,8 +155,11 @@ bool compute_metrics(int nd, int p, long long E, const double* xyz, const dgk::R
       }
       for (int j = 0; j < 3; ++j) {
         const int m = (j + 1) % 3, l = (j + 2) % 3;
+        // X_l relative to the element's first node: the curl of c grad X_m is zero for constant c, so the metric
+        // is unchanged, and the rounding of the products scales with the element size instead of with |x|.
+        const double x0 = X[(size_t)l * Nd];
         for (int k = 0; k < 3; ++k)
-          for (int i = 0; i < Nd; ++i) V[k * Nd + i] = X[(size_t)l * Nd + i] * g[(k * 3 + m) * Nd + i];
+          for (int i = 0; i < Nd; ++i) V[k * Nd + i] = (X[(size_t)l * Nd + i] - x0) * g[(k * 3 + m) * Nd + i];
         for (int n = 0; n < 3; ++n) {
           const int n1 = (n + 1) % 3, n2 = (n + 2) % 3;
           deriv(3, N, t.D, n1, &V[n2 * Nd], a.data());

@@ -70,13 +70,20 @@ __global__ void __launch_bounds__(kRedThreads)
     const double p = (gamma - 1.0) * (ue[(ND + 1) * ndof] - 0.5 * m2 / rho);
     const double ent = log(p) - gamma * log(rho);
     const double beta = rho / p;
-    double t = ((gamma - ent) / (gamma - 1.0) - 0.5 * beta * m2 / (rho * rho)) * de[0];
+    const double jw = JW[g];
+    double t = jw * ((gamma - ent) / (gamma - 1.0) - 0.5 * beta * m2 / (rho * rho)) * de[0];
+    double ta = fabs(t);
 #pragma unroll
-    for (int j = 0; j < ND; ++j) t += (ue[(1 + j) * ndof] / p) * de[(1 + j) * ndof];
-    t -= beta * de[(ND + 1) * ndof];
-    t *= JW[g];
+    for (int j = 0; j < ND; ++j) {
+      const double tj = jw * (ue[(1 + j) * ndof] / p) * de[(1 + j) * ndof];
+      t += tj;
+      ta += fabs(tj);
+    }
+    const double te = -jw * beta * de[(ND + 1) * ndof];
+    t += te;
+    ta += fabs(te);
     s += t;
-    sa += fabs(t);
+    sa += ta;
   }
   __shared__ double sh[2][kRedThreads];
   sh[0][threadIdx.x] = s;

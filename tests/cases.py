@@ -66,6 +66,12 @@ class Scenario:
             self._du = orc.rhs(self.nd, self.p, self.nelem, self.Ja, self.J, self.u, llf=self.llf)
         return self._du
 
+    def du_scale(self):
+        """(1/J) sum |terms| of the RHS sum at each node (oracle scale mode)."""
+        if getattr(self, "_scale", None) is None:
+            self._scale = orc.rhs(self.nd, self.p, self.nelem, self.Ja, self.J, self.u, llf=self.llf, scale=True)
+        return self._scale
+
     def dg_kwargs(self):
         kw = dict(ndims=self.nd, nelem=self.nelem, polydeg=self.p, lo=self.lo, hi=self.hi,
                   surface="llf" if self.llf else "ec")
@@ -88,3 +94,19 @@ def rel_err_per_var(got, ref):
         scale = np.max(np.abs(ref[:, c]))
         out.append(np.max(np.abs(got[:, c] - ref[:, c])) / (scale if scale > 0 else 1.0))
     return np.array(out)
+
+
+def parity_errors(got, ref, scale):
+    """Per variable: (plain, term) errors. plain = max|got - ref| / max|ref|; term = max|got - ref| / max scale,
+    with scale = (1/J) sum |terms| of the RHS sum (oracle scale mode): the magnitude that the rounding of any
+    FP64 evaluation of the sum is proportional to. The two coincide up to the cancellation factor
+    kappa = max scale / max|ref| of the data."""
+    got = np.asarray(got)
+    ref = np.asarray(ref)
+    plain, term = [], []
+    for c in range(ref.shape[1]):
+        d = np.max(np.abs(got[:, c] - ref[:, c]))
+        r = np.max(np.abs(ref[:, c]))
+        plain.append(d / (r if r > 0 else 1.0))
+        term.append(d / np.max(scale[:, c]))
+    return np.array(plain), np.array(term)

@@ -351,7 +351,9 @@ def test_free_stream_preservation(nd, nelem, p, curved):
     u = inputs.free_stream(xyz)
     for llf in (False, True):
         du = orc.rhs(nd, p, nelem, Ja, J, u, llf=llf)
+        scale = orc.rhs(nd, p, nelem, Ja, J, u, llf=llf, scale=True)
         assert np.max(np.abs(du)) < 1e-12
+        assert np.max(np.abs(du)) < 1e-13 * np.max(scale)
 
 
 def test_free_stream_on_twisted_mesh_needs_curl_metrics():
@@ -404,6 +406,18 @@ def test_pressure_equilibrium(nd, nelem, p, curved):
         for j in range(nd):
             np.testing.assert_allclose(du[:, 1 + j], v[j] * du[:, 0], rtol=0, atol=1e-12 * scale)
         np.testing.assert_allclose(du[:, -1], 0.5 * np.dot(v, v) * du[:, 0], rtol=0, atol=1e-12 * scale)
+
+
+def test_scale_mode_bounds_the_rhs():
+    # scale = (1/J) sum |terms| >= |(1/J) sum terms| = |du| at every node (triangle inequality), and it is
+    # equal for a single term: free stream on an affine mesh makes every term cancel against another one
+    nd, nelem, p = 3, [3, 2, 3], 3
+    xyz, Ja, J = mesh(nd, nelem, p, True)
+    u = inputs.smooth_random(xyz, seed=3)
+    du = orc.rhs(nd, p, nelem, Ja, J, u)
+    sc = orc.rhs(nd, p, nelem, Ja, J, u, scale=True)
+    assert np.all(sc >= np.abs(du) * (1 - 1e-14))
+    assert np.all(sc > 0)
 
 
 # ---- exact time derivatives of smooth solutions: pins every term of the RHS on curved meshes ----
