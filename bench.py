@@ -131,17 +131,17 @@ def source_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def committed_traffic(precision: str):
-    """DRAM bytes per volume-kernel launch from the committed ncu summary, if it was taken on the current
-    kernel source (same digest); else None."""
-    path = os.path.join(ROOT, "profiles", "volume_kernel_tgv16_p3.md")
+def committed_traffic(precision: str, ndofs: int):
+    """DRAM bytes per volume-kernel launch: bytes per DOF from the committed ncu capture (32^3 case, inputs larger
+    than L2) times the DOF of this launch; None unless the capture was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "volume_kernel_tgv32_p3.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
-    m = re.search(r"traffic_bytes_per_launch_%s:\s*([0-9.eE+]+)\s+source_digest:\s*([0-9a-f]+)" % precision, text)
+    m = re.search(r"traffic_bytes_per_dof_%s:\s*([0-9.eE+]+)\s+source_digest:\s*([0-9a-f]+)" % precision, text)
     if not m or m.group(2) != source_digest():
         return None
-    return float(m.group(1))
+    return float(m.group(1)) * ndofs
 
 
 def measured_peaks():
@@ -281,7 +281,7 @@ def run_ours(args, rank, world, local_rank):
             res["roofline"] = {"bound": "alu", "achieved": achieved,
                                "peak": peak / 1e12 if peak else None, "unit": "TFLOP/s",
                                "frac": achieved / (peak / 1e12) if peak else None,
-                               "traffic": committed_traffic("fp64"),
+                               "traffic": committed_traffic("fp64", ndofs),
                                "peak_source": "measured live: libdgpeaks fp64 FMA chain x 2 flop",
                                "algorithmic_flops_per_launch": vflops}
         else:
@@ -290,7 +290,7 @@ def run_ours(args, rank, world, local_rank):
             achieved = vbytes / vol_avg_s / 1e9
             peak32 = peaks_alu.get("fp32")
             res["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                               "frac": achieved / hbm, "traffic": committed_traffic("fp32"),
+                               "frac": achieved / hbm, "traffic": committed_traffic("fp32", ndofs),
                                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
                                "algorithmic_bytes_per_launch": vbytes,
                                "alu_frac_of_fp32_peak": (vflops / vol_avg_s) / peak32 if peak32 else None}
