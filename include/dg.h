@@ -148,6 +148,38 @@ long long dg_launch_count(const dg_ctx* ctx);
 void dg_free(dg_ctx* ctx);
 const char* dg_status_string(dg_status s);
 
+/* ---------------------------------------------------------------------------------------------------------
+ * dg_rhs_noalloc -- the paper has no counterpart to this entry point; it serves callers of this library.
+ *
+ * Computes the same du = RHS(u) as dg_rhs, without a context and without allocating any memory. It is for
+ * callers that cannot call cudaMalloc: an application whose memory manager owns all device memory (every
+ * allocation has to go through its pool and its accounting), or code on a latency-critical path where an
+ * allocation or a free could synchronize the device. Such a caller keeps u, du and the metric terms in its own
+ * device memory; the interface fluxes, which dg_rhs keeps in a per-context workspace, go to one fixed device
+ * array of DG_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads the library holds until the
+ * process exits. The call uses no cudaMalloc, cudaFree or allocating library routine.
+ *
+ *   ndims, nelem[ndims], polydeg, precision, surface_flux, gamma: as in dg_mesh / dg_opts (periodic box,
+ *        structured, lexicographic element order).
+ *   u, du  device [E][nvar][Nd] doubles, distinct and not overlapping (layout as for dg_rhs).
+ *   Ja     device metric terms [E][ndims][ndims][Nd], Ja[e][n][j][i] = (Ja^n)_j at node i: doubles for DG_FP64,
+ *          floats for DG_FP32 (dg_get_metrics returns them in FP64).
+ *   invJ   device [E][Nd] doubles, 1/J at every node.
+ *   flag   optional device int: set to 0 at the start of the call, then non-zero if a kernel meets rho <= 0,
+ *          p <= 0 or NaN. NULL uses a slot in the library's array.
+ * Returns DG_ERR_UNSUPPORTED when the interface fluxes of the mesh do not fit the array (ndims * E * nvar *
+ * (p+1)^(ndims-1) values of the flux precision, plus 256 bytes; at 64 MiB this admits 32^3 elements at p = 3 in
+ * FP64) or polydeg is outside 1..7, DG_ERR_ARG for other invalid arguments, DG_ERR_CUDA if a launch fails.
+ * The first call made on a device looks up the array's device address for that device (cudaGetSymbolAddress);
+ * make that first call before any stream capture. Every call on a device shares the one array, and it keeps
+ * the last call's contents: calls that may overlap on the GPU (different streams, or threads without ordering)
+ * race on it and must be serialized by the caller. Work is queued on `stream`; the host is not synchronized.
+ * --------------------------------------------------------------------------------------------------------- */
+#define DG_NOALLOC_SCRATCH_BYTES (64u << 20)
+dg_status dg_rhs_noalloc(int ndims, const int* nelem, int polydeg, int precision, int surface_flux, double gamma,
+                         const double* u, const void* Ja, const double* invJ, double* du, int* flag,
+                         dg_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,7 +32,7 @@ KERNEL_VOLUME, KERNEL_INTERFACE, KERNEL_UPDATE = 0, 1, 2
 
 EXPORTED = ["dg_init", "dg_rhs", "dg_step", "dg_entropy_rate", "dg_check_status", "dg_get_info",
             "dg_get_node_coords", "dg_get_metrics", "dg_profile_enable", "dg_profile_read", "dg_launch_count",
-            "dg_free", "dg_status_string"]
+            "dg_free", "dg_status_string", "dg_rhs_noalloc"]
 
 
 class DgMesh(ctypes.Structure):
@@ -73,6 +73,8 @@ _sig = {
     "dg_launch_count": (ctypes.c_longlong, [_vp]),
     "dg_free": (None, [_vp]),
     "dg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "dg_rhs_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
