@@ -22,6 +22,14 @@ int dgpk_num_kinds(void);
    cudaError_t value. */
 int dgpk_measure(int kind, double min_seconds, double* ops_per_s, double* seconds);
 
+/* Arithmetic self-test of the RHS kernels' device code (the same source as libdg): for i < n, on device arrays,
+   L[i] = {{a1[i], b1[i]}}_log by Algorithm 2 and Li[i] = 1/{{a2[i], b2[i]}}_log by Algorithm 3 (Sec. 3.1), from the
+   single reciprocal the flux kernels share, and r[i] = the kernels' reciprocal of a1[i]. precision 0: FP64;
+   1: FP32 (inputs rounded to float). Inputs must be positive. Synchronizes the device; returns 0 or a
+   cudaError_t value. */
+int dgpk_eval_logmeans(long long n, int precision, const double* a1, const double* b1, const double* a2,
+                       const double* b2, double* L, double* Li, double* r);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,7 @@ LIBS = {
     "libdg.so": ["host.cu", "volume.cu", "interface.cu", "misc.cu", "noalloc.cu"],
     "libdgpeaks.so": ["peaks.cu"],
 }
-HEADERS = ["dg_internal.h", "kernels.cuh"]
+HEADERS = ["dg_internal.h", "kernels.cuh", "dgmath.cuh"]
 
 
 def _nvcc() -> str:
@@ -52,7 +52,7 @@ def build(force: bool = False, ptxas_info: bool = False, verbose: bool = False) 
     for lib, srcs in LIBS.items():
         target = lib_path(lib)
         src_paths = [os.path.join(CSRC, s) for s in srcs]
-        deps = src_paths + headers
+        deps = src_paths + headers + [os.path.join(ROOT, "include", "dg_peaks.h")]
         if not force and os.path.exists(target) and os.path.getmtime(target) >= _newest(deps):
             out[lib] = target
             continue

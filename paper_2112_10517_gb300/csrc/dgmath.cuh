@@ -1,0 +1,147 @@
+// Device arithmetic of the two-point flux: reciprocals, the logarithmic mean and its inverse (Sec. 3.1,
+// Algorithms 2 and 3), per-node quantities and Ranocha's flux (Sec. 3.2, Eq. flux_ranocha).
+// Shared by the RHS kernels (libdg) and by the arithmetic self-test entry of libdgpeaks.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dgk {
+
+// ---------------------------------------------------------------------------------------------------
+// Precision traits. On GB300 an FP64 FMA issues at 2 per clock per SM; a correctly rounded FP64 reciprocal
+// costs about 7 FMA slots, a division 10 and a logarithm 37 (measured with libdgpeaks), so the FP64 kernels
+// avoid them where the mathematics allows.
+// ---------------------------------------------------------------------------------------------------
+template <typename T>
+struct Num;
+
+template <>
+struct Num<double> {
+  // 1/s by the Newton-Raphson iteration r <- r + r (1 - s r), which doubles the number of correct bits per
+  // step, started from the hardware approximation rcp.approx.ftz.f64; two steps reach the rounding limit
+  // (result within 1 ulp of 1/s). Valid for normal positive and negative s; s = 0 gives a non-finite result.
+  __device__ static __forceinline__ double rcp(double s) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(s));
+    double e = fma(-s, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-s, r, 1.0);
+    return fma(r, e, r);
+  }
+  __device__ static __forceinline__ double log(double x) { return ::log(x); }
+  __device__ static __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+  __device__ static __forceinline__ double abs(double x) { return ::fabs(x); }
+  // u < 1e-4, the threshold of the series branch of Algorithms 2 and 3 for 64-bit floats (Sec. 3.1), tested on
+  // the high 32 bits of u >= 0 (an integer comparison): the effective threshold is the largest double whose
+  // high word is below that of 1e-4, 1e-4 to within a relative 1e-6; both branches are accurate there.
+  __device__ static __forceinline__ bool series(double u) {
+    return __double2hiint(u) < 0x3F1A36E2;  // high word of 1e-4 = 0x3F1A36E2EB1C432D
+  }
+};
+
+template <>
+struct Num<float> {
+  // rcp.approx.ftz.f32 and one Newton-Raphson step (FP32 flux mode)
+  __device__ static __forceinline__ float rcp(float s) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(s));
+    return fmaf(r, fmaf(-s, r, 1.0f), r);
+  }
+  __device__ static __forceinline__ float log(float x) { return ::logf(x); }
+  __device__ static __forceinline__ float sqrt(float x) { return ::sqrtf(x); }
+  __device__ static __forceinline__ float abs(float x) { return ::fabsf(x); }
+  // The paper states the threshold for 64-bit floats only. In FP32 the truncated series is accurate to about
+  // 0.03 u^4 relative and the log branch loses about eps32/(2 sqrt(u)); 1e-2 keeps both near 1 ulp.
+  __device__ static __forceinline__ bool series(float u) { return u < 1e-2f; }
+};
+
+// ---------------------------------------------------------------------------------------------------
+// The two logarithmic means of Ranocha's flux from ONE reciprocal (Sec. 3.1 and 3.2):
+//   L  = {{a}}_log                for (a1, b1)                (Algorithm 2)
+//   Li = 1/{{c}}_log              for (a2, b2)                (Algorithm 3)
+// With s = a + b and f = (b - a)/s, u = f^2 equals the u of Algorithms 2 and 3 (their numerator and
+// denominator are (b - a)^2 and (b + a)^2). R = 1/(s1 s2) gives 1/s1 = s2 R and 1/s2 = s1 R.
+// Series branches: L = s1 (1/2 - u/6 - 2u^2/45 - 22u^3/945), the polynomial form of 1/log of Sec. 3.1
+// (a multiplication instead of a division), and Li = (2 + 2u/3 + 2u^2/5 + 2u^3/7)/s2 (Algorithm 3).
+// Log branches: L = (b - a)/log(b/a), Li = log(b/a)/(b - a), as in Algorithms 2 and 3.
+// ---------------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void log_means(T a1, T b1, T a2, T b2, T& L, T& Li) {
+  const T s1 = a1 + b1, d1 = b1 - a1;
+  const T s2 = a2 + b2, d2 = b2 - a2;
+  const T R = Num<T>::rcp(s1 * s2);
+  const T r1 = s2 * R, r2 = s1 * R;
+  const T f1 = d1 * r1, f2 = d2 * r2;
+  const T u1 = f1 * f1, u2 = f2 * f2;
+  if (Num<T>::series(u1))
+    L = s1 * (T(0.5) + u1 * (T(-1.0 / 6.0) + u1 * (T(-2.0 / 45.0) + u1 * T(-22.0 / 945.0))));
+  else
+    L = d1 / Num<T>::log(b1 / a1);
+  if (Num<T>::series(u2))
+    Li = r2 * (T(2.0) + u2 * (T(2.0 / 3.0) + u2 * (T(2.0 / 5.0) + u2 * T(2.0 / 7.0))));
+  else
+    Li = Num<T>::log(b2 / a2) / d2;
+}
+
+// ---------------------------------------------------------------------------------------------------
+// Per-node quantities for the pair flux (Sec. 7.1: computed once per node, not once per pair):
+//   q = (rho, v_1..v_d, pp = 2p, pg = 2p/(gamma - 1))                            NQ = d + 3 values
+// from conserved u; returns false for rho <= 0, p <= 0 or NaN.
+// ---------------------------------------------------------------------------------------------------
+template <int ND>
+struct NodeQ {
+  static constexpr int NQ = ND + 3;
+  static constexpr int RHO = 0, V = 1, PP = ND + 1, PG = ND + 2;
+};
+
+template <int ND, typename T>
+__device__ __forceinline__ bool node_quantities(const double* uc, T gm1, T two_over_gm1, T* q) {
+  const T rho = (T)uc[0];
+  const T ir = Num<T>::rcp(rho);
+  T ke = T(0);
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    const T m = (T)uc[1 + j];
+    const T v = m * ir;
+    q[1 + j] = v;
+    ke += m * v;
+  }
+  const T p = gm1 * ((T)uc[ND + 1] - T(0.5) * ke);
+  q[0] = rho;
+  q[NodeQ<ND>::PP] = p + p;
+  q[NodeQ<ND>::PG] = p * two_over_gm1;
+  return rho > T(0) && p > T(0);
+}
+
+// ---------------------------------------------------------------------------------------------------
+// Ranocha's EC/KEP/PEP flux in directional form (Eq. flux_ranocha), scaled by 8:
+//   F = 8 f(u_a, u_b, n2/2),  n2 = Ja^n_a + Ja^n_b (twice the averaged contravariant vector, Sec. 2.3).
+// With A = v_a.n2, B = v_b.n2, L = {{rho}}_log, Li = 1/{{rho_a pp_b, rho_b pp_a}}_log, Q = L (A + B):
+//   F_rho  = 2 Q                                          (8 {{rho}}_log {{v.n}})
+//   F_rhov = Q (v_a + v_b) + (pp_a + pp_b) n2             (8 (f_rho {{v}} + {{p}} n))
+//   F_rhoe = Q (v_a.v_b + pg_a pp_b Li) + pp_a B + pp_b A (8 (f_rho (v_a.v_b/2 + 1/({{rho/p}}_log (gamma-1)))
+//                                                             + ((p; v.n))))
+// using 1/{{rho/p}}_log = p_a p_b / {{rho_a p_b, rho_b p_a}}_log (Sec. 3.2) and the homogeneity of the mean.
+// ---------------------------------------------------------------------------------------------------
+template <int ND, typename T>
+__device__ __forceinline__ void ranocha_flux8(const T* a, const T* b, const T* n2, T* F) {
+  using Q = NodeQ<ND>;
+  T A = a[1] * n2[0], B = b[1] * n2[0], vv = a[1] * b[1];
+#pragma unroll
+  for (int j = 1; j < ND; ++j) {
+    A += a[1 + j] * n2[j];
+    B += b[1 + j] * n2[j];
+    vv += a[1 + j] * b[1 + j];
+  }
+  T L, Li;
+  log_means<T>(a[Q::RHO], b[Q::RHO], a[Q::RHO] * b[Q::PP], b[Q::RHO] * a[Q::PP], L, Li);
+  const T q = L * (A + B);
+  const T ps = a[Q::PP] + b[Q::PP];
+  F[0] = q + q;
+#pragma unroll
+  for (int j = 0; j < ND; ++j) F[1 + j] = q * (a[1 + j] + b[1 + j]) + ps * n2[j];
+  F[ND + 1] = q * (vv + a[Q::PG] * b[Q::PP] * Li) + (a[Q::PP] * B + b[Q::PP] * A);
+}
+
+}  // namespace dgk

@@ -6,112 +6,9 @@
 #include <stdint.h>
 
 #include "dg_internal.h"
+#include "dgmath.cuh"
 
 namespace dgk {
-
-// ---------------------------------------------------------------------------------------------------
-// Precision traits
-// ---------------------------------------------------------------------------------------------------
-template <typename T>
-struct Num;
-
-template <>
-struct Num<double> {
-  __device__ static __forceinline__ double rcp(double x) { return __drcp_rn(x); }
-  __device__ static __forceinline__ double log(double x) { return ::log(x); }
-  __device__ static __forceinline__ double sqrt(double x) { return ::sqrt(x); }
-  __device__ static __forceinline__ double abs(double x) { return ::fabs(x); }
-  // threshold of the series branch of Algorithms 2 and 3 (Sec. 3.1; the value stated for 64-bit floats)
-  static constexpr double kLogMeanEps = 1e-4;
-};
-
-template <>
-struct Num<float> {
-  __device__ static __forceinline__ float rcp(float x) { return __frcp_rn(x); }
-  __device__ static __forceinline__ float log(float x) { return ::logf(x); }
-  __device__ static __forceinline__ float sqrt(float x) { return ::sqrtf(x); }
-  __device__ static __forceinline__ float abs(float x) { return ::fabsf(x); }
-  // The paper states the threshold for 64-bit floats only. In FP32 the truncated series is accurate to
-  // about 0.03 u^4 relative, and the log branch loses about eps32/(2 sqrt(u)): 1e-2 keeps both near 1 ulp.
-  static constexpr float kLogMeanEps = 1e-2f;
-};
-
-// ---------------------------------------------------------------------------------------------------
-// Logarithmic means (Sec. 3.1). With s = a+b and f = (b-a)/s, u = f^2 is the quantity of Algorithms 2 and 3
-// (their numerator and denominator are (b-a)^2 and (b+a)^2); it is formed here from one reciprocal 1/s,
-// which the series branches reuse. The series of Algorithm 2 uses the polynomial form of 1/log given in
-// Sec. 3.1 (multiplication instead of division); the series of Algorithm 3 is used as printed.
-// ---------------------------------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T ln_mean(T a, T b) {
-  const T s = a + b, d = b - a;
-  const T r = Num<T>::rcp(s);
-  const T f = d * r;
-  const T u = f * f;
-  if (u < T(Num<T>::kLogMeanEps))
-    return s * (T(0.5) + u * (T(-1.0 / 6.0) + u * (T(-2.0 / 45.0) + u * T(-22.0 / 945.0))));
-  return d / Num<T>::log(b / a);
-}
-
-template <typename T>
-__device__ __forceinline__ T inv_ln_mean(T a, T b) {
-  const T s = a + b, d = b - a;
-  const T r = Num<T>::rcp(s);
-  const T f = d * r;
-  const T u = f * f;
-  if (u < T(Num<T>::kLogMeanEps)) return r * (T(2.0) + u * (T(2.0 / 3.0) + u * (T(2.0 / 5.0) + u * T(2.0 / 7.0))));
-  return Num<T>::log(b / a) / d;
-}
-
-// ---------------------------------------------------------------------------------------------------
-// Primitive variables (Sec. 7.1: computed once per node, not once per pair). P = (rho, v_1..v_d, p).
-// Returns false for rho <= 0, p <= 0 or NaN.
-// ---------------------------------------------------------------------------------------------------
-template <int ND, typename T>
-__device__ __forceinline__ bool cons_to_prim(const double* uc, T gm1, T* P) {
-  const T rho = (T)uc[0];
-  const T ir = Num<T>::rcp(rho);
-  T ke = T(0);
-#pragma unroll
-  for (int j = 0; j < ND; ++j) {
-    const T m = (T)uc[1 + j];
-    const T v = m * ir;
-    P[1 + j] = v;
-    ke += m * v;
-  }
-  const T p = gm1 * ((T)uc[ND + 1] - T(0.5) * ke);
-  P[0] = rho;
-  P[ND + 1] = p;
-  return rho > T(0) && p > T(0);
-}
-
-// ---------------------------------------------------------------------------------------------------
-// Ranocha's EC/KEP/PEP flux in directional form (Sec. 3.2, Eq. flux_ranocha) for a direction n of any length
-// (the flux is linear in n; Sec. 2.3 uses the averaged contravariant vector). 1/{{rho/p}}_log is evaluated as
-// p_a p_b / {{rho_a p_b, rho_b p_a}}_log (division-free rewrite of Sec. 3.2) and 1/(gamma-1) is a factor.
-//   f_rho  = {{rho}}_log {{v.n}}
-//   f_rhov = f_rho {{v}} + {{p}} n
-//   f_rhoe = f_rho (v_a.v_b/2 + 1/({{rho/p}}_log (gamma-1))) + ((p; v.n))
-// ---------------------------------------------------------------------------------------------------
-template <int ND, typename T>
-__device__ __forceinline__ void ranocha_flux(const T* a, const T* b, const T* n, T inv_gm1, T* f) {
-  T vna = a[1] * n[0], vnb = b[1] * n[0], vv = a[1] * b[1];
-#pragma unroll
-  for (int j = 1; j < ND; ++j) {
-    vna += a[1 + j] * n[j];
-    vnb += b[1 + j] * n[j];
-    vv += a[1 + j] * b[1 + j];
-  }
-  const T pa = a[ND + 1], pb = b[ND + 1];
-  const T rho_mean = ln_mean<T>(a[0], b[0]);
-  const T inv_rho_p_mean = pa * pb * inv_ln_mean<T>(a[0] * pb, b[0] * pa);
-  const T p_avg = T(0.5) * (pa + pb);
-  const T f_rho = rho_mean * T(0.5) * (vna + vnb);
-  f[0] = f_rho;
-#pragma unroll
-  for (int j = 0; j < ND; ++j) f[1 + j] = f_rho * T(0.5) * (a[1 + j] + b[1 + j]) + p_avg * n[j];
-  f[ND + 1] = f_rho * (T(0.5) * vv + inv_rho_p_mean * inv_gm1) + T(0.5) * (pa * vnb + pb * vna);
-}
 
 // ---------------------------------------------------------------------------------------------------
 // Geometry of an element: N nodes per line, NL = N^(ND-1) lines per direction, NDOF = N^ND nodes.
@@ -150,8 +47,8 @@ __device__ __forceinline__ int neighbor(const MeshDims& md, int e, int n, int di
 
 template <int N, typename T>
 struct OpTable {
-  T Dt[N * N];  // flux-differencing matrix 2D - M^{-1}B (Eq. opDsplit)
-  T winv;       // 1/w_0 = 1/w_p = p(p+1)/2: the lift M^{-1} R^T B at the end nodes
+  T Dt8[N * N];  // flux-differencing matrix 2D - M^{-1}B (Eq. opDsplit), divided by 8 (fluxes come scaled by 8)
+  T winv;        // 1/w_0 = 1/w_p = p(p+1)/2: the lift M^{-1} R^T B at the end nodes
 };
 
 // ---------------------------------------------------------------------------------------------------
@@ -184,25 +81,32 @@ __global__ void __launch_bounds__(256) interface_kernel(const double* __restrict
     uL[c] = u[((size_t)e * G::NV + c) * G::NDOF + nodeL];
     uR[c] = u[((size_t)eR * G::NV + c) * G::NDOF + nodeR];
   }
-  T m[ND];
+  T m[ND], m2[ND];
 #pragma unroll
-  for (int j = 0; j < ND; ++j) m[j] = Ja[(((size_t)e * ND + n) * ND + j) * G::NDOF + nodeL];
+  for (int j = 0; j < ND; ++j) {
+    m[j] = Ja[(((size_t)e * ND + n) * ND + j) * G::NDOF + nodeL];
+    m2[j] = m[j] + m[j];
+  }
   const T gm1 = gamma - T(1);
-  T PL[G::NV], PR[G::NV], f[G::NV];
-  const bool ok = cons_to_prim<ND, T>(uL, gm1, PL) & cons_to_prim<ND, T>(uR, gm1, PR);
+  T qL[NodeQ<ND>::NQ], qR[NodeQ<ND>::NQ], f[G::NV];
+  const bool ok = node_quantities<ND, T>(uL, gm1, T(2) / gm1, qL) & node_quantities<ND, T>(uR, gm1, T(2) / gm1, qR);
   if (!ok) atomicOr(flag, 1);
-  ranocha_flux<ND, T>(PL, PR, m, T(1) / gm1, f);
+  ranocha_flux8<ND, T>(qL, qR, m2, f);
+#pragma unroll
+  for (int c = 0; c < G::NV; ++c) f[c] *= T(0.125);
   if (LLF) {
-    T mm = m[0] * m[0], vnL = PL[1] * m[0], vnR = PR[1] * m[0];
+    T mm = m[0] * m[0], vnL = qL[1] * m[0], vnR = qR[1] * m[0];
 #pragma unroll
     for (int j = 1; j < ND; ++j) {
       mm += m[j] * m[j];
-      vnL += PL[1 + j] * m[j];
-      vnR += PR[1 + j] * m[j];
+      vnL += qL[1 + j] * m[j];
+      vnR += qR[1 + j] * m[j];
     }
+    // c = sqrt(gamma p / rho) with p = pp/2
+    const T hg = T(0.5) * gamma;
     const T mn = Num<T>::sqrt(mm);
-    const T lamL = Num<T>::abs(vnL) + Num<T>::sqrt(gamma * PL[ND + 1] / PL[0]) * mn;
-    const T lamR = Num<T>::abs(vnR) + Num<T>::sqrt(gamma * PR[ND + 1] / PR[0]) * mn;
+    const T lamL = Num<T>::abs(vnL) + Num<T>::sqrt(hg * qL[NodeQ<ND>::PP] * Num<T>::rcp(qL[0])) * mn;
+    const T lamR = Num<T>::abs(vnR) + Num<T>::sqrt(hg * qR[NodeQ<ND>::PP] * Num<T>::rcp(qR[0])) * mn;
     const T half_lam = T(0.5) * (lamL > lamR ? lamL : lamR);
 #pragma unroll
     for (int c = 0; c < G::NV; ++c) f[c] -= half_lam * (T)(uR[c] - uL[c]);
@@ -217,7 +121,8 @@ __global__ void __launch_bounds__(256) interface_kernel(const double* __restrict
 //   du_i = -(1/J_i) [ sum_n sum_{k on i's line along n} Dt_{i_n k_n} f(u_i, u_k, (Ja^n_i + Ja^n_k)/2)
 //                   + sum_n ([i_n = p] f*_up - [i_n = 0] f*_down) / w_0 ].
 // Each CTA handles EPB elements.
-//   A. stage primitive variables and metric terms of the elements in shared memory (coalesced loads);
+//   A. stage the node quantities (rho, v, 2p, 2p/(gamma-1)) and metric terms of the elements in shared memory
+//      (coalesced loads);
 //   B. one thread per (element, direction n, line): every pair i < k of the line is evaluated ONCE
 //      (Sec. 2.2: Dt has zero diagonal and M Dt is skew-symmetric; f is symmetric) and added to both nodes
 //      with Dt_ik and Dt_ki; the line's sums stay in registers and go to shared memory per direction;
@@ -226,7 +131,7 @@ __global__ void __launch_bounds__(256) interface_kernel(const double* __restrict
 template <int ND, int N, typename T>
 struct VolumeSmem {
   using G = Geo<ND, N>;
-  static constexpr int kPrim = G::NV * G::NDOF;            // per element
+  static constexpr int kPrim = NodeQ<ND>::NQ * G::NDOF;    // per element: node quantities
   static constexpr int kJa = ND * ND * G::NDOF;            // per element
   static constexpr int kAcc = ND * G::NV * G::NDOF;        // per element
   static constexpr int kPerElem = kPrim + kJa + kAcc;      // elements of T
@@ -250,7 +155,8 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE)
   const int nel = min(EPB, md.E - e0);
   const T gm1 = gamma - T(1);
 
-  // ---- A: primitives and metric terms -> shared memory
+  // ---- A: node quantities and metric terms -> shared memory
+  constexpr int NQ = NodeQ<ND>::NQ;
   bool ok = true;
   for (int idx = tid; idx < nel * G::NDOF; idx += kThreads) {
     const int el = idx / G::NDOF, i = idx - el * G::NDOF;
@@ -258,10 +164,10 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE)
     double uc[G::NV];
 #pragma unroll
     for (int c = 0; c < G::NV; ++c) uc[c] = ue[c * G::NDOF];
-    T P[G::NV];
-    ok &= cons_to_prim<ND, T>(uc, gm1, P);
+    T q[NQ];
+    ok &= node_quantities<ND, T>(uc, gm1, T(2) / gm1, q);
 #pragma unroll
-    for (int c = 0; c < G::NV; ++c) s_prim[(el * G::NV + c) * G::NDOF + i] = P[c];
+    for (int c = 0; c < NQ; ++c) s_prim[(el * NQ + c) * G::NDOF + i] = q[c];
   }
   if (!ok) atomicOr(flag, 1);
   {
@@ -277,7 +183,6 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE)
     const int st = G::stride(n), base = G::line_base(n, l);
     const T* sp = s_prim + el * S::kPrim + base;
     const T* sj = s_ja + (el * ND + n) * ND * G::NDOF + base;
-    const T inv_gm1 = T(1) / gm1;
     T acc[N][G::NV];
 #pragma unroll
     for (int i = 0; i < N; ++i)
@@ -285,20 +190,20 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE)
       for (int c = 0; c < G::NV; ++c) acc[i][c] = T(0);
 #pragma unroll
     for (int i = 0; i < N - 1; ++i) {
-      T a[G::NV], ja_i[ND];
+      T a[NQ], ja_i[ND];
 #pragma unroll
-      for (int c = 0; c < G::NV; ++c) a[c] = sp[c * G::NDOF + i * st];
+      for (int c = 0; c < NQ; ++c) a[c] = sp[c * G::NDOF + i * st];
 #pragma unroll
       for (int j = 0; j < ND; ++j) ja_i[j] = sj[j * G::NDOF + i * st];
 #pragma unroll
       for (int k = i + 1; k < N; ++k) {
-        T b[G::NV], nrm[ND], f[G::NV];
+        T b[NQ], n2[ND], f[G::NV];
 #pragma unroll
-        for (int c = 0; c < G::NV; ++c) b[c] = sp[c * G::NDOF + k * st];
+        for (int c = 0; c < NQ; ++c) b[c] = sp[c * G::NDOF + k * st];
 #pragma unroll
-        for (int j = 0; j < ND; ++j) nrm[j] = T(0.5) * (ja_i[j] + sj[j * G::NDOF + k * st]);
-        ranocha_flux<ND, T>(a, b, nrm, inv_gm1, f);
-        const T dik = op.Dt[i * N + k], dki = op.Dt[k * N + i];
+        for (int j = 0; j < ND; ++j) n2[j] = ja_i[j] + sj[j * G::NDOF + k * st];
+        ranocha_flux8<ND, T>(a, b, n2, f);
+        const T dik = op.Dt8[i * N + k], dki = op.Dt8[k * N + i];
 #pragma unroll
         for (int c = 0; c < G::NV; ++c) {
           acc[i][c] += dik * f[c];

@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dgmath.cuh"
+
 namespace {
 
 constexpr int kChains = 8;
@@ -96,9 +98,40 @@ cudaError_t launch_kind(int kind, int blocks, int threads, double* sink, int ite
   }
 }
 
+template <typename T>
+__global__ void logmeans_kernel(long long n, const double* a1, const double* b1, const double* a2, const double* b2,
+                                double* L, double* Li, double* r) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T l, li;
+  dgk::log_means<T>((T)a1[i], (T)b1[i], (T)a2[i], (T)b2[i], l, li);
+  L[i] = (double)l;
+  Li[i] = (double)li;
+  r[i] = (double)dgk::Num<T>::rcp((T)a1[i]);
+}
+
 }  // namespace
 
 extern "C" {
+
+// Evaluates the RHS kernels' device arithmetic on n inputs (device arrays): L = {{a1, b1}}_log (Algorithm 2),
+// Li = 1/{{a2, b2}}_log (Algorithm 3), both from the single shared reciprocal, and r = the reciprocal of a1,
+// in FP64 (precision 0) or FP32 (precision 1; inputs rounded to float, results widened). Queues on the legacy
+// default stream and synchronizes. Returns 0 or a cudaError_t value.
+int dgpk_eval_logmeans(long long n, int precision, const double* a1, const double* b1, const double* a2,
+                       const double* b2, double* L, double* Li, double* r) {
+  if (n <= 0) return 0;
+  const int threads = 256;
+  const long long blocks = (n + threads - 1) / threads;
+  if (precision == 1)
+    logmeans_kernel<float><<<(unsigned)blocks, threads>>>(n, a1, b1, a2, b2, L, Li, r);
+  else
+    logmeans_kernel<double><<<(unsigned)blocks, threads>>>(n, a1, b1, a2, b2, L, Li, r);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return (int)e;
+}
+
 
 // Number of benchmark kinds; kind ids are listed in include/dg_peaks.h.
 int dgpk_num_kinds(void) { return K_NKINDS; }

@@ -26,7 +26,7 @@ cudaError_t launch_volume_t(MeshDims md, const double* u, const T* Ja, const dou
   }
   OpTable<N, T> op;
   const RefTables& t = ref_tables(N - 1);
-  for (int i = 0; i < N * N; ++i) op.Dt[i] = (T)t.Dt[i];
+  for (int i = 0; i < N * N; ++i) op.Dt8[i] = (T)(0.125 * t.Dt[i]);
   op.winv = (T)(1.0 / t.w[0]);
   const int blocks = (md.E + EPB - 1) / EPB;
   kern<<<blocks, threads, smem, s>>>(u, Ja, invJ, face, du, md, op, (T)gamma, flag);
