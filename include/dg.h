@@ -118,7 +118,8 @@ dg_status dg_rhs(dg_ctx* ctx, const double* u, double* du, double t, dg_stream_t
 /* One explicit time step u <- u + dt * (...) of the low-storage Runge-Kutta method `scheme` (Sec. 4.1):
    DG_RK4_CLASSIC  classical four-stage RK4 in low-storage form; scratch = 2 state arrays (2*state_len);
    DG_LSRK45_CK    five-stage fourth-order 2N method of Carpenter and Kennedy; scratch = 1 state array.
-   u and scratch are device memory; scratch contents on entry are ignored. RK accumulation is FP64. */
+   u and scratch are device memory, not overlapping; scratch contents on entry are ignored. Each stage queues
+   2 kernels: the interface fluxes, then the volume term whose epilogue applies the stage update in FP64. */
 dg_status dg_step(dg_ctx* ctx, double* u, double* scratch, double t, double dt, int scheme, dg_stream_t stream);
 
 /* Entropy rate dS/dt = sum_e sum_i J_i W_i w(u_i) . du_i (Sec. 2: EC/ED semidiscretizations; W the tensor
@@ -138,9 +139,9 @@ dg_status dg_get_node_coords(const dg_ctx* ctx, double* xyz_host /* [E][ndims][N
 dg_status dg_get_metrics(const dg_ctx* ctx, double* Ja_host /* [E][d][d][Nd] */, double* J_host /* [E][Nd] */);
 
 /* Kernel timing with CUDA events recorded on the launching stream around every launch of kernel `which`
-   (0 = volume, 1 = interface, 2 = RK update) while enabled. dg_profile_read returns the summed milliseconds
-   and the launch count since the last enable, and synchronizes. dg_launch_count counts every kernel the
-   context has launched since dg_init. */
+   (0 = volume term with surface lift and Jacobian, which in dg_step also applies the RK stage update;
+   1 = interface flux) while enabled. dg_profile_read returns the summed milliseconds and the launch count since
+   the last enable, and synchronizes. dg_launch_count counts every kernel the context has launched since dg_init. */
 dg_status dg_profile_enable(dg_ctx* ctx, int on);
 dg_status dg_profile_read(dg_ctx* ctx, int which, double* total_ms, long long* launches);
 long long dg_launch_count(const dg_ctx* ctx);

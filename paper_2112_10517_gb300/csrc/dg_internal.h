@@ -24,24 +24,37 @@ struct RefTables {
 };
 
 // Kernel ids for profiling
-enum { KID_VOLUME = 0, KID_INTERFACE = 1, KID_UPDATE = 2, KID_COUNT = 3 };
+enum { KID_VOLUME = 0, KID_INTERFACE = 1, KID_COUNT = 2 };
 
 // Reference tables of degree p (1..7), computed once on the host.
 const RefTables& ref_tables(int p);
+
+// What the volume kernel does with the RHS value k at each node: store it as du, or apply the stage update of
+// a Runge-Kutta method in place of a separate update kernel.
+enum { EPI_STORE = 0, EPI_RK4 = 1, EPI_CK45 = 2 };
+struct Epilogue {
+  int mode;        // EPI_*
+  int stage;       // stage index
+  double dt;       // time step
+  double a, b;     // CK45: A_s, B_s
+  double* u;       // RK4: solution at the start of the step (updated at the last stage); CK45: the state
+  double* y;       // RK4: next stage state; CK45: the K register
+  double* acc;     // RK4: accumulated sum of b_s dt k_s
+};
 
 // RHS kernels. Each returns the launch error. Ja is FP64 for precision DG_FP64 and FP32 for DG_FP32; the face
 // buffer holds the same type.
 cudaError_t launch_interface(int nd, int p, int precision, int llf, MeshDims md, const double* u, const void* Ja,
                              void* face, double gamma, int* flag, cudaStream_t s);
+// epi == nullptr stores du; otherwise du is unused and the stage update of *epi is applied.
 cudaError_t launch_volume(int nd, int p, int precision, MeshDims md, const double* u, const void* Ja, const double* invJ,
-                          const void* face, double* du, double gamma, int* flag, cudaStream_t s);
-// RK stage update (FP64).
-cudaError_t launch_rk_update(int scheme, int stage, size_t n, double dt, double* u, double* y, double* acc,
-                             const double* du, cudaStream_t s);
+                          const void* face, double* du, double gamma, int* flag, cudaStream_t s,
+                          const Epilogue* epi = nullptr);
 // Entropy-rate partial sums into partial[nblocks][2]; then a single block reduces into out[2].
 cudaError_t launch_entropy_rate(int nd, int p, MeshDims md, const double* u, const double* du, const double* JW,
                                 double gamma, double* partial, int nblocks, double* out, cudaStream_t s);
 int entropy_rate_blocks();
+void ck45_coefficients(int stage, double* a, double* b);
 
 }  // namespace dgk
 
@@ -63,7 +76,6 @@ struct dg_ctx {
   double* d_invJ;  // [E][Nd]
   double* d_JW;    // J * tensor LGL weight, [E][Nd]
   void* d_face;    // face fluxes [nd][E][nv][N^(nd-1)], FP64 or FP32
-  double* d_du;    // RHS workspace for dg_step
   double* d_red;   // entropy-rate partials + result
   int* d_flag;     // non-physical-state flag
   cudaStream_t last_stream;

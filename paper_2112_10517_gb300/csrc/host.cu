@@ -199,7 +199,6 @@ void release(dg_ctx* c) {
   cudaFree(c->d_invJ);
   cudaFree(c->d_JW);
   cudaFree(c->d_face);
-  cudaFree(c->d_du);
   cudaFree(c->d_red);
   cudaFree(c->d_flag);
   if (c->prof_ev) {
@@ -446,26 +445,40 @@ dg_status dg_rhs(dg_ctx* c, const double* u, double* du, double t, dg_stream_t s
 }
 
 dg_status dg_step(dg_ctx* c, double* u, double* scratch, double t, double dt, int scheme, dg_stream_t stream) {
+  (void)t;
   if (!c || !u || !scratch) return DG_ERR_ARG;
   if (scheme != DG_RK4_CLASSIC && scheme != DG_LSRK45_CK) return DG_ERR_ARG;
   if (!(dt == dt)) return DG_ERR_ARG;
+  if (((uintptr_t)u | (uintptr_t)scratch) & 7) return DG_ERR_ARG;
+  const size_t n = (size_t)c->state_len;
+  const size_t bytes = n * sizeof(double) * (scheme == DG_RK4_CLASSIC ? 2 : 1);
+  const char *ub = (const char*)u, *sb = (const char*)scratch;
+  if (ub < sb + bytes && sb < ub + n * sizeof(double)) return DG_ERR_ARG;  // u overlaps the scratch
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;
-  if (!c->d_du) {
-    cudaError_t e = dev_alloc(&c->d_du, (size_t)c->state_len);
-    if (e != cudaSuccess) return cuda_status(e);
-  }
-  const size_t n = (size_t)c->state_len;
   const int stages = scheme == DG_RK4_CLASSIC ? 4 : 5;
-  double* y = scratch;
-  double* acc = scheme == DG_RK4_CLASSIC ? scratch + n : nullptr;
+  const void* ja = c->precision == DG_FP32 ? (const void*)c->d_Ja32 : (const void*)c->d_Ja;
+  dgk::Epilogue epi{};
+  epi.mode = scheme == DG_RK4_CLASSIC ? dgk::EPI_RK4 : dgk::EPI_CK45;
+  epi.dt = dt;
+  epi.u = u;
+  epi.y = scratch;
+  epi.acc = scheme == DG_RK4_CLASSIC ? scratch + n : nullptr;
   for (int st = 0; st < stages; ++st) {
-    const double* in = (scheme == DG_RK4_CLASSIC && st > 0) ? y : u;
-    dg_status r = dg_rhs(c, in, c->d_du, t, stream);
-    if (r != DG_OK) return r;
+    // stage state: RK4 evaluates u, then y; CK45 evaluates u (updated in place)
+    const double* in = (scheme == DG_RK4_CLASSIC && st > 0) ? scratch : u;
+    epi.stage = st;
+    if (scheme == DG_LSRK45_CK) dgk::ck45_coefficients(st, &epi.a, &epi.b);
     int slot;
-    dgk::prof_begin(c, dgk::KID_UPDATE, s, &slot);
-    cudaError_t e = dgk::launch_rk_update(scheme, st, n, dt, u, y, acc, c->d_du, s);
+    dgk::prof_begin(c, dgk::KID_INTERFACE, s, &slot);
+    cudaError_t e = dgk::launch_interface(c->nd, c->p, c->precision, c->surface_flux == DG_SURF_EC_LLF, c->md, in,
+                                          ja, c->d_face, c->gamma, c->d_flag, s);
+    dgk::prof_end(c, s, slot);
+    if (e != cudaSuccess) return cuda_status(e);
+    // volume term with the stage update fused into its epilogue (no du round trip, no update kernel)
+    dgk::prof_begin(c, dgk::KID_VOLUME, s, &slot);
+    e = dgk::launch_volume(c->nd, c->p, c->precision, c->md, in, ja, c->d_invJ, c->d_face, nullptr, c->gamma,
+                           c->d_flag, s, &epi);
     dgk::prof_end(c, s, slot);
     if (e != cudaSuccess) return cuda_status(e);
   }

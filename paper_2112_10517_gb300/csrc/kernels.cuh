@@ -135,25 +135,56 @@ struct VolumeSmem {
   static constexpr int kJa = ND * ND * G::NDOF;            // per element
   static constexpr int kAcc = ND * G::NV * G::NDOF;        // per element
   static constexpr int kPerElem = kPrim + kJa + kAcc;      // elements of T
-  static constexpr size_t bytes(int epb) { return (size_t)epb * kPerElem * sizeof(T); }
+  static constexpr int kState = G::NV * G::NDOF;           // doubles per element of one state array
+  // with a fused stage update, two FP64 state arrays of the CTA's elements are prefetched into shared memory
+  static constexpr size_t bytes(int epb, bool fused) {
+    return (size_t)epb * kPerElem * sizeof(T) + (fused ? (size_t)2 * epb * kState * sizeof(double) : 0);
+  }
 };
 
-template <int ND, int N, typename T, int EPB>
+// Asynchronous 8-byte global -> shared copies (cp.async): issued early, completed before the values are used.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// EPI selects the epilogue: store du, or apply a Runge-Kutta stage update (in place of a separate kernel; the
+// stage arithmetic is the same as rk4_kernel / rk_ck45_kernel). With a stage update the kernel writes arrays
+// that alias its input u (the CTA has read its own elements before the barrier; no other CTA reads them).
+template <int ND, int N, typename T, int EPB, int EPI>
 __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE)
-    volume_kernel(const double* __restrict__ u, const T* __restrict__ Ja, const double* __restrict__ invJ,
-                  const T* __restrict__ face, double* __restrict__ du, MeshDims md, OpTable<N, T> op, T gamma,
-                  int* flag) {
+    volume_kernel(const double* u, const T* __restrict__ Ja, const double* __restrict__ invJ,
+                  const T* __restrict__ face, double* du, MeshDims md, OpTable<N, T> op, T gamma, int* flag,
+                  Epilogue epi) {
   using G = Geo<ND, N>;
   using S = VolumeSmem<ND, N, T>;
+  constexpr bool kFused = EPI != EPI_STORE;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* s_prim = reinterpret_cast<T*>(smem_raw);  // [EPB][NV][NDOF]
-  T* s_ja = s_prim + EPB * S::kPrim;           // [EPB][ND][ND][NDOF]
-  T* s_acc = s_ja + EPB * S::kJa;              // [EPB][ND][NV][NDOF]
+  double* s_eu = reinterpret_cast<double*>(smem_raw);      // [EPB][NV][NDOF] fused update: u
+  double* s_ey = s_eu + (kFused ? EPB * S::kState : 0);     // [EPB][NV][NDOF] fused update: acc (RK4) / K (CK45)
+  T* s_prim = reinterpret_cast<T*>(s_ey + (kFused ? EPB * S::kState : 0));  // [EPB][NQ][NDOF]
+  T* s_ja = s_prim + EPB * S::kPrim;                       // [EPB][ND][ND][NDOF]
+  T* s_acc = s_ja + EPB * S::kJa;                          // [EPB][ND][NV][NDOF]
   const int tid = threadIdx.x;
   constexpr int kThreads = EPB * G::TPE;
   const int e0 = blockIdx.x * EPB;
   const int nel = min(EPB, md.E - e0);
   const T gm1 = gamma - T(1);
+
+  // ---- prefetch the FP64 arrays the fused stage update reads, so that they arrive during the pair phase
+  if (kFused) {
+    const size_t base = (size_t)e0 * S::kState;
+    const int cnt = nel * S::kState;
+    const bool need_y = (EPI == EPI_RK4) ? epi.stage > 0 : epi.stage > 0;  // acc / K are read after stage 0
+    const double* gy = EPI == EPI_RK4 ? epi.acc : epi.y;
+    for (int idx = tid; idx < cnt; idx += kThreads) {
+      cp_async8(s_eu + idx, epi.u + base + idx);
+      if (need_y) cp_async8(s_ey + idx, gy + base + idx);
+    }
+    cp_async_commit();
+  }
 
   // ---- A: node quantities and metric terms -> shared memory
   constexpr int NQ = NodeQ<ND>::NQ;
@@ -220,6 +251,10 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE)
   __syncthreads();
 
   // ---- C: sum directions, lift interface fluxes, scale by -1/J
+  if (kFused) {
+    cp_async_wait_all();
+    __syncthreads();
+  }
   for (int idx = tid; idx < nel * G::NDOF; idx += kThreads) {
     const int el = idx / G::NDOF, i = idx - el * G::NDOF;
     const int ge = e0 + el;
@@ -244,9 +279,35 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE)
       }
     }
     const double sj = -invJ[(size_t)ge * G::NDOF + i];
-    double* d = du + (size_t)ge * G::NV * G::NDOF + i;
+    const size_t off = (size_t)ge * G::NV * G::NDOF + i;
 #pragma unroll
-    for (int c = 0; c < G::NV; ++c) d[c * G::NDOF] = sj * (double)tot[c];
+    for (int c = 0; c < G::NV; ++c) {
+      const size_t o = off + (size_t)c * G::NDOF;
+      const int so = (el * G::NV + c) * G::NDOF + i;  // same value, prefetched into shared memory
+      const double k = sj * (double)tot[c];
+      if (EPI == EPI_STORE) {
+        du[o] = k;
+      } else if (EPI == EPI_RK4) {
+        const double dt = epi.dt;
+        const double uo = s_eu[so];
+        if (epi.stage == 0) {
+          epi.acc[o] = (dt / 6.0) * k;
+          epi.y[o] = uo + (0.5 * dt) * k;
+        } else if (epi.stage == 1) {
+          epi.acc[o] = s_ey[so] + (dt / 3.0) * k;
+          epi.y[o] = uo + (0.5 * dt) * k;
+        } else if (epi.stage == 2) {
+          epi.acc[o] = s_ey[so] + (dt / 3.0) * k;
+          epi.y[o] = uo + dt * k;
+        } else {
+          epi.u[o] = uo + s_ey[so] + (dt / 6.0) * k;
+        }
+      } else {
+        const double kk = (epi.stage == 0 ? 0.0 : epi.a * s_ey[so]) + epi.dt * k;
+        epi.y[o] = kk;
+        epi.u[o] = s_eu[so] + epi.b * kk;
+      }
+    }
   }
 }
 

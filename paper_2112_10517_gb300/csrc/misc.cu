@@ -1,51 +1,16 @@
-// Time-stepping update and the entropy-rate diagnostic (both FP64).
+// Runge-Kutta coefficients and the entropy-rate diagnostic (FP64). The stage updates themselves run in the
+// volume kernel's epilogue.
 #include "kernels.cuh"
 
 namespace dgk {
 namespace {
 
 // Carpenter-Kennedy five-stage fourth-order 2N-storage coefficients (Sec. 4.1; Carpenter and Kennedy 1994).
-__constant__ double kCkA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
-                               -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
-__constant__ double kCkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
-                               1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
-                               2277821191437.0 / 14882151754819.0};
-
-// 2N Williamson stage: K <- A_s K + dt du; u <- u + B_s K  (K in y)
-__global__ void rk_ck45_kernel(size_t n, int stage, double dt, double* __restrict__ u, double* __restrict__ k,
-                               const double* __restrict__ du) {
-  const double A = kCkA[stage], B = kCkB[stage];
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double kk = (stage == 0 ? 0.0 : A * k[i]) + dt * du[i];
-    k[i] = kk;
-    u[i] += B * kk;
-  }
-}
-
-// Classical RK4 with two scratch registers: y (stage state) and acc (sum of b_s dt k_s so far):
-//   stage 0: acc  = dt/6 k1;  y = u + dt/2 k1
-//   stage 1: acc += dt/3 k2;  y = u + dt/2 k2
-//   stage 2: acc += dt/3 k3;  y = u + dt k3
-//   stage 3: u    = u + acc + dt/6 k4
-__global__ void rk4_kernel(size_t n, int stage, double dt, double* __restrict__ u, double* __restrict__ y,
-                           double* __restrict__ acc, const double* __restrict__ du) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double k = du[i];
-    if (stage == 0) {
-      acc[i] = (dt / 6.0) * k;
-      y[i] = u[i] + (0.5 * dt) * k;
-    } else if (stage == 1) {
-      acc[i] += (dt / 3.0) * k;
-      y[i] = u[i] + (0.5 * dt) * k;
-    } else if (stage == 2) {
-      acc[i] += (dt / 3.0) * k;
-      y[i] = u[i] + dt * k;
-    } else {
-      u[i] = u[i] + acc[i] + (dt / 6.0) * k;
-    }
-  }
-}
-
+constexpr double kCkAh[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                             -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+constexpr double kCkBh[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                             1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                             2277821191437.0 / 14882151754819.0};
 constexpr int kRedThreads = 256;
 constexpr int kRedBlocks = 1024;
 
@@ -130,21 +95,9 @@ __global__ void __launch_bounds__(kRedThreads) reduce_pairs_kernel(const double*
 
 int entropy_rate_blocks() { return kRedBlocks; }
 
-cudaError_t launch_rk_update(int scheme, int stage, size_t n, double dt, double* u, double* y, double* acc,
-                             const double* du, cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int threads = 256;
-  size_t blocks = (n + threads - 1) / threads;
-  const size_t cap = (size_t)sms * 8;
-  if (blocks > cap) blocks = cap;
-  if (scheme == DG_LSRK45_CK)
-    rk_ck45_kernel<<<(unsigned)blocks, threads, 0, s>>>(n, stage, dt, u, y, du);
-  else
-    rk4_kernel<<<(unsigned)blocks, threads, 0, s>>>(n, stage, dt, u, y, acc, du);
-  return cudaGetLastError();
+void ck45_coefficients(int stage, double* a, double* b) {
+  *a = kCkAh[stage];
+  *b = kCkBh[stage];
 }
 
 cudaError_t launch_entropy_rate(int nd, int p, MeshDims md, const double* u, const double* du, const double* JW,

@@ -28,7 +28,7 @@ DG_SURF_EC, DG_SURF_EC_LLF = 0, 1
 DG_FP64, DG_FP32 = 0, 1
 DG_VOL_RANOCHA = 0
 DG_RK4_CLASSIC, DG_LSRK45_CK = 0, 1
-KERNEL_VOLUME, KERNEL_INTERFACE, KERNEL_UPDATE = 0, 1, 2
+KERNEL_VOLUME, KERNEL_INTERFACE = 0, 1
 
 EXPORTED = ["dg_init", "dg_rhs", "dg_step", "dg_entropy_rate", "dg_check_status", "dg_get_info",
             "dg_get_node_coords", "dg_get_metrics", "dg_profile_enable", "dg_profile_read", "dg_launch_count",
