@@ -150,6 +150,34 @@ void dg_free(dg_ctx* ctx);
 const char* dg_status_string(dg_status s);
 
 /* ---------------------------------------------------------------------------------------------------------
+ * Batched RHS: many independent meshes of uneven size and degree in one persistent launch.
+ * The per-element work is that of dg_rhs (Eq. fluxdiff-SBP-opDsplit); only the scheduling differs.
+ *
+ * dg_batch_create binds n contexts and their state buffers: u[i], du[i] are device arrays of context i's
+ * layout (distinct, not overlapping; the caller keeps them valid for the plan's lifetime and may change their
+ * contents between calls). All contexts must be 3D, on the current device, with one precision, surface flux and
+ * gamma, and polydeg <= 5 (DG_ERR_UNSUPPORTED otherwise). Uses the contexts' metric terms, interface-flux
+ * workspaces and non-physical flags (dg_check_status of each context reports its instance). Allocates small
+ * device tables (work lists) and synchronizes.
+ * dg_batch_rhs computes du[i] = RHS_i(u[i]) for every instance: it queues one memset and two kernels on `stream`
+ * (all instances' interface fluxes, then one persistent volume kernel whose CTAs take element tiles, most
+ * expensive first, from a shared counter). It allocates nothing and does not synchronize, so a sequence of calls
+ * can be captured in a CUDA graph after a first call outside the capture. Plans sharing a context must not run
+ * concurrently (they share its workspace).
+ * dg_batch_autotune times every tile shape (threads per CTA 128/192/256, which sets the elements per tile of
+ * each degree) and persistent grid size (1..occupancy CTAs per SM) on the bound buffers, keeps the fastest, and
+ * when cache_path is not NULL reads the choice from, or appends it to, that text file (one line per
+ * device + batch signature). Synchronizes. dg_batch_set_tuning sets a choice directly (ctas_per_sm 0 = occupancy).
+ * --------------------------------------------------------------------------------------------------------- */
+typedef struct dg_batch dg_batch;
+dg_status dg_batch_create(dg_batch** out, dg_ctx* const* ctxs, int n, const double* const* u, double* const* du);
+dg_status dg_batch_rhs(dg_batch* batch, dg_stream_t stream);
+dg_status dg_batch_autotune(dg_batch* batch, const char* cache_path, dg_stream_t stream, int* threads_out,
+                            int* ctas_per_sm_out);
+dg_status dg_batch_set_tuning(dg_batch* batch, int threads, int ctas_per_sm);
+void dg_batch_free(dg_batch* batch);
+
+/* ---------------------------------------------------------------------------------------------------------
  * dg_rhs_noalloc -- the paper has no counterpart to this entry point; it serves callers of this library.
  *
  * Computes the same du = RHS(u) as dg_rhs, without a context and without allocating any memory. It is for

@@ -1,0 +1,498 @@
+// Batched RHS: many independent meshes of uneven size and polynomial degree in one persistent launch.
+//
+// Every instance is a dg_ctx (its own mesh, metrics and interface-flux workspace). A plan binds the instances
+// and their state buffers; dg_batch_rhs then queues one memset and two launches on a stream:
+//   1. one interface-flux launch over the face nodes of all instances (the instance is found by binary search
+//      in the prefix sums of the face-node counts),
+//   2. one persistent volume launch: each CTA repeatedly takes the next element tile from a global work
+//      counter (tiles ordered by decreasing cost) and runs the volume/lift/Jacobian code of that tile's degree.
+// The work is the same per element as dg_rhs (Eq. fluxdiff-SBP-opDsplit); only the scheduling differs.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace dgk {
+namespace {
+
+constexpr int kBatchMaxP = 5;  // degrees 1..5 in a batch
+const int kThreadChoices[] = {128, 192, 256};
+constexpr int kNumThreadChoices = 3;
+
+struct BatchInst {
+  const double* u;
+  double* du;
+  const void* Ja;
+  const double* invJ;
+  void* face;
+  int* flag;
+  MeshDims md;
+  int p;
+  long long face_begin;  // first face node of this instance in the flattened interface launch
+};
+
+struct BatchTile {
+  int inst;
+  int e0;
+};
+
+// flux-differencing tables of every degree in constant memory (one copy per device, uploaded at plan creation)
+#define DG_BATCH_CONST_OP(NN)                                                       \
+  __constant__ OpTable<NN, double> c_opd_##NN;                                      \
+  __constant__ OpTable<NN, float> c_opf_##NN;
+DG_BATCH_CONST_OP(2)
+DG_BATCH_CONST_OP(3)
+DG_BATCH_CONST_OP(4)
+DG_BATCH_CONST_OP(5)
+DG_BATCH_CONST_OP(6)
+
+template <int N, typename T>
+struct ConstOp;
+#define DG_BATCH_CONST_GET(NN)                                                                           \
+  template <>                                                                                            \
+  struct ConstOp<NN, double> {                                                                           \
+    __device__ static __forceinline__ const OpTable<NN, double>& get() { return c_opd_##NN; }           \
+  };                                                                                                     \
+  template <>                                                                                            \
+  struct ConstOp<NN, float> {                                                                            \
+    __device__ static __forceinline__ const OpTable<NN, float>& get() { return c_opf_##NN; }            \
+  };
+DG_BATCH_CONST_GET(2)
+DG_BATCH_CONST_GET(3)
+DG_BATCH_CONST_GET(4)
+DG_BATCH_CONST_GET(5)
+DG_BATCH_CONST_GET(6)
+
+// elements per tile for degree N at a CTA size: as many element line sets as fit, capped by shared memory
+template <int N, typename T, int THREADS>
+struct BatchEpb {
+  static constexpr int kByThreads = THREADS / Geo<3, N>::TPE;
+  static constexpr int kBySmem = (int)(200 * 1024 / VolumeSmem<3, N, T>::bytes(1, false));
+  static constexpr int value = kByThreads < kBySmem ? kByThreads : kBySmem;
+  static_assert(value >= 1, "CTA too small for this degree");
+};
+
+int batch_epb(int p, int precision, int threads) {
+  const int N = p + 1;
+  const int tpe = 3 * N * N;
+  const size_t per = (size_t)(6 + 9 + 15) * N * N * N * (precision == DG_FP32 ? 4 : 8);
+  const int by_t = threads / tpe, by_s = (int)(200 * 1024 / per);
+  return std::max(1, std::min(by_t, by_s));
+}
+
+size_t batch_smem(int p, int precision, int threads) {
+  const int N = p + 1;
+  const size_t per = (size_t)(6 + 9 + 15) * N * N * N * (precision == DG_FP32 ? 4 : 8);
+  return per * batch_epb(p, precision, threads);
+}
+
+template <typename T, bool LLF>
+__global__ void __launch_bounds__(256) batch_interface_kernel(const BatchInst* __restrict__ insts, int n,
+                                                              long long total, T gamma) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  int lo = 0, hi = n - 1;  // last instance with face_begin <= g
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (insts[mid].face_begin <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  const BatchInst& in = insts[lo];
+  const long long idx = g - in.face_begin;
+  const double* u = in.u;
+  const T* ja = static_cast<const T*>(in.Ja);
+  T* face = static_cast<T*>(in.face);
+  switch (in.p) {
+    case 1: interface_node<3, 2, T, LLF>(u, ja, face, in.md, gamma, in.flag, idx); break;
+    case 2: interface_node<3, 3, T, LLF>(u, ja, face, in.md, gamma, in.flag, idx); break;
+    case 3: interface_node<3, 4, T, LLF>(u, ja, face, in.md, gamma, in.flag, idx); break;
+    case 4: interface_node<3, 5, T, LLF>(u, ja, face, in.md, gamma, in.flag, idx); break;
+    case 5: interface_node<3, 6, T, LLF>(u, ja, face, in.md, gamma, in.flag, idx); break;
+    default: break;
+  }
+}
+
+template <int N, typename T, int THREADS>
+__device__ __forceinline__ void batch_tile(const BatchInst& in, int e0, T gamma, unsigned char* smem) {
+  constexpr int EPB = BatchEpb<N, T, THREADS>::value;
+  Epilogue none{};
+  none.mode = EPI_STORE;
+  volume_tile<3, N, T, EPB, EPI_STORE, THREADS>(in.u, static_cast<const T*>(in.Ja), in.invJ,
+                                                static_cast<const T*>(in.face), in.du, in.md, ConstOp<N, T>::get(),
+                                                gamma, in.flag, none, e0, smem);
+}
+
+template <typename T, int THREADS>
+__global__ void __launch_bounds__(THREADS) batch_volume_kernel(const BatchInst* __restrict__ insts,
+                                                               const BatchTile* __restrict__ tiles, int ntiles,
+                                                               int* counter, T gamma) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_tile;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= ntiles) break;
+    const BatchTile tl = tiles[t];
+    const BatchInst& in = insts[tl.inst];
+    switch (in.p) {
+      case 1: batch_tile<2, T, THREADS>(in, tl.e0, gamma, smem); break;
+      case 2: batch_tile<3, T, THREADS>(in, tl.e0, gamma, smem); break;
+      case 3: batch_tile<4, T, THREADS>(in, tl.e0, gamma, smem); break;
+      case 4: batch_tile<5, T, THREADS>(in, tl.e0, gamma, smem); break;
+      case 5: batch_tile<6, T, THREADS>(in, tl.e0, gamma, smem); break;
+      default: break;
+    }
+    __syncthreads();  // the next tile reuses shared memory and s_tile
+  }
+}
+
+template <typename T>
+cudaError_t upload_const_ops() {
+  cudaError_t e = cudaSuccess;
+#define DG_BATCH_UPLOAD(NN, SYM)                                               \
+  if (e == cudaSuccess) {                                                      \
+    OpTable<NN, T> op;                                                         \
+    const RefTables& t = ref_tables(NN - 1);                                   \
+    for (int i = 0; i < NN * NN; ++i) op.Dt8[i] = (T)(0.125 * t.Dt[i]);        \
+    op.winv = (T)(1.0 / t.w[0]);                                               \
+    e = cudaMemcpyToSymbol(SYM, &op, sizeof(op));                              \
+  }
+  if (sizeof(T) == 8) {
+    DG_BATCH_UPLOAD(2, c_opd_2) DG_BATCH_UPLOAD(3, c_opd_3) DG_BATCH_UPLOAD(4, c_opd_4)
+    DG_BATCH_UPLOAD(5, c_opd_5) DG_BATCH_UPLOAD(6, c_opd_6)
+  } else {
+    DG_BATCH_UPLOAD(2, c_opf_2) DG_BATCH_UPLOAD(3, c_opf_3) DG_BATCH_UPLOAD(4, c_opf_4)
+    DG_BATCH_UPLOAD(5, c_opf_5) DG_BATCH_UPLOAD(6, c_opf_6)
+  }
+#undef DG_BATCH_UPLOAD
+  return e;
+}
+
+std::mutex g_upload_mutex;
+bool g_uploaded[64] = {false};
+
+cudaError_t ensure_const_ops(int device) {
+  if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_upload_mutex);
+  if (g_uploaded[device]) return cudaSuccess;
+  cudaError_t e = upload_const_ops<double>();
+  if (e == cudaSuccess) e = upload_const_ops<float>();
+  if (e == cudaSuccess) g_uploaded[device] = true;
+  return e;
+}
+
+template <typename T, int THREADS>
+cudaError_t launch_batch_volume_t(const BatchInst* insts, const BatchTile* tiles, int ntiles, int* counter,
+                                  double gamma, size_t smem, int grid, cudaStream_t s) {
+  auto kern = batch_volume_kernel<T, THREADS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, THREADS, smem, s>>>(insts, tiles, ntiles, counter, (T)gamma);
+  return cudaGetLastError();
+}
+
+template <typename T, int THREADS>
+int batch_occupancy(size_t smem) {
+  int blocks = 0;
+  auto kern = batch_volume_kernel<T, THREADS>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, THREADS, smem) != cudaSuccess) return 0;
+  return blocks;
+}
+
+int occupancy_for(int precision, int threads, size_t smem) {
+  if (precision == DG_FP32) {
+    if (threads == 128) return batch_occupancy<float, 128>(smem);
+    if (threads == 192) return batch_occupancy<float, 192>(smem);
+    return batch_occupancy<float, 256>(smem);
+  }
+  if (threads == 128) return batch_occupancy<double, 128>(smem);
+  if (threads == 192) return batch_occupancy<double, 192>(smem);
+  return batch_occupancy<double, 256>(smem);
+}
+
+cudaError_t launch_volume_for(int precision, int threads, const BatchInst* insts, const BatchTile* tiles, int ntiles,
+                              int* counter, double gamma, size_t smem, int grid, cudaStream_t s) {
+  if (precision == DG_FP32) {
+    if (threads == 128) return launch_batch_volume_t<float, 128>(insts, tiles, ntiles, counter, gamma, smem, grid, s);
+    if (threads == 192) return launch_batch_volume_t<float, 192>(insts, tiles, ntiles, counter, gamma, smem, grid, s);
+    return launch_batch_volume_t<float, 256>(insts, tiles, ntiles, counter, gamma, smem, grid, s);
+  }
+  if (threads == 128) return launch_batch_volume_t<double, 128>(insts, tiles, ntiles, counter, gamma, smem, grid, s);
+  if (threads == 192) return launch_batch_volume_t<double, 192>(insts, tiles, ntiles, counter, gamma, smem, grid, s);
+  return launch_batch_volume_t<double, 256>(insts, tiles, ntiles, counter, gamma, smem, grid, s);
+}
+
+}  // namespace
+}  // namespace dgk
+
+// ---------------------------------------------------------------------------------------------------------
+// The plan
+// ---------------------------------------------------------------------------------------------------------
+struct dg_batch {
+  int device = 0, n = 0, precision = 0, llf = 0, sms = 0;
+  double gamma = 1.4;
+  long long total_face_nodes = 0;
+  dgk::BatchInst* d_inst = nullptr;
+  dgk::BatchTile* d_tiles[dgk::kNumThreadChoices] = {nullptr, nullptr, nullptr};
+  int ntiles[dgk::kNumThreadChoices] = {0, 0, 0};
+  size_t smem[dgk::kNumThreadChoices] = {0, 0, 0};
+  int* d_counter = nullptr;
+  int threads_idx = 1;  // 192 threads per CTA until tuned
+  int ctas_per_sm = 0;  // 0: the occupancy limit
+  std::string signature;
+};
+
+namespace {
+
+void batch_release(dg_batch* b) {
+  if (!b) return;
+  cudaFree(b->d_inst);
+  for (int i = 0; i < dgk::kNumThreadChoices; ++i) cudaFree(b->d_tiles[i]);
+  cudaFree(b->d_counter);
+  delete b;
+}
+
+dg_status to_status(cudaError_t e) {
+  if (e == cudaSuccess) return DG_OK;
+  return e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
+}
+
+int grid_for(const dg_batch* b, int ti) {
+  const int occ = dgk::occupancy_for(b->precision, dgk::kThreadChoices[ti], b->smem[ti]);
+  if (occ <= 0) return 0;
+  const int per_sm = b->ctas_per_sm > 0 ? std::min(b->ctas_per_sm, occ) : occ;
+  return std::max(1, std::min(per_sm * b->sms, b->ntiles[ti]));
+}
+
+dg_status batch_launch(dg_batch* b, int ti, int grid, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return to_status(e);
+  if (b->total_face_nodes > 0) {
+    const long long blocks = (b->total_face_nodes + 255) / 256;
+    if (b->precision == DG_FP32) {
+      if (b->llf)
+        dgk::batch_interface_kernel<float, true><<<(unsigned)blocks, 256, 0, s>>>(b->d_inst, b->n, b->total_face_nodes,
+                                                                                 (float)b->gamma);
+      else
+        dgk::batch_interface_kernel<float, false><<<(unsigned)blocks, 256, 0, s>>>(b->d_inst, b->n,
+                                                                                  b->total_face_nodes, (float)b->gamma);
+    } else {
+      if (b->llf)
+        dgk::batch_interface_kernel<double, true><<<(unsigned)blocks, 256, 0, s>>>(b->d_inst, b->n,
+                                                                                  b->total_face_nodes, b->gamma);
+      else
+        dgk::batch_interface_kernel<double, false><<<(unsigned)blocks, 256, 0, s>>>(b->d_inst, b->n,
+                                                                                   b->total_face_nodes, b->gamma);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return to_status(e);
+  }
+  e = dgk::launch_volume_for(b->precision, dgk::kThreadChoices[ti], b->d_inst, b->d_tiles[ti], b->ntiles[ti],
+                             b->d_counter, b->gamma, b->smem[ti], grid, s);
+  return to_status(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+dg_status dg_batch_create(dg_batch** out, dg_ctx* const* ctxs, int n, const double* const* u, double* const* du) {
+  if (!out || !ctxs || !u || !du || n < 1 || n > 65536) return DG_ERR_ARG;
+  *out = nullptr;
+  const dg_ctx* c0 = ctxs[0];
+  if (!c0) return DG_ERR_ARG;
+  for (int i = 0; i < n; ++i) {
+    const dg_ctx* c = ctxs[i];
+    if (!c || !u[i] || !du[i]) return DG_ERR_ARG;
+    if (c->device != c0->device || c->precision != c0->precision || c->surface_flux != c0->surface_flux ||
+        c->gamma != c0->gamma)
+      return DG_ERR_ARG;
+    if (c->nd != 3 || c->p > dgk::kBatchMaxP) return DG_ERR_UNSUPPORTED;
+    if (((uintptr_t)u[i] | (uintptr_t)du[i]) & 7) return DG_ERR_ARG;
+    const size_t bytes = (size_t)c->state_len * sizeof(double);
+    const char *ub = (const char*)u[i], *db = (const char*)du[i];
+    if (ub < db + bytes && db < ub + bytes) return DG_ERR_ARG;
+  }
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != c0->device) return DG_ERR_ARG;
+  dg_batch* b = new (std::nothrow) dg_batch();
+  if (!b) return DG_ERR_OOM;
+  b->device = c0->device;
+  b->n = n;
+  b->precision = c0->precision;
+  b->llf = c0->surface_flux == DG_SURF_EC_LLF;
+  b->gamma = c0->gamma;
+  cudaError_t e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (e == cudaSuccess) e = dgk::ensure_const_ops(b->device);
+  if (e != cudaSuccess) {
+    batch_release(b);
+    return to_status(e);
+  }
+  std::vector<dgk::BatchInst> inst(n);
+  int hist[dgk::kBatchMaxP + 1] = {0};
+  long long elems = 0;
+  for (int i = 0; i < n; ++i) {
+    const dg_ctx* c = ctxs[i];
+    dgk::BatchInst& bi = inst[i];
+    bi.u = u[i];
+    bi.du = du[i];
+    bi.Ja = c->precision == DG_FP32 ? (const void*)c->d_Ja32 : (const void*)c->d_Ja;
+    bi.invJ = c->d_invJ;
+    bi.face = c->d_face;
+    bi.flag = c->d_flag;
+    bi.md = c->md;
+    bi.p = c->p;
+    bi.face_begin = b->total_face_nodes;
+    b->total_face_nodes += 3LL * c->E * c->N * c->N;
+    hist[c->p]++;
+    elems += c->E;
+  }
+  char sig[256];
+  snprintf(sig, sizeof(sig), "%s n=%d E=%lld p1-5=%d,%d,%d,%d,%d", c0->precision == DG_FP32 ? "fp32" : "fp64", n, elems,
+           hist[1], hist[2], hist[3], hist[4], hist[5]);
+  b->signature = sig;
+  // tile lists per CTA size, most expensive tiles first (pairs per tile ~ elements x p^4) for load balance
+  for (int ti = 0; ti < dgk::kNumThreadChoices && e == cudaSuccess; ++ti) {
+    const int threads = dgk::kThreadChoices[ti];
+    std::vector<std::pair<double, dgk::BatchTile>> tl;
+    size_t smem = 0;
+    for (int i = 0; i < n; ++i) {
+      const int p = ctxs[i]->p, N = p + 1;
+      const int epb = dgk::batch_epb(p, b->precision, threads);
+      smem = std::max(smem, dgk::batch_smem(p, b->precision, threads));
+      const double cost = (double)epb * N * N * N * (double)N * (N - 1);
+      for (int e0 = 0; e0 < ctxs[i]->md.E; e0 += epb) {
+        const int nel = std::min(epb, ctxs[i]->md.E - e0);
+        tl.push_back({cost * nel / epb, dgk::BatchTile{i, e0}});
+      }
+    }
+    std::stable_sort(tl.begin(), tl.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    std::vector<dgk::BatchTile> tiles(tl.size());
+    for (size_t k = 0; k < tl.size(); ++k) tiles[k] = tl[k].second;
+    b->ntiles[ti] = (int)tiles.size();
+    b->smem[ti] = smem;
+    e = cudaMalloc(&b->d_tiles[ti], tiles.size() * sizeof(dgk::BatchTile));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(b->d_tiles[ti], tiles.data(), tiles.size() * sizeof(dgk::BatchTile), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_inst, n * sizeof(dgk::BatchInst));
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_inst, inst.data(), n * sizeof(dgk::BatchInst), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int));
+  if (e != cudaSuccess) {
+    batch_release(b);
+    return to_status(e);
+  }
+  *out = b;
+  return DG_OK;
+}
+
+dg_status dg_batch_rhs(dg_batch* b, dg_stream_t stream) {
+  if (!b) return DG_ERR_ARG;
+  const int grid = grid_for(b, b->threads_idx);
+  if (grid <= 0) return DG_ERR_CUDA;
+  return batch_launch(b, b->threads_idx, grid, (cudaStream_t)stream);
+}
+
+dg_status dg_batch_autotune(dg_batch* b, const char* cache_path, dg_stream_t stream, int* threads_out,
+                            int* ctas_per_sm_out) {
+  if (!b) return DG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  char devname[256] = "device";
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, b->device) == cudaSuccess) snprintf(devname, sizeof(devname), "%s", prop.name);
+  const std::string key = std::string(devname) + " | " + b->signature;
+  // cached choice: lines "key<TAB>threads<TAB>ctas_per_sm"
+  if (cache_path) {
+    FILE* f = fopen(cache_path, "r");
+    if (f) {
+      char line[1024];
+      while (fgets(line, sizeof(line), f)) {
+        char* tab = strchr(line, '\t');
+        if (!tab) continue;
+        *tab = 0;
+        int th = 0, cps = 0;
+        if (key == line && sscanf(tab + 1, "%d\t%d", &th, &cps) == 2) {
+          for (int ti = 0; ti < dgk::kNumThreadChoices; ++ti)
+            if (dgk::kThreadChoices[ti] == th) {
+              b->threads_idx = ti;
+              b->ctas_per_sm = cps;
+            }
+          fclose(f);
+          if (threads_out) *threads_out = dgk::kThreadChoices[b->threads_idx];
+          if (ctas_per_sm_out) *ctas_per_sm_out = b->ctas_per_sm;
+          return DG_OK;
+        }
+      }
+      fclose(f);
+    }
+  }
+  cudaEvent_t t0, t1;
+  cudaError_t e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  if (e != cudaSuccess) return to_status(e);
+  float best = 1e30f;
+  int best_ti = b->threads_idx, best_cps = b->ctas_per_sm;
+  dg_status st = DG_OK;
+  for (int ti = 0; ti < dgk::kNumThreadChoices && st == DG_OK; ++ti) {
+    const int occ = dgk::occupancy_for(b->precision, dgk::kThreadChoices[ti], b->smem[ti]);
+    for (int cps = 1; cps <= occ && st == DG_OK; ++cps) {
+      b->ctas_per_sm = cps;
+      const int grid = grid_for(b, ti);
+      if (grid <= 0) continue;
+      st = batch_launch(b, ti, grid, s);  // warm-up
+      cudaEventRecord(t0, s);
+      for (int r = 0; r < 3 && st == DG_OK; ++r) st = batch_launch(b, ti, grid, s);
+      cudaEventRecord(t1, s);
+      if (st != DG_OK) break;
+      if (cudaEventSynchronize(t1) != cudaSuccess) {
+        st = DG_ERR_CUDA;
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, t0, t1);
+      if (ms < best) {
+        best = ms;
+        best_ti = ti;
+        best_cps = cps;
+      }
+    }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  b->threads_idx = best_ti;
+  b->ctas_per_sm = best_cps;
+  if (st != DG_OK) return st;
+  if (cache_path) {
+    FILE* f = fopen(cache_path, "a");
+    if (f) {
+      fprintf(f, "%s\t%d\t%d\n", key.c_str(), dgk::kThreadChoices[best_ti], best_cps);
+      fclose(f);
+    }
+  }
+  if (threads_out) *threads_out = dgk::kThreadChoices[best_ti];
+  if (ctas_per_sm_out) *ctas_per_sm_out = best_cps;
+  return DG_OK;
+}
+
+dg_status dg_batch_set_tuning(dg_batch* b, int threads, int ctas_per_sm) {
+  if (!b || ctas_per_sm < 0) return DG_ERR_ARG;
+  for (int ti = 0; ti < dgk::kNumThreadChoices; ++ti)
+    if (dgk::kThreadChoices[ti] == threads) {
+      b->threads_idx = ti;
+      b->ctas_per_sm = ctas_per_sm;
+      return DG_OK;
+    }
+  return DG_ERR_ARG;
+}
+
+void dg_batch_free(dg_batch* b) { batch_release(b); }
+
+}  // extern "C"

@@ -58,13 +58,12 @@ struct OpTable {
 // lambda = max(|v_L.m| + c_L|m|, |v_R.m| + c_R|m|), c = sqrt(gamma p/rho).
 // face layout [n][E][NV][NL].
 // ---------------------------------------------------------------------------------------------------
+// Interface flux at face node `idx` of a mesh, idx = (n * E + e) * NL + fn.
 template <int ND, int N, typename T, bool LLF>
-__global__ void __launch_bounds__(256) interface_kernel(const double* __restrict__ u, const T* __restrict__ Ja,
-                                                        T* __restrict__ face, MeshDims md, T gamma, int* flag) {
+__device__ __forceinline__ void interface_node(const double* __restrict__ u, const T* __restrict__ Ja,
+                                               T* __restrict__ face, const MeshDims& md, T gamma, int* flag,
+                                               long long idx) {
   using G = Geo<ND, N>;
-  const long long total = (long long)ND * md.E * G::NL;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
   const int fn = (int)(idx % G::NL);
   const long long t = idx / G::NL;
   const int e = (int)(t % md.E);
@@ -116,6 +115,14 @@ __global__ void __launch_bounds__(256) interface_kernel(const double* __restrict
   for (int c = 0; c < G::NV; ++c) fo[c * G::NL] = f[c];
 }
 
+template <int ND, int N, typename T, bool LLF>
+__global__ void __launch_bounds__(256) interface_kernel(const double* __restrict__ u, const T* __restrict__ Ja,
+                                                        T* __restrict__ face, MeshDims md, T gamma, int* flag) {
+  const long long total = (long long)ND * md.E * Geo<ND, N>::NL;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < total) interface_node<ND, N, T, LLF>(u, Ja, face, md, gamma, flag, idx);
+}
+
 // ---------------------------------------------------------------------------------------------------
 // Volume term + surface lift + Jacobian scaling (Eq. fluxdiff-SBP-opDsplit with Eq. curvilinear-rearrange):
 //   du_i = -(1/J_i) [ sum_n sum_{k on i's line along n} Dt_{i_n k_n} f(u_i, u_k, (Ja^n_i + Ja^n_k)/2)
@@ -153,23 +160,23 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // EPI selects the epilogue: store du, or apply a Runge-Kutta stage update (in place of a separate kernel; the
 // stage arithmetic is the same as rk4_kernel / rk_ck45_kernel). With a stage update the kernel writes arrays
 // that alias its input u (the CTA has read its own elements before the barrier; no other CTA reads them).
-template <int ND, int N, typename T, int EPB, int EPI>
-__global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE)
-    volume_kernel(const double* u, const T* __restrict__ Ja, const double* __restrict__ invJ,
-                  const T* __restrict__ face, double* du, MeshDims md, OpTable<N, T> op, T gamma, int* flag,
-                  Epilogue epi) {
+// One tile of EPB elements starting at element e0, computed by the kThreads threads of a CTA (kThreads >=
+// EPB * TPE; threads beyond EPB * TPE only join the cooperative loops). smem_raw holds VolumeSmem::bytes(EPB).
+template <int ND, int N, typename T, int EPB, int EPI, int kThreads>
+__device__ __forceinline__ void volume_tile(const double* u, const T* __restrict__ Ja, const double* __restrict__ invJ,
+                                            const T* __restrict__ face, double* du, const MeshDims& md,
+                                            const OpTable<N, T>& op, T gamma, int* flag, const Epilogue& epi, int e0,
+                                            unsigned char* smem_raw) {
   using G = Geo<ND, N>;
   using S = VolumeSmem<ND, N, T>;
+  static_assert(kThreads >= EPB * G::TPE, "a tile needs one thread per element line");
   constexpr bool kFused = EPI != EPI_STORE;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   double* s_eu = reinterpret_cast<double*>(smem_raw);      // [EPB][NV][NDOF] fused update: u
   double* s_ey = s_eu + (kFused ? EPB * S::kState : 0);     // [EPB][NV][NDOF] fused update: acc (RK4) / K (CK45)
   T* s_prim = reinterpret_cast<T*>(s_ey + (kFused ? EPB * S::kState : 0));  // [EPB][NQ][NDOF]
   T* s_ja = s_prim + EPB * S::kPrim;                       // [EPB][ND][ND][NDOF]
   T* s_acc = s_ja + EPB * S::kJa;                          // [EPB][ND][NV][NDOF]
   const int tid = threadIdx.x;
-  constexpr int kThreads = EPB * G::TPE;
-  const int e0 = blockIdx.x * EPB;
   const int nel = min(EPB, md.E - e0);
   const T gm1 = gamma - T(1);
 
@@ -309,6 +316,16 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE)
       }
     }
   }
+}
+
+template <int ND, int N, typename T, int EPB, int EPI>
+__global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE)
+    volume_kernel(const double* u, const T* __restrict__ Ja, const double* __restrict__ invJ,
+                  const T* __restrict__ face, double* du, MeshDims md, OpTable<N, T> op, T gamma, int* flag,
+                  Epilogue epi) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  volume_tile<ND, N, T, EPB, EPI, EPB * Geo<ND, N>::TPE>(u, Ja, invJ, face, du, md, op, gamma, flag, epi,
+                                                         blockIdx.x * EPB, smem_raw);
 }
 
 }  // namespace dgk

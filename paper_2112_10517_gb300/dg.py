@@ -32,7 +32,8 @@ KERNEL_VOLUME, KERNEL_INTERFACE = 0, 1
 
 EXPORTED = ["dg_init", "dg_rhs", "dg_step", "dg_entropy_rate", "dg_check_status", "dg_get_info",
             "dg_get_node_coords", "dg_get_metrics", "dg_profile_enable", "dg_profile_read", "dg_launch_count",
-            "dg_free", "dg_status_string", "dg_rhs_noalloc"]
+            "dg_free", "dg_status_string", "dg_rhs_noalloc", "dg_batch_create", "dg_batch_rhs",
+            "dg_batch_autotune", "dg_batch_set_tuning", "dg_batch_free"]
 
 
 class DgMesh(ctypes.Structure):
@@ -75,6 +76,13 @@ _sig = {
     "dg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "dg_rhs_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
                                       ctypes.c_int, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "dg_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp),
+                                       ctypes.POINTER(_vp)]),
+    "dg_batch_rhs": (ctypes.c_int, [_vp, _vp]),
+    "dg_batch_autotune": (ctypes.c_int, [_vp, ctypes.c_char_p, _vp, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int)]),
+    "dg_batch_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "dg_batch_free": (None, [_vp]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -228,3 +236,47 @@ class DG:
 
     def launch_count(self) -> int:
         return int(dg_launch_count(self.ctx))
+
+
+class DGBatch:
+    """A batch plan (dg_batch_create): contexts `ctxs` (DG objects) bound to state tensors u[i], du[i]."""
+
+    def __init__(self, ctxs, us, dus):
+        if not (len(ctxs) == len(us) == len(dus)) or not ctxs:
+            raise ValueError("need one u and one du per context")
+        for c, u, du in zip(ctxs, us, dus):
+            c._state(u, "u")
+            c._state(du, "du")
+        n = len(ctxs)
+        self.ctxs, self.us, self.dus = list(ctxs), list(us), list(dus)  # keep alive
+        carr = (_vp * n)(*[c.ctx.value for c in ctxs])
+        uarr = (_vp * n)(*[u.data_ptr() for u in us])
+        darr = (_vp * n)(*[d.data_ptr() for d in dus])
+        b = ctypes.c_void_p()
+        check(dg_batch_create(ctypes.byref(b), carr, n, uarr, darr), "dg_batch_create")
+        self.b = b
+        self.ndofs = sum(c.ndofs for c in ctxs)
+
+    def rhs(self, stream=None):
+        check(dg_batch_rhs(self.b, _stream_handle(stream)), "dg_batch_rhs")
+
+    def autotune(self, cache_path=None, stream=None):
+        th = ctypes.c_int()
+        cps = ctypes.c_int()
+        check(dg_batch_autotune(self.b, cache_path.encode() if cache_path else None, _stream_handle(stream),
+                                ctypes.byref(th), ctypes.byref(cps)), "dg_batch_autotune")
+        return th.value, cps.value
+
+    def set_tuning(self, threads: int, ctas_per_sm: int = 0):
+        check(dg_batch_set_tuning(self.b, int(threads), int(ctas_per_sm)), "dg_batch_set_tuning")
+
+    def close(self):
+        if getattr(self, "b", None):
+            dg_batch_free(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
