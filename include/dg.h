@@ -129,6 +129,15 @@ dg_status dg_step(dg_ctx* ctx, double* u, double* scratch, double t, double dt, 
 dg_status dg_entropy_rate(dg_ctx* ctx, const double* u, const double* du, double* out_host, double* abs_out_host,
                           dg_stream_t stream);
 
+/* Vector-Jacobian product (adjoint) of dg_rhs: ubar = (d RHS/du (u))^T gbar, FP64. u, gbar, ubar: device arrays of
+   the state layout; ubar must not overlap u or gbar. The derivative of every step of the RHS is hand-written:
+   the logarithmic means of Algorithms 2-3 (exact derivatives of the means in both branches), Ranocha's flux
+   (Eq. flux_ranocha), the LLF dissipation (subgradient at its max/abs switches: the branch the forward flux
+   takes, sign(0) = +1), the primitive variables, the flux-differencing sums (Eq. fluxdiff-SBP-opDsplit), the
+   lift and the Jacobian scaling. Two kernels; the first call allocates the context's face-adjoint workspace
+   (8 nvar (p+1)^(d-1) d bytes per element). FP64 contexts with polydeg <= 5; DG_ERR_UNSUPPORTED otherwise. */
+dg_status dg_vjp(dg_ctx* ctx, const double* u, const double* gbar, double* ubar, dg_stream_t stream);
+
 /* Reads and clears the asynchronous flag of non-physical states. Waits (bounded, 60 s) for the work queued
    on the stream of the last call; returns DG_OK, DG_ERR_NONPHYSICAL or DG_ERR_TIMEOUT. */
 dg_status dg_check_status(dg_ctx* ctx);

@@ -25,17 +25,21 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRC_DUAL = [os.path.join(_HERE, "oracle_dual.cpp"), os.path.join(_HERE, "dual.h")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_LIB_DUAL = os.path.join(_BUILD, "liboracle_dual.so")
 _lock = threading.Lock()
 _lib = None
+_libd = None
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c with gcc (plain -O2, no fast-math, portable flags) into oracle/_build."""
+    """Compile oracle.c with gcc (plain -O2, no fast-math, portable flags) into oracle/_build, and the same
+    source with dual numbers (oracle_dual.cpp, g++) for the JVP."""
     os.makedirs(_BUILD, exist_ok=True)
     stale = (not os.path.exists(_LIB_PATH)) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)
     if force or stale:
@@ -43,6 +47,13 @@ def build(force: bool = False) -> str:
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
                                "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
+    deps = [_SRC] + _SRC_DUAL
+    stale = (not os.path.exists(_LIB_DUAL)) or os.path.getmtime(_LIB_DUAL) < max(os.path.getmtime(d) for d in deps)
+    if force or stale:
+        tmp = _LIB_DUAL + ".tmp%d" % os.getpid()
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fno-fast-math",
+                               "-ffp-contract=off", "-o", tmp, _SRC_DUAL[0], "-lm"])
+        os.replace(tmp, _LIB_DUAL)
     return _LIB_PATH
 
 
@@ -58,6 +69,19 @@ def _load():
             lib.orc_entropy.restype = ctypes.c_double
             _lib = lib
     return _lib
+
+
+def _load_dual():
+    global _libd
+    _load()
+    with _lock:
+        if _libd is None:
+            _libd = ctypes.CDLL(_LIB_DUAL)
+    return _libd
+
+
+class _Dual(ctypes.Structure):
+    _fields_ = [("v", ctypes.c_double), ("d", ctypes.c_double)]
 
 
 def _ptr(a: np.ndarray):
@@ -260,3 +284,40 @@ def rk_step(scheme: int, ndims: int, p: int, nelem, Ja, J, u, dt: float, gamma: 
     _check(lib.orc_rk_step(scheme, ndims, p, _ivec(nelem), _ptr(_f64(Ja)), _ptr(_f64(J)),
                            ctypes.c_double(gamma), int(bool(llf)), ctypes.c_double(dt), _ptr(u)), "rk_step")
     return u
+
+
+def logmean_grad(a, b):
+    """(dL/da, dL/db) of the oracle's logarithmic mean, by its dual-number evaluation."""
+    lib = _load_dual()
+    lib.orc_logmean.restype = _Dual
+    lib.orc_logmean.argtypes = [_Dual, _Dual]
+    a = np.atleast_1d(_f64(a))
+    b = np.atleast_1d(_f64(np.broadcast_to(b, a.shape)))
+    ga = np.array([lib.orc_logmean(_Dual(x, 1.0), _Dual(y, 0.0)).d for x, y in zip(a, b)])
+    gb = np.array([lib.orc_logmean(_Dual(x, 0.0), _Dual(y, 1.0)).d for x, y in zip(a, b)])
+    return ga, gb
+
+
+def jvp(ndims: int, p: int, nelem, Ja, J, u, delta, gamma: float = 1.4, llf: bool = True):
+    """(RHS(u), J(u) delta): the oracle's RHS evaluated in dual numbers (oracle_dual.cpp compiles oracle.c with
+    `double` taken as a dual number), i.e. forward-mode differentiation, exact up to rounding."""
+    lib = _load_dual()
+    u = _f64(u)
+    delta = _f64(np.broadcast_to(delta, u.shape))
+    E = num_elements(ndims, nelem)
+    assert u.shape == (E, ndims + 2, (p + 1) ** ndims), u.shape
+
+    def dual_of(v, d=None):
+        out = np.zeros(np.shape(v) + (2,))
+        out[..., 0] = v
+        if d is not None:
+            out[..., 1] = d
+        return out
+
+    Jad = dual_of(_f64(Ja))
+    Jd = dual_of(_f64(J))
+    ud = dual_of(u, delta)
+    dud = np.zeros_like(ud)
+    _check(lib.orc_rhs(ndims, p, _ivec(nelem), _ptr(Jad), _ptr(Jd), _ptr(ud), _Dual(gamma, 0.0),
+                       int(bool(llf)), 0, E, 0, _ptr(dud)), "rhs (dual)")
+    return dud[..., 0].copy(), dud[..., 1].copy()

@@ -15,7 +15,7 @@
  *     (Sec. 2.3, Eq. curvilinear-rewrite), not directional ones,
  *   - the plain logarithmic mean (Sec. 3.1, Eq. logmean) evaluated with log1p, not Algorithms 1-3,
  *   - 1/{{rho/p}}_log taken literally (Eq. flux_ranocha), not the division-free rewrite.
- * All arithmetic is IEEE double (long double only for the LGL tables). Loops are in the paper's order.
+ * All arithmetic is IEEE double (orc_ld_t only for the LGL tables). Loops are in the paper's order.
  *
  * Data layout (shared with the test harness, not with the library):
  *   node index   i = i1 + N*i2 + N*N*i3 (i1 along xi_1 fastest), N = p+1, Nd = N^ndims nodes
@@ -29,6 +29,12 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Long double for the LGL tables; a typedef so that oracle_dual.cpp can compile this file with `double` taken
+   as a dual number (forward-mode derivatives for the JVP). */
+#ifndef ORC_LD_DEFINED
+typedef long double orc_ld_t;
+#endif
+
 #define ORC_MAXN 16
 #define ORC_PI_L 3.141592653589793238462643383279502884L
 
@@ -38,11 +44,11 @@
 /* ------------------------------------------------------------------------------------------------ */
 
 /* P_p(x) and P_{p-1}(x) by the three-term recurrence (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1}. */
-static void orc_legendre(long double x, int p, long double* Pp, long double* Pm1) {
-  long double P0 = 1.0L, P1 = x;
+static void orc_legendre(orc_ld_t x, int p, orc_ld_t* Pp, orc_ld_t* Pm1) {
+  orc_ld_t P0 = 1.0L, P1 = x;
   if (p == 0) { *Pp = 1.0L; *Pm1 = 0.0L; return; }
   for (int k = 1; k < p; ++k) {
-    long double P2 = ((2.0L * k + 1.0L) * x * P1 - (long double)k * P0) / (k + 1.0L);
+    orc_ld_t P2 = ((2.0L * k + 1.0L) * x * P1 - (orc_ld_t)k * P0) / (k + 1.0L);
     P0 = P1;
     P1 = P2;
   }
@@ -52,30 +58,30 @@ static void orc_legendre(long double x, int p, long double* Pp, long double* Pm1
 
 int orc_lgl(int p, double* x, double* w) {
   if (p < 1 || p >= ORC_MAXN) return -1;
-  long double X[ORC_MAXN];
+  orc_ld_t X[ORC_MAXN];
   X[0] = -1.0L;
   X[p] = 1.0L;
   for (int i = 1; i < p; ++i) {
     /* Newton on P_p'(x) = 0. P_p' from (1-x^2) P_p' = p (P_{p-1} - x P_p); P_p'' from Legendre's ODE
        (1-x^2) P'' - 2x P' + p(p+1) P = 0. Start from the Chebyshev-Lobatto point. */
-    long double xi = -cosl(ORC_PI_L * (long double)i / (long double)p);
+    orc_ld_t xi = -cosl(ORC_PI_L * (orc_ld_t)i / (orc_ld_t)p);
     for (int it = 0; it < 200; ++it) {
-      long double P, Pm;
+      orc_ld_t P, Pm;
       orc_legendre(xi, p, &P, &Pm);
-      long double one_m = 1.0L - xi * xi;
-      long double dP = (long double)p * (Pm - xi * P) / one_m;
-      long double d2P = (2.0L * xi * dP - (long double)p * (p + 1.0L) * P) / one_m;
-      long double dx = dP / d2P;
+      orc_ld_t one_m = 1.0L - xi * xi;
+      orc_ld_t dP = (orc_ld_t)p * (Pm - xi * P) / one_m;
+      orc_ld_t d2P = (2.0L * xi * dP - (orc_ld_t)p * (p + 1.0L) * P) / one_m;
+      orc_ld_t dx = dP / d2P;
       xi -= dx;
       if (fabsl(dx) < 1e-19L) break;
     }
     X[i] = xi;
   }
   for (int i = 0; i <= p; ++i) {
-    long double P, Pm;
+    orc_ld_t P, Pm;
     orc_legendre(X[i], p, &P, &Pm);
     x[i] = (double)X[i];
-    w[i] = (double)(2.0L / ((long double)p * (p + 1.0L) * P * P));
+    w[i] = (double)(2.0L / ((orc_ld_t)p * (p + 1.0L) * P * P));
   }
   return 0;
 }
@@ -87,18 +93,18 @@ int orc_lgl(int p, double* x, double* w) {
 int orc_dmat(int p, const double* x, double* D) {
   if (p < 1 || p >= ORC_MAXN) return -1;
   const int N = p + 1;
-  long double lam[ORC_MAXN];
+  orc_ld_t lam[ORC_MAXN];
   for (int k = 0; k < N; ++k) {
-    long double prod = 1.0L;
+    orc_ld_t prod = 1.0L;
     for (int m = 0; m < N; ++m)
-      if (m != k) prod *= ((long double)x[k] - (long double)x[m]);
+      if (m != k) prod *= ((orc_ld_t)x[k] - (orc_ld_t)x[m]);
     lam[k] = 1.0L / prod;
   }
   for (int i = 0; i < N; ++i) {
-    long double diag = 0.0L;
+    orc_ld_t diag = 0.0L;
     for (int k = 0; k < N; ++k) {
       if (k == i) continue;
-      long double dik = (lam[k] / lam[i]) / ((long double)x[i] - (long double)x[k]);
+      orc_ld_t dik = (lam[k] / lam[i]) / ((orc_ld_t)x[i] - (orc_ld_t)x[k]);
       D[i * N + k] = (double)dik;
       diag -= dik;
     }
@@ -131,12 +137,24 @@ void orc_euler_flux(const double* u, int nd, double gamma, int j, double* f) {
   f[nd + 1] = (u[nd + 1] + p) * v[j];
 }
 
-/* logarithmic mean {{a}}_log = [[a]]/[[log a]] (Sec. 3.1, Eq. logmean), written with log1p so that
-   it stays accurate for a_+ close to a_- (and equals a for a_+ = a_-). NOT Algorithms 1-3. */
+/* logarithmic mean {{a}}_log = [[a]]/[[log a]] (Sec. 3.1, Eq. logmean) = a x/log(1 + x), x = (b - a)/a,
+   written with log1p so that it stays accurate for b close to a. For abs(x) < 0.05 it is evaluated by the
+   Taylor series of x/log(1 + x) through x^10 (the Gregory coefficients; truncation below 3e-17 relative): the
+   closed form keeps its value there but its derivative loses about eps/abs(x) to cancellation (the dual-number
+   JVP differentiates this function). NOT Algorithms 1-3. */
+static const double ORC_GREGORY[11] = {1.0, 1.0 / 2.0, -1.0 / 12.0, 1.0 / 24.0, -19.0 / 720.0, 3.0 / 160.0,
+                                       -863.0 / 60480.0, 275.0 / 24192.0, -33953.0 / 3628800.0, 8183.0 / 1036800.0,
+                                       -3250433.0 / 479001600.0};
+
 double orc_logmean(double a, double b) {
-  if (a == b) return a;
   double d = b - a;
-  return d / log1p(d / a);
+  double x = d / a;
+  if (fabs(x) < 0.05) {
+    double s = ORC_GREGORY[10];
+    for (int k = 9; k >= 0; --k) s = ORC_GREGORY[k] + x * s;
+    return a * s;
+  }
+  return d / log1p(x);
 }
 
 /* Ranocha's EC/KEP/PEP flux in Cartesian direction j (Sec. 3.2, Eq. flux_ranocha with n = e_j):

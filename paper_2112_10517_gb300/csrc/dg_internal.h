@@ -76,6 +76,7 @@ struct dg_ctx {
   double* d_invJ;  // [E][Nd]
   double* d_JW;    // J * tensor LGL weight, [E][Nd]
   void* d_face;    // face fluxes [nd][E][nv][N^(nd-1)], FP64 or FP32
+  double* d_fadj;  // dg_vjp: face adjoint contributions [nd][E][2][nv][N^(nd-1)] (allocated at the first dg_vjp)
   double* d_red;   // entropy-rate partials + result
   int* d_flag;     // non-physical-state flag
   cudaStream_t last_stream;

@@ -145,3 +145,125 @@ __device__ __forceinline__ void ranocha_flux8(const T* a, const T* b, const T* n
 }
 
 }  // namespace dgk
+
+namespace dgk {
+
+// ---------------------------------------------------------------------------------------------------
+// Adjoint (reverse-mode derivative) arithmetic for dg_vjp.
+// ---------------------------------------------------------------------------------------------------
+
+// The two means of log_means and their exact partial derivatives. Series branches (u small):
+//   L  = s P(u),  P = 1/2 - u/6 - 2u^2/45 - 22u^3/945,  dL/da = P - 4 (b/s) f P'(u),  dL/db = P + 4 (a/s) f P'(u)
+//   Li = Q(u)/s,  Q = 2 + 2u/3 + 2u^2/5 + 2u^3/7,      dLi/da = -(Q + 4 (b/s) f Q'(u))/s^2,
+//                                                      dLi/db = -(Q - 4 (a/s) f Q'(u))/s^2
+// with s = a + b, f = (b - a)/s, u = f^2 (du/da = -4 b f/s^2, du/db = 4 a f/s^2). P' and Q' carry the next
+// series term (856/14175 and 8/9) so that the derivatives are as accurate as the values.
+// Log branches with l = log(b/a), d = b - a:  dL/da = (d/a - l)/l^2, dL/db = (l - d/b)/l^2,
+//                                             dLi/da = (l - d/a)/d^2, dLi/db = (d/b - l)/d^2.
+template <typename T>
+__device__ __forceinline__ void log_means_grad(T a1, T b1, T a2, T b2, T& L, T& Li, T& dLa, T& dLb, T& dLia,
+                                               T& dLib) {
+  const T s1 = a1 + b1, d1 = b1 - a1;
+  const T s2 = a2 + b2, d2 = b2 - a2;
+  const T R = Num<T>::rcp(s1 * s2);
+  const T r1 = s2 * R, r2 = s1 * R;
+  const T f1 = d1 * r1, f2 = d2 * r2;
+  const T u1 = f1 * f1, u2 = f2 * f2;
+  if (Num<T>::series(u1)) {
+    const T P = T(0.5) + u1 * (T(-1.0 / 6.0) + u1 * (T(-2.0 / 45.0) + u1 * T(-22.0 / 945.0)));
+    const T dP = T(-1.0 / 6.0) + u1 * (T(-4.0 / 45.0) + u1 * (T(-66.0 / 945.0) + u1 * T(-856.0 / 14175.0)));
+    L = s1 * P;
+    const T g = T(4.0) * f1 * r1 * dP;  // 4 f P'/s
+    dLa = P - b1 * g;
+    dLb = P + a1 * g;
+  } else {
+    const T l = Num<T>::log(b1 / a1);
+    const T il = T(1) / l;
+    L = d1 * il;
+    dLa = (d1 / a1 - l) * il * il;
+    dLb = (l - d1 / b1) * il * il;
+  }
+  if (Num<T>::series(u2)) {
+    const T Qv = T(2.0) + u2 * (T(2.0 / 3.0) + u2 * (T(2.0 / 5.0) + u2 * T(2.0 / 7.0)));
+    const T dQ = T(2.0 / 3.0) + u2 * (T(4.0 / 5.0) + u2 * (T(6.0 / 7.0) + u2 * T(8.0 / 9.0)));
+    Li = r2 * Qv;
+    const T g = T(4.0) * f2 * r2 * dQ;  // 4 f Q'/s
+    const T r22 = r2 * r2;
+    dLia = -(Qv + b2 * g) * r22;
+    dLib = -(Qv - a2 * g) * r22;
+  } else {
+    const T l = Num<T>::log(b2 / a2);
+    const T id = T(1) / d2;
+    Li = l * id;
+    dLia = (l - d2 / a2) * id * id;
+    dLib = (d2 / b2 - l) * id * id;
+  }
+}
+
+// Adjoint of ranocha_flux8: given Fb = dJ/dF for F = ranocha_flux8(a, b, n2), adds dJ/da to abar and dJ/db to
+// bbar (node quantities; n2 is geometry and has no adjoint here).
+template <int ND, typename T>
+__device__ __forceinline__ void ranocha_flux8_adjoint(const T* a, const T* b, const T* n2, const T* Fb, T* abar,
+                                                      T* bbar) {
+  using Q = NodeQ<ND>;
+  T A = a[1] * n2[0], B = b[1] * n2[0], vv = a[1] * b[1];
+#pragma unroll
+  for (int j = 1; j < ND; ++j) {
+    A += a[1 + j] * n2[j];
+    B += b[1 + j] * n2[j];
+    vv += a[1 + j] * b[1 + j];
+  }
+  T L, Li, dLa, dLb, dLix, dLiy;
+  log_means_grad<T>(a[Q::RHO], b[Q::RHO], a[Q::RHO] * b[Q::PP], b[Q::RHO] * a[Q::PP], L, Li, dLa, dLb, dLix, dLiy);
+  const T q = L * (A + B);
+  const T t = a[Q::PG] * b[Q::PP] * Li;
+  const T Fe = Fb[ND + 1];
+  T qb = T(2) * Fb[0] + Fe * (vv + t);
+  T psb = T(0);
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    qb += Fb[1 + j] * (a[1 + j] + b[1 + j]);
+    psb += Fb[1 + j] * n2[j];
+  }
+  const T vvb = Fe * q, tb = Fe * q;
+  const T Ab = Fe * b[Q::PP] + qb * L;
+  const T Bb = Fe * a[Q::PP] + qb * L;
+  const T Lb = qb * (A + B);
+  const T Lib = tb * a[Q::PG] * b[Q::PP];
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    abar[1 + j] += Fb[1 + j] * q + vvb * b[1 + j] + Ab * n2[j];
+    bbar[1 + j] += Fb[1 + j] * q + vvb * a[1 + j] + Bb * n2[j];
+  }
+  abar[Q::PG] += tb * b[Q::PP] * Li;
+  bbar[Q::PP] += tb * a[Q::PG] * Li + Fe * A + psb;
+  abar[Q::PP] += Fe * B + psb;
+  const T x2b = Lib * dLix, y2b = Lib * dLiy;  // x2 = rho_a pp_b, y2 = rho_b pp_a
+  abar[Q::RHO] += Lb * dLa + x2b * b[Q::PP];
+  bbar[Q::RHO] += Lb * dLb + y2b * a[Q::PP];
+  bbar[Q::PP] += x2b * a[Q::RHO];
+  abar[Q::PP] += y2b * b[Q::RHO];
+}
+
+// Adjoint of node_quantities: ubar = (dq/du)^T qbar for q = (rho, v = m/rho, pp = 2p, pg = 2p/(gamma-1)),
+// p = (gamma - 1)(E - |m|^2/(2 rho)).
+template <int ND, typename T>
+__device__ __forceinline__ void node_quantities_adjoint(const double* uc, T gm1, T two_over_gm1, const T* qbar,
+                                                        T* ubar) {
+  using Q = NodeQ<ND>;
+  const T rho = (T)uc[0];
+  const T ir = Num<T>::rcp(rho);
+  const T pb = T(2) * qbar[Q::PP] + two_over_gm1 * qbar[Q::PG];
+  T rb = qbar[Q::RHO], v2 = T(0);
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    const T v = (T)uc[1 + j] * ir;
+    v2 += v * v;
+    rb -= qbar[1 + j] * v * ir;
+    ubar[1 + j] = qbar[1 + j] * ir - pb * gm1 * v;
+  }
+  ubar[0] = rb + pb * gm1 * T(0.5) * v2;
+  ubar[ND + 1] = pb * gm1;
+}
+
+}  // namespace dgk

@@ -199,6 +199,7 @@ void release(dg_ctx* c) {
   cudaFree(c->d_invJ);
   cudaFree(c->d_JW);
   cudaFree(c->d_face);
+  cudaFree(c->d_fadj);
   cudaFree(c->d_red);
   cudaFree(c->d_flag);
   if (c->prof_ev) {

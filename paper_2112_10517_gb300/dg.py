@@ -33,7 +33,7 @@ KERNEL_VOLUME, KERNEL_INTERFACE = 0, 1
 EXPORTED = ["dg_init", "dg_rhs", "dg_step", "dg_entropy_rate", "dg_check_status", "dg_get_info",
             "dg_get_node_coords", "dg_get_metrics", "dg_profile_enable", "dg_profile_read", "dg_launch_count",
             "dg_free", "dg_status_string", "dg_rhs_noalloc", "dg_batch_create", "dg_batch_rhs",
-            "dg_batch_autotune", "dg_batch_set_tuning", "dg_batch_free"]
+            "dg_batch_autotune", "dg_batch_set_tuning", "dg_batch_free", "dg_vjp"]
 
 
 class DgMesh(ctypes.Structure):
@@ -83,6 +83,7 @@ _sig = {
                                          ctypes.POINTER(ctypes.c_int)]),
     "dg_batch_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "dg_batch_free": (None, [_vp]),
+    "dg_vjp": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -204,6 +205,15 @@ class DG:
                       _stream_handle(stream)), "dg_step")
         return u
 
+    def vjp(self, u, gbar, ubar=None, stream=None):
+        """ubar = (d RHS/du)^T gbar (dg_vjp)."""
+        import torch
+        if ubar is None:
+            ubar = torch.empty_like(u)
+        check(dg_vjp(self.ctx, self._state(u, "u"), self._state(gbar, "gbar"), self._state(ubar, "ubar"),
+                     _stream_handle(stream)), "dg_vjp")
+        return ubar
+
     def entropy_rate(self, u, du, stream=None):
         out = ctypes.c_double()
         ab = ctypes.c_double()
@@ -280,3 +290,22 @@ class DGBatch:
             self.close()
         except Exception:
             pass
+
+
+def rhs_function():
+    """torch.autograd.Function: forward = dg_rhs, backward = dg_vjp. Usage: DGRhs.apply(ctx, u)."""
+    import torch
+
+    class DGRhs(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, ctx, u):
+            fctx.dg = ctx
+            fctx.save_for_backward(u)
+            return ctx.rhs(u.contiguous())
+
+        @staticmethod
+        def backward(fctx, grad):
+            (u,) = fctx.saved_tensors
+            return None, fctx.dg.vjp(u.contiguous(), grad.contiguous())
+
+    return DGRhs

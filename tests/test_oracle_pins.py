@@ -108,6 +108,26 @@ def test_logmean_against_high_precision():
     assert worst < 1e-15, worst
 
 
+def test_logmean_derivatives_against_high_precision():
+    # the dual-number derivatives of the oracle's mean (used by its JVP), including arguments equal to rounding
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 50
+    rng = np.random.Generator(np.random.PCG64(5))
+    ratios = np.concatenate([1.0 + np.logspace(-16, 0.5, 120), 1.0 - np.logspace(-16, -0.1, 60), [1.0]])
+    a = rng.uniform(0.2, 5.0, size=ratios.size)
+    b = a * ratios
+    ga, gb = orc.logmean_grad(a, b)
+    for x, y, da, db in zip(a, b, ga, gb):
+        X, Y = mpmath.mpf(float(x)), mpmath.mpf(float(y))
+        if X == Y:
+            ra = rb = mpmath.mpf(0.5)
+        else:
+            ln = mpmath.log(Y) - mpmath.log(X)
+            ra = ((Y - X) / X - ln) / ln ** 2
+            rb = (ln - (Y - X) / Y) / ln ** 2
+        assert abs(da - float(ra)) <= 2e-14 and abs(db - float(rb)) <= 2e-14, (x, y, da, float(ra), db, float(rb))
+
+
 # ------------------------------------------------------------------------------------------------
 # Euler flux (Eq. Euler): pinned by the eigenvalues of its Jacobian, v.n and v.n +- c|n|.
 # A wrong sign or a dropped pressure term anywhere changes them.
@@ -591,3 +611,36 @@ def test_rk_step_fourth_order_on_dg_system(scheme):
     e2 = np.max(np.abs(integrate(8) - ref))
     order = math.log2(e1 / e2)
     assert order > 3.6, (e1, e2, order)
+
+
+# ------------------------------------------------------------------------------------------------
+# The oracle's JVP (oracle.c compiled with dual numbers): pinned by its value part (the double oracle) and by
+# central finite differences of the double oracle
+# ------------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nd,nelem,p,llf", [(3, [2, 3, 2], 3, True), (2, [3, 4], 4, False), (3, [2, 2, 2], 2, True)])
+def test_dual_jvp_value_and_finite_differences(nd, nelem, p, llf):
+    xyz, Ja, J = mesh(nd, nelem, p, True)
+    u = inputs.smooth_random(xyz, seed=21) + 0.01 * inputs.random_state(xyz, seed=22)
+    delta = inputs.perturbation(u.shape, seed=23) * np.abs(u)
+    val, jd = orc.jvp(nd, p, nelem, Ja, J, u, delta, llf=llf)
+    np.testing.assert_array_equal(val, orc.rhs(nd, p, nelem, Ja, J, u, llf=llf))
+    # eps small enough that no LLF switch (max, abs) lies within u +- eps delta for these seeds
+    eps = 1e-6
+    fd = (orc.rhs(nd, p, nelem, Ja, J, u + eps * delta, llf=llf) -
+          orc.rhs(nd, p, nelem, Ja, J, u - eps * delta, llf=llf)) / (2 * eps)
+    for c in range(nd + 2):
+        scale = np.max(np.abs(jd[:, c]))
+        assert np.max(np.abs(jd[:, c] - fd[:, c])) <= 1e-6 * scale, c
+
+
+def test_dual_logmean_derivative_at_equal_arguments():
+    # d/da {{a, b}}_log at a = b is 1/2 per argument; the dual JVP of a constant-density state sees it
+    nd, nelem, p = 3, [2, 2, 2], 2
+    xyz, Ja, J = mesh(nd, nelem, p, True)
+    u = inputs.free_stream(xyz)
+    delta = inputs.perturbation(u.shape, seed=24)
+    _, jd = orc.jvp(nd, p, nelem, Ja, J, u, delta, llf=True)
+    eps = 1e-6
+    fd = (orc.rhs(nd, p, nelem, Ja, J, u + eps * delta) - orc.rhs(nd, p, nelem, Ja, J, u - eps * delta)) / (2 * eps)
+    np.testing.assert_allclose(jd, fd, rtol=0, atol=1e-6 * np.max(np.abs(jd)))
