@@ -169,6 +169,21 @@ def alu_peaks():
     return out
 
 
+def max_over_ranks(value: float, device) -> float:
+    """The largest value over all ranks (the step time of a multi-GPU run is that of its slowest rank)."""
+    import torch
+    if not torch.distributed.is_initialized() or torch.distributed.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_pid(ms_per_step: float, ndofs_per_rank: int, world: int, rhs_per_step: int = STAGES) -> float:
+    """PID of the whole job: step time over all DOF processed by all ranks (weak scaling: each rank its own copy)."""
+    return ms_per_step * 1e6 / (rhs_per_step * ndofs_per_rank * world)
+
+
 def make_state(ctx):
     from paper_2112_10517_gb300 import inputs
     return inputs.taylor_green(ctx.node_coords(), mach=MACH)
@@ -232,16 +247,12 @@ def run_ours(args, rank, world, local_rank):
         vol_ms, vol_n = ctx.profile_read(dg.KERNEL_VOLUME)
         ifc_ms, ifc_n = ctx.profile_read(dg.KERNEL_INTERFACE)
         ctx.profile(False)
-        ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
-        if world > 1:
-            t = torch.tensor([ms], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps, dev)
         status = ctx.check_status()
         if status != dg.DG_OK:
             raise RuntimeError("non-physical state during the timed steps")
         ndofs = ctx.ndofs
-        pid = ms * 1e6 / (STAGES * ndofs * world)
+        pid = whole_job_pid(ms, ndofs, world)
         vol_avg_s = vol_ms / max(vol_n, 1) * 1e-3
         res = {"ms_per_step": ms, "pid_ns": pid, "launches": launches, "clocks": clk,
                "volume_ms_avg": vol_avg_s * 1e3, "interface_ms_avg": ifc_ms / max(ifc_n, 1),
@@ -266,12 +277,8 @@ def run_ours(args, rank, world, local_rank):
                 u_out.copy_(ud, non_blocking=True)
                 e1[k].record(stream)
             torch.cuda.synchronize()
-            ems = sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / args.steps
-            if world > 1:
-                t = torch.tensor([ems], dtype=torch.float64, device=dev)
-                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-                ems = float(t.item())
-            res["e2e_pid_ns"] = ems * 1e6 / (STAGES * ndofs * world)
+            ems = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / args.steps, dev)
+            res["e2e_pid_ns"] = whole_job_pid(ems, ndofs, world)
             res["e2e_bytes"] = int(u_host.numel() * 8)
         # roofline of the dominant kernel (volume): FP64 is bound by the FP64 pipe, FP32 by HBM
         vflops = VOLUME_FLOPS_PER_DOF * ndofs
@@ -353,6 +360,48 @@ def run_batch(args, dev):
     return out
 
 
+def run_diff_and_scale(args, dev):
+    """The differentiation workload (dg_vjp on 8^3, p = 4, FP64) and forward RHS throughput at 64^3, p = 3."""
+    import torch
+    from paper_2112_10517_gb300 import dg, inputs
+    lo, hi = [-math.pi] * 3, [math.pi] * 3
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / args.steps
+
+    out = {}
+    ctx = dg.DG(3, [8, 8, 8], 4, lo=lo, hi=hi, mapping="sine", amp=AMP, surface="llf")
+    u = torch.from_numpy(inputs.smooth_random(ctx.node_coords(), seed=40)).to(dev)
+    g = torch.from_numpy(inputs.perturbation(tuple(u.shape), 41)).to(dev)
+    du, ub = torch.empty_like(u), torch.empty_like(u)
+    ms_f = timed(lambda: ctx.rhs(u, du))
+    ms_b = timed(lambda: ctx.vjp(u, g, ub))
+    out["vjp_8cubed_p4_fp64"] = {"rhs_ms": ms_f, "vjp_ms": ms_b, "vjp_over_rhs": ms_b / ms_f,
+                                 "pid_rhs_ns": ms_f * 1e6 / ctx.ndofs, "pid_vjp_ns": ms_b * 1e6 / ctx.ndofs}
+    del ctx, u, g, du, ub
+    for precision in ("fp64", "fp32"):
+        ctx = dg.DG(3, [64, 64, 64], 3, lo=lo, hi=hi, mapping="sine", amp=AMP, surface="llf", precision=precision)
+        u = torch.from_numpy(inputs.taylor_green(ctx.node_coords(), mach=MACH)).to(dev)
+        du = torch.empty_like(u)
+        ms = timed(lambda: ctx.rhs(u, du))
+        out["rhs_64cubed_p3_" + precision] = {"ms": ms, "pid_ns": ms * 1e6 / ctx.ndofs, "ndofs": ctx.ndofs}
+        del ctx, u, du
+    out["workload"] = ("dg_vjp vs dg_rhs on 3D curvilinear 8^3, p = 4, FP64 (smooth random state); dg_rhs at 64^3, "
+                       "p = 3 (16.8M DOF) Taylor-Green, FP64 and FP32; back-to-back calls, inputs larger than L2 "
+                       "at 64^3")
+    return out
+
+
 def oracle_pid(seconds_target: float, elements=None):
     """Time the CPU oracle RHS on the same workload; returns (pid_ns, sample description, reps)."""
     import numpy as np
@@ -422,6 +471,7 @@ def main():
         torch.distributed.init_process_group("nccl")
     results, peaks_alu = run_ours(args, rank, world, local_rank)
     batch = run_batch(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
+    diff = run_diff_and_scale(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
     if rank == 0 and args.only:
         for label, res in results.items():
             print(json.dumps({"configuration": label, "pid_ns": res["pid_ns"], "ms_per_step": res["ms_per_step"],
@@ -467,6 +517,7 @@ def main():
                                         "interface": b32["interface_ms_avg"]}},
                 "speedup_fp32_vs_fp64": b64["pid_ns"] / b32["pid_ns"]},
             "batch_64": batch,
+            "differentiation_and_scale": diff,
             "alu_peaks_measured_tflops": {k: (v / 1e12 if v else None) for k, v in peaks_alu.items()},
         }
         print(json.dumps(line), flush=True)
