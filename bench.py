@@ -127,7 +127,7 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------------------
 def source_digest() -> str:
     h = hashlib.sha256()
-    for f in ("kernels.cuh", "volume.cu"):
+    for f in ("dgmath.cuh", "kernels.cuh", "volume.cu"):
         with open(os.path.join(ROOT, "paper_2112_10517_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
