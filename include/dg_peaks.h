@@ -30,6 +30,12 @@ int dgpk_measure(int kind, double min_seconds, double* ops_per_s, double* second
 int dgpk_eval_logmeans(long long n, int precision, const double* a1, const double* b1, const double* a2,
                        const double* b2, double* L, double* Li, double* r);
 
+/* Self-test of the integer-pipe IEEE conversions the FP32 flux mode uses (binary64 -> binary32 round to nearest
+   even with flush to zero below the normal range; binary32 -> binary64 exact) against the hardware conversions:
+   f_int/f_hw receive the float bit patterns of d2f_int(x) and __double2float_rn(x), d_int/d_hw the widenings of that
+   float. Device arrays of n elements; synchronizes; returns 0 or a cudaError_t value. */
+int dgpk_eval_convert(long long n, const double* x, unsigned* f_int, unsigned* f_hw, double* d_int, double* d_hw);
+
 #ifdef __cplusplus
 }
 #endif

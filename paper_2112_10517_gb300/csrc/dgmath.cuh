@@ -57,6 +57,42 @@ struct Num<float> {
 };
 
 // ---------------------------------------------------------------------------------------------------
+// IEEE format conversions on the integer pipe. On GB300 a hardware FP64<->FP32 conversion issues on the FP64
+// pipe (2 per clock per SM), which the FP32 flux mode would otherwise saturate converting every state value.
+//   d2f_int: binary64 -> binary32, round to nearest even; results below the smallest normal float flush to
+//            signed zero (the FP32 mode's flush-to-zero); infinities and NaN are not preserved.
+//   f2d_int: binary32 -> binary64, exact for normal floats and zero (subnormals flush to zero).
+// ---------------------------------------------------------------------------------------------------
+__device__ __forceinline__ float d2f_int(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFull;
+  // keep 23 of the 52 mantissa bits: adding 2^28 - 1 plus the lowest kept bit rounds to nearest, ties to even;
+  // a carry out of the mantissa correctly increments the exponent
+  const unsigned long long r = mag + 0x0FFFFFFFull + ((mag >> 29) & 1ull);
+  const int e = (int)(r >> 52) - 1023 + 127;
+  const unsigned m = (unsigned)(r >> 29) & 0x7FFFFFu;
+  return __uint_as_float(e <= 0 ? sign : (sign | ((unsigned)e << 23) | m));
+}
+
+__device__ __forceinline__ double f2d_int(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned sign = b & 0x80000000u;
+  const unsigned em = b & 0x7FFFFFFFu;
+  const unsigned hi = em < 0x00800000u ? sign : (sign | ((em >> 3) + ((1023u - 127u) << 20)));
+  const unsigned lo = em < 0x00800000u ? 0u : (em << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// state value (FP64 in memory) in the flux precision T
+template <typename T>
+__device__ __forceinline__ T to_flux(double x);
+template <>
+__device__ __forceinline__ double to_flux<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float to_flux<float>(double x) { return d2f_int(x); }
+
+// ---------------------------------------------------------------------------------------------------
 // The two logarithmic means of Ranocha's flux from ONE reciprocal (Sec. 3.1 and 3.2):
 //   L  = {{a}}_log                for (a1, b1)                (Algorithm 2)
 //   Li = 1/{{c}}_log              for (a2, b2)                (Algorithm 3)
@@ -97,17 +133,17 @@ struct NodeQ {
 
 template <int ND, typename T>
 __device__ __forceinline__ bool node_quantities(const double* uc, T gm1, T two_over_gm1, T* q) {
-  const T rho = (T)uc[0];
+  const T rho = to_flux<T>(uc[0]);
   const T ir = Num<T>::rcp(rho);
   T ke = T(0);
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
-    const T m = (T)uc[1 + j];
+    const T m = to_flux<T>(uc[1 + j]);
     const T v = m * ir;
     q[1 + j] = v;
     ke += m * v;
   }
-  const T p = gm1 * ((T)uc[ND + 1] - T(0.5) * ke);
+  const T p = gm1 * (to_flux<T>(uc[ND + 1]) - T(0.5) * ke);
   q[0] = rho;
   q[NodeQ<ND>::PP] = p + p;
   q[NodeQ<ND>::PG] = p * two_over_gm1;

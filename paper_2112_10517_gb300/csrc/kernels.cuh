@@ -108,7 +108,11 @@ __device__ __forceinline__ void interface_node(const double* __restrict__ u, con
     const T lamR = Num<T>::abs(vnR) + Num<T>::sqrt(hg * qR[NodeQ<ND>::PP] * Num<T>::rcp(qR[0])) * mn;
     const T half_lam = T(0.5) * (lamL > lamR ? lamL : lamR);
 #pragma unroll
-    for (int c = 0; c < G::NV; ++c) f[c] -= half_lam * (T)(uR[c] - uL[c]);
+    for (int c = 0; c < G::NV; ++c) {
+      // FP64: the jump in FP64; FP32 mode: both states rounded to FP32 first (no FP64 arithmetic)
+      const T jump = sizeof(T) == 8 ? (T)(uR[c] - uL[c]) : to_flux<T>(uR[c]) - to_flux<T>(uL[c]);
+      f[c] -= half_lam * jump;
+    }
   }
   T* fo = face + ((size_t)n * md.E + e) * G::NV * G::NL + fn;
 #pragma unroll
@@ -286,12 +290,15 @@ __device__ __forceinline__ void volume_tile(const double* u, const T* __restrict
       }
     }
     const double sj = -invJ[(size_t)ge * G::NDOF + i];
+    const T sjT = sizeof(T) == 8 ? T(0) : -to_flux<T>(invJ[(size_t)ge * G::NDOF + i]);
     const size_t off = (size_t)ge * G::NV * G::NDOF + i;
 #pragma unroll
     for (int c = 0; c < G::NV; ++c) {
       const size_t o = off + (size_t)c * G::NDOF;
       const int so = (el * G::NV + c) * G::NDOF + i;  // same value, prefetched into shared memory
-      const double k = sj * (double)tot[c];
+      // FP64: k = -(1/J) tot in FP64. FP32 mode: the scaling in FP32 and an exact integer-pipe widening, so the
+      // FP64 pipe only carries the RK accumulation below.
+      const double k = sizeof(T) == 8 ? sj * (double)tot[c] : f2d_int((float)(sjT * tot[c]));
       if (EPI == EPI_STORE) {
         du[o] = k;
       } else if (EPI == EPI_RK4) {

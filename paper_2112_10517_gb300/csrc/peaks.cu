@@ -110,9 +110,31 @@ __global__ void logmeans_kernel(long long n, const double* a1, const double* b1,
   r[i] = (double)dgk::Num<T>::rcp((T)a1[i]);
 }
 
+__global__ void convert_kernel(long long n, const double* x, unsigned* f_int, unsigned* f_hw, double* d_int,
+                               double* d_hw) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float hw = __double2float_rn(x[i]);
+  f_int[i] = __float_as_uint(dgk::d2f_int(x[i]));
+  f_hw[i] = __float_as_uint(hw);
+  d_int[i] = dgk::f2d_int(hw);
+  d_hw[i] = (double)hw;
+}
+
 }  // namespace
 
 extern "C" {
+
+// Self-test of the integer-pipe format conversions of the RHS kernels against the hardware conversions: for
+// i < n, f_int[i] / f_hw[i] = bits of d2f_int(x[i]) / __double2float_rn(x[i]); d_int[i] / d_hw[i] = f2d_int and
+// the hardware widening of that float. Device arrays; synchronizes; returns 0 or a cudaError_t value.
+int dgpk_eval_convert(long long n, const double* x, unsigned* f_int, unsigned* f_hw, double* d_int, double* d_hw) {
+  if (n <= 0) return 0;
+  convert_kernel<<<(unsigned)((n + 255) / 256), 256>>>(n, x, f_int, f_hw, d_int, d_hw);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return (int)e;
+}
 
 // Evaluates the RHS kernels' device arithmetic on n inputs (device arrays): L = {{a1, b1}}_log (Algorithm 2),
 // Li = 1/{{a2, b2}}_log (Algorithm 3), both from the single shared reciprocal, and r = the reciprocal of a1,
