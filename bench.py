@@ -360,6 +360,49 @@ def run_batch(args, dev):
     return out
 
 
+def run_variants(args, dev):
+    """dg_rhs throughput of the flux and geometry variants on the 32^3, p = 3 Taylor-Green vortex: Ranocha and
+    Shima et al. volume fluxes, curvilinear (sine-perturbed) and Cartesian (affine, constant metrics) meshes,
+    FP64 and FP32 flux arithmetic. L2 is flushed before every timed call."""
+    import torch
+    from paper_2112_10517_gb300 import dg, inputs
+    lo, hi = [-math.pi] * 3, [math.pi] * 3
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for flux in ("ranocha", "shima"):
+        for geo in ("curved", "cartesian"):
+            for precision in ("fp64", "fp32"):
+                kw = dict(mapping="sine", amp=AMP) if geo == "curved" else dict(mapping="affine")
+                ctx = dg.DG(3, NELEM_LARGE, POLYDEG, lo=lo, hi=hi, surface="llf", precision=precision, flux=flux,
+                            **kw)
+                u = torch.from_numpy(inputs.taylor_green(ctx.node_coords(), mach=MACH)).to(dev)
+                du = torch.empty_like(u)
+                for _ in range(args.warmup):
+                    ctx.rhs(u, du)
+                torch.cuda.synchronize()
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(args.steps)]
+                ctx.profile(True)
+                for a, b in ev:
+                    flush.zero_()
+                    a.record(stream)
+                    ctx.rhs(u, du)
+                    b.record(stream)
+                torch.cuda.synchronize()
+                vol_ms, vol_n = ctx.profile_read(dg.KERNEL_VOLUME)
+                ctx.profile(False)
+                if ctx.check_status() != dg.DG_OK:
+                    raise RuntimeError("non-physical state in the variant runs")
+                ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+                out["%s_%s_%s" % (flux, geo, precision)] = {"ms": ms, "pid_ns": ms * 1e6 / ctx.ndofs,
+                                                            "volume_ms": vol_ms / max(vol_n, 1)}
+                del ctx, u, du
+    out["workload"] = ("dg_rhs (one RHS: interface + volume kernel) on the 32^3, p = 3 Taylor-Green vortex, Mach 0.1, "
+                       "2,097,152 DOF; curved = sine-perturbed mesh, cartesian = affine mesh; L2 flushed per call")
+    return out
+
+
 def run_diff_and_scale(args, dev):
     """The differentiation workload (dg_vjp on 8^3, p = 4, FP64) and forward RHS throughput at 64^3, p = 3."""
     import torch
@@ -472,6 +515,7 @@ def main():
     results, peaks_alu = run_ours(args, rank, world, local_rank)
     batch = run_batch(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
     diff = run_diff_and_scale(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
+    variants = run_variants(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
     if rank == 0 and args.only:
         for label, res in results.items():
             print(json.dumps({"configuration": label, "pid_ns": res["pid_ns"], "ms_per_step": res["ms_per_step"],
@@ -518,6 +562,7 @@ def main():
                 "speedup_fp32_vs_fp64": b64["pid_ns"] / b32["pid_ns"]},
             "batch_64": batch,
             "differentiation_and_scale": diff,
+            "flux_and_geometry_variants": variants,
             "alu_peaks_measured_tflops": {k: (v / 1e12 if v else None) for k, v in peaks_alu.items()},
         }
         print(json.dumps(line), flush=True)

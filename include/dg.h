@@ -57,7 +57,7 @@ typedef enum dg_status {
 enum { DG_MAP_AFFINE = 0, DG_MAP_SINE = 1, DG_MAP_NODES = 2 };
 enum { DG_SURF_EC = 0, DG_SURF_EC_LLF = 1 };
 enum { DG_FP64 = 0, DG_FP32 = 1 };
-enum { DG_VOL_RANOCHA = 0 };
+enum { DG_VOL_RANOCHA = 0, DG_VOL_SHIMA = 1 };
 enum { DG_RK4_CLASSIC = 0, DG_LSRK45_CK = 1 };
 
 /* Periodic box [lo, hi] with nelem[m] elements per direction (nelem[2], lo[2], hi[2] ignored in 2D).
@@ -84,8 +84,11 @@ typedef struct dg_metrics {
   const double* J_host;
 } dg_metrics;
 
-/* gamma: ratio of specific heats (> 1). volume_flux: DG_VOL_RANOCHA (Eq. flux_ranocha).
-   surface_flux: DG_SURF_EC (Ranocha flux) or DG_SURF_EC_LLF (plus local Lax-Friedrichs dissipation).
+/* gamma: ratio of specific heats (> 1). volume_flux: the two-point flux of the volume term and of the interfaces
+   (as in the paper's runs, Sec. 4.1): DG_VOL_RANOCHA (Eq. flux_ranocha, entropy conservative) or DG_VOL_SHIMA
+   (Eq. flux_shima_etal, kinetic energy and pressure equilibrium preserving, not entropy conservative; dg_vjp and
+   dg_batch_* support DG_VOL_RANOCHA only).
+   surface_flux: DG_SURF_EC (the two-point flux alone) or DG_SURF_EC_LLF (plus local Lax-Friedrichs dissipation).
    precision: DG_FP64, or DG_FP32 (two-point fluxes and line sums in FP32; metric terms computed in
    FP64 and rounded once; state, du, RK accumulation and the entropy diagnostic in FP64). */
 typedef struct dg_opts {
@@ -107,6 +110,8 @@ typedef struct dg_info {
 
 /* Build a context: LGL tables (Sec. 2), node coordinates, metric terms and Jacobian (Sec. 2.3) in FP64
    on the host, uploaded to the current device. Allocates device memory (about 100 bytes per DOF).
+   With DG_MAP_AFFINE and no metric override the kernels use the Cartesian specialisation: the metric terms of an
+   axis-aligned box element are constant and diagonal, so dg_rhs and dg_step read no metric arrays.
    Returns DG_ERR_ARG for a bad mesh/options, DG_ERR_UNSUPPORTED for polydeg outside 1..7, DG_ERR_OOM. */
 dg_status dg_init(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metrics* metrics, const dg_opts* opts);
 

@@ -152,27 +152,35 @@ def euler_flux(u, j: int, ndims: int, gamma: float = 1.4) -> np.ndarray:
     return f
 
 
-def flux_ranocha(um, up, m, ndims: int, gamma: float = 1.4) -> np.ndarray:
-    """Directional Ranocha flux f(u-, u+, m) = sum_j m_j F_j (Eq. flux_ranocha; Sec. 2.3)."""
+FLUXES = {"ranocha": 0, "shima": 1}
+
+
+def flux_dir(um, up, m, ndims: int, gamma: float = 1.4, flux: str = "ranocha") -> np.ndarray:
+    """Directional two-point flux f(u-, u+, m) = sum_j m_j F_j (Eq. flux_ranocha or Eq. flux_shima_etal)."""
     lib = _load()
     um = _f64(um)
     up = _f64(np.broadcast_to(up, um.shape))
     n = um.size // (ndims + 2)
     m = _f64(np.broadcast_to(m, (n, ndims)))
     f = np.zeros_like(um)
-    lib.orc_flux_ranocha_dir_batch(n, _ptr(um), _ptr(up), ndims, ctypes.c_double(gamma), _ptr(m), _ptr(f))
+    lib.orc_flux_dir_batch(FLUXES[flux], n, _ptr(um), _ptr(up), ndims, ctypes.c_double(gamma), _ptr(m), _ptr(f))
     return f
 
 
-def surface_flux(uin, uout, m, ndims: int, gamma: float = 1.4, llf: bool = True) -> np.ndarray:
-    """Surface flux: Ranocha flux minus local Lax-Friedrichs dissipation when llf (Sec. 4.2)."""
+def flux_ranocha(um, up, m, ndims: int, gamma: float = 1.4) -> np.ndarray:
+    """Directional Ranocha flux f(u-, u+, m) = sum_j m_j F_j (Eq. flux_ranocha; Sec. 2.3)."""
+    return flux_dir(um, up, m, ndims, gamma, "ranocha")
+
+
+def surface_flux(uin, uout, m, ndims: int, gamma: float = 1.4, llf: bool = True, flux: str = "ranocha") -> np.ndarray:
+    """Surface flux: the two-point flux minus local Lax-Friedrichs dissipation when llf (Sec. 4.2)."""
     lib = _load()
     uin = _f64(uin)
     uout = _f64(np.broadcast_to(uout, uin.shape))
     n = uin.size // (ndims + 2)
     m = _f64(np.broadcast_to(m, (n, ndims)))
     f = np.zeros_like(uin)
-    lib.orc_surface_flux_batch(n, _ptr(uin), _ptr(uout), ndims, ctypes.c_double(gamma), _ptr(m),
+    lib.orc_surface_flux_batch(FLUXES[flux], n, _ptr(uin), _ptr(uout), ndims, ctypes.c_double(gamma), _ptr(m),
                                int(bool(llf)), _ptr(f))
     return f
 
@@ -220,7 +228,7 @@ def metrics(ndims: int, p: int, xyz, curl_form: bool = True):
 
 
 def rhs(ndims: int, p: int, nelem, Ja, J, u, gamma: float = 1.4, llf: bool = True,
-        elem_range=None, scale: bool = False) -> np.ndarray:
+        elem_range=None, scale: bool = False, flux: str = "ranocha") -> np.ndarray:
     """du/dt of the flux-differencing LGL-DGSEM (Eq. strong-form-SBP with Eq. fluxdiff-SBP,
     curvilinear via Eq. curvilinear-rewrite). elem_range=(b, e) computes only elements [b, e) and returns
     that slice [e-b, nvar, Nd]. scale=True returns instead (1/J) x the sum of |terms| of that sum, the
@@ -235,7 +243,7 @@ def rhs(ndims: int, p: int, nelem, Ja, J, u, gamma: float = 1.4, llf: bool = Tru
     assert 0 <= b <= e <= E
     du = np.zeros((e - b,) + u.shape[1:])
     _check(lib.orc_rhs(ndims, p, _ivec(nelem), _ptr(Ja), _ptr(J), _ptr(u), ctypes.c_double(gamma),
-                       int(bool(llf)), int(b), int(e), int(bool(scale)), _ptr(du)), "rhs")
+                       FLUXES[flux], int(bool(llf)), int(b), int(e), int(bool(scale)), _ptr(du)), "rhs")
     return du
 
 
@@ -277,12 +285,13 @@ def ck45_coefficients():
 
 
 def rk_step(scheme: int, ndims: int, p: int, nelem, Ja, J, u, dt: float, gamma: float = 1.4,
-            llf: bool = True) -> np.ndarray:
+            llf: bool = True, flux: str = "ranocha") -> np.ndarray:
     """One time step (Sec. 4.1): scheme 0 classical RK4, scheme 1 Carpenter-Kennedy 5-stage 2N."""
     lib = _load()
     u = _f64(u).copy()
     _check(lib.orc_rk_step(scheme, ndims, p, _ivec(nelem), _ptr(_f64(Ja)), _ptr(_f64(J)),
-                           ctypes.c_double(gamma), int(bool(llf)), ctypes.c_double(dt), _ptr(u)), "rk_step")
+                           ctypes.c_double(gamma), FLUXES[flux], int(bool(llf)), ctypes.c_double(dt), _ptr(u)),
+           "rk_step")
     return u
 
 
@@ -298,7 +307,7 @@ def logmean_grad(a, b):
     return ga, gb
 
 
-def jvp(ndims: int, p: int, nelem, Ja, J, u, delta, gamma: float = 1.4, llf: bool = True):
+def jvp(ndims: int, p: int, nelem, Ja, J, u, delta, gamma: float = 1.4, llf: bool = True, flux: str = "ranocha"):
     """(RHS(u), J(u) delta): the oracle's RHS evaluated in dual numbers (oracle_dual.cpp compiles oracle.c with
     `double` taken as a dual number), i.e. forward-mode differentiation, exact up to rounding."""
     lib = _load_dual()
@@ -319,5 +328,5 @@ def jvp(ndims: int, p: int, nelem, Ja, J, u, delta, gamma: float = 1.4, llf: boo
     ud = dual_of(u, delta)
     dud = np.zeros_like(ud)
     _check(lib.orc_rhs(ndims, p, _ivec(nelem), _ptr(Jad), _ptr(Jd), _ptr(ud), _Dual(gamma, 0.0),
-                       int(bool(llf)), 0, E, 0, _ptr(dud)), "rhs (dual)")
+                       FLUXES[flux], int(bool(llf)), 0, E, 0, _ptr(dud)), "rhs (dual)")
     return dud[..., 0].copy(), dud[..., 1].copy()

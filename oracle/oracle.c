@@ -178,28 +178,56 @@ void orc_flux_ranocha_cart(const double* um, const double* up, int nd, double ga
   f[nd + 1] = f[0] * vv_prod / 2.0 + f[0] / (beta_log * (gamma - 1.0)) + pvj_prod;
 }
 
-/* Directional Ranocha flux in a (not necessarily unit) direction m: the flux is linear in the
+/* Flux of Shima et al. (kinetic energy and pressure equilibrium preserving, not EC) in Cartesian direction j
+   (Sec. 3.2, Eq. flux_shima_etal with n = e_j):
+     f_rho  = {{rho}} {{v_j}}
+     f_rhov = f_rho {{v}} + {{p}} e_j
+     f_rhoe = f_rho ((v;v))/2 + {{p}} {{v_j}} / (gamma-1) + ((p; v_j)) */
+void orc_flux_shima_cart(const double* um, const double* up, int nd, double gamma, int j, double* f) {
+  double rm, vm[3], pm, rp, vp[3], pp;
+  orc_prim(um, nd, gamma, &rm, vm, &pm);
+  orc_prim(up, nd, gamma, &rp, vp, &pp);
+  double rho_avg = 0.5 * (rm + rp);
+  double vj_avg = 0.5 * (vm[j] + vp[j]);
+  double p_avg = 0.5 * (pm + pp);
+  double vv_prod = 0.0;
+  for (int i = 0; i < nd; ++i) vv_prod += 0.5 * (vp[i] * vm[i] + vm[i] * vp[i]);
+  double pvj_prod = 0.5 * (pp * vm[j] + pm * vp[j]);
+  f[0] = rho_avg * vj_avg;
+  for (int i = 0; i < nd; ++i) f[1 + i] = f[0] * 0.5 * (vm[i] + vp[i]) + (i == j ? p_avg : 0.0);
+  f[nd + 1] = f[0] * vv_prod / 2.0 + p_avg * vj_avg / (gamma - 1.0) + pvj_prod;
+}
+
+/* Cartesian two-point flux: flux 0 = Ranocha (Eq. flux_ranocha), 1 = Shima et al. (Eq. flux_shima_etal) */
+static void orc_flux_cart(int flux, const double* um, const double* up, int nd, double gamma, int j, double* f) {
+  if (flux == 1)
+    orc_flux_shima_cart(um, up, nd, gamma, j, f);
+  else
+    orc_flux_ranocha_cart(um, up, nd, gamma, j, f);
+}
+
+/* Directional two-point flux in a (not necessarily unit) direction m: the fluxes are linear in the
    direction, so f(u-, u+, m) = sum_j m_j F_j(u-, u+) (Sec. 2.3, the directional flux obtained from
    Eq. curvilinear-rearrange); the length of m scales the result as in the last step of Alg. 4. */
-void orc_flux_ranocha_dir(const double* um, const double* up, int nd, double gamma, const double* m,
-                          double* f) {
+void orc_flux_dir(int flux, const double* um, const double* up, int nd, double gamma, const double* m, double* f) {
   const int nv = nd + 2;
   double Fj[5];
   for (int c = 0; c < nv; ++c) f[c] = 0.0;
   for (int j = 0; j < nd; ++j) {
-    orc_flux_ranocha_cart(um, up, nd, gamma, j, Fj);
+    orc_flux_cart(flux, um, up, nd, gamma, j, Fj);
     for (int c = 0; c < nv; ++c) f[c] += m[j] * Fj[c];
   }
 }
 
-/* Surface flux f*(u_in, u_out, m): the directional Ranocha flux, minus (when llf != 0) local
+/* Surface flux f*(u_in, u_out, m): the directional two-point flux (the volume flux, as in the paper's runs,
+   Sec. 4.1), minus (when llf != 0) local
    Lax-Friedrichs dissipation lambda/2 (u_out - u_in) with
    lambda = max(|v_in.m| + c_in |m|, |v_out.m| + c_out |m|), c = sqrt(gamma p / rho)
    (Sec. 4.2, surface dissipation; the formula is the standard Rusanov flux, not printed in the paper). */
-void orc_surface_flux(const double* uin, const double* uout, int nd, double gamma, const double* m, int llf,
-                      double* f) {
+void orc_surface_flux(int flux, const double* uin, const double* uout, int nd, double gamma, const double* m,
+                      int llf, double* f) {
   const int nv = nd + 2;
-  orc_flux_ranocha_dir(uin, uout, nd, gamma, m, f);
+  orc_flux_dir(flux, uin, uout, nd, gamma, m, f);
   if (!llf) return;
   double ri, vi[3], pi, ro, vo[3], po;
   orc_prim(uin, nd, gamma, &ri, vi, &pi);
@@ -218,16 +246,16 @@ void orc_surface_flux(const double* uin, const double* uout, int nd, double gamm
 }
 
 /* Batched wrappers used by the tests (n states, each nvar contiguous). */
-void orc_flux_ranocha_dir_batch(int n, const double* um, const double* up, int nd, double gamma,
-                                const double* m, double* f) {
+void orc_flux_dir_batch(int flux, int n, const double* um, const double* up, int nd, double gamma, const double* m,
+                        double* f) {
   const int nv = nd + 2;
-  for (int s = 0; s < n; ++s) orc_flux_ranocha_dir(um + s * nv, up + s * nv, nd, gamma, m + s * nd, f + s * nv);
+  for (int s = 0; s < n; ++s) orc_flux_dir(flux, um + s * nv, up + s * nv, nd, gamma, m + s * nd, f + s * nv);
 }
-void orc_surface_flux_batch(int n, const double* uin, const double* uout, int nd, double gamma,
+void orc_surface_flux_batch(int flux, int n, const double* uin, const double* uout, int nd, double gamma,
                             const double* m, int llf, double* f) {
   const int nv = nd + 2;
   for (int s = 0; s < n; ++s)
-    orc_surface_flux(uin + s * nv, uout + s * nv, nd, gamma, m + s * nd, llf, f + s * nv);
+    orc_surface_flux(flux, uin + s * nv, uout + s * nv, nd, gamma, m + s * nd, llf, f + s * nv);
 }
 void orc_euler_flux_batch(int n, const double* u, int nd, double gamma, int j, double* f) {
   const int nv = nd + 2;
@@ -414,6 +442,7 @@ int orc_metrics(int nd, int p, int nelem_total, const double* xyz, int curl_form
 
 /* ------------------------------------------------------------------------------------------------ */
 /* The semidiscretization (Sec. 2, Eq. strong-form-SBP with the volume term of Eq. fluxdiff-SBP,     */
+/* volume and surface two-point flux `flux`: 0 Ranocha, 1 Shima et al.)                               */
 /* on curvilinear elements via Eq. curvilinear-rewrite):                                             */
 /*                                                                                                   */
 /*  du_i = -(1/J_i) [ sum_n sum_{k on i's line along xi_n} D_{i_n k_n} sum_j (Ja^n_j(i) + Ja^n_j(k))  */
@@ -435,7 +464,7 @@ int orc_metrics(int nd, int p, int nelem_total, const double* xyz, int curl_form
 /* ------------------------------------------------------------------------------------------------ */
 
 int orc_rhs(int nd, int p, const int* nelem, const double* Ja, const double* J, const double* u, double gamma,
-            int llf, int elem_begin, int elem_end, int scale_mode, double* du) {
+            int flux, int llf, int elem_begin, int elem_end, int scale_mode, double* du) {
   if (nd < 2 || nd > 3 || p < 1 || p >= ORC_MAXN) return -1;
   const int N = p + 1, Nd = orc_ipow(N, nd), nv = nd + 2;
   const int n1 = nelem[0], n2 = nelem[1], n3 = nd == 3 ? nelem[2] : 1;
@@ -459,7 +488,7 @@ int orc_rhs(int nd, int p, const int* nelem, const double* Ja, const double* J, 
           for (int j = 0; j < nd; ++j) {
             const double a = Ja[(((size_t)e * nd + n) * nd + j) * Nd + i] +
                              Ja[(((size_t)e * nd + n) * nd + j) * Nd + k];
-            orc_flux_ranocha_cart(ui, uk, nd, gamma, j, F);
+            orc_flux_cart(flux, ui, uk, nd, gamma, j, F);
             for (int c = 0; c < nv; ++c) {
               const double term = D[ii[n] * N + kn] * a * F[c];
               acc[c] += scale_mode ? fabs(term) : term;
@@ -484,7 +513,7 @@ int orc_rhs(int nd, int p, const int* nelem, const double* Ja, const double* J, 
             m[j] = sgn * Ja[(((size_t)e * nd + n) * nd + j) * Nd + i];
             mf[j] = side == 0 ? m[j] : -Ja[(((size_t)enb * nd + n) * nd + j) * Nd + inb];
           }
-          orc_surface_flux(ui, unb, nd, gamma, mf, llf, fstar);
+          orc_surface_flux(flux, ui, unb, nd, gamma, mf, llf, fstar);
           for (int j = 0; j < nd; ++j) {
             orc_euler_flux(ui, nd, gamma, j, fj);
             for (int c = 0; c < nv; ++c) fn[c] += m[j] * fj[c];
@@ -575,8 +604,8 @@ void orc_ck45_coeffs(double* A, double* B) {
   }
 }
 
-int orc_rk_step(int scheme, int nd, int p, const int* nelem, const double* Ja, const double* J, double gamma, int llf,
-                double dt, double* u) {
+int orc_rk_step(int scheme, int nd, int p, const int* nelem, const double* Ja, const double* J, double gamma, int flux,
+                int llf, double dt, double* u) {
   const int N = p + 1, Nd = orc_ipow(N, nd), nv = nd + 2;
   const int E = nelem[0] * nelem[1] * (nd == 3 ? nelem[2] : 1);
   const size_t n = (size_t)E * nv * Nd;
@@ -584,13 +613,13 @@ int orc_rk_step(int scheme, int nd, int p, const int* nelem, const double* Ja, c
     double* k[4];
     double* y = (double*)malloc(sizeof(double) * n);
     for (int s = 0; s < 4; ++s) k[s] = (double*)malloc(sizeof(double) * n);
-    orc_rhs(nd, p, nelem, Ja, J, u, gamma, llf, 0, E, 0, k[0]);
+    orc_rhs(nd, p, nelem, Ja, J, u, gamma, flux, llf, 0, E, 0, k[0]);
     for (size_t q = 0; q < n; ++q) y[q] = u[q] + 0.5 * dt * k[0][q];
-    orc_rhs(nd, p, nelem, Ja, J, y, gamma, llf, 0, E, 0, k[1]);
+    orc_rhs(nd, p, nelem, Ja, J, y, gamma, flux, llf, 0, E, 0, k[1]);
     for (size_t q = 0; q < n; ++q) y[q] = u[q] + 0.5 * dt * k[1][q];
-    orc_rhs(nd, p, nelem, Ja, J, y, gamma, llf, 0, E, 0, k[2]);
+    orc_rhs(nd, p, nelem, Ja, J, y, gamma, flux, llf, 0, E, 0, k[2]);
     for (size_t q = 0; q < n; ++q) y[q] = u[q] + dt * k[2][q];
-    orc_rhs(nd, p, nelem, Ja, J, y, gamma, llf, 0, E, 0, k[3]);
+    orc_rhs(nd, p, nelem, Ja, J, y, gamma, flux, llf, 0, E, 0, k[3]);
     for (size_t q = 0; q < n; ++q) u[q] += dt / 6.0 * (k[0][q] + 2.0 * k[1][q] + 2.0 * k[2][q] + k[3][q]);
     free(y);
     for (int s = 0; s < 4; ++s) free(k[s]);
@@ -600,7 +629,7 @@ int orc_rk_step(int scheme, int nd, int p, const int* nelem, const double* Ja, c
     double* K = (double*)calloc(n, sizeof(double));
     double* f = (double*)malloc(sizeof(double) * n);
     for (int s = 0; s < 5; ++s) {
-      orc_rhs(nd, p, nelem, Ja, J, u, gamma, llf, 0, E, 0, f);
+      orc_rhs(nd, p, nelem, Ja, J, u, gamma, flux, llf, 0, E, 0, f);
       for (size_t q = 0; q < n; ++q) {
         K[q] = ORC_CK_A[s] * K[q] + dt * f[q];
         u[q] += ORC_CK_B[s] * K[q];

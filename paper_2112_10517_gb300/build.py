@@ -22,10 +22,11 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", os.path.join(ROOT, "include")]
 
 LIBS = {
-    "libdg.so": ["host.cu", "volume.cu", "interface.cu", "misc.cu", "noalloc.cu", "batch.cu", "vjp.cu"],
+    "libdg.so": ["host.cu", "volume.cu", "volume_2d_f64.cu", "volume_2d_f32.cu", "volume_3d_f64.cu",
+                 "volume_3d_f32.cu", "interface.cu", "misc.cu", "noalloc.cu", "batch.cu", "vjp.cu"],
     "libdgpeaks.so": ["peaks.cu"],
 }
-HEADERS = ["dg_internal.h", "kernels.cuh", "dgmath.cuh"]
+HEADERS = ["dg_internal.h", "kernels.cuh", "dgmath.cuh", "volume_impl.cuh"]
 
 
 def _nvcc() -> str:

@@ -92,6 +92,16 @@ size_t batch_smem(int p, int precision, int threads) {
   return per * batch_epb(p, precision, threads);
 }
 
+// batches use Ranocha's flux on the instances' metric arrays (a compile-time variant, so only that loop is built)
+__device__ __forceinline__ Variant general_variant() {
+  Variant v;
+  v.flux = 0;
+  v.cart = 0;
+  v.jn[0] = v.jn[1] = v.jn[2] = 0.0;
+  v.invJ = 0.0;
+  return v;
+}
+
 template <typename T, bool LLF>
 __global__ void __launch_bounds__(256) batch_interface_kernel(const BatchInst* __restrict__ insts, int n,
                                                               long long total, T gamma) {
@@ -109,11 +119,11 @@ __global__ void __launch_bounds__(256) batch_interface_kernel(const BatchInst* _
   const T* ja = static_cast<const T*>(in.Ja);
   T* face = static_cast<T*>(in.face);
   switch (in.p) {
-    case 1: interface_node<3, 2, T, LLF>(u, ja, face, in.md, gamma, in.flag, idx); break;
-    case 2: interface_node<3, 3, T, LLF>(u, ja, face, in.md, gamma, in.flag, idx); break;
-    case 3: interface_node<3, 4, T, LLF>(u, ja, face, in.md, gamma, in.flag, idx); break;
-    case 4: interface_node<3, 5, T, LLF>(u, ja, face, in.md, gamma, in.flag, idx); break;
-    case 5: interface_node<3, 6, T, LLF>(u, ja, face, in.md, gamma, in.flag, idx); break;
+    case 1: interface_node<3, 2, T, LLF, 0>(u, ja, face, in.md, gamma, in.flag, idx, general_variant()); break;
+    case 2: interface_node<3, 3, T, LLF, 0>(u, ja, face, in.md, gamma, in.flag, idx, general_variant()); break;
+    case 3: interface_node<3, 4, T, LLF, 0>(u, ja, face, in.md, gamma, in.flag, idx, general_variant()); break;
+    case 4: interface_node<3, 5, T, LLF, 0>(u, ja, face, in.md, gamma, in.flag, idx, general_variant()); break;
+    case 5: interface_node<3, 6, T, LLF, 0>(u, ja, face, in.md, gamma, in.flag, idx, general_variant()); break;
     default: break;
   }
 }
@@ -125,7 +135,7 @@ __device__ __forceinline__ void batch_tile(const BatchInst& in, int e0, T gamma,
   none.mode = EPI_STORE;
   volume_tile<3, N, T, EPB, EPI_STORE, THREADS>(in.u, static_cast<const T*>(in.Ja), in.invJ,
                                                 static_cast<const T*>(in.face), in.du, in.md, ConstOp<N, T>::get(),
-                                                gamma, in.flag, none, e0, smem);
+                                                gamma, in.flag, none, e0, smem, general_variant());
 }
 
 template <typename T, int THREADS>
@@ -315,7 +325,7 @@ dg_status dg_batch_create(dg_batch** out, dg_ctx* const* ctxs, int n, const doub
     if (c->device != c0->device || c->precision != c0->precision || c->surface_flux != c0->surface_flux ||
         c->gamma != c0->gamma)
       return DG_ERR_ARG;
-    if (c->nd != 3 || c->p > dgk::kBatchMaxP) return DG_ERR_UNSUPPORTED;
+    if (c->nd != 3 || c->p > dgk::kBatchMaxP || c->volume_flux != DG_VOL_RANOCHA) return DG_ERR_UNSUPPORTED;
     if (((uintptr_t)u[i] | (uintptr_t)du[i]) & 7) return DG_ERR_ARG;
     const size_t bytes = (size_t)c->state_len * sizeof(double);
     const char *ub = (const char*)u[i], *db = (const char*)du[i];

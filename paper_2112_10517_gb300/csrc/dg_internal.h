@@ -42,14 +42,23 @@ struct Epilogue {
   double* acc;     // RK4: accumulated sum of b_s dt k_s
 };
 
+// Runtime variant of the RHS kernels (uniform over a launch): the two-point flux and the Cartesian
+// specialisation of affine axis-aligned meshes, whose metric terms are the constants Ja^n = jn[n] e_n and J = 1/invJ.
+struct Variant {
+  int flux;      // DG_VOL_RANOCHA or DG_VOL_SHIMA (volume and surface)
+  int cart;      // 1: constant diagonal metrics from jn/invJ, the metric arrays are not read
+  double jn[3];  // Ja^n_n of a Cartesian mesh
+  double invJ;   // 1/J of a Cartesian mesh
+};
+
 // RHS kernels. Each returns the launch error. Ja is FP64 for precision DG_FP64 and FP32 for DG_FP32; the face
 // buffer holds the same type.
 cudaError_t launch_interface(int nd, int p, int precision, int llf, MeshDims md, const double* u, const void* Ja,
-                             void* face, double gamma, int* flag, cudaStream_t s);
+                             void* face, double gamma, int* flag, cudaStream_t s, const Variant* var = nullptr);
 // epi == nullptr stores du; otherwise du is unused and the stage update of *epi is applied.
 cudaError_t launch_volume(int nd, int p, int precision, MeshDims md, const double* u, const void* Ja, const double* invJ,
                           const void* face, double* du, double gamma, int* flag, cudaStream_t s,
-                          const Epilogue* epi = nullptr);
+                          const Epilogue* epi = nullptr, const Variant* var = nullptr);
 // Entropy-rate partial sums into partial[nblocks][2]; then a single block reduces into out[2].
 cudaError_t launch_entropy_rate(int nd, int p, MeshDims md, const double* u, const double* du, const double* JW,
                                 double gamma, double* partial, int nblocks, double* out, cudaStream_t s);
@@ -66,6 +75,7 @@ struct dg_ctx {
   long long E, ndofs, state_len;
   double gamma;
   int precision, surface_flux, volume_flux;
+  dgk::Variant var;  // flux and Cartesian specialisation used by dg_rhs / dg_step
   // host copies (FP64)
   double* h_xyz;  // [E][nd][Nd]
   double* h_Ja;   // [E][nd][nd][Nd]

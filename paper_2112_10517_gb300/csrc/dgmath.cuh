@@ -180,6 +180,75 @@ __device__ __forceinline__ void ranocha_flux8(const T* a, const T* b, const T* n
   F[ND + 1] = q * (vv + a[Q::PG] * b[Q::PP] * Li) + (a[Q::PP] * B + b[Q::PP] * A);
 }
 
+// ---------------------------------------------------------------------------------------------------
+// Flux of Shima et al. (Sec. 3.2, Eq. flux_shima_etal; kinetic energy and pressure equilibrium preserving, the
+// paper's "cheap" flux), scaled by 8 like ranocha_flux8. With A = v_a.n2, B = v_b.n2, q = (rho_a + rho_b)(A + B):
+//   F_rho  = q                                              (8 {{rho}} {{v.n}})
+//   F_rhov = q (v_a + v_b)/2 + (pp_a + pp_b) n2              (8 (f_rho {{v}} + {{p}} n))
+//   F_rhoe = q v_a.v_b/2 + (pg_a + pg_b)(A + B)/2 + pp_a B + pp_b A
+//                                                          (8 (f_rho ((v;v))/2 + {{p}}{{v.n}}/(gamma-1) + ((p; v.n))))
+// ---------------------------------------------------------------------------------------------------
+template <int ND, typename T>
+__device__ __forceinline__ void shima_flux8(const T* a, const T* b, const T* n2, T* F) {
+  using Q = NodeQ<ND>;
+  T A = a[1] * n2[0], B = b[1] * n2[0], vv = a[1] * b[1];
+#pragma unroll
+  for (int j = 1; j < ND; ++j) {
+    A += a[1 + j] * n2[j];
+    B += b[1 + j] * n2[j];
+    vv += a[1 + j] * b[1 + j];
+  }
+  const T AB = A + B;
+  const T q = (a[Q::RHO] + b[Q::RHO]) * AB;
+  const T hq = T(0.5) * q;
+  const T ps = a[Q::PP] + b[Q::PP];
+  F[0] = q;
+#pragma unroll
+  for (int j = 0; j < ND; ++j) F[1 + j] = hq * (a[1 + j] + b[1 + j]) + ps * n2[j];
+  F[ND + 1] = hq * vv + T(0.5) * (a[Q::PG] + b[Q::PG]) * AB + (a[Q::PP] * B + b[Q::PP] * A);
+}
+
+// ---------------------------------------------------------------------------------------------------
+// The same fluxes on a Cartesian (affine, axis-aligned) element: the averaged contravariant vector of direction n
+// has the single component n2n = 2 Ja^n_n along axis n, so v.n2 is one product and the pressure acts on one
+// momentum component (van, vbn: the velocity components along n).
+// ---------------------------------------------------------------------------------------------------
+template <int ND, typename T, int FLUX>
+__device__ __forceinline__ void pair_flux8_cart(const T* a, const T* b, T van, T vbn, T n2n, int n, T* F) {
+  using Q = NodeQ<ND>;
+  const T A = van * n2n, B = vbn * n2n;
+  T vv = a[1] * b[1];
+#pragma unroll
+  for (int j = 1; j < ND; ++j) vv += a[1 + j] * b[1 + j];
+  const T pn = (a[Q::PP] + b[Q::PP]) * n2n;
+  T qv, e;
+  if (FLUX == 0) {
+    T L, Li;
+    log_means<T>(a[Q::RHO], b[Q::RHO], a[Q::RHO] * b[Q::PP], b[Q::RHO] * a[Q::PP], L, Li);
+    const T q = L * (A + B);
+    F[0] = q + q;
+    qv = q;
+    e = q * (vv + a[Q::PG] * b[Q::PP] * Li);
+  } else {
+    const T AB = A + B;
+    const T q = (a[Q::RHO] + b[Q::RHO]) * AB;
+    F[0] = q;
+    qv = T(0.5) * q;
+    e = qv * vv + T(0.5) * (a[Q::PG] + b[Q::PG]) * AB;
+  }
+#pragma unroll
+  for (int j = 0; j < ND; ++j) F[1 + j] = qv * (a[1 + j] + b[1 + j]) + (j == n ? pn : T(0));
+  F[ND + 1] = e + (a[Q::PP] * B + b[Q::PP] * A);
+}
+
+template <int ND, typename T, int FLUX>
+__device__ __forceinline__ void pair_flux8(const T* a, const T* b, const T* n2, T* F) {
+  if (FLUX == 0)
+    ranocha_flux8<ND, T>(a, b, n2, F);
+  else
+    shima_flux8<ND, T>(a, b, n2, F);
+}
+
 }  // namespace dgk
 
 namespace dgk {

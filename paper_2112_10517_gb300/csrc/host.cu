@@ -306,7 +306,7 @@ dg_status dg_init(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metri
   if (mesh->mapping < DG_MAP_AFFINE || mesh->mapping > DG_MAP_NODES) return DG_ERR_ARG;
   if (mesh->mapping == DG_MAP_NODES && !mesh->node_xyz_host) return DG_ERR_ARG;
   if (!(opts->gamma > 1.0)) return DG_ERR_ARG;
-  if (opts->volume_flux != DG_VOL_RANOCHA) return DG_ERR_UNSUPPORTED;
+  if (opts->volume_flux != DG_VOL_RANOCHA && opts->volume_flux != DG_VOL_SHIMA) return DG_ERR_ARG;
   if (opts->surface_flux != DG_SURF_EC && opts->surface_flux != DG_SURF_EC_LLF) return DG_ERR_ARG;
   if (opts->precision != DG_FP64 && opts->precision != DG_FP32) return DG_ERR_ARG;
   for (int r = 0; r < 5; ++r)
@@ -341,6 +341,18 @@ dg_status dg_init(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metri
   c->precision = opts->precision;
   c->surface_flux = opts->surface_flux;
   c->volume_flux = opts->volume_flux;
+  // Cartesian specialisation: an affine box mesh has Ja^n = (prod_{k != n} h_k/2) e_n and J = prod_k h_k/2
+  c->var.flux = opts->volume_flux;
+  c->var.cart = (mesh->mapping == DG_MAP_AFFINE && !(metrics && metrics->Ja_host)) ? 1 : 0;
+  {
+    double hh[3] = {1.0, 1.0, 1.0}, jac = 1.0;
+    for (int d = 0; d < nd; ++d) {
+      hh[d] = 0.5 * (mesh->hi[d] - mesh->lo[d]) / mesh->nelem[d];
+      jac *= hh[d];
+    }
+    for (int d = 0; d < 3; ++d) c->var.jn[d] = d < nd ? jac / hh[d] : 0.0;
+    c->var.invJ = 1.0 / jac;
+  }
 
   const dgk::RefTables& t = dgk::ref_tables(polydeg);
   const size_t nx = (size_t)E * nd * Nd, nja = (size_t)E * nd * nd * Nd, nj = (size_t)E * Nd;
@@ -436,11 +448,12 @@ dg_status dg_rhs(dg_ctx* c, const double* u, double* du, double t, dg_stream_t s
   dgk::prof_begin(c, dgk::KID_INTERFACE, s, &slot);
   const void* ja = c->precision == DG_FP32 ? (const void*)c->d_Ja32 : (const void*)c->d_Ja;
   cudaError_t e = dgk::launch_interface(c->nd, c->p, c->precision, c->surface_flux == DG_SURF_EC_LLF, c->md, u, ja,
-                                        c->d_face, c->gamma, c->d_flag, s);
+                                        c->d_face, c->gamma, c->d_flag, s, &c->var);
   dgk::prof_end(c, s, slot);
   if (e != cudaSuccess) return cuda_status(e);
   dgk::prof_begin(c, dgk::KID_VOLUME, s, &slot);
-  e = dgk::launch_volume(c->nd, c->p, c->precision, c->md, u, ja, c->d_invJ, c->d_face, du, c->gamma, c->d_flag, s);
+  e = dgk::launch_volume(c->nd, c->p, c->precision, c->md, u, ja, c->d_invJ, c->d_face, du, c->gamma, c->d_flag, s,
+                         nullptr, &c->var);
   dgk::prof_end(c, s, slot);
   return cuda_status(e);
 }
@@ -473,13 +486,13 @@ dg_status dg_step(dg_ctx* c, double* u, double* scratch, double t, double dt, in
     int slot;
     dgk::prof_begin(c, dgk::KID_INTERFACE, s, &slot);
     cudaError_t e = dgk::launch_interface(c->nd, c->p, c->precision, c->surface_flux == DG_SURF_EC_LLF, c->md, in,
-                                          ja, c->d_face, c->gamma, c->d_flag, s);
+                                          ja, c->d_face, c->gamma, c->d_flag, s, &c->var);
     dgk::prof_end(c, s, slot);
     if (e != cudaSuccess) return cuda_status(e);
     // volume term with the stage update fused into its epilogue (no du round trip, no update kernel)
     dgk::prof_begin(c, dgk::KID_VOLUME, s, &slot);
     e = dgk::launch_volume(c->nd, c->p, c->precision, c->md, in, ja, c->d_invJ, c->d_face, nullptr, c->gamma,
-                           c->d_flag, s, &epi);
+                           c->d_flag, s, &epi, &c->var);
     dgk::prof_end(c, s, slot);
     if (e != cudaSuccess) return cuda_status(e);
   }

@@ -6,30 +6,30 @@ namespace {
 
 template <int ND, int N, typename T>
 cudaError_t launch_interface_t(int llf, MeshDims md, const double* u, const T* Ja, T* face, double gamma, int* flag,
-                               cudaStream_t s) {
+                               cudaStream_t s, const Variant& var) {
   const long long total = (long long)ND * md.E * Geo<ND, N>::NL;
   const int threads = 256;
   const long long blocks = (total + threads - 1) / threads;
   if (llf)
-    interface_kernel<ND, N, T, true><<<(unsigned)blocks, threads, 0, s>>>(u, Ja, face, md, (T)gamma, flag);
+    interface_kernel<ND, N, T, true><<<(unsigned)blocks, threads, 0, s>>>(u, Ja, face, md, (T)gamma, flag, var);
   else
-    interface_kernel<ND, N, T, false><<<(unsigned)blocks, threads, 0, s>>>(u, Ja, face, md, (T)gamma, flag);
+    interface_kernel<ND, N, T, false><<<(unsigned)blocks, threads, 0, s>>>(u, Ja, face, md, (T)gamma, flag, var);
   return cudaGetLastError();
 }
 
 template <int ND, typename T>
 cudaError_t dispatch_p(int p, int llf, MeshDims md, const double* u, const void* Ja, void* face, double gamma,
-                       int* flag, cudaStream_t s) {
+                       int* flag, cudaStream_t s, const Variant& var) {
   const T* ja = static_cast<const T*>(Ja);
   T* fc = static_cast<T*>(face);
   switch (p) {
-    case 1: return launch_interface_t<ND, 2, T>(llf, md, u, ja, fc, gamma, flag, s);
-    case 2: return launch_interface_t<ND, 3, T>(llf, md, u, ja, fc, gamma, flag, s);
-    case 3: return launch_interface_t<ND, 4, T>(llf, md, u, ja, fc, gamma, flag, s);
-    case 4: return launch_interface_t<ND, 5, T>(llf, md, u, ja, fc, gamma, flag, s);
-    case 5: return launch_interface_t<ND, 6, T>(llf, md, u, ja, fc, gamma, flag, s);
-    case 6: return launch_interface_t<ND, 7, T>(llf, md, u, ja, fc, gamma, flag, s);
-    case 7: return launch_interface_t<ND, 8, T>(llf, md, u, ja, fc, gamma, flag, s);
+    case 1: return launch_interface_t<ND, 2, T>(llf, md, u, ja, fc, gamma, flag, s, var);
+    case 2: return launch_interface_t<ND, 3, T>(llf, md, u, ja, fc, gamma, flag, s, var);
+    case 3: return launch_interface_t<ND, 4, T>(llf, md, u, ja, fc, gamma, flag, s, var);
+    case 4: return launch_interface_t<ND, 5, T>(llf, md, u, ja, fc, gamma, flag, s, var);
+    case 5: return launch_interface_t<ND, 6, T>(llf, md, u, ja, fc, gamma, flag, s, var);
+    case 6: return launch_interface_t<ND, 7, T>(llf, md, u, ja, fc, gamma, flag, s, var);
+    case 7: return launch_interface_t<ND, 8, T>(llf, md, u, ja, fc, gamma, flag, s, var);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -37,13 +37,15 @@ cudaError_t dispatch_p(int p, int llf, MeshDims md, const double* u, const void*
 }  // namespace
 
 cudaError_t launch_interface(int nd, int p, int precision, int llf, MeshDims md, const double* u, const void* Ja,
-                             void* face, double gamma, int* flag, cudaStream_t s) {
+                             void* face, double gamma, int* flag, cudaStream_t s, const Variant* var) {
   if (md.E <= 0) return cudaSuccess;
+  Variant v{};  // default: Ranocha's flux, metric arrays
+  if (var) v = *var;
   if (nd == 2)
-    return precision == DG_FP32 ? dispatch_p<2, float>(p, llf, md, u, Ja, face, gamma, flag, s)
-                                : dispatch_p<2, double>(p, llf, md, u, Ja, face, gamma, flag, s);
-  return precision == DG_FP32 ? dispatch_p<3, float>(p, llf, md, u, Ja, face, gamma, flag, s)
-                              : dispatch_p<3, double>(p, llf, md, u, Ja, face, gamma, flag, s);
+    return precision == DG_FP32 ? dispatch_p<2, float>(p, llf, md, u, Ja, face, gamma, flag, s, v)
+                                : dispatch_p<2, double>(p, llf, md, u, Ja, face, gamma, flag, s, v);
+  return precision == DG_FP32 ? dispatch_p<3, float>(p, llf, md, u, Ja, face, gamma, flag, s, v)
+                              : dispatch_p<3, double>(p, llf, md, u, Ja, face, gamma, flag, s, v);
 }
 
 }  // namespace dgk

@@ -36,6 +36,9 @@ struct Geo {
   }
 };
 
+// Ja^n_n of a Cartesian mesh for direction n (selects, no dynamic indexing of the parameter struct)
+__device__ __forceinline__ double cart_jn(const Variant& v, int n) { return n == 0 ? v.jn[0] : (n == 1 ? v.jn[1] : v.jn[2]); }
+
 // element neighbour across direction n (dir = +1 or -1), periodic
 __device__ __forceinline__ int neighbor(const MeshDims& md, int e, int n, int dir) {
   int e1 = e % md.n1, t = e / md.n1, e2 = t % md.n2, e3 = t / md.n2;
@@ -58,11 +61,12 @@ struct OpTable {
 // lambda = max(|v_L.m| + c_L|m|, |v_R.m| + c_R|m|), c = sqrt(gamma p/rho).
 // face layout [n][E][NV][NL].
 // ---------------------------------------------------------------------------------------------------
-// Interface flux at face node `idx` of a mesh, idx = (n * E + e) * NL + fn.
-template <int ND, int N, typename T, bool LLF>
+// Interface flux at face node `idx` of a mesh, idx = (n * E + e) * NL + fn. FLUX: 0 Ranocha, 1 Shima et al.
+// cart: metric terms are the Cartesian constants of `var` (Ja is not read).
+template <int ND, int N, typename T, bool LLF, int FLUX>
 __device__ __forceinline__ void interface_node(const double* __restrict__ u, const T* __restrict__ Ja,
                                                T* __restrict__ face, const MeshDims& md, T gamma, int* flag,
-                                               long long idx) {
+                                               long long idx, const Variant& var) {
   using G = Geo<ND, N>;
   const int fn = (int)(idx % G::NL);
   const long long t = idx / G::NL;
@@ -83,14 +87,14 @@ __device__ __forceinline__ void interface_node(const double* __restrict__ u, con
   T m[ND], m2[ND];
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
-    m[j] = Ja[(((size_t)e * ND + n) * ND + j) * G::NDOF + nodeL];
+    m[j] = var.cart ? (j == n ? (T)cart_jn(var, n) : T(0)) : Ja[(((size_t)e * ND + n) * ND + j) * G::NDOF + nodeL];
     m2[j] = m[j] + m[j];
   }
   const T gm1 = gamma - T(1);
   T qL[NodeQ<ND>::NQ], qR[NodeQ<ND>::NQ], f[G::NV];
   const bool ok = node_quantities<ND, T>(uL, gm1, T(2) / gm1, qL) & node_quantities<ND, T>(uR, gm1, T(2) / gm1, qR);
   if (!ok) atomicOr(flag, 1);
-  ranocha_flux8<ND, T>(qL, qR, m2, f);
+  pair_flux8<ND, T, FLUX>(qL, qR, m2, f);
 #pragma unroll
   for (int c = 0; c < G::NV; ++c) f[c] *= T(0.125);
   if (LLF) {
@@ -121,10 +125,15 @@ __device__ __forceinline__ void interface_node(const double* __restrict__ u, con
 
 template <int ND, int N, typename T, bool LLF>
 __global__ void __launch_bounds__(256) interface_kernel(const double* __restrict__ u, const T* __restrict__ Ja,
-                                                        T* __restrict__ face, MeshDims md, T gamma, int* flag) {
+                                                        T* __restrict__ face, MeshDims md, T gamma, int* flag,
+                                                        Variant var) {
   const long long total = (long long)ND * md.E * Geo<ND, N>::NL;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx < total) interface_node<ND, N, T, LLF>(u, Ja, face, md, gamma, flag, idx);
+  if (idx >= total) return;
+  if (var.flux == 0)
+    interface_node<ND, N, T, LLF, 0>(u, Ja, face, md, gamma, flag, idx, var);
+  else
+    interface_node<ND, N, T, LLF, 1>(u, Ja, face, md, gamma, flag, idx, var);
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -164,13 +173,63 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // EPI selects the epilogue: store du, or apply a Runge-Kutta stage update (in place of a separate kernel; the
 // stage arithmetic is the same as rk4_kernel / rk_ck45_kernel). With a stage update the kernel writes arrays
 // that alias its input u (the CTA has read its own elements before the barrier; no other CTA reads them).
+// The pairs i < k of one line (Sec. 2.2): sp/sj point at the line's first node in the node-quantity and metric
+// arrays (stride st), sa at its accumulator slots; each pair's flux is evaluated once and added to both nodes.
+template <int ND, int N, typename T, int FLUX, bool CART>
+__device__ __forceinline__ void line_pairs(const T* sp, const T* sj, int st, int n, T n2n, const OpTable<N, T>& op,
+                                           T* sa) {
+  using G = Geo<ND, N>;
+  constexpr int NQ = NodeQ<ND>::NQ;
+  T acc[N][G::NV];
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int c = 0; c < G::NV; ++c) acc[i][c] = T(0);
+#pragma unroll
+  for (int i = 0; i < N - 1; ++i) {
+    T a[NQ], ja_i[ND], va_n = T(0);
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) a[c] = sp[c * G::NDOF + i * st];
+    if (CART) {
+      va_n = sp[(1 + n) * G::NDOF + i * st];
+    } else {
+#pragma unroll
+      for (int j = 0; j < ND; ++j) ja_i[j] = sj[j * G::NDOF + i * st];
+    }
+#pragma unroll
+    for (int k = i + 1; k < N; ++k) {
+      T b[NQ], f[G::NV];
+#pragma unroll
+      for (int c = 0; c < NQ; ++c) b[c] = sp[c * G::NDOF + k * st];
+      if (CART) {
+        pair_flux8_cart<ND, T, FLUX>(a, b, va_n, sp[(1 + n) * G::NDOF + k * st], n2n, n, f);
+      } else {
+        T n2[ND];
+#pragma unroll
+        for (int j = 0; j < ND; ++j) n2[j] = ja_i[j] + sj[j * G::NDOF + k * st];
+        pair_flux8<ND, T, FLUX>(a, b, n2, f);
+      }
+      const T dik = op.Dt8[i * N + k], dki = op.Dt8[k * N + i];
+#pragma unroll
+      for (int c = 0; c < G::NV; ++c) {
+        acc[i][c] += dik * f[c];
+        acc[k][c] += dki * f[c];
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int c = 0; c < G::NV; ++c) sa[c * G::NDOF + i * st] = acc[i][c];
+}
+
 // One tile of EPB elements starting at element e0, computed by the kThreads threads of a CTA (kThreads >=
 // EPB * TPE; threads beyond EPB * TPE only join the cooperative loops). smem_raw holds VolumeSmem::bytes(EPB).
 template <int ND, int N, typename T, int EPB, int EPI, int kThreads>
 __device__ __forceinline__ void volume_tile(const double* u, const T* __restrict__ Ja, const double* __restrict__ invJ,
                                             const T* __restrict__ face, double* du, const MeshDims& md,
                                             const OpTable<N, T>& op, T gamma, int* flag, const Epilogue& epi, int e0,
-                                            unsigned char* smem_raw) {
+                                            unsigned char* smem_raw, const Variant& var) {
   using G = Geo<ND, N>;
   using S = VolumeSmem<ND, N, T>;
   static_assert(kThreads >= EPB * G::TPE, "a tile needs one thread per element line");
@@ -212,52 +271,27 @@ __device__ __forceinline__ void volume_tile(const double* u, const T* __restrict
     for (int c = 0; c < NQ; ++c) s_prim[(el * NQ + c) * G::NDOF + i] = q[c];
   }
   if (!ok) atomicOr(flag, 1);
-  {
+  if (!var.cart) {
     const T* jae = Ja + (size_t)e0 * S::kJa;
     for (int idx = tid; idx < nel * S::kJa; idx += kThreads) s_ja[idx] = jae[idx];
   }
   __syncthreads();
 
-  // ---- B: pairs along lines
+  // ---- B: pairs along lines (the flux and the Cartesian specialisation select one of four loop bodies)
   if (tid < nel * G::TPE) {
     const int el = tid / G::TPE, r = tid - el * G::TPE;
     const int n = r / G::NL, l = r - n * G::NL;
     const int st = G::stride(n), base = G::line_base(n, l);
     const T* sp = s_prim + el * S::kPrim + base;
     const T* sj = s_ja + (el * ND + n) * ND * G::NDOF + base;
-    T acc[N][G::NV];
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-#pragma unroll
-      for (int c = 0; c < G::NV; ++c) acc[i][c] = T(0);
-#pragma unroll
-    for (int i = 0; i < N - 1; ++i) {
-      T a[NQ], ja_i[ND];
-#pragma unroll
-      for (int c = 0; c < NQ; ++c) a[c] = sp[c * G::NDOF + i * st];
-#pragma unroll
-      for (int j = 0; j < ND; ++j) ja_i[j] = sj[j * G::NDOF + i * st];
-#pragma unroll
-      for (int k = i + 1; k < N; ++k) {
-        T b[NQ], n2[ND], f[G::NV];
-#pragma unroll
-        for (int c = 0; c < NQ; ++c) b[c] = sp[c * G::NDOF + k * st];
-#pragma unroll
-        for (int j = 0; j < ND; ++j) n2[j] = ja_i[j] + sj[j * G::NDOF + k * st];
-        ranocha_flux8<ND, T>(a, b, n2, f);
-        const T dik = op.Dt8[i * N + k], dki = op.Dt8[k * N + i];
-#pragma unroll
-        for (int c = 0; c < G::NV; ++c) {
-          acc[i][c] += dik * f[c];
-          acc[k][c] += dki * f[c];
-        }
-      }
-    }
     T* sa = s_acc + (el * ND + n) * G::NV * G::NDOF + base;
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-#pragma unroll
-      for (int c = 0; c < G::NV; ++c) sa[c * G::NDOF + i * st] = acc[i][c];
+    const T n2n = T(2) * (T)cart_jn(var, n);
+    switch (var.flux * 2 + var.cart) {
+      case 0: line_pairs<ND, N, T, 0, false>(sp, sj, st, n, n2n, op, sa); break;
+      case 1: line_pairs<ND, N, T, 0, true>(sp, sj, st, n, n2n, op, sa); break;
+      case 2: line_pairs<ND, N, T, 1, false>(sp, sj, st, n, n2n, op, sa); break;
+      default: line_pairs<ND, N, T, 1, true>(sp, sj, st, n, n2n, op, sa); break;
+    }
   }
   __syncthreads();
 
@@ -289,8 +323,9 @@ __device__ __forceinline__ void volume_tile(const double* u, const T* __restrict
         for (int c = 0; c < G::NV; ++c) tot[c] += sgn * fp[c * G::NL];
       }
     }
-    const double sj = -invJ[(size_t)ge * G::NDOF + i];
-    const T sjT = sizeof(T) == 8 ? T(0) : -to_flux<T>(invJ[(size_t)ge * G::NDOF + i]);
+    const double ij = var.cart ? var.invJ : invJ[(size_t)ge * G::NDOF + i];
+    const double sj = -ij;
+    const T sjT = sizeof(T) == 8 ? T(0) : -to_flux<T>(ij);
     const size_t off = (size_t)ge * G::NV * G::NDOF + i;
 #pragma unroll
     for (int c = 0; c < G::NV; ++c) {
@@ -329,10 +364,10 @@ template <int ND, int N, typename T, int EPB, int EPI>
 __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE)
     volume_kernel(const double* u, const T* __restrict__ Ja, const double* __restrict__ invJ,
                   const T* __restrict__ face, double* du, MeshDims md, OpTable<N, T> op, T gamma, int* flag,
-                  Epilogue epi) {
+                  Epilogue epi, Variant var) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   volume_tile<ND, N, T, EPB, EPI, EPB * Geo<ND, N>::TPE>(u, Ja, invJ, face, du, md, op, gamma, flag, epi,
-                                                         blockIdx.x * EPB, smem_raw);
+                                                         blockIdx.x * EPB, smem_raw, var);
 }
 
 }  // namespace dgk

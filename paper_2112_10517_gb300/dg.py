@@ -26,7 +26,8 @@ DG_OK, DG_ERR_ARG, DG_ERR_CUDA, DG_ERR_OOM, DG_ERR_UNSUPPORTED, DG_ERR_NONPHYSIC
 DG_MAP_AFFINE, DG_MAP_SINE, DG_MAP_NODES = 0, 1, 2
 DG_SURF_EC, DG_SURF_EC_LLF = 0, 1
 DG_FP64, DG_FP32 = 0, 1
-DG_VOL_RANOCHA = 0
+DG_VOL_RANOCHA, DG_VOL_SHIMA = 0, 1
+FLUXES = {"ranocha": DG_VOL_RANOCHA, "shima": DG_VOL_SHIMA}
 DG_RK4_CLASSIC, DG_LSRK45_CK = 0, 1
 KERNEL_VOLUME, KERNEL_INTERFACE = 0, 1
 
@@ -118,12 +119,14 @@ class DG:
     """One context of the flux-differencing LGL-DGSEM RHS on the current CUDA device.
 
     mapping: "affine", "sine" (x = xi + amp prod sin) or "nodes" (node_xyz [E, d, Nd] given).
-    surface: "ec" or "llf"; precision: "fp64" or "fp32".
+    surface: "ec" or "llf"; precision: "fp64" or "fp32"; flux: "ranocha" (Ranocha's EC/KEP/PEP flux) or
+    "shima" (the KEEP/PEP flux of Shima et al.), used in the volume and as the surface flux's central part.
+    An affine mesh without node or metric overrides runs the Cartesian specialisation (constant Ja, 1/J).
     """
 
     def __init__(self, ndims: int, nelem, polydeg: int, lo=None, hi=None, mapping: str = "affine", amp: float = 0.0,
                  node_xyz=None, Ja=None, J=None, gamma: float = 1.4, surface: str = "llf",
-                 precision: str = "fp64"):
+                 precision: str = "fp64", flux: str = "ranocha"):
         mesh = DgMesh()
         mesh.ndims = ndims
         ne = list(nelem) + [1] * (3 - len(nelem))
@@ -148,7 +151,7 @@ class DG:
             met = DgMetrics(_dptr(Ja), _dptr(J))
         opts = DgOpts()
         opts.gamma = gamma
-        opts.volume_flux = DG_VOL_RANOCHA
+        opts.volume_flux = FLUXES[flux]
         opts.surface_flux = {"ec": DG_SURF_EC, "llf": DG_SURF_EC_LLF}[surface]
         opts.precision = {"fp64": DG_FP64, "fp32": DG_FP32}[precision]
         ctx = ctypes.c_void_p()

@@ -26,12 +26,15 @@ def twisted_coords(nd, nelem, p, amp=0.1):
 class Scenario:
     """A mesh + state, with the oracle's metrics and (lazily) its RHS."""
 
-    def __init__(self, nd, nelem, p, mapping="sine", amp=0.1, box=None, ic="smooth", llf=True, seed=0):
+    def __init__(self, nd, nelem, p, mapping="sine", amp=0.1, box=None, ic="smooth", llf=True, seed=0,
+                 flux="ranocha"):
         self.nd, self.nelem, self.p = nd, list(nelem), p
-        self.mapping, self.amp, self.llf = mapping, amp, llf
+        self.mapping, self.amp, self.llf, self.flux = mapping, amp, llf, flux
         self.lo, self.hi = box if box is not None else ([-PI] * nd, [PI] * nd)
         if mapping == "twisted":
             self.xyz = twisted_coords(nd, nelem, p, amp)
+        elif mapping == "affine_nodes":  # affine coordinates handed over as nodes: the general (curved) code path
+            self.xyz = orc.coords(nd, nelem, self.lo, self.hi, p, mapping=0, amp=0.0)
         else:
             self.xyz = orc.coords(nd, nelem, self.lo, self.hi, p, mapping=1 if mapping == "sine" else 0,
                                   amp=amp if mapping == "sine" else 0.0)
@@ -63,19 +66,20 @@ class Scenario:
 
     def du_ref(self):
         if self._du is None:
-            self._du = orc.rhs(self.nd, self.p, self.nelem, self.Ja, self.J, self.u, llf=self.llf)
+            self._du = orc.rhs(self.nd, self.p, self.nelem, self.Ja, self.J, self.u, llf=self.llf, flux=self.flux)
         return self._du
 
     def du_scale(self):
         """(1/J) sum |terms| of the RHS sum at each node (oracle scale mode)."""
         if getattr(self, "_scale", None) is None:
-            self._scale = orc.rhs(self.nd, self.p, self.nelem, self.Ja, self.J, self.u, llf=self.llf, scale=True)
+            self._scale = orc.rhs(self.nd, self.p, self.nelem, self.Ja, self.J, self.u, llf=self.llf, scale=True,
+                                  flux=self.flux)
         return self._scale
 
     def dg_kwargs(self):
         kw = dict(ndims=self.nd, nelem=self.nelem, polydeg=self.p, lo=self.lo, hi=self.hi,
-                  surface="llf" if self.llf else "ec")
-        if self.mapping == "twisted":
+                  surface="llf" if self.llf else "ec", flux=self.flux)
+        if self.mapping in ("twisted", "affine_nodes"):
             kw.update(mapping="nodes", node_xyz=self.xyz)
         elif self.mapping == "sine":
             kw.update(mapping="sine", amp=self.amp)

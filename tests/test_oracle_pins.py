@@ -644,3 +644,70 @@ def test_dual_logmean_derivative_at_equal_arguments():
     eps = 1e-6
     fd = (orc.rhs(nd, p, nelem, Ja, J, u + eps * delta) - orc.rhs(nd, p, nelem, Ja, J, u - eps * delta)) / (2 * eps)
     np.testing.assert_allclose(jd, fd, rtol=0, atol=1e-6 * np.max(np.abs(jd)))
+
+
+# ------------------------------------------------------------------------------------------------
+# Flux of Shima et al. (Sec. 3.2, Eq. flux_shima_etal): consistent, symmetric, kinetic-energy and pressure-
+# equilibrium preserving, conservative and order-p accurate in the scheme, but not entropy conservative
+# ------------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nd", [2, 3])
+def test_shima_flux_consistency_symmetry_and_structure(nd):
+    n = 2000
+    a = random_states(n, nd, seed=30)
+    b = random_states(n, nd, seed=31)
+    m = np.random.Generator(np.random.PCG64(32)).standard_normal((n, nd))
+    phys = sum(m[:, j:j + 1] * orc.euler_flux(a, j, nd) for j in range(nd))
+    np.testing.assert_allclose(orc.flux_dir(a, a, m, nd, flux="shima"), phys, rtol=1e-13, atol=1e-13)
+    f = orc.flux_dir(a, b, m, nd, flux="shima")
+    np.testing.assert_allclose(f, orc.flux_dir(b, a, m, nd, flux="shima"), rtol=1e-14, atol=1e-14)
+    va, vb = a[:, 1:nd + 1] / a[:, :1], b[:, 1:nd + 1] / b[:, :1]
+    pa = (G - 1) * (a[:, -1] - 0.5 * np.sum(a[:, 1:nd + 1] * va, axis=1))
+    pb = (G - 1) * (b[:, -1] - 0.5 * np.sum(b[:, 1:nd + 1] * vb, axis=1))
+    vn = 0.5 * np.sum((va + vb) * m, axis=1)
+    # mass flux {{rho}}{{v.n}}; momentum f_rho {{v}} + {{p}} n; energy as printed
+    np.testing.assert_allclose(f[:, 0], 0.5 * (a[:, 0] + b[:, 0]) * vn, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(f[:, 1:nd + 1], f[:, :1] * 0.5 * (va + vb) + 0.5 * (pa + pb)[:, None] * m,
+                               rtol=1e-13, atol=1e-13)
+    ener = (f[:, 0] * 0.5 * np.sum(va * vb, axis=1) + 0.5 * (pa + pb) * vn / (G - 1)
+            + 0.5 * (pa * np.sum(vb * m, axis=1) + pb * np.sum(va * m, axis=1)))
+    np.testing.assert_allclose(f[:, -1], ener, rtol=1e-12, atol=1e-12)
+
+
+def test_shima_scheme_conservative_pep_not_ec():
+    nd, nelem, p = 3, [3, 2, 3], 3
+    xyz, Ja, J = mesh(nd, nelem, p, True)
+    u = inputs.random_state(xyz, seed=33)
+    du = orc.rhs(nd, p, nelem, Ja, J, u, llf=True, flux="shima")
+    tot, ab = orc.integrate(nd, p, J, du)
+    assert np.all(np.abs(tot) <= 1e-13 * ab)
+    du = orc.rhs(nd, p, nelem, Ja, J, u, llf=False, flux="shima")
+    s, ab = orc.entropy_rate(nd, p, J, u, du)
+    assert abs(s) > 1e-6 * ab  # not entropy conservative (contrast with Ranocha's flux)
+    v = [0.1, -0.2, 0.3]
+    u = inputs.pressure_equilibrium(xyz, seed=34, v=v)
+    du = orc.rhs(nd, p, nelem, Ja, J, u, llf=True, flux="shima")
+    scale = np.max(np.abs(du[:, 0]))
+    for j in range(nd):
+        np.testing.assert_allclose(du[:, 1 + j], v[j] * du[:, 0], rtol=0, atol=1e-12 * scale)
+    np.testing.assert_allclose(du[:, 4], 0.5 * np.dot(v, v) * du[:, 0], rtol=0, atol=1e-12 * scale)
+
+
+def test_shima_rhs_converges_to_exact_derivative_tgv_curved():
+    sp = pytest.importorskip("sympy")
+    x, y, z = sp.symbols("x y z")
+    M = 0.5
+    prim = (sp.Integer(1), [sp.sin(x) * sp.cos(y) * sp.cos(z), -sp.cos(x) * sp.sin(y) * sp.cos(z), sp.Integer(0)],
+            1 / (G * M ** 2) + (sp.cos(2 * x) + sp.cos(2 * y)) * (sp.cos(2 * z) + 2) / 16)
+    fns = _sympy_euler_dudt(3, prim, (x, y, z))
+    p = 3
+    errs = []
+    for ne in [8, 16]:
+        nelem = [ne] * 3
+        xyz, Ja, J = mesh(3, nelem, p, True)
+        u = inputs.taylor_green(xyz, mach=M)
+        du = orc.rhs(3, p, nelem, Ja, J, u, llf=True, flux="shima")
+        ex = _eval(fns, xyz)
+        errs.append(np.array([np.max(np.abs(du[:, c] - ex[:, c])) for c in range(5)]))
+    order = np.log2(errs[0] / errs[1])
+    assert np.all(order > p - 0.6), (errs, order)
