@@ -61,8 +61,9 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (debug runs)")
-    ap.add_argument("--only", default="", help="comma-separated subset of fp64_16,fp32_16,fp64_32,fp32_32 "
-                    "(profiling runs; prints one line per configuration instead of the contract line)")
+    ap.add_argument("--only", default="", help="comma-separated subset of fp64_16,fp32_16,fp64_32,fp32_32, "
+                    "variants, ablation (profiling runs; prints one line per configuration instead of the "
+                    "contract line)")
     return ap.parse_args()
 
 
@@ -127,7 +128,7 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------------------
 def source_digest() -> str:
     h = hashlib.sha256()
-    for f in ("dgmath.cuh", "kernels.cuh", "volume.cu"):
+    for f in ("dgmath.cuh", "kernels.cuh", "volume.cu", "volume_impl.cuh", "volume_inst.cu"):
         with open(os.path.join(ROOT, "paper_2112_10517_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -403,6 +404,67 @@ def run_variants(args, dev):
     return out
 
 
+def run_logmean_ablation(args, dev):
+    """Volume-term time of the log-mean variants (Sec. 3.1: Algorithms 2/3 with divisions, with the polynomial 1/log
+    form; Sec. 7.2: logarithms precomputed per node) against the default (no division, one shared reciprocal),
+    on the three initial conditions of the paper's ablation, 2D and 3D, p = 3 and 7, on the sine-perturbed mesh of
+    [-5, 5]^d. FP64; FP32 for 3D p = 3. Each entry is the mean of `steps` dg_rhs calls, L2 flushed before each."""
+    import torch
+    from paper_2112_10517_gb300 import dg, inputs
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    geos = [(3, [32, 32, 32], 3, "fp64"), (3, [16, 16, 16], 7, "fp64"), (2, [256, 256], 3, "fp64"),
+            (2, [128, 128], 7, "fp64"), (3, [32, 32, 32], 3, "fp32")]
+    variants = [("default", {}), ("precomputed_logs", dict(precompute_logs=True)), ("alg23", dict(logmean="alg")),
+                ("alg23_poly", dict(logmean="alg_poly"))]
+    out = {}
+    for nd, nelem, p, precision in geos:
+        lo, hi = [-5.0] * nd, [5.0] * nd
+        states = None
+        geo = {}
+        for vname, vkw in variants:
+            ctx = dg.DG(nd, nelem, p, lo=lo, hi=hi, mapping="sine", amp=AMP, surface="llf", precision=precision,
+                        **vkw)
+            if states is None:
+                xyz = ctx.node_coords()
+                states = {"vortex": inputs.isentropic_vortex(xyz, eps=20.0), "sine": inputs.sine_paper(xyz),
+                          "random": inputs.random_state(xyz, seed=0)}
+            for ic, u0 in states.items():
+                u = torch.from_numpy(u0).to(dev)
+                du = torch.empty_like(u)
+                for _ in range(args.warmup):
+                    ctx.rhs(u, du)
+                torch.cuda.synchronize()
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(args.steps)]
+                ctx.profile(True)
+                for a, b in ev:
+                    flush.zero_()
+                    a.record(stream)
+                    ctx.rhs(u, du)
+                    b.record(stream)
+                torch.cuda.synchronize()
+                vol_ms, vol_n = ctx.profile_read(dg.KERNEL_VOLUME)
+                ctx.profile(False)
+                if ctx.check_status() != dg.DG_OK:
+                    raise RuntimeError("non-physical state in the log-mean ablation")
+                geo.setdefault(ic, {})[vname] = {
+                    "volume_ms": vol_ms / max(vol_n, 1),
+                    "rhs_ms": sum(a.elapsed_time(b) for a, b in ev) / args.steps}
+                del u, du
+            del ctx
+        for ic, row in geo.items():
+            base = row["default"]["volume_ms"]
+            for vname in row:
+                row[vname]["volume_rel_to_default"] = row[vname]["volume_ms"] / base
+            row["precomputed_rel_to_per_pair"] = row["precomputed_logs"]["volume_ms"] / base
+        out["%dd_p%d_%s" % (nd, p, precision)] = geo
+    out["workload"] = ("dg_rhs on the sine-perturbed mesh of [-5,5]^d: 3D 32^3 p=3 and 16^3 p=7 (2,097,152 DOF), "
+                       "2D 256^2 p=3 and 128^2 p=7 (1,048,576 DOF); initial conditions: isentropic vortex eps=20, "
+                       "rho = 2 + prod sin(pi x/5) with p = rho^gamma, seeded random; Ranocha + LLF")
+    return out
+
+
 def run_diff_and_scale(args, dev):
     """The differentiation workload (dg_vjp on 8^3, p = 4, FP64) and forward RHS throughput at 64^3, p = 3."""
     import torch
@@ -516,11 +578,18 @@ def main():
     batch = run_batch(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
     diff = run_diff_and_scale(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
     variants = run_variants(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
+    ablation = run_logmean_ablation(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
     if rank == 0 and args.only:
         for label, res in results.items():
             print(json.dumps({"configuration": label, "pid_ns": res["pid_ns"], "ms_per_step": res["ms_per_step"],
                               "volume_ms": res["volume_ms_avg"], "interface_ms": res["interface_ms_avg"]}),
                   flush=True)
+        only = args.only.split(",")
+        dev = torch.device("cuda", local_rank)
+        if "variants" in only:
+            print(json.dumps({"configuration": "variants", "result": run_variants(args, dev)}), flush=True)
+        if "ablation" in only:
+            print(json.dumps({"configuration": "ablation", "result": run_logmean_ablation(args, dev)}), flush=True)
     elif rank == 0:
         r64, r32 = results["fp64_16"], results["fp32_16"]
         b64, b32 = results["fp64_32"], results["fp32_32"]
@@ -563,6 +632,7 @@ def main():
             "batch_64": batch,
             "differentiation_and_scale": diff,
             "flux_and_geometry_variants": variants,
+            "logmean_ablation": ablation,
             "alu_peaks_measured_tflops": {k: (v / 1e12 if v else None) for k, v in peaks_alu.items()},
         }
         print(json.dumps(line), flush=True)

@@ -90,13 +90,29 @@ typedef struct dg_metrics {
    dg_batch_* support DG_VOL_RANOCHA only).
    surface_flux: DG_SURF_EC (the two-point flux alone) or DG_SURF_EC_LLF (plus local Lax-Friedrichs dissipation).
    precision: DG_FP64, or DG_FP32 (two-point fluxes and line sums in FP32; metric terms computed in
-   FP64 and rounded once; state, du, RK accumulation and the entropy diagnostic in FP64). */
+   FP64 and rounded once; state, du, RK accumulation and the entropy diagnostic in FP64).
+   precompute_logs, logmean: how the volume terms of Ranocha's flux evaluate the logarithmic mean of density and
+   the inverse logarithmic mean of rho/p (Sec. 3.1, Algorithms 2 and 3; Sec. 7.2), for ablation studies. All
+   variants compute the same means up to rounding; the default (both 0) is the fastest on this hardware.
+     logmean = DG_LOGMEAN_SHARED_RCP  no division: one Newton reciprocal serves both means' u and the inverse
+                                      mean's series; the mean's series in the polynomial 1/log form;
+               DG_LOGMEAN_ALG         Algorithms 2 and 3 as stated (divisions, log of the ratio per pair);
+               DG_LOGMEAN_ALG_POLY    the same with the polynomial 1/log form of the mean's series branch.
+     precompute_logs = 1              logarithms of density and rho/p once per node instead of once per pair
+                                      (with DG_LOGMEAN_SHARED_RCP only; taken relative to each element's first
+                                      node, which leaves the differences, i.e. the logs of the ratios, unchanged).
+   Non-default values need DG_VOL_RANOCHA (else DG_ERR_UNSUPPORTED); the DG_LOGMEAN_ALG* variants run the
+   general metric path on an affine mesh and are available in dg_rhs only (dg_step returns DG_ERR_UNSUPPORTED).
+   The interface fluxes always use the default. dg_vjp and dg_batch_* accept the default only. */
+enum { DG_LOGMEAN_SHARED_RCP = 0, DG_LOGMEAN_ALG = 1, DG_LOGMEAN_ALG_POLY = 2 };
 typedef struct dg_opts {
   double gamma;
   int volume_flux;
   int surface_flux;
   int precision;
-  int reserved[5]; /* must be zero */
+  int precompute_logs; /* 0 or 1 */
+  int logmean;         /* DG_LOGMEAN_* */
+  int reserved[3];     /* must be zero */
 } dg_opts;
 
 /* Sizes of a context. */

@@ -97,6 +97,7 @@ __device__ __forceinline__ Variant general_variant() {
   Variant v;
   v.flux = 0;
   v.cart = 0;
+  v.lm = 0;
   v.jn[0] = v.jn[1] = v.jn[2] = 0.0;
   v.invJ = 0.0;
   return v;
@@ -325,7 +326,9 @@ dg_status dg_batch_create(dg_batch** out, dg_ctx* const* ctxs, int n, const doub
     if (c->device != c0->device || c->precision != c0->precision || c->surface_flux != c0->surface_flux ||
         c->gamma != c0->gamma)
       return DG_ERR_ARG;
-    if (c->nd != 3 || c->p > dgk::kBatchMaxP || c->volume_flux != DG_VOL_RANOCHA) return DG_ERR_UNSUPPORTED;
+    if (c->nd != 3 || c->p > dgk::kBatchMaxP || c->volume_flux != DG_VOL_RANOCHA ||
+      c->var.lm != 0)
+    return DG_ERR_UNSUPPORTED;
     if (((uintptr_t)u[i] | (uintptr_t)du[i]) & 7) return DG_ERR_ARG;
     const size_t bytes = (size_t)c->state_len * sizeof(double);
     const char *ub = (const char*)u[i], *db = (const char*)du[i];

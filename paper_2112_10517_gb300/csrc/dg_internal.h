@@ -44,9 +44,15 @@ struct Epilogue {
 
 // Runtime variant of the RHS kernels (uniform over a launch): the two-point flux and the Cartesian
 // specialisation of affine axis-aligned meshes, whose metric terms are the constants Ja^n = jn[n] e_n and J = 1/invJ.
+// Log-mean variants of the volume terms (see log_means_alg / log_means_prelog in dgmath.cuh); 0..2 equal the
+// DG_LOGMEAN_* codes of the ABI.
+enum { LM_SHARED_RCP = 0, LM_ALG = 1, LM_ALG_POLY = 2, LM_PRELOG = 3 };
+static_assert((int)LM_ALG == (int)DG_LOGMEAN_ALG && (int)LM_ALG_POLY == (int)DG_LOGMEAN_ALG_POLY, "log-mean codes");
+
 struct Variant {
   int flux;      // DG_VOL_RANOCHA or DG_VOL_SHIMA (volume and surface)
   int cart;      // 1: constant diagonal metrics from jn/invJ, the metric arrays are not read
+  int lm;        // log-mean variant of the volume terms (LM_* in dgmath.cuh; Ranocha's flux only)
   double jn[3];  // Ja^n_n of a Cartesian mesh
   double invJ;   // 1/J of a Cartesian mesh
 };

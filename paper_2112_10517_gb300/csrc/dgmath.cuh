@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dg_internal.h"
+
 namespace dgk {
 
 // ---------------------------------------------------------------------------------------------------
@@ -30,11 +32,14 @@ struct Num<double> {
     return fma(r, e, r);
   }
   __device__ static __forceinline__ double log(double x) { return ::log(x); }
+  __device__ static __forceinline__ double log1p(double x) { return ::log1p(x); }
   __device__ static __forceinline__ double sqrt(double x) { return ::sqrt(x); }
   __device__ static __forceinline__ double abs(double x) { return ::fabs(x); }
   // u < 1e-4, the threshold of the series branch of Algorithms 2 and 3 for 64-bit floats (Sec. 3.1), tested on
   // the high 32 bits of u >= 0 (an integer comparison): the effective threshold is the largest double whose
   // high word is below that of 1e-4, 1e-4 to within a relative 1e-6; both branches are accurate there.
+  // values within this ratio give u = ((r - 1)/(r + 1))^2 <= 8.9e-5: the series branch with margin
+  __device__ static __forceinline__ double series_range() { return 1.019; }
   __device__ static __forceinline__ bool series(double u) {
     return __double2hiint(u) < 0x3F1A36E2;  // high word of 1e-4 = 0x3F1A36E2EB1C432D
   }
@@ -49,10 +54,13 @@ struct Num<float> {
     return fmaf(r, fmaf(-s, r, 1.0f), r);
   }
   __device__ static __forceinline__ float log(float x) { return ::logf(x); }
+  __device__ static __forceinline__ float log1p(float x) { return ::log1pf(x); }
   __device__ static __forceinline__ float sqrt(float x) { return ::sqrtf(x); }
   __device__ static __forceinline__ float abs(float x) { return ::fabsf(x); }
   // The paper states the threshold for 64-bit floats only. In FP32 the truncated series is accurate to about
   // 0.03 u^4 relative and the log branch loses about eps32/(2 sqrt(u)); 1e-2 keeps both near 1 ulp.
+  // values within this ratio give u <= 7.6e-3: the series branch with margin
+  __device__ static __forceinline__ float series_range() { return 1.19f; }
   __device__ static __forceinline__ bool series(float u) { return u < 1e-2f; }
 };
 
@@ -151,6 +159,91 @@ __device__ __forceinline__ bool node_quantities(const double* uc, T gm1, T two_o
 }
 
 // ---------------------------------------------------------------------------------------------------
+// Variants of the two means for the ablation of Sec. 3.1 and Sec. 7.2 (volume terms only):
+//   LM_SHARED_RCP  log_means above: no division; one reciprocal shared by u1, u2 and the inverse mean's series,
+//                  the mean's series in the polynomial 1/log form (a product);
+//   LM_ALG         Algorithm 2 (mean) and Algorithm 3 (inverse mean) as stated: u by a division, the series
+//                  branches by a division, the log branches as log(b/a) with two divisions;
+//   LM_ALG_POLY    the same with the polynomial 1/log form of the mean's series branch (Sec. 3.1), i.e. one
+//                  division fewer there;
+//   LM_PRELOG      LM_SHARED_RCP with logarithms computed once per node instead of once per pair (Sec. 7.2): the
+//                  log branches take log(b/a) as a difference of the per-node values.
+// ---------------------------------------------------------------------------------------------------
+// (the LM_* codes are defined in dg_internal.h)
+
+template <typename T, int LM>
+__device__ __forceinline__ void log_means_alg(T a1, T b1, T a2, T b2, T& L, T& Li) {
+  const T u1 = (a1 * (a1 - T(2) * b1) + b1 * b1) / (a1 * (a1 + T(2) * b1) + b1 * b1);
+  const T u2 = (a2 * (a2 - T(2) * b2) + b2 * b2) / (a2 * (a2 + T(2) * b2) + b2 * b2);
+  if (Num<T>::series(u1)) {
+    if (LM == LM_ALG_POLY)
+      L = (a1 + b1) * (T(0.5) + u1 * (T(-1.0 / 6.0) + u1 * (T(-2.0 / 45.0) + u1 * T(-22.0 / 945.0))));
+    else
+      L = (a1 + b1) / (T(2.0) + u1 * (T(2.0 / 3.0) + u1 * (T(2.0 / 5.0) + u1 * T(2.0 / 7.0))));
+  } else {
+    L = (b1 - a1) / Num<T>::log(b1 / a1);
+  }
+  if (Num<T>::series(u2))
+    Li = (T(2.0) + u2 * (T(2.0 / 3.0) + u2 * (T(2.0 / 5.0) + u2 * T(2.0 / 7.0)))) / (a2 + b2);
+  else
+    Li = Num<T>::log(b2 / a2) / (b2 - a2);
+}
+
+// LM_PRELOG: as log_means, with l1 = log(b1 / a1) and l2 = log(b2 / a2) taken from per-node logarithms (la, lb:
+// the two nodes' [LR, LB] values, ls apart in shared memory, read only in the log branches); the log branches
+// become L = d1 / l1 and Li = l2 / d2, each by a Newton reciprocal.
+template <typename T>
+__device__ __forceinline__ void log_means_prelog(T a1, T b1, T a2, T b2, const T* la, const T* lb, int ls, T& L,
+                                                 T& Li) {
+  const T s1 = a1 + b1, d1 = b1 - a1;
+  const T s2 = a2 + b2, d2 = b2 - a2;
+  const T R = Num<T>::rcp(s1 * s2);
+  const T r1 = s2 * R, r2 = s1 * R;
+  const T f1 = d1 * r1, f2 = d2 * r2;
+  const T u1 = f1 * f1, u2 = f2 * f2;
+  if (Num<T>::series(u1))
+    L = s1 * (T(0.5) + u1 * (T(-1.0 / 6.0) + u1 * (T(-2.0 / 45.0) + u1 * T(-22.0 / 945.0))));
+  else
+    L = d1 * Num<T>::rcp(lb[0] - la[0]);
+  if (Num<T>::series(u2))
+    Li = r2 * (T(2.0) + u2 * (T(2.0 / 3.0) + u2 * (T(2.0 / 5.0) + u2 * T(2.0 / 7.0))));
+  else
+    Li = (lb[ls] - la[ls]) * Num<T>::rcp(d2);
+}
+
+// Per-node logarithms for LM_PRELOG, relative to the element's first node (rho0, pp0): LR = log(rho/rho0),
+// LB = log(rho/pp) - log(rho0/pp0). Differences of these are the logarithms of ratios the paper's per-node
+// log(rho), log(p) give (the reference cancels), without the cancellation of two large logarithms: each value is
+// log1p of a small relative change, so a difference carries the rounding of the change, not of log(rho).
+template <int ND, typename T>
+__device__ __forceinline__ void node_logs(const T* q, T rho0, T pp0, T& lr, T& lb) {
+  using Q = NodeQ<ND>;
+  lr = Num<T>::log1p((q[Q::RHO] - rho0) * Num<T>::rcp(rho0));
+  const T lp = Num<T>::log1p((q[Q::PP] - pp0) * Num<T>::rcp(pp0));
+  lb = lr - lp;
+}
+
+// The per-node logarithms of LM_PRELOG, passed to the flux: node a's and node b's LR values, LB ls further on.
+template <typename T>
+struct LogRef {
+  const T* la;
+  const T* lb;
+  int ls;
+};
+
+template <int ND, typename T, int LM>
+__device__ __forceinline__ void ranocha_means(const T* a, const T* b, T& L, T& Li, const LogRef<T>& lg) {
+  using Q = NodeQ<ND>;
+  const T a2 = a[Q::RHO] * b[Q::PP], b2 = b[Q::RHO] * a[Q::PP];
+  if constexpr (LM == LM_PRELOG)
+    log_means_prelog<T>(a[Q::RHO], b[Q::RHO], a2, b2, lg.la, lg.lb, lg.ls, L, Li);
+  else if constexpr (LM == LM_ALG || LM == LM_ALG_POLY)
+    log_means_alg<T, LM>(a[Q::RHO], b[Q::RHO], a2, b2, L, Li);
+  else
+    log_means<T>(a[Q::RHO], b[Q::RHO], a2, b2, L, Li);
+}
+
+// ---------------------------------------------------------------------------------------------------
 // Ranocha's EC/KEP/PEP flux in directional form (Eq. flux_ranocha), scaled by 8:
 //   F = 8 f(u_a, u_b, n2/2),  n2 = Ja^n_a + Ja^n_b (twice the averaged contravariant vector, Sec. 2.3).
 // With A = v_a.n2, B = v_b.n2, L = {{rho}}_log, Li = 1/{{rho_a pp_b, rho_b pp_a}}_log, Q = L (A + B):
@@ -160,8 +253,9 @@ __device__ __forceinline__ bool node_quantities(const double* uc, T gm1, T two_o
 //                                                             + ((p; v.n))))
 // using 1/{{rho/p}}_log = p_a p_b / {{rho_a p_b, rho_b p_a}}_log (Sec. 3.2) and the homogeneity of the mean.
 // ---------------------------------------------------------------------------------------------------
-template <int ND, typename T>
-__device__ __forceinline__ void ranocha_flux8(const T* a, const T* b, const T* n2, T* F) {
+template <int ND, typename T, int LM = LM_SHARED_RCP>
+__device__ __forceinline__ void ranocha_flux8(const T* a, const T* b, const T* n2, T* F,
+                                              const LogRef<T>& lg = LogRef<T>{nullptr, nullptr, 0}) {
   using Q = NodeQ<ND>;
   T A = a[1] * n2[0], B = b[1] * n2[0], vv = a[1] * b[1];
 #pragma unroll
@@ -171,7 +265,7 @@ __device__ __forceinline__ void ranocha_flux8(const T* a, const T* b, const T* n
     vv += a[1 + j] * b[1 + j];
   }
   T L, Li;
-  log_means<T>(a[Q::RHO], b[Q::RHO], a[Q::RHO] * b[Q::PP], b[Q::RHO] * a[Q::PP], L, Li);
+  ranocha_means<ND, T, LM>(a, b, L, Li, lg);
   const T q = L * (A + B);
   const T ps = a[Q::PP] + b[Q::PP];
   F[0] = q + q;
@@ -213,8 +307,9 @@ __device__ __forceinline__ void shima_flux8(const T* a, const T* b, const T* n2,
 // has the single component n2n = 2 Ja^n_n along axis n, so v.n2 is one product and the pressure acts on one
 // momentum component (van, vbn: the velocity components along n).
 // ---------------------------------------------------------------------------------------------------
-template <int ND, typename T, int FLUX>
-__device__ __forceinline__ void pair_flux8_cart(const T* a, const T* b, T van, T vbn, T n2n, int n, T* F) {
+template <int ND, typename T, int FLUX, int LM = LM_SHARED_RCP>
+__device__ __forceinline__ void pair_flux8_cart(const T* a, const T* b, T van, T vbn, T n2n, int n, T* F,
+                                                const LogRef<T>& lg = LogRef<T>{nullptr, nullptr, 0}) {
   using Q = NodeQ<ND>;
   const T A = van * n2n, B = vbn * n2n;
   T vv = a[1] * b[1];
@@ -224,7 +319,7 @@ __device__ __forceinline__ void pair_flux8_cart(const T* a, const T* b, T van, T
   T qv, e;
   if (FLUX == 0) {
     T L, Li;
-    log_means<T>(a[Q::RHO], b[Q::RHO], a[Q::RHO] * b[Q::PP], b[Q::RHO] * a[Q::PP], L, Li);
+    ranocha_means<ND, T, LM>(a, b, L, Li, lg);
     const T q = L * (A + B);
     F[0] = q + q;
     qv = q;
@@ -241,10 +336,11 @@ __device__ __forceinline__ void pair_flux8_cart(const T* a, const T* b, T van, T
   F[ND + 1] = e + (a[Q::PP] * B + b[Q::PP] * A);
 }
 
-template <int ND, typename T, int FLUX>
-__device__ __forceinline__ void pair_flux8(const T* a, const T* b, const T* n2, T* F) {
+template <int ND, typename T, int FLUX, int LM = LM_SHARED_RCP>
+__device__ __forceinline__ void pair_flux8(const T* a, const T* b, const T* n2, T* F,
+                                           const LogRef<T>& lg = LogRef<T>{nullptr, nullptr, 0}) {
   if (FLUX == 0)
-    ranocha_flux8<ND, T>(a, b, n2, F);
+    ranocha_flux8<ND, T, LM>(a, b, n2, F, lg);
   else
     shima_flux8<ND, T>(a, b, n2, F);
 }

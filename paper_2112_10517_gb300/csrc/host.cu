@@ -309,8 +309,12 @@ dg_status dg_init(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metri
   if (opts->volume_flux != DG_VOL_RANOCHA && opts->volume_flux != DG_VOL_SHIMA) return DG_ERR_ARG;
   if (opts->surface_flux != DG_SURF_EC && opts->surface_flux != DG_SURF_EC_LLF) return DG_ERR_ARG;
   if (opts->precision != DG_FP64 && opts->precision != DG_FP32) return DG_ERR_ARG;
-  for (int r = 0; r < 5; ++r)
+  for (int r = 0; r < 3; ++r)
     if (opts->reserved[r] != 0) return DG_ERR_ARG;
+  if (opts->precompute_logs != 0 && opts->precompute_logs != 1) return DG_ERR_ARG;
+  if (opts->logmean < DG_LOGMEAN_SHARED_RCP || opts->logmean > DG_LOGMEAN_ALG_POLY) return DG_ERR_ARG;
+  if ((opts->precompute_logs || opts->logmean) && opts->volume_flux != DG_VOL_RANOCHA) return DG_ERR_UNSUPPORTED;
+  if (opts->precompute_logs && opts->logmean != DG_LOGMEAN_SHARED_RCP) return DG_ERR_UNSUPPORTED;
   if (metrics && ((metrics->Ja_host == nullptr) != (metrics->J_host == nullptr))) return DG_ERR_ARG;
   const long long n3 = nd == 3 ? mesh->nelem[2] : 1;
   const long long E = (long long)mesh->nelem[0] * mesh->nelem[1] * n3;
@@ -343,7 +347,9 @@ dg_status dg_init(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metri
   c->volume_flux = opts->volume_flux;
   // Cartesian specialisation: an affine box mesh has Ja^n = (prod_{k != n} h_k/2) e_n and J = prod_k h_k/2
   c->var.flux = opts->volume_flux;
-  c->var.cart = (mesh->mapping == DG_MAP_AFFINE && !(metrics && metrics->Ja_host)) ? 1 : 0;
+  c->var.cart = (mesh->mapping == DG_MAP_AFFINE && !(metrics && metrics->Ja_host) &&
+                 opts->logmean == DG_LOGMEAN_SHARED_RCP) ? 1 : 0;
+  c->var.lm = opts->precompute_logs ? dgk::LM_PRELOG : opts->logmean;  // DG_LOGMEAN_* equal LM_* 0..2
   {
     double hh[3] = {1.0, 1.0, 1.0}, jac = 1.0;
     for (int d = 0; d < nd; ++d) {
@@ -463,6 +469,7 @@ dg_status dg_step(dg_ctx* c, double* u, double* scratch, double t, double dt, in
   if (!c || !u || !scratch) return DG_ERR_ARG;
   if (scheme != DG_RK4_CLASSIC && scheme != DG_LSRK45_CK) return DG_ERR_ARG;
   if (!(dt == dt)) return DG_ERR_ARG;
+  if (c->var.lm == dgk::LM_ALG || c->var.lm == dgk::LM_ALG_POLY) return DG_ERR_UNSUPPORTED;  // dg_rhs only
   if (((uintptr_t)u | (uintptr_t)scratch) & 7) return DG_ERR_ARG;
   const size_t n = (size_t)c->state_len;
   const size_t bytes = n * sizeof(double) * (scheme == DG_RK4_CLASSIC ? 2 : 1);

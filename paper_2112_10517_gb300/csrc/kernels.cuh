@@ -148,6 +148,23 @@ __global__ void __launch_bounds__(256) interface_kernel(const double* __restrict
 //      with Dt_ik and Dt_ki; the line's sums stay in registers and go to shared memory per direction;
 //   C. one thread per node: sum the directions, add the lifted interface fluxes, scale by -1/J, store.
 // ---------------------------------------------------------------------------------------------------
+// Positive floating-point values order like their bit patterns read as unsigned integers: shared-memory integer
+// atomicMin/atomicMax then give a tile's value range.
+template <typename T>
+struct RangeBits;
+template <>
+struct RangeBits<double> {
+  using type = unsigned long long;
+  __device__ static __forceinline__ type bits(double x) { return (type)__double_as_longlong(x); }
+  __device__ static __forceinline__ double value(type b) { return __longlong_as_double((long long)b); }
+};
+template <>
+struct RangeBits<float> {
+  using type = unsigned int;
+  __device__ static __forceinline__ type bits(float x) { return __float_as_uint(x); }
+  __device__ static __forceinline__ float value(type b) { return __uint_as_float(b); }
+};
+
 template <int ND, int N, typename T>
 struct VolumeSmem {
   using G = Geo<ND, N>;
@@ -156,9 +173,12 @@ struct VolumeSmem {
   static constexpr int kAcc = ND * G::NV * G::NDOF;        // per element
   static constexpr int kPerElem = kPrim + kJa + kAcc;      // elements of T
   static constexpr int kState = G::NV * G::NDOF;           // doubles per element of one state array
+  // per element with precomputed logarithms: [2][NDOF] logs, then (with the whole tile's logs first) 4 range slots
+  static constexpr int kLog = 2 * G::NDOF + 4;
   // with a fused stage update, two FP64 state arrays of the CTA's elements are prefetched into shared memory
-  static constexpr size_t bytes(int epb, bool fused) {
-    return (size_t)epb * kPerElem * sizeof(T) + (fused ? (size_t)2 * epb * kState * sizeof(double) : 0);
+  static constexpr size_t bytes(int epb, bool fused, bool logs = false) {
+    return (size_t)epb * (kPerElem + (logs ? kLog : 0)) * sizeof(T) +
+           (fused ? (size_t)2 * epb * kState * sizeof(double) : 0);
   }
 };
 
@@ -170,14 +190,15 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// EPI selects the epilogue: store du, or apply a Runge-Kutta stage update (in place of a separate kernel; the
-// stage arithmetic is the same as rk4_kernel / rk_ck45_kernel). With a stage update the kernel writes arrays
-// that alias its input u (the CTA has read its own elements before the barrier; no other CTA reads them).
+// EPI selects the epilogue: store du, or apply a Runge-Kutta stage update (in place of a separate kernel). With a
+// stage update the kernel writes arrays that alias its input u (the CTA has read its own elements before the
+// barrier; no other CTA reads them).
 // The pairs i < k of one line (Sec. 2.2): sp/sj point at the line's first node in the node-quantity and metric
 // arrays (stride st), sa at its accumulator slots; each pair's flux is evaluated once and added to both nodes.
-template <int ND, int N, typename T, int FLUX, bool CART>
-__device__ __forceinline__ void line_pairs(const T* sp, const T* sj, int st, int n, T n2n, const OpTable<N, T>& op,
-                                           T* sa) {
+// With LM == LM_PRELOG, sl points at the line's first node in the per-node logarithm array [2][NDOF].
+template <int ND, int N, typename T, int FLUX, bool CART, int LM = LM_SHARED_RCP>
+__device__ __forceinline__ void line_pairs(const T* sp, const T* sj, const T* sl, int st, int n, T n2n,
+                                           const OpTable<N, T>& op, T* sa) {
   using G = Geo<ND, N>;
   constexpr int NQ = NodeQ<ND>::NQ;
   T acc[N][G::NV];
@@ -201,13 +222,14 @@ __device__ __forceinline__ void line_pairs(const T* sp, const T* sj, int st, int
       T b[NQ], f[G::NV];
 #pragma unroll
       for (int c = 0; c < NQ; ++c) b[c] = sp[c * G::NDOF + k * st];
+      const LogRef<T> lg{sl + i * st, sl + k * st, G::NDOF};
       if (CART) {
-        pair_flux8_cart<ND, T, FLUX>(a, b, va_n, sp[(1 + n) * G::NDOF + k * st], n2n, n, f);
+        pair_flux8_cart<ND, T, FLUX, LM>(a, b, va_n, sp[(1 + n) * G::NDOF + k * st], n2n, n, f, lg);
       } else {
         T n2[ND];
 #pragma unroll
         for (int j = 0; j < ND; ++j) n2[j] = ja_i[j] + sj[j * G::NDOF + k * st];
-        pair_flux8<ND, T, FLUX>(a, b, n2, f);
+        pair_flux8<ND, T, FLUX, LM>(a, b, n2, f, lg);
       }
       const T dik = op.Dt8[i * N + k], dki = op.Dt8[k * N + i];
 #pragma unroll
@@ -225,7 +247,7 @@ __device__ __forceinline__ void line_pairs(const T* sp, const T* sj, int st, int
 
 // One tile of EPB elements starting at element e0, computed by the kThreads threads of a CTA (kThreads >=
 // EPB * TPE; threads beyond EPB * TPE only join the cooperative loops). smem_raw holds VolumeSmem::bytes(EPB).
-template <int ND, int N, typename T, int EPB, int EPI, int kThreads>
+template <int ND, int N, typename T, int EPB, int EPI, int kThreads, int LMK = LM_SHARED_RCP>
 __device__ __forceinline__ void volume_tile(const double* u, const T* __restrict__ Ja, const double* __restrict__ invJ,
                                             const T* __restrict__ face, double* du, const MeshDims& md,
                                             const OpTable<N, T>& op, T gamma, int* flag, const Epilogue& epi, int e0,
@@ -239,6 +261,7 @@ __device__ __forceinline__ void volume_tile(const double* u, const T* __restrict
   T* s_prim = reinterpret_cast<T*>(s_ey + (kFused ? EPB * S::kState : 0));  // [EPB][NQ][NDOF]
   T* s_ja = s_prim + EPB * S::kPrim;                       // [EPB][ND][ND][NDOF]
   T* s_acc = s_ja + EPB * S::kJa;                          // [EPB][ND][NV][NDOF]
+  T* s_log = s_acc + EPB * S::kAcc;                        // [EPB][2][NDOF], then [EPB][4] (LM_PRELOG only)
   const int tid = threadIdx.x;
   const int nel = min(EPB, md.E - e0);
   const T gm1 = gamma - T(1);
@@ -258,6 +281,12 @@ __device__ __forceinline__ void volume_tile(const double* u, const T* __restrict
 
   // ---- A: node quantities and metric terms -> shared memory
   constexpr int NQ = NodeQ<ND>::NQ;
+  typename RangeBits<T>::type* s_rng =  // [EPB][4]: min/max of rho and pp/rho per element (precomputed logs)
+      reinterpret_cast<typename RangeBits<T>::type*>(s_log + EPB * 2 * G::NDOF);
+  if constexpr (LMK == LM_PRELOG) {
+    for (int idx = tid; idx < nel * 4; idx += kThreads) s_rng[idx] = (idx & 1) ? 0 : ~(typename RangeBits<T>::type)0;
+    __syncthreads();
+  }
   bool ok = true;
   for (int idx = tid; idx < nel * G::NDOF; idx += kThreads) {
     const int el = idx / G::NDOF, i = idx - el * G::NDOF;
@@ -269,6 +298,13 @@ __device__ __forceinline__ void volume_tile(const double* u, const T* __restrict
     ok &= node_quantities<ND, T>(uc, gm1, T(2) / gm1, q);
 #pragma unroll
     for (int c = 0; c < NQ; ++c) s_prim[(el * NQ + c) * G::NDOF + i] = q[c];
+    if constexpr (LMK == LM_PRELOG) {  // the element's range of rho and w = pp/rho (positive floats order as integers)
+      const T w = q[NodeQ<ND>::PP] * Num<T>::rcp(q[NodeQ<ND>::RHO]);
+      atomicMin(&s_rng[el * 4 + 0], RangeBits<T>::bits(q[NodeQ<ND>::RHO]));
+      atomicMax(&s_rng[el * 4 + 1], RangeBits<T>::bits(q[NodeQ<ND>::RHO]));
+      atomicMin(&s_rng[el * 4 + 2], RangeBits<T>::bits(w));
+      atomicMax(&s_rng[el * 4 + 3], RangeBits<T>::bits(w));
+    }
   }
   if (!ok) atomicOr(flag, 1);
   if (!var.cart) {
@@ -277,6 +313,28 @@ __device__ __forceinline__ void volume_tile(const double* u, const T* __restrict
   }
   __syncthreads();
 
+  // ---- A2 (precomputed logarithms): per-node logs of the elements where a pair can reach a log branch. The
+  // mean of rho compares rho_b/rho_a, the inverse mean compares (rho_b pp_a)/(rho_a pp_b) = w_a/w_b with w = pp/rho.
+  // If rho_max <= r rho_min and w_max <= r w_min (r = Num<T>::series_range()), every pair of the element takes
+  // both series branches and the element needs no logarithm.
+  if constexpr (LMK == LM_PRELOG) {
+    for (int idx = tid; idx < nel * G::NDOF; idx += kThreads) {
+      const int el = idx / G::NDOF, i = idx - el * G::NDOF;
+      const T rmin = RangeBits<T>::value(s_rng[el * 4 + 0]), rmax = RangeBits<T>::value(s_rng[el * 4 + 1]);
+      const T wmin = RangeBits<T>::value(s_rng[el * 4 + 2]), wmax = RangeBits<T>::value(s_rng[el * 4 + 3]);
+      if (rmax <= Num<T>::series_range() * rmin && wmax <= Num<T>::series_range() * wmin) continue;
+      const T* qe = s_prim + el * S::kPrim;
+      T q[NQ];
+#pragma unroll
+      for (int c = 0; c < NQ; ++c) q[c] = qe[c * G::NDOF + i];
+      T lr, lb;  // relative to the element's first node
+      node_logs<ND, T>(q, qe[NodeQ<ND>::RHO * G::NDOF], qe[NodeQ<ND>::PP * G::NDOF], lr, lb);
+      s_log[(el * 2 + 0) * G::NDOF + i] = lr;
+      s_log[(el * 2 + 1) * G::NDOF + i] = lb;
+    }
+    __syncthreads();
+  }
+
   // ---- B: pairs along lines (the flux and the Cartesian specialisation select one of four loop bodies)
   if (tid < nel * G::TPE) {
     const int el = tid / G::TPE, r = tid - el * G::TPE;
@@ -284,13 +342,23 @@ __device__ __forceinline__ void volume_tile(const double* u, const T* __restrict
     const int st = G::stride(n), base = G::line_base(n, l);
     const T* sp = s_prim + el * S::kPrim + base;
     const T* sj = s_ja + (el * ND + n) * ND * G::NDOF + base;
+    const T* sl = s_log + el * 2 * G::NDOF + base;
     T* sa = s_acc + (el * ND + n) * G::NV * G::NDOF + base;
     const T n2n = T(2) * (T)cart_jn(var, n);
-    switch (var.flux * 2 + var.cart) {
-      case 0: line_pairs<ND, N, T, 0, false>(sp, sj, st, n, n2n, op, sa); break;
-      case 1: line_pairs<ND, N, T, 0, true>(sp, sj, st, n, n2n, op, sa); break;
-      case 2: line_pairs<ND, N, T, 1, false>(sp, sj, st, n, n2n, op, sa); break;
-      default: line_pairs<ND, N, T, 1, true>(sp, sj, st, n, n2n, op, sa); break;
+    if constexpr (LMK == LM_SHARED_RCP) {
+      switch (var.flux * 2 + var.cart) {
+        case 0: line_pairs<ND, N, T, 0, false>(sp, sj, sl, st, n, n2n, op, sa); break;
+        case 1: line_pairs<ND, N, T, 0, true>(sp, sj, sl, st, n, n2n, op, sa); break;
+        case 2: line_pairs<ND, N, T, 1, false>(sp, sj, sl, st, n, n2n, op, sa); break;
+        default: line_pairs<ND, N, T, 1, true>(sp, sj, sl, st, n, n2n, op, sa); break;
+      }
+    } else if constexpr (LMK == LM_PRELOG) {
+      if (var.cart)
+        line_pairs<ND, N, T, 0, true, LM_PRELOG>(sp, sj, sl, st, n, n2n, op, sa);
+      else
+        line_pairs<ND, N, T, 0, false, LM_PRELOG>(sp, sj, sl, st, n, n2n, op, sa);
+    } else {
+      line_pairs<ND, N, T, 0, false, LMK>(sp, sj, sl, st, n, n2n, op, sa);
     }
   }
   __syncthreads();
@@ -360,14 +428,17 @@ __device__ __forceinline__ void volume_tile(const double* u, const T* __restrict
   }
 }
 
-template <int ND, int N, typename T, int EPB, int EPI>
+// LMK, the log-mean variant, is a template parameter so that each variant's kernel has its own register
+// allocation (the default kernels do not carry the registers of the ablation variants); the flux and the
+// Cartesian specialisation are selected at run time inside the default kernel.
+template <int ND, int N, typename T, int EPB, int EPI, int LMK>
 __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE)
     volume_kernel(const double* u, const T* __restrict__ Ja, const double* __restrict__ invJ,
                   const T* __restrict__ face, double* du, MeshDims md, OpTable<N, T> op, T gamma, int* flag,
                   Epilogue epi, Variant var) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  volume_tile<ND, N, T, EPB, EPI, EPB * Geo<ND, N>::TPE>(u, Ja, invJ, face, du, md, op, gamma, flag, epi,
-                                                         blockIdx.x * EPB, smem_raw, var);
+  volume_tile<ND, N, T, EPB, EPI, EPB * Geo<ND, N>::TPE, LMK>(u, Ja, invJ, face, du, md, op, gamma, flag, epi,
+                                                              blockIdx.x * EPB, smem_raw, var);
 }
 
 }  // namespace dgk

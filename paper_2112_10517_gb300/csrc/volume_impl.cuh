@@ -1,5 +1,5 @@
-// Volume-kernel launchers, instantiated per dimension and flux precision in volume_{2d,3d}_{f64,f32}.cu (separate
-// translation units so that the build compiles them in parallel).
+// Volume-kernel launchers. volume_inst.cu instantiates launch_volume_n for one dimension, one flux precision and a
+// range of node counts per object file (compiled several times with different -D settings, in parallel).
 #pragma once
 
 #include "kernels.cuh"
@@ -15,13 +15,13 @@ constexpr int elems_per_block() {
   return Geo<ND, N>::TPE >= kTargetThreads ? 1 : kTargetThreads / Geo<ND, N>::TPE;
 }
 
-template <int ND, int N, typename T, int EPI>
-cudaError_t launch_volume_e(MeshDims md, const double* u, const T* Ja, const double* invJ, const T* face, double* du,
+template <int ND, int N, typename T, int EPI, int LMK>
+cudaError_t launch_volume_k(MeshDims md, const double* u, const T* Ja, const double* invJ, const T* face, double* du,
                             double gamma, int* flag, cudaStream_t s, const Epilogue& epi, const Variant& var) {
   constexpr int EPB = elems_per_block<ND, N>();
   constexpr int threads = EPB * Geo<ND, N>::TPE;
-  const size_t smem = VolumeSmem<ND, N, T>::bytes(EPB, EPI != EPI_STORE);
-  auto kern = volume_kernel<ND, N, T, EPB, EPI>;
+  const size_t smem = VolumeSmem<ND, N, T>::bytes(EPB, EPI != EPI_STORE, LMK == LM_PRELOG);
+  auto kern = volume_kernel<ND, N, T, EPB, EPI, LMK>;
   static bool attr_set = false;  // idempotent; a benign race sets the same value twice
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -35,6 +35,23 @@ cudaError_t launch_volume_e(MeshDims md, const double* u, const T* Ja, const dou
   const int blocks = (md.E + EPB - 1) / EPB;
   kern<<<blocks, threads, smem, s>>>(u, Ja, invJ, face, du, md, op, (T)gamma, flag, epi, var);
   return cudaGetLastError();
+}
+
+// the log-mean variants: all four for dg_rhs; the default and precomputed logarithms for the fused stage update
+template <int ND, int N, typename T, int EPI>
+cudaError_t launch_volume_e(MeshDims md, const double* u, const T* Ja, const double* invJ, const T* face, double* du,
+                            double gamma, int* flag, cudaStream_t s, const Epilogue& epi, const Variant& var) {
+  if (var.lm == LM_PRELOG)
+    return launch_volume_k<ND, N, T, EPI, LM_PRELOG>(md, u, Ja, invJ, face, du, gamma, flag, s, epi, var);
+  if constexpr (EPI == EPI_STORE) {
+    if (var.lm == LM_ALG)
+      return launch_volume_k<ND, N, T, EPI, LM_ALG>(md, u, Ja, invJ, face, du, gamma, flag, s, epi, var);
+    if (var.lm == LM_ALG_POLY)
+      return launch_volume_k<ND, N, T, EPI, LM_ALG_POLY>(md, u, Ja, invJ, face, du, gamma, flag, s, epi, var);
+  } else {
+    if (var.lm != LM_SHARED_RCP) return cudaErrorInvalidValue;
+  }
+  return launch_volume_k<ND, N, T, EPI, LM_SHARED_RCP>(md, u, Ja, invJ, face, du, gamma, flag, s, epi, var);
 }
 
 template <int ND, int N, typename T>
@@ -52,30 +69,12 @@ cudaError_t launch_volume_t(MeshDims md, const double* u, const T* Ja, const dou
   return launch_volume_e<ND, N, T, EPI_CK45>(md, u, Ja, invJ, face, du, gamma, flag, s, *epi, v);
 }
 
-template <int ND, typename T>
-cudaError_t dispatch_p_impl(int p, MeshDims md, const double* u, const void* Ja, const double* invJ, const void* face,
-                       double* du, double gamma, int* flag, cudaStream_t s, const Epilogue* epi, const Variant* var) {
-  const T* ja = static_cast<const T*>(Ja);
-  const T* fc = static_cast<const T*>(face);
-  switch (p) {
-    case 1: return launch_volume_t<ND, 2, T>(md, u, ja, invJ, fc, du, gamma, flag, s, epi, var);
-    case 2: return launch_volume_t<ND, 3, T>(md, u, ja, invJ, fc, du, gamma, flag, s, epi, var);
-    case 3: return launch_volume_t<ND, 4, T>(md, u, ja, invJ, fc, du, gamma, flag, s, epi, var);
-    case 4: return launch_volume_t<ND, 5, T>(md, u, ja, invJ, fc, du, gamma, flag, s, epi, var);
-    case 5: return launch_volume_t<ND, 6, T>(md, u, ja, invJ, fc, du, gamma, flag, s, epi, var);
-    case 6: return launch_volume_t<ND, 7, T>(md, u, ja, invJ, fc, du, gamma, flag, s, epi, var);
-    case 7: return launch_volume_t<ND, 8, T>(md, u, ja, invJ, fc, du, gamma, flag, s, epi, var);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
 }  // namespace volume_detail
 
-template <int ND, typename T>
-cudaError_t volume_dispatch(int p, MeshDims md, const double* u, const void* Ja, const double* invJ, const void* face,
-                            double* du, double gamma, int* flag, cudaStream_t s, const Epilogue* epi,
-                            const Variant* var) {
-  return volume_detail::dispatch_p_impl<ND, T>(p, md, u, Ja, invJ, face, du, gamma, flag, s, epi, var);
+template <int ND, int N, typename T>
+cudaError_t launch_volume_n(MeshDims md, const double* u, const T* Ja, const double* invJ, const T* face, double* du,
+                            double gamma, int* flag, cudaStream_t s, const Epilogue* epi, const Variant* var) {
+  return volume_detail::launch_volume_t<ND, N, T>(md, u, Ja, invJ, face, du, gamma, flag, s, epi, var);
 }
 
 }  // namespace dgk

@@ -28,6 +28,8 @@ DG_SURF_EC, DG_SURF_EC_LLF = 0, 1
 DG_FP64, DG_FP32 = 0, 1
 DG_VOL_RANOCHA, DG_VOL_SHIMA = 0, 1
 FLUXES = {"ranocha": DG_VOL_RANOCHA, "shima": DG_VOL_SHIMA}
+DG_LOGMEAN_SHARED_RCP, DG_LOGMEAN_ALG, DG_LOGMEAN_ALG_POLY = 0, 1, 2
+LOGMEANS = {"rcp": DG_LOGMEAN_SHARED_RCP, "alg": DG_LOGMEAN_ALG, "alg_poly": DG_LOGMEAN_ALG_POLY}
 DG_RK4_CLASSIC, DG_LSRK45_CK = 0, 1
 KERNEL_VOLUME, KERNEL_INTERFACE = 0, 1
 
@@ -49,7 +51,8 @@ class DgMetrics(ctypes.Structure):
 
 class DgOpts(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("volume_flux", ctypes.c_int), ("surface_flux", ctypes.c_int),
-                ("precision", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("precision", ctypes.c_int), ("precompute_logs", ctypes.c_int), ("logmean", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 class DgInfo(ctypes.Structure):
@@ -122,11 +125,14 @@ class DG:
     surface: "ec" or "llf"; precision: "fp64" or "fp32"; flux: "ranocha" (Ranocha's EC/KEP/PEP flux) or
     "shima" (the KEEP/PEP flux of Shima et al.), used in the volume and as the surface flux's central part.
     An affine mesh without node or metric overrides runs the Cartesian specialisation (constant Ja, 1/J).
+    logmean ("rcp", "alg", "alg_poly") and precompute_logs select how the volume terms evaluate the logarithmic
+    means of Ranocha's flux (Sec. 3.1, 7.2; see dg_opts in include/dg.h); the defaults are the fastest.
     """
 
     def __init__(self, ndims: int, nelem, polydeg: int, lo=None, hi=None, mapping: str = "affine", amp: float = 0.0,
                  node_xyz=None, Ja=None, J=None, gamma: float = 1.4, surface: str = "llf",
-                 precision: str = "fp64", flux: str = "ranocha"):
+                 precision: str = "fp64", flux: str = "ranocha", logmean: str = "rcp",
+                 precompute_logs: bool = False):
         mesh = DgMesh()
         mesh.ndims = ndims
         ne = list(nelem) + [1] * (3 - len(nelem))
@@ -152,6 +158,8 @@ class DG:
         opts = DgOpts()
         opts.gamma = gamma
         opts.volume_flux = FLUXES[flux]
+        opts.logmean = LOGMEANS[logmean]
+        opts.precompute_logs = 1 if precompute_logs else 0
         opts.surface_flux = {"ec": DG_SURF_EC, "llf": DG_SURF_EC_LLF}[surface]
         opts.precision = {"fp64": DG_FP64, "fp32": DG_FP32}[precision]
         ctx = ctypes.c_void_p()

@@ -57,6 +57,21 @@ def test_argument_errors_without_gpu(built):
     opts.reserved[0] = 1
     assert dg.dg_init(ctypes.byref(ctx), ctypes.byref(mesh), 3, None, ctypes.byref(opts)) == dg.DG_ERR_ARG
     opts.reserved[0] = 0
+    # log-mean options: out of range, or combinations without a kernel, are rejected before any device call
+    init = lambda: dg.dg_init(ctypes.byref(ctx), ctypes.byref(mesh), 3, None, ctypes.byref(opts))
+    opts.precompute_logs = 2
+    assert init() == dg.DG_ERR_ARG
+    opts.precompute_logs = 0
+    opts.logmean = 3
+    assert init() == dg.DG_ERR_ARG
+    opts.logmean, opts.precompute_logs = dg.DG_LOGMEAN_ALG, 1  # precomputed logs need the default log mean
+    assert init() == dg.DG_ERR_UNSUPPORTED
+    opts.logmean, opts.volume_flux = 0, dg.DG_VOL_SHIMA  # the Shima flux has no logarithmic means
+    assert init() == dg.DG_ERR_UNSUPPORTED
+    opts.precompute_logs, opts.volume_flux = 0, dg.DG_VOL_RANOCHA
+    opts.volume_flux = 2
+    assert init() == dg.DG_ERR_ARG
+    opts.volume_flux = dg.DG_VOL_RANOCHA
     mesh.hi[1] = -2.0  # empty box
     assert dg.dg_init(ctypes.byref(ctx), ctypes.byref(mesh), 3, None, ctypes.byref(opts)) == dg.DG_ERR_ARG
     mesh.hi[1] = 1.0
