@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(256) batch_interface_kernel(const BatchInst* _
     else hi = mid - 1;
   }
   const BatchInst& in = insts[lo];
-  const long long idx = g - in.face_begin;
+  const int idx = (int)(g - in.face_begin);  // < 3 E NL < 2^31 per instance
   const double* u = in.u;
   const T* ja = static_cast<const T*>(in.Ja);
   T* face = static_cast<T*>(in.face);
@@ -173,6 +173,7 @@ cudaError_t upload_const_ops() {
     const RefTables& t = ref_tables(NN - 1);                                   \
     for (int i = 0; i < NN * NN; ++i) op.Dt8[i] = (T)(0.125 * t.Dt[i]);        \
     op.winv = (T)(1.0 / t.w[0]);                                               \
+    op.lift8 = (T)(0.125 / t.w[0]);                                            \
     e = cudaMemcpyToSymbol(SYM, &op, sizeof(op));                              \
   }
   if (sizeof(T) == 8) {

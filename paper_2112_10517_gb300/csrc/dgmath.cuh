@@ -140,9 +140,10 @@ struct NodeQ {
 };
 
 template <int ND, typename T>
-__device__ __forceinline__ bool node_quantities(const double* uc, T gm1, T two_over_gm1, T* q) {
+__device__ __forceinline__ bool node_quantities(const double* uc, T gm1, T two_over_gm1, T* q, T* ir_out = nullptr) {
   const T rho = to_flux<T>(uc[0]);
   const T ir = Num<T>::rcp(rho);
+  if (ir_out) *ir_out = ir;  // 1/rho, for callers that need it again (the LLF wave speed)
   T ke = T(0);
 #pragma unroll
   for (int j = 0; j < ND; ++j) {

@@ -48,10 +48,23 @@ __device__ __forceinline__ int neighbor(const MeshDims& md, int e, int n, int di
   return e1 + md.n1 * (e2 + md.n2 * e3);
 }
 
+// upper neighbour of element e across direction n (periodic), with one or two divisions
+__device__ __forceinline__ int upper_neighbor(const MeshDims& md, int e, int n) {
+  if (n == 0) {
+    const int e1 = e % md.n1;
+    return e1 == md.n1 - 1 ? e - e1 : e + 1;
+  }
+  const int s = n == 1 ? md.n1 : md.n1 * md.n2;  // element stride along n
+  const int c = n == 1 ? (e / md.n1) % md.n2 : e / s;  // coordinate along n
+  const int len = n == 1 ? md.n2 : md.n3;
+  return c == len - 1 ? e - c * s : e + s;
+}
+
 template <int N, typename T>
 struct OpTable {
   T Dt8[N * N];  // flux-differencing matrix 2D - M^{-1}B (Eq. opDsplit), divided by 8 (fluxes come scaled by 8)
   T winv;        // 1/w_0 = 1/w_p = p(p+1)/2: the lift M^{-1} R^T B at the end nodes
+  T lift8;       // winv / 8: the lift of the face buffer, which holds interface fluxes scaled by 8
 };
 
 // ---------------------------------------------------------------------------------------------------
@@ -61,18 +74,20 @@ struct OpTable {
 // lambda = max(|v_L.m| + c_L|m|, |v_R.m| + c_R|m|), c = sqrt(gamma p/rho).
 // face layout [n][E][NV][NL].
 // ---------------------------------------------------------------------------------------------------
-// Interface flux at face node `idx` of a mesh, idx = (n * E + e) * NL + fn. FLUX: 0 Ranocha, 1 Shima et al.
+// Interface flux at face node `idx` of a mesh, idx = (e * ND + n) * NL + fn: the faces on an element's upper side
+// in all directions are neighbours in the launch, so the element's data are fetched once for them and its lower
+// neighbours' visits follow closely. FLUX: 0 Ranocha, 1 Shima et al.
 // cart: metric terms are the Cartesian constants of `var` (Ja is not read).
 template <int ND, int N, typename T, bool LLF, int FLUX>
 __device__ __forceinline__ void interface_node(const double* __restrict__ u, const T* __restrict__ Ja,
                                                T* __restrict__ face, const MeshDims& md, T gamma, int* flag,
-                                               long long idx, const Variant& var) {
+                                               int idx, const Variant& var) {
   using G = Geo<ND, N>;
-  const int fn = (int)(idx % G::NL);
-  const long long t = idx / G::NL;
-  const int e = (int)(t % md.E);
-  const int n = (int)(t / md.E);
-  const int eR = neighbor(md, e, n, +1);
+  const int fn = idx % G::NL;
+  const int t = idx / G::NL;
+  const int n = t % ND;
+  const int e = t / ND;
+  const int eR = upper_neighbor(md, e, n);
   // node with i_n = N-1 (lower element) and i_n = 0 (upper element) for face node fn
   const int st = G::stride(n);
   const int lo = fn % st, hi = fn / st;
@@ -91,12 +106,11 @@ __device__ __forceinline__ void interface_node(const double* __restrict__ u, con
     m2[j] = m[j] + m[j];
   }
   const T gm1 = gamma - T(1);
-  T qL[NodeQ<ND>::NQ], qR[NodeQ<ND>::NQ], f[G::NV];
-  const bool ok = node_quantities<ND, T>(uL, gm1, T(2) / gm1, qL) & node_quantities<ND, T>(uR, gm1, T(2) / gm1, qR);
+  T qL[NodeQ<ND>::NQ], qR[NodeQ<ND>::NQ], f[G::NV], irL, irR;
+  const bool ok = node_quantities<ND, T>(uL, gm1, T(2) / gm1, qL, &irL) &
+                  node_quantities<ND, T>(uR, gm1, T(2) / gm1, qR, &irR);
   if (!ok) atomicOr(flag, 1);
-  pair_flux8<ND, T, FLUX>(qL, qR, m2, f);
-#pragma unroll
-  for (int c = 0; c < G::NV; ++c) f[c] *= T(0.125);
+  pair_flux8<ND, T, FLUX>(qL, qR, m2, f);  // 8 f(u_L, u_R, m); the face buffer keeps this scale (lift8)
   if (LLF) {
     T mm = m[0] * m[0], vnL = qL[1] * m[0], vnR = qR[1] * m[0];
 #pragma unroll
@@ -105,17 +119,16 @@ __device__ __forceinline__ void interface_node(const double* __restrict__ u, con
       vnL += qL[1 + j] * m[j];
       vnR += qR[1 + j] * m[j];
     }
-    // c = sqrt(gamma p / rho) with p = pp/2
-    const T hg = T(0.5) * gamma;
-    const T mn = Num<T>::sqrt(mm);
-    const T lamL = Num<T>::abs(vnL) + Num<T>::sqrt(hg * qL[NodeQ<ND>::PP] * Num<T>::rcp(qL[0])) * mn;
-    const T lamR = Num<T>::abs(vnR) + Num<T>::sqrt(hg * qR[NodeQ<ND>::PP] * Num<T>::rcp(qR[0])) * mn;
-    const T half_lam = T(0.5) * (lamL > lamR ? lamL : lamR);
+    // c |m| = sqrt(gamma p |m|^2 / rho) with p = pp/2: one root per side
+    const T hgm = T(0.5) * gamma * mm;
+    const T lamL = Num<T>::abs(vnL) + Num<T>::sqrt(hgm * qL[NodeQ<ND>::PP] * irL);
+    const T lamR = Num<T>::abs(vnR) + Num<T>::sqrt(hgm * qR[NodeQ<ND>::PP] * irR);
+    const T lam4 = T(4) * (lamL > lamR ? lamL : lamR);  // 8 (lambda / 2)
 #pragma unroll
     for (int c = 0; c < G::NV; ++c) {
       // FP64: the jump in FP64; FP32 mode: both states rounded to FP32 first (no FP64 arithmetic)
       const T jump = sizeof(T) == 8 ? (T)(uR[c] - uL[c]) : to_flux<T>(uR[c]) - to_flux<T>(uL[c]);
-      f[c] -= half_lam * jump;
+      f[c] -= lam4 * jump;
     }
   }
   T* fo = face + ((size_t)n * md.E + e) * G::NV * G::NL + fn;
@@ -127,13 +140,13 @@ template <int ND, int N, typename T, bool LLF>
 __global__ void __launch_bounds__(256) interface_kernel(const double* __restrict__ u, const T* __restrict__ Ja,
                                                         T* __restrict__ face, MeshDims md, T gamma, int* flag,
                                                         Variant var) {
-  const long long total = (long long)ND * md.E * Geo<ND, N>::NL;
+  const long long total = (long long)ND * md.E * Geo<ND, N>::NL;  // < 2^31 (checked at dg_init)
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= total) return;
   if (var.flux == 0)
-    interface_node<ND, N, T, LLF, 0>(u, Ja, face, md, gamma, flag, idx, var);
+    interface_node<ND, N, T, LLF, 0>(u, Ja, face, md, gamma, flag, (int)idx, var);
   else
-    interface_node<ND, N, T, LLF, 1>(u, Ja, face, md, gamma, flag, idx, var);
+    interface_node<ND, N, T, LLF, 1>(u, Ja, face, md, gamma, flag, (int)idx, var);
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -385,7 +398,7 @@ __device__ __forceinline__ void volume_tile(const double* u, const T* __restrict
       if (in == N - 1 || in == 0) {
         const int fn = G::face_index(n, i);
         const int fe = in == N - 1 ? ge : neighbor(md, ge, n, -1);
-        const T sgn = in == N - 1 ? op.winv : -op.winv;
+        const T sgn = in == N - 1 ? op.lift8 : -op.lift8;
         const T* fp = face + ((size_t)n * md.E + fe) * G::NV * G::NL + fn;
 #pragma unroll
         for (int c = 0; c < G::NV; ++c) tot[c] += sgn * fp[c * G::NL];

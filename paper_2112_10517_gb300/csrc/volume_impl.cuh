@@ -32,6 +32,7 @@ cudaError_t launch_volume_k(MeshDims md, const double* u, const T* Ja, const dou
   const RefTables& t = ref_tables(N - 1);
   for (int i = 0; i < N * N; ++i) op.Dt8[i] = (T)(0.125 * t.Dt[i]);
   op.winv = (T)(1.0 / t.w[0]);
+  op.lift8 = (T)(0.125 / t.w[0]);
   const int blocks = (md.E + EPB - 1) / EPB;
   kern<<<blocks, threads, smem, s>>>(u, Ja, invJ, face, du, md, op, (T)gamma, flag, epi, var);
   return cudaGetLastError();
