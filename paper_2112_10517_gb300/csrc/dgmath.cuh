@@ -72,14 +72,17 @@ struct Num<float> {
 //   f2d_int: binary32 -> binary64, exact for normal floats and zero (subnormals flush to zero).
 // ---------------------------------------------------------------------------------------------------
 __device__ __forceinline__ float d2f_int(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-  const unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFull;
-  // keep 23 of the 52 mantissa bits: adding 2^28 - 1 plus the lowest kept bit rounds to nearest, ties to even;
-  // a carry out of the mantissa correctly increments the exponent
-  const unsigned long long r = mag + 0x0FFFFFFFull + ((mag >> 29) & 1ull);
-  const int e = (int)(r >> 52) - 1023 + 127;
-  const unsigned m = (unsigned)(r >> 29) & 0x7FFFFFu;
+  // on the two 32-bit halves: a 64-bit mask of the sign bit may be turned into an FP64 absolute value
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u;
+  const unsigned mhi = hi & 0x7FFFFFFFu;
+  // keep 23 of the 52 mantissa bits: adding 2^28 - 1 plus the lowest kept bit (bit 29 of the low word) rounds to
+  // nearest, ties to even; the carry into the high word, and out of the mantissa into the exponent, is exact
+  const unsigned add = 0x0FFFFFFFu + ((lo >> 29) & 1u);
+  const unsigned rlo = lo + add;
+  const unsigned rhi = mhi + (rlo < add ? 1u : 0u);
+  const int e = (int)(rhi >> 20) - 1023 + 127;
+  const unsigned m = ((rhi & 0xFFFFFu) << 3) | (rlo >> 29);
   return __uint_as_float(e <= 0 ? sign : (sign | ((unsigned)e << 23) | m));
 }
 
