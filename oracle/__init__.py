@@ -25,6 +25,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRC_GAUSS = os.path.join(_HERE, "gauss.c")
 _SRC_DUAL = [os.path.join(_HERE, "oracle_dual.cpp"), os.path.join(_HERE, "dual.h")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
@@ -38,14 +39,15 @@ _ip = ctypes.POINTER(ctypes.c_int)
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c with gcc (plain -O2, no fast-math, portable flags) into oracle/_build, and the same
-    source with dual numbers (oracle_dual.cpp, g++) for the JVP."""
+    """Compile oracle.c and gauss.c with gcc (plain -O2, no fast-math, portable flags) into oracle/_build, and the
+    LGL source with dual numbers (oracle_dual.cpp, g++) for the JVP."""
     os.makedirs(_BUILD, exist_ok=True)
-    stale = (not os.path.exists(_LIB_PATH)) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)
+    stale = (not os.path.exists(_LIB_PATH)) or os.path.getmtime(_LIB_PATH) < max(
+        os.path.getmtime(_SRC), os.path.getmtime(_SRC_GAUSS))
     if force or stale:
         tmp = _LIB_PATH + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
-                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+                               "-ffp-contract=off", "-o", tmp, _SRC, _SRC_GAUSS, "-lm"])
         os.replace(tmp, _LIB_PATH)
     deps = [_SRC] + _SRC_DUAL
     stale = (not os.path.exists(_LIB_DUAL)) or os.path.getmtime(_LIB_DUAL) < max(os.path.getmtime(d) for d in deps)
@@ -330,3 +332,75 @@ def jvp(ndims: int, p: int, nelem, Ja, J, u, delta, gamma: float = 1.4, llf: boo
     _check(lib.orc_rhs(ndims, p, _ivec(nelem), _ptr(Jad), _ptr(Jd), _ptr(ud), _Dual(gamma, 0.0),
                        FLUXES[flux], int(bool(llf)), 0, E, 0, _ptr(dud)), "rhs (dual)")
     return dud[..., 0].copy(), dud[..., 1].copy()
+
+
+# --------------------------------------------------------------------------------------------
+# Legendre-Gauss collocation with entropy projection (Sec. 6, gauss.c), affine periodic boxes
+# --------------------------------------------------------------------------------------------
+
+def gauss(p: int):
+    """Legendre-Gauss nodes and weights with p + 1 points (Sec. 6)."""
+    lib = _load()
+    x = np.zeros(p + 1)
+    w = np.zeros(p + 1)
+    _check(lib.org_gauss(p, _ptr(x), _ptr(w)), "org_gauss")
+    return x, w
+
+
+def lagrange_at(p: int, x, s: float) -> np.ndarray:
+    """Lagrange basis of the nodes x at the point s (the rows of the face restriction R)."""
+    lib = _load()
+    x = _f64(x)
+    out = np.zeros(p + 1)
+    lib.org_lagrange_at(p, _ptr(x), ctypes.c_double(s), _ptr(out))
+    return out
+
+
+def cons_from_entropy(w, ndims: int, gamma: float = 1.4) -> np.ndarray:
+    """u(w), the inverse of the entropy-variable map (Sec. 2), for states w[..., nvar]."""
+    lib = _load()
+    w = _f64(w)
+    u = np.zeros_like(w)
+    lib.org_cons_from_entropy_batch(w.size // (ndims + 2), _ptr(w), ndims, ctypes.c_double(gamma), _ptr(u))
+    return u
+
+
+def gauss_coords(ndims: int, nelem, lo, hi, p: int) -> np.ndarray:
+    """Node coordinates [E, ndims, Nd] of the Gauss collocation mesh of the box [lo, hi]."""
+    lib = _load()
+    E = num_elements(ndims, nelem)
+    xyz = np.zeros((E, ndims, (p + 1) ** ndims))
+    _check(lib.org_gauss_coords(ndims, _ivec(nelem), _dvec(lo), _dvec(hi), p, _ptr(xyz)), "org_gauss_coords")
+    return xyz
+
+
+def gauss_rhs(ndims: int, p: int, nelem, lo, hi, u, gamma: float = 1.4, llf: bool = False) -> np.ndarray:
+    """du/dt of the Legendre-Gauss collocation scheme with entropy projection (Sec. 6, Eq. fluxdiff-GSBP-opDsplit
+    and Eq. hybridized_gauss_formulation), Ranocha's flux in the volume and at the surface, optional LLF."""
+    lib = _load()
+    u = _f64(u)
+    du = np.zeros_like(u)
+    _check(lib.org_gauss_rhs(ndims, p, _ivec(nelem), _dvec(lo), _dvec(hi), _ptr(u), ctypes.c_double(gamma),
+                             int(llf), _ptr(du)), "org_gauss_rhs")
+    return du
+
+
+def dmat_nodes(p: int, x) -> np.ndarray:
+    """Nodal derivative matrix of arbitrary distinct nodes x (barycentric form, as dmat)."""
+    lib = _load()
+    x = _f64(x)
+    D = np.zeros((p + 1, p + 1))
+    _check(lib.orc_dmat(p, _ptr(x), _ptr(D)), "orc_dmat")
+    return D
+
+
+def gauss_project(ndims: int, p: int, u, gamma: float = 1.4) -> np.ndarray:
+    """The entropy projection (Sec. 6): face states u(R w(u)) [E, 2 ndims (p+1)^(ndims-1), nvar], face node
+    f = (n*2 + s)*NL + t (direction n, side s = 0 at xi_n = -1, t over the other directions)."""
+    lib = _load()
+    u = _f64(u)
+    E = u.shape[0]
+    NL = (p + 1) ** (ndims - 1)
+    out = np.zeros((E, 2 * ndims * NL, ndims + 2))
+    _check(lib.org_gauss_project(ndims, p, E, _ptr(u), ctypes.c_double(gamma), _ptr(out)), "org_gauss_project")
+    return out
