@@ -62,7 +62,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (debug runs)")
     ap.add_argument("--only", default="", help="comma-separated subset of fp64_16,fp32_16,fp64_32,fp32_32, "
-                    "variants, ablation (profiling runs; prints one line per configuration instead of the "
+                    "variants, ablation, gauss (profiling runs; prints one line per configuration instead of the "
                     "contract line)")
     return ap.parse_args()
 
@@ -465,6 +465,51 @@ def run_logmean_ablation(args, dev):
     return out
 
 
+def run_gauss(args, dev):
+    """Legendre-Gauss collocation with entropy projection (Sec. 6) against LGL-DGSEM on the same affine mesh:
+    dg_rhs time per DOF and the per-kernel breakdown (entropy projection, interface flux, volume term), Taylor-Green
+    vortex on [-pi, pi]^3, FP64, EC surface fluxes as in the paper's Gauss runs. L2 flushed before every call."""
+    import torch
+    from paper_2112_10517_gb300 import dg, inputs
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    lo, hi = [-math.pi] * 3, [math.pi] * 3
+    out = {}
+    for nelem, p in (([32, 32, 32], 3), ([16, 16, 16], 7)):
+        row = {}
+        for nodes in ("lgl", "gauss"):
+            ctx = dg.DG(3, nelem, p, lo=lo, hi=hi, mapping="affine", surface="ec", nodes=nodes)
+            u = torch.from_numpy(inputs.taylor_green(ctx.node_coords(), mach=MACH)).to(dev)
+            du = torch.empty_like(u)
+            for _ in range(args.warmup):
+                ctx.rhs(u, du)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            ctx.profile(True)
+            for a, b in ev:
+                flush.zero_()
+                a.record(stream)
+                ctx.rhs(u, du)
+                b.record(stream)
+            torch.cuda.synchronize()
+            parts = {name: ctx.profile_read(kid)[0] / args.steps for name, kid in
+                     (("volume_ms", dg.KERNEL_VOLUME), ("interface_ms", dg.KERNEL_INTERFACE),
+                      ("projection_ms", dg.KERNEL_PROJECT))}
+            ctx.profile(False)
+            if ctx.check_status() != dg.DG_OK:
+                raise RuntimeError("non-physical state in the Gauss comparison")
+            ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+            row[nodes] = dict(ms=ms, pid_ns=ms * 1e6 / ctx.ndofs, **parts)
+            del ctx, u, du
+        row["gauss_over_lgl"] = row["gauss"]["pid_ns"] / row["lgl"]["pid_ns"]
+        out["3d_%d_p%d" % (nelem[0], p)] = row
+    out["workload"] = ("dg_rhs, Taylor-Green vortex Mach 0.1 on the affine [-pi,pi]^3 mesh, 32^3 p=3 and 16^3 p=7 "
+                       "(2,097,152 DOF), Ranocha's flux, EC surface flux, FP64; LGL-DGSEM vs Legendre-Gauss "
+                       "collocation with entropy projection")
+    return out
+
+
 def run_diff_and_scale(args, dev):
     """The differentiation workload (dg_vjp on 8^3, p = 4, FP64) and forward RHS throughput at 64^3, p = 3."""
     import torch
@@ -579,6 +624,7 @@ def main():
     diff = run_diff_and_scale(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
     variants = run_variants(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
     ablation = run_logmean_ablation(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
+    gauss = run_gauss(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
     if rank == 0 and args.only:
         for label, res in results.items():
             print(json.dumps({"configuration": label, "pid_ns": res["pid_ns"], "ms_per_step": res["ms_per_step"],
@@ -590,6 +636,8 @@ def main():
             print(json.dumps({"configuration": "variants", "result": run_variants(args, dev)}), flush=True)
         if "ablation" in only:
             print(json.dumps({"configuration": "ablation", "result": run_logmean_ablation(args, dev)}), flush=True)
+        if "gauss" in only:
+            print(json.dumps({"configuration": "gauss", "result": run_gauss(args, dev)}), flush=True)
     elif rank == 0:
         r64, r32 = results["fp64_16"], results["fp32_16"]
         b64, b32 = results["fp64_32"], results["fp32_32"]
@@ -633,6 +681,7 @@ def main():
             "differentiation_and_scale": diff,
             "flux_and_geometry_variants": variants,
             "logmean_ablation": ablation,
+            "gauss_collocation": gauss,
             "alu_peaks_measured_tflops": {k: (v / 1e12 if v else None) for k, v in peaks_alu.items()},
         }
         print(json.dumps(line), flush=True)

@@ -103,8 +103,16 @@ typedef struct dg_metrics {
                                       node, which leaves the differences, i.e. the logs of the ratios, unchanged).
    Non-default values need DG_VOL_RANOCHA (else DG_ERR_UNSUPPORTED); the DG_LOGMEAN_ALG* variants run the
    general metric path on an affine mesh and are available in dg_rhs only (dg_step returns DG_ERR_UNSUPPORTED).
-   The interface fluxes always use the default. dg_vjp and dg_batch_* accept the default only. */
+   The interface fluxes always use the default. dg_vjp and dg_batch_* accept the default only.
+   nodes: DG_NODES_LGL, the flux-differencing LGL-DGSEM above, or DG_NODES_GAUSS, the Legendre-Gauss collocation
+   scheme with entropy projection (Sec. 6, Eq. fluxdiff-GSBP-opDsplit with the hybridized volume terms of Eq.
+   hybridized_gauss_formulation): the state lives at the tensor-product Gauss nodes (dg_get_node_coords), face
+   states are u(R w(u)) of each element, interface fluxes are computed once per face node. DG_NODES_GAUSS needs
+   DG_MAP_AFFINE without overrides, DG_VOL_RANOCHA, DG_FP64 and the default log mean (else DG_ERR_UNSUPPORTED);
+   dg_vjp and dg_batch_* do not support it. Its face states need the entropy variables interpolated to the faces
+   to stay admissible (rho/p > 0); otherwise the non-physical flag is raised. */
 enum { DG_LOGMEAN_SHARED_RCP = 0, DG_LOGMEAN_ALG = 1, DG_LOGMEAN_ALG_POLY = 2 };
+enum { DG_NODES_LGL = 0, DG_NODES_GAUSS = 1 };
 typedef struct dg_opts {
   double gamma;
   int volume_flux;
@@ -112,7 +120,8 @@ typedef struct dg_opts {
   int precision;
   int precompute_logs; /* 0 or 1 */
   int logmean;         /* DG_LOGMEAN_* */
-  int reserved[3];     /* must be zero */
+  int nodes;           /* DG_NODES_* */
+  int reserved[2];     /* must be zero */
 } dg_opts;
 
 /* Sizes of a context. */
@@ -170,7 +179,7 @@ dg_status dg_get_metrics(const dg_ctx* ctx, double* Ja_host /* [E][d][d][Nd] */,
 
 /* Kernel timing with CUDA events recorded on the launching stream around every launch of kernel `which`
    (0 = volume term with surface lift and Jacobian, which in dg_step also applies the RK stage update;
-   1 = interface flux) while enabled. dg_profile_read returns the summed milliseconds and the launch count since
+   1 = interface flux; 2 = entropy projection of DG_NODES_GAUSS) while enabled. dg_profile_read returns the summed milliseconds and the launch count since
    the last enable, and synchronizes. dg_launch_count counts every kernel the context has launched since dg_init. */
 dg_status dg_profile_enable(dg_ctx* ctx, int on);
 dg_status dg_profile_read(dg_ctx* ctx, int which, double* total_ms, long long* launches);

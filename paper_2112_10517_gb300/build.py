@@ -29,7 +29,7 @@ VOLUME_OBJS = [("volume_inst.cu", "vol%dd_%s_n%d%d" % (nd, t, lo, hi),
                for nd in (2, 3) for t in ("f64", "f32") for lo, hi in ((2, 5), (6, 7), (8, 8))]
 
 LIBS = {
-    "libdg.so": ["host.cu", "volume.cu", "interface.cu", "misc.cu", "noalloc.cu", "batch.cu", "vjp.cu"]
+    "libdg.so": ["host.cu", "volume.cu", "interface.cu", "misc.cu", "noalloc.cu", "batch.cu", "vjp.cu", "gauss.cu"]
                 + VOLUME_OBJS,
     "libdgpeaks.so": ["peaks.cu"],
 }

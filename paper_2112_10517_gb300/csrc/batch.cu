@@ -328,7 +328,7 @@ dg_status dg_batch_create(dg_batch** out, dg_ctx* const* ctxs, int n, const doub
         c->gamma != c0->gamma)
       return DG_ERR_ARG;
     if (c->nd != 3 || c->p > dgk::kBatchMaxP || c->volume_flux != DG_VOL_RANOCHA ||
-      c->var.lm != 0)
+      c->var.lm != 0 || c->nodes != DG_NODES_LGL)
     return DG_ERR_UNSUPPORTED;
     if (((uintptr_t)u[i] | (uintptr_t)du[i]) & 7) return DG_ERR_ARG;
     const size_t bytes = (size_t)c->state_len * sizeof(double);

@@ -23,8 +23,8 @@ struct RefTables {
   double Dt[DG_MAXN * DG_MAXN];  // flux-differencing matrix 2D - M^{-1}B (Eq. opDsplit), zero diagonal
 };
 
-// Kernel ids for profiling
-enum { KID_VOLUME = 0, KID_INTERFACE = 1, KID_COUNT = 2 };
+// Kernel ids for profiling (KID_PROJECT: the entropy projection of the Gauss collocation scheme)
+enum { KID_VOLUME = 0, KID_INTERFACE = 1, KID_PROJECT = 2, KID_COUNT = 3 };
 
 // Reference tables of degree p (1..7), computed once on the host.
 const RefTables& ref_tables(int p);
@@ -71,6 +71,32 @@ cudaError_t launch_entropy_rate(int nd, int p, MeshDims md, const double* u, con
 int entropy_rate_blocks();
 void ck45_coefficients(int stage, double* a, double* b);
 
+// Legendre-Gauss reference tables of degree p (Sec. 6): nodes, weights and derivative matrix in `ref` (ref.Dt is
+// unused), and the Lagrange basis at xi = -1 and +1 (the rows of the face restriction R along a line).
+struct GaussTables {
+  RefTables ref;
+  double lm[DG_MAXN], lp[DG_MAXN];
+};
+const GaussTables& gauss_tables(int p);
+
+// One part of the Gauss collocation RHS (Sec. 6) on a Cartesian mesh: part 0 the entropy projection (u -> gface),
+// part 1 the interface fluxes (gface -> fstar), part 2 the volume term, lift and surface term (-> du, or the
+// stage update of *epi).
+struct GaussLaunch {
+  int nd, p, llf, part;
+  MeshDims md;
+  const double* u;
+  double* gface;  // [nd][E][2][nv][N^(nd-1)] entropy-projected face states (side 0: xi_n = -1)
+  double* fstar;  // [nd][E][nv][N^(nd-1)] outward flux of each element's upper face, scaled by 8
+  double* du;
+  double c[3];    // 2/h_n
+  double gamma;
+  int* flag;
+  const Epilogue* epi;
+  cudaStream_t s;
+};
+cudaError_t launch_gauss(const GaussLaunch& L);
+
 }  // namespace dgk
 
 // The context behind the opaque dg_ctx handle.
@@ -81,6 +107,8 @@ struct dg_ctx {
   long long E, ndofs, state_len;
   double gamma;
   int precision, surface_flux, volume_flux;
+  int nodes;          // DG_NODES_LGL or DG_NODES_GAUSS
+  double gauss_c[3];  // Gauss collocation: 2/h_n
   dgk::Variant var;  // flux and Cartesian specialisation used by dg_rhs / dg_step
   // host copies (FP64)
   double* h_xyz;  // [E][nd][Nd]
@@ -93,6 +121,7 @@ struct dg_ctx {
   double* d_JW;    // J * tensor LGL weight, [E][Nd]
   void* d_face;    // face fluxes [nd][E][nv][N^(nd-1)], FP64 or FP32
   double* d_fadj;  // dg_vjp: face adjoint contributions [nd][E][2][nv][N^(nd-1)] (allocated at the first dg_vjp)
+  double* d_gface;  // Gauss collocation: projected face states [nd][E][2][nv][N^(nd-1)]
   double* d_red;   // entropy-rate partials + result
   int* d_flag;     // non-physical-state flag
   cudaStream_t last_stream;

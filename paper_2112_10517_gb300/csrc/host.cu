@@ -200,6 +200,7 @@ void release(dg_ctx* c) {
   cudaFree(c->d_JW);
   cudaFree(c->d_face);
   cudaFree(c->d_fadj);
+  cudaFree(c->d_gface);
   cudaFree(c->d_red);
   cudaFree(c->d_flag);
   if (c->prof_ev) {
@@ -243,6 +244,42 @@ dg_status bounded_sync(cudaStream_t s, double seconds) {
   return st;
 }
 
+}  // namespace
+
+namespace dgk {
+void prof_begin(dg_ctx* c, int kid, cudaStream_t s, int* slot);
+void prof_end(dg_ctx* c, cudaStream_t s, int slot);
+}  // namespace dgk
+
+namespace {
+// The Gauss collocation RHS (Sec. 6): entropy projection, interface fluxes, volume term (store du, or the stage
+// update of *epi).
+dg_status gauss_rhs(dg_ctx* c, const double* u, double* du, const dgk::Epilogue* epi, cudaStream_t s) {
+  dgk::GaussLaunch L{};
+  L.nd = c->nd;
+  L.p = c->p;
+  L.llf = c->surface_flux == DG_SURF_EC_LLF;
+  L.md = c->md;
+  L.u = u;
+  L.gface = c->d_gface;
+  L.fstar = static_cast<double*>(c->d_face);
+  L.du = du;
+  for (int d = 0; d < 3; ++d) L.c[d] = c->gauss_c[d];
+  L.gamma = c->gamma;
+  L.flag = c->d_flag;
+  L.epi = epi;
+  L.s = s;
+  const int kid[3] = {dgk::KID_PROJECT, dgk::KID_INTERFACE, dgk::KID_VOLUME};
+  for (int part = 0; part < 3; ++part) {
+    L.part = part;
+    int slot;
+    dgk::prof_begin(c, kid[part], s, &slot);
+    const cudaError_t e = dgk::launch_gauss(L);
+    dgk::prof_end(c, s, slot);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return DG_OK;
+}
 }  // namespace
 
 namespace dgk {
@@ -309,8 +346,13 @@ dg_status dg_init(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metri
   if (opts->volume_flux != DG_VOL_RANOCHA && opts->volume_flux != DG_VOL_SHIMA) return DG_ERR_ARG;
   if (opts->surface_flux != DG_SURF_EC && opts->surface_flux != DG_SURF_EC_LLF) return DG_ERR_ARG;
   if (opts->precision != DG_FP64 && opts->precision != DG_FP32) return DG_ERR_ARG;
-  for (int r = 0; r < 3; ++r)
+  for (int r = 0; r < 2; ++r)
     if (opts->reserved[r] != 0) return DG_ERR_ARG;
+  if (opts->nodes != DG_NODES_LGL && opts->nodes != DG_NODES_GAUSS) return DG_ERR_ARG;
+  const bool gauss = opts->nodes == DG_NODES_GAUSS;
+  if (gauss && (mesh->mapping != DG_MAP_AFFINE || (metrics && metrics->Ja_host) || opts->precision != DG_FP64 ||
+                opts->volume_flux != DG_VOL_RANOCHA || opts->precompute_logs || opts->logmean))
+    return DG_ERR_UNSUPPORTED;
   if (opts->precompute_logs != 0 && opts->precompute_logs != 1) return DG_ERR_ARG;
   if (opts->logmean < DG_LOGMEAN_SHARED_RCP || opts->logmean > DG_LOGMEAN_ALG_POLY) return DG_ERR_ARG;
   if ((opts->precompute_logs || opts->logmean) && opts->volume_flux != DG_VOL_RANOCHA) return DG_ERR_UNSUPPORTED;
@@ -345,6 +387,7 @@ dg_status dg_init(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metri
   c->precision = opts->precision;
   c->surface_flux = opts->surface_flux;
   c->volume_flux = opts->volume_flux;
+  c->nodes = opts->nodes;
   // Cartesian specialisation: an affine box mesh has Ja^n = (prod_{k != n} h_k/2) e_n and J = prod_k h_k/2
   c->var.flux = opts->volume_flux;
   c->var.cart = (mesh->mapping == DG_MAP_AFFINE && !(metrics && metrics->Ja_host) &&
@@ -358,9 +401,11 @@ dg_status dg_init(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metri
     }
     for (int d = 0; d < 3; ++d) c->var.jn[d] = d < nd ? jac / hh[d] : 0.0;
     c->var.invJ = 1.0 / jac;
+    for (int d = 0; d < 3; ++d) c->gauss_c[d] = d < nd ? 1.0 / hh[d] : 0.0;  // 2/h_n
   }
 
-  const dgk::RefTables& t = dgk::ref_tables(polydeg);
+  // LGL or Legendre-Gauss tables: node coordinates, metric terms and the quadrature weights of J*W follow them
+  const dgk::RefTables& t = gauss ? dgk::gauss_tables(polydeg).ref : dgk::ref_tables(polydeg);
   const size_t nx = (size_t)E * nd * Nd, nja = (size_t)E * nd * nd * Nd, nj = (size_t)E * Nd;
   c->h_xyz = (double*)malloc(nx * sizeof(double));
   c->h_Ja = (double*)malloc(nja * sizeof(double));
@@ -408,6 +453,7 @@ dg_status dg_init(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metri
   if (ce == cudaSuccess) ce = dev_alloc(&c->d_red, (size_t)2 * dgk::entropy_rate_blocks() + 2);
   if (ce == cudaSuccess) ce = dev_alloc(&c->d_flag, 1);
   if (ce == cudaSuccess && c->precision == DG_FP32) ce = dev_alloc(&c->d_Ja32, nja);
+  if (ce == cudaSuccess && gauss) ce = dev_alloc(&c->d_gface, 2 * nface);
   if (ce == cudaSuccess) ce = cudaMemcpy(c->d_Ja, c->h_Ja, nja * sizeof(double), cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) ce = cudaMemcpy(c->d_invJ, invJ.data(), nj * sizeof(double), cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) ce = cudaMemcpy(c->d_JW, JW.data(), nj * sizeof(double), cudaMemcpyHostToDevice);
@@ -450,6 +496,7 @@ dg_status dg_rhs(dg_ctx* c, const double* u, double* du, double t, dg_stream_t s
   if (((uintptr_t)u | (uintptr_t)du) & 7) return DG_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;
+  if (c->nodes == DG_NODES_GAUSS) return gauss_rhs(c, u, du, nullptr, s);
   int slot;
   dgk::prof_begin(c, dgk::KID_INTERFACE, s, &slot);
   const void* ja = c->precision == DG_FP32 ? (const void*)c->d_Ja32 : (const void*)c->d_Ja;
@@ -490,6 +537,11 @@ dg_status dg_step(dg_ctx* c, double* u, double* scratch, double t, double dt, in
     const double* in = (scheme == DG_RK4_CLASSIC && st > 0) ? scratch : u;
     epi.stage = st;
     if (scheme == DG_LSRK45_CK) dgk::ck45_coefficients(st, &epi.a, &epi.b);
+    if (c->nodes == DG_NODES_GAUSS) {
+      const dg_status gs = gauss_rhs(c, in, nullptr, &epi, s);
+      if (gs != DG_OK) return gs;
+      continue;
+    }
     int slot;
     dgk::prof_begin(c, dgk::KID_INTERFACE, s, &slot);
     cudaError_t e = dgk::launch_interface(c->nd, c->p, c->precision, c->surface_flux == DG_SURF_EC_LLF, c->md, in,

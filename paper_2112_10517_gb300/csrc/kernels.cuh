@@ -161,6 +161,33 @@ __global__ void __launch_bounds__(256) interface_kernel(const double* __restrict
 //      with Dt_ik and Dt_ki; the line's sums stay in registers and go to shared memory per direction;
 //   C. one thread per node: sum the directions, add the lifted interface fluxes, scale by -1/J, store.
 // ---------------------------------------------------------------------------------------------------
+// The Runge-Kutta stage update at state offset o with the RHS value k (FP64), given the values of u (uo) and of
+// the stage register yo (RK4: acc, CK45: K; read only after stage 0):
+//   classical RK4, low storage: acc accumulates sum b_s dt k_s, y is the next stage state, u is updated last;
+//   CK(5,4) 2N: K = A_s K + dt k, u = u + B_s K (Sec. 4.1).
+template <int EPI>
+__device__ __forceinline__ void stage_update(const Epilogue& epi, size_t o, double k, double uo, double yo) {
+  if (EPI == EPI_RK4) {
+    const double dt = epi.dt;
+    if (epi.stage == 0) {
+      epi.acc[o] = (dt / 6.0) * k;
+      epi.y[o] = uo + (0.5 * dt) * k;
+    } else if (epi.stage == 1) {
+      epi.acc[o] = yo + (dt / 3.0) * k;
+      epi.y[o] = uo + (0.5 * dt) * k;
+    } else if (epi.stage == 2) {
+      epi.acc[o] = yo + (dt / 3.0) * k;
+      epi.y[o] = uo + dt * k;
+    } else {
+      epi.u[o] = uo + yo + (dt / 6.0) * k;
+    }
+  } else {
+    const double kk = (epi.stage == 0 ? 0.0 : epi.a * yo) + epi.dt * k;
+    epi.y[o] = kk;
+    epi.u[o] = uo + epi.b * kk;
+  }
+}
+
 // Positive floating-point values order like their bit patterns read as unsigned integers: shared-memory integer
 // atomicMin/atomicMax then give a tile's value range.
 template <typename T>
@@ -415,28 +442,10 @@ __device__ __forceinline__ void volume_tile(const double* u, const T* __restrict
       // FP64: k = -(1/J) tot in FP64. FP32 mode: the scaling in FP32 and an exact integer-pipe widening, so the
       // FP64 pipe only carries the RK accumulation below.
       const double k = sizeof(T) == 8 ? sj * (double)tot[c] : f2d_int((float)(sjT * tot[c]));
-      if (EPI == EPI_STORE) {
+      if (EPI == EPI_STORE)
         du[o] = k;
-      } else if (EPI == EPI_RK4) {
-        const double dt = epi.dt;
-        const double uo = s_eu[so];
-        if (epi.stage == 0) {
-          epi.acc[o] = (dt / 6.0) * k;
-          epi.y[o] = uo + (0.5 * dt) * k;
-        } else if (epi.stage == 1) {
-          epi.acc[o] = s_ey[so] + (dt / 3.0) * k;
-          epi.y[o] = uo + (0.5 * dt) * k;
-        } else if (epi.stage == 2) {
-          epi.acc[o] = s_ey[so] + (dt / 3.0) * k;
-          epi.y[o] = uo + dt * k;
-        } else {
-          epi.u[o] = uo + s_ey[so] + (dt / 6.0) * k;
-        }
-      } else {
-        const double kk = (epi.stage == 0 ? 0.0 : epi.a * s_ey[so]) + epi.dt * k;
-        epi.y[o] = kk;
-        epi.u[o] = s_eu[so] + epi.b * kk;
-      }
+      else
+        stage_update<EPI>(epi, o, k, s_eu[so], s_ey[so]);
     }
   }
 }

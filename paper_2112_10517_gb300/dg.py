@@ -30,8 +30,10 @@ DG_VOL_RANOCHA, DG_VOL_SHIMA = 0, 1
 FLUXES = {"ranocha": DG_VOL_RANOCHA, "shima": DG_VOL_SHIMA}
 DG_LOGMEAN_SHARED_RCP, DG_LOGMEAN_ALG, DG_LOGMEAN_ALG_POLY = 0, 1, 2
 LOGMEANS = {"rcp": DG_LOGMEAN_SHARED_RCP, "alg": DG_LOGMEAN_ALG, "alg_poly": DG_LOGMEAN_ALG_POLY}
+DG_NODES_LGL, DG_NODES_GAUSS = 0, 1
+NODES = {"lgl": DG_NODES_LGL, "gauss": DG_NODES_GAUSS}
 DG_RK4_CLASSIC, DG_LSRK45_CK = 0, 1
-KERNEL_VOLUME, KERNEL_INTERFACE = 0, 1
+KERNEL_VOLUME, KERNEL_INTERFACE, KERNEL_PROJECT = 0, 1, 2
 
 EXPORTED = ["dg_init", "dg_rhs", "dg_step", "dg_entropy_rate", "dg_check_status", "dg_get_info",
             "dg_get_node_coords", "dg_get_metrics", "dg_profile_enable", "dg_profile_read", "dg_launch_count",
@@ -52,7 +54,7 @@ class DgMetrics(ctypes.Structure):
 class DgOpts(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("volume_flux", ctypes.c_int), ("surface_flux", ctypes.c_int),
                 ("precision", ctypes.c_int), ("precompute_logs", ctypes.c_int), ("logmean", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("nodes", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class DgInfo(ctypes.Structure):
@@ -127,12 +129,14 @@ class DG:
     An affine mesh without node or metric overrides runs the Cartesian specialisation (constant Ja, 1/J).
     logmean ("rcp", "alg", "alg_poly") and precompute_logs select how the volume terms evaluate the logarithmic
     means of Ranocha's flux (Sec. 3.1, 7.2; see dg_opts in include/dg.h); the defaults are the fastest.
+    nodes: "lgl" (flux-differencing LGL-DGSEM) or "gauss" (Legendre-Gauss collocation with entropy projection,
+    Sec. 6; affine meshes, FP64, Ranocha's flux).
     """
 
     def __init__(self, ndims: int, nelem, polydeg: int, lo=None, hi=None, mapping: str = "affine", amp: float = 0.0,
                  node_xyz=None, Ja=None, J=None, gamma: float = 1.4, surface: str = "llf",
                  precision: str = "fp64", flux: str = "ranocha", logmean: str = "rcp",
-                 precompute_logs: bool = False):
+                 precompute_logs: bool = False, nodes: str = "lgl"):
         mesh = DgMesh()
         mesh.ndims = ndims
         ne = list(nelem) + [1] * (3 - len(nelem))
@@ -160,6 +164,7 @@ class DG:
         opts.volume_flux = FLUXES[flux]
         opts.logmean = LOGMEANS[logmean]
         opts.precompute_logs = 1 if precompute_logs else 0
+        opts.nodes = NODES[nodes]
         opts.surface_flux = {"ec": DG_SURF_EC, "llf": DG_SURF_EC_LLF}[surface]
         opts.precision = {"fp64": DG_FP64, "fp32": DG_FP32}[precision]
         ctx = ctypes.c_void_p()
