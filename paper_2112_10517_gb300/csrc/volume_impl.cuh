@@ -8,17 +8,27 @@ namespace dgk {
 namespace volume_detail {
 
 
-constexpr int kTargetThreads = 192;
+// Threads per CTA the element tile aims at (elements per CTA = this / threads per element), by flux precision;
+// compile-time tuning parameters. Measured at 16^3 and 32^3, p = 3 (3D): FP64 best at 192 (two CTAs of six warps
+// per SM, bound by the FP64 pipe), FP32 at 96 (finer tiles and smaller shared-memory footprint for the
+// memory-latency-bound kernel); tiles that leave a partial warp (144, 240) lose 10-20%.
+#ifndef DG_VOLUME_TARGET_THREADS_F64
+#define DG_VOLUME_TARGET_THREADS_F64 192
+#endif
+#ifndef DG_VOLUME_TARGET_THREADS_F32
+#define DG_VOLUME_TARGET_THREADS_F32 96
+#endif
 
-template <int ND, int N>
+template <int ND, int N, typename T>
 constexpr int elems_per_block() {
-  return Geo<ND, N>::TPE >= kTargetThreads ? 1 : kTargetThreads / Geo<ND, N>::TPE;
+  constexpr int target = sizeof(T) == 8 ? DG_VOLUME_TARGET_THREADS_F64 : DG_VOLUME_TARGET_THREADS_F32;
+  return Geo<ND, N>::TPE >= target ? 1 : target / Geo<ND, N>::TPE;
 }
 
 template <int ND, int N, typename T, int EPI, int LMK>
 cudaError_t launch_volume_k(MeshDims md, const double* u, const T* Ja, const double* invJ, const T* face, double* du,
                             double gamma, int* flag, cudaStream_t s, const Epilogue& epi, const Variant& var) {
-  constexpr int EPB = elems_per_block<ND, N>();
+  constexpr int EPB = elems_per_block<ND, N, T>();
   constexpr int threads = EPB * Geo<ND, N>::TPE;
   const size_t smem = VolumeSmem<ND, N, T>::bytes(EPB, EPI != EPI_STORE, LMK == LM_PRELOG);
   auto kern = volume_kernel<ND, N, T, EPB, EPI, LMK>;
