@@ -118,8 +118,9 @@ struct GaussOps {
 //   u(w): b = -w_E = rho/p, v = w_v/b, s = gamma - (gamma-1)(w_0 + b|v|^2/2), rho = exp((s + log b)/(1-gamma)).
 // Each returns false for a state outside the admissible set (rho, p or b not positive).
 // ---------------------------------------------------------------------------------------------------
+// igm1 = 1/(gamma - 1), passed in so that neither map divides.
 template <int ND>
-__device__ __forceinline__ bool entropy_vars(const double* u, double gamma, double* w) {
+__device__ __forceinline__ bool entropy_vars(const double* u, double gamma, double igm1, double* w) {
   const double rho = u[0];
   const double ir = Num<double>::rcp(rho);
   double v[ND], mv = 0.0;
@@ -131,7 +132,7 @@ __device__ __forceinline__ bool entropy_vars(const double* u, double gamma, doub
   const double p = (gamma - 1.0) * (u[ND + 1] - 0.5 * mv);
   const double b = rho * Num<double>::rcp(p);  // rho / p
   const double s = log(p) - gamma * log(rho);
-  w[0] = (gamma - s) / (gamma - 1.0) - 0.5 * b * (mv * ir);
+  w[0] = (gamma - s) * igm1 - 0.5 * b * (mv * ir);
 #pragma unroll
   for (int j = 0; j < ND; ++j) w[1 + j] = b * v[j];
   w[ND + 1] = -b;
@@ -139,7 +140,7 @@ __device__ __forceinline__ bool entropy_vars(const double* u, double gamma, doub
 }
 
 template <int ND>
-__device__ __forceinline__ bool cons_from_entropy(const double* w, double gamma, double* u) {
+__device__ __forceinline__ bool cons_from_entropy(const double* w, double gamma, double igm1, double* u) {
   const double b = -w[ND + 1];
   const double ib = Num<double>::rcp(b);
   double v[ND], v2 = 0.0;
@@ -149,12 +150,12 @@ __device__ __forceinline__ bool cons_from_entropy(const double* w, double gamma,
     v2 += v[j] * v[j];
   }
   const double s = gamma - (gamma - 1.0) * (w[0] + 0.5 * b * v2);
-  const double rho = exp((s + log(b)) / (1.0 - gamma));
+  const double rho = exp(-(s + log(b)) * igm1);
   const double p = rho * ib;
   u[0] = rho;
 #pragma unroll
   for (int j = 0; j < ND; ++j) u[1 + j] = rho * v[j];
-  u[ND + 1] = p / (gamma - 1.0) + 0.5 * rho * v2;
+  u[ND + 1] = p * igm1 + 0.5 * rho * v2;
   return b > 0.0 && rho > 0.0 && rho < 1e300;
 }
 
@@ -187,6 +188,7 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE)
   __shared__ double s_w[EPB * G::NV * G::NDOF];
   const int e0 = blockIdx.x * EPB, tid = threadIdx.x;
   const int nel = min(EPB, md.E - e0);
+  const double igm1 = 1.0 / (gamma - 1.0);
   bool ok = true;
   for (int idx = tid; idx < nel * G::NDOF; idx += kThreads) {
     const int el = idx / G::NDOF, i = idx - el * G::NDOF;
@@ -194,7 +196,7 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE)
     double uc[G::NV], w[G::NV];
 #pragma unroll
     for (int c = 0; c < G::NV; ++c) uc[c] = ue[c * G::NDOF];
-    ok &= entropy_vars<ND>(uc, gamma, w);
+    ok &= entropy_vars<ND>(uc, gamma, igm1, w);
 #pragma unroll
     for (int c = 0; c < G::NV; ++c) s_w[(el * G::NV + c) * G::NDOF + i] = w[c];
   }
@@ -218,8 +220,8 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE)
       wp[c] = ap;
     }
     double um[G::NV], up[G::NV];
-    ok &= cons_from_entropy<ND>(wm, gamma, um);
-    ok &= cons_from_entropy<ND>(wp, gamma, up);
+    ok &= cons_from_entropy<ND>(wm, gamma, igm1, um);
+    ok &= cons_from_entropy<ND>(wp, gamma, igm1, up);
     double* gf = gface + ((size_t)n * md.E + (e0 + el)) * 2 * G::NV * G::NL + l;
 #pragma unroll
     for (int c = 0; c < G::NV; ++c) {
