@@ -5,7 +5,8 @@
  * device's rates for these operations bound the kernel.
  *
  * Kinds: 0 fp64 FMA, 1 fp32 FMA, 2 fp64 division, 3 fp64 log, 4 fp32 logf, 5 fp32 lg2.approx (special-function
- * unit), 6 fp32 rcp.approx, 7 fp32 division, 8 fp64 reciprocal (round to nearest).
+ * unit), 6 fp32 rcp.approx, 7 fp32 division, 8 fp64 reciprocal (round to nearest), 9 the RHS kernels' fp64
+ * logarithm (log_f64), 10 fp64 exp.
  * Runs on the current device; allocates and frees a small device buffer; synchronizes the device.
  */
 #ifndef DG_PEAKS_H
@@ -35,6 +36,11 @@ int dgpk_eval_logmeans(long long n, int precision, const double* a1, const doubl
    f_int/f_hw receive the float bit patterns of d2f_int(x) and __double2float_rn(x), d_int/d_hw the widenings of that
    float. Device arrays of n elements; synchronizes; returns 0 or a cudaError_t value. */
 int dgpk_eval_convert(long long n, const double* x, unsigned* f_int, unsigned* f_hw, double* d_int, double* d_hw);
+
+/* Self-test of the RHS kernels' FP64 natural logarithm (Cody and Waite's argument reduction with an atanh series;
+   used by the logarithmic means and the entropy projection) against CUDA's log: log_own/log_ref receive
+   log_f64(x[i]) / log(x[i]). Device arrays of n elements; synchronizes; returns 0 or a cudaError_t value. */
+int dgpk_eval_log(long long n, const double* x, double* log_own, double* log_ref);
 
 #ifdef __cplusplus
 }

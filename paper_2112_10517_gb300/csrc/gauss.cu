@@ -131,7 +131,7 @@ __device__ __forceinline__ bool entropy_vars(const double* u, double gamma, doub
   }
   const double p = (gamma - 1.0) * (u[ND + 1] - 0.5 * mv);
   const double b = rho * Num<double>::rcp(p);  // rho / p
-  const double s = log(p) - gamma * log(rho);
+  const double s = log_f64(p) - gamma * log_f64(rho);
   w[0] = (gamma - s) * igm1 - 0.5 * b * (mv * ir);
 #pragma unroll
   for (int j = 0; j < ND; ++j) w[1 + j] = b * v[j];
@@ -150,7 +150,7 @@ __device__ __forceinline__ bool cons_from_entropy(const double* w, double gamma,
     v2 += v[j] * v[j];
   }
   const double s = gamma - (gamma - 1.0) * (w[0] + 0.5 * b * v2);
-  const double rho = exp(-(s + log(b)) * igm1);
+  const double rho = exp(-(s + log_f64(b)) * igm1);
   const double p = rho * ib;
   u[0] = rho;
 #pragma unroll

@@ -25,7 +25,9 @@ enum Kind : int {
   K_MUFU_RCP = 6,  // fp32 rcp.approx (special-function unit)
   K_FDIV = 7,      // fp32 IEEE division
   K_DRCP = 8,      // fp64 reciprocal, round to nearest
-  K_NKINDS = 9
+  K_DLOG_OWN = 9,  // fp64 log_f64 of the RHS kernels
+  K_DEXP = 10,     // fp64 exp()
+  K_NKINDS = 11
 };
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -66,6 +68,8 @@ __global__ void chain_kernel(double* sink, int iters, double seed) {
       if (KIND == K_MUFU_RCP) f[c] = rcp_approx(f[c] + af);
       if (KIND == K_FDIV) f[c] = 2.0f + bf / f[c];
       if (KIND == K_DRCP) d[c] = 2.0 + __drcp_rn(d[c]);
+      if (KIND == K_DLOG_OWN) d[c] = 1.0 + dgk::log_f64(d[c] + b);
+      if (KIND == K_DEXP) d[c] = exp(0.5 - d[c] * a);
     }
   }
   double acc = 0.0;
@@ -94,6 +98,8 @@ cudaError_t launch_kind(int kind, int blocks, int threads, double* sink, int ite
     case K_MUFU_RCP: return launch<K_MUFU_RCP>(blocks, threads, sink, iters, s);
     case K_FDIV: return launch<K_FDIV>(blocks, threads, sink, iters, s);
     case K_DRCP: return launch<K_DRCP>(blocks, threads, sink, iters, s);
+    case K_DLOG_OWN: return launch<K_DLOG_OWN>(blocks, threads, sink, iters, s);
+    case K_DEXP: return launch<K_DEXP>(blocks, threads, sink, iters, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -121,9 +127,26 @@ __global__ void convert_kernel(long long n, const double* x, unsigned* f_int, un
   d_hw[i] = (double)hw;
 }
 
+__global__ void log_kernel(long long n, const double* x, double* log_own, double* log_ref) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  log_own[i] = dgk::log_f64(x[i]);
+  log_ref[i] = log(x[i]);
+}
+
 }  // namespace
 
 extern "C" {
+
+// Self-test of the RHS kernels' FP64 logarithm against CUDA's log: for i < n, log_own/log_ref = log_f64(x[i]) /
+// log(x[i]). Device arrays; synchronizes; returns 0 or a cudaError_t value.
+int dgpk_eval_log(long long n, const double* x, double* log_own, double* log_ref) {
+  if (n <= 0) return 0;
+  log_kernel<<<(unsigned)((n + 255) / 256), 256>>>(n, x, log_own, log_ref);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return (int)e;
+}
 
 // Self-test of the integer-pipe format conversions of the RHS kernels against the hardware conversions: for
 // i < n, f_int[i] / f_hw[i] = bits of d2f_int(x[i]) / __double2float_rn(x[i]); d_int[i] / d_hw[i] = f2d_int and
