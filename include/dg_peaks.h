@@ -6,7 +6,7 @@
  *
  * Kinds: 0 fp64 FMA, 1 fp32 FMA, 2 fp64 division, 3 fp64 log, 4 fp32 logf, 5 fp32 lg2.approx (special-function
  * unit), 6 fp32 rcp.approx, 7 fp32 division, 8 fp64 reciprocal (round to nearest), 9 the RHS kernels' fp64
- * logarithm (log_f64), 10 fp64 exp.
+ * logarithm (log_f64), 10 fp64 exp, 11 fp64 sqrt, 12 the RHS kernels' fp64 square root (sqrt_f64).
  * Runs on the current device; allocates and frees a small device buffer; synchronizes the device.
  */
 #ifndef DG_PEAKS_H
@@ -41,6 +41,11 @@ int dgpk_eval_convert(long long n, const double* x, unsigned* f_int, unsigned* f
    used by the logarithmic means and the entropy projection) against CUDA's log: log_own/log_ref receive
    log_f64(x[i]) / log(x[i]). Device arrays of n elements; synchronizes; returns 0 or a cudaError_t value. */
 int dgpk_eval_log(long long n, const double* x, double* log_own, double* log_ref);
+
+/* Self-test of the RHS kernels' FP64 square root (Goldschmidt's iteration from rsqrt.approx; the LLF wave speeds)
+   against CUDA's sqrt: own/ref receive sqrt_f64(x[i]) / sqrt(x[i]). Device arrays; synchronizes; returns 0 or a
+   cudaError_t value. */
+int dgpk_eval_sqrt(long long n, const double* x, double* own, double* ref);
 
 #ifdef __cplusplus
 }

@@ -68,6 +68,23 @@ __device__ __forceinline__ double log_f64(double x) {
   return fma(kd, kLn2Head, fma(kd, kLn2Tail, logm));
 }
 
+// sqrt x for positive normal x by Goldschmidt's iteration for the square root: from r ~ 1/sqrt(x)
+// (rsqrt.approx.ftz.f64), g = x r ~ sqrt(x) and h = r/2 are refined together by e = 1/2 - g h,
+// g <- g + g e, h <- h + h e, which doubles the number of correct bits per step; two steps reach the rounding
+// limit (about 1 ulp). x = 0 gives 0; other non-positive or non-finite x give NaN or inf.
+__device__ __forceinline__ double sqrt_f64(double x) {
+  if (!(x > 0.0) || x == __longlong_as_double(0x7FF0000000000000LL))
+    return x == 0.0 ? x : (x > 0.0 ? x : __longlong_as_double(0x7FF8000000000000LL));
+  double r;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double g = x * r, h = 0.5 * r;
+  double e = fma(-g, h, 0.5);
+  g = fma(g, e, g);
+  h = fma(h, e, h);
+  e = fma(-g, h, 0.5);
+  return fma(g, e, g);
+}
+
 template <typename T>
 struct Num;
 
@@ -86,7 +103,7 @@ struct Num<double> {
   }
   __device__ static __forceinline__ double log(double x) { return log_f64(x); }
   __device__ static __forceinline__ double log1p(double x) { return ::log1p(x); }
-  __device__ static __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+  __device__ static __forceinline__ double sqrt(double x) { return sqrt_f64(x); }
   __device__ static __forceinline__ double abs(double x) { return ::fabs(x); }
   // u < 1e-4, the threshold of the series branch of Algorithms 2 and 3 for 64-bit floats (Sec. 3.1), tested on
   // the high 32 bits of u >= 0 (an integer comparison): the effective threshold is the largest double whose

@@ -27,7 +27,9 @@ enum Kind : int {
   K_DRCP = 8,      // fp64 reciprocal, round to nearest
   K_DLOG_OWN = 9,  // fp64 log_f64 of the RHS kernels
   K_DEXP = 10,     // fp64 exp()
-  K_NKINDS = 11
+  K_DSQRT = 11,    // fp64 sqrt()
+  K_DSQRT_OWN = 12,  // fp64 sqrt_f64 of the RHS kernels
+  K_NKINDS = 13
 };
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -70,6 +72,8 @@ __global__ void chain_kernel(double* sink, int iters, double seed) {
       if (KIND == K_DRCP) d[c] = 2.0 + __drcp_rn(d[c]);
       if (KIND == K_DLOG_OWN) d[c] = 1.0 + dgk::log_f64(d[c] + b);
       if (KIND == K_DEXP) d[c] = exp(0.5 - d[c] * a);
+      if (KIND == K_DSQRT) d[c] = 0.5 + sqrt(d[c] + b);
+      if (KIND == K_DSQRT_OWN) d[c] = 0.5 + dgk::sqrt_f64(d[c] + b);
     }
   }
   double acc = 0.0;
@@ -100,6 +104,8 @@ cudaError_t launch_kind(int kind, int blocks, int threads, double* sink, int ite
     case K_DRCP: return launch<K_DRCP>(blocks, threads, sink, iters, s);
     case K_DLOG_OWN: return launch<K_DLOG_OWN>(blocks, threads, sink, iters, s);
     case K_DEXP: return launch<K_DEXP>(blocks, threads, sink, iters, s);
+    case K_DSQRT: return launch<K_DSQRT>(blocks, threads, sink, iters, s);
+    case K_DSQRT_OWN: return launch<K_DSQRT_OWN>(blocks, threads, sink, iters, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -134,9 +140,25 @@ __global__ void log_kernel(long long n, const double* x, double* log_own, double
   log_ref[i] = log(x[i]);
 }
 
+__global__ void sqrt_kernel(long long n, const double* x, double* own, double* ref) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  own[i] = dgk::sqrt_f64(x[i]);
+  ref[i] = sqrt(x[i]);
+}
+
 }  // namespace
 
 extern "C" {
+
+// Self-test of the RHS kernels' FP64 square root against CUDA's sqrt: own/ref = sqrt_f64(x[i]) / sqrt(x[i]).
+int dgpk_eval_sqrt(long long n, const double* x, double* own, double* ref) {
+  if (n <= 0) return 0;
+  sqrt_kernel<<<(unsigned)((n + 255) / 256), 256>>>(n, x, own, ref);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return (int)e;
+}
 
 // Self-test of the RHS kernels' FP64 logarithm against CUDA's log: for i < n, log_own/log_ref = log_f64(x[i]) /
 // log(x[i]). Device arrays; synchronizes; returns 0 or a cudaError_t value.
