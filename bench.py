@@ -356,7 +356,8 @@ def run_batch(args, dev):
         del ctxs, us, dus
     out["workload"] = ("64 independent 3D Euler instances, n^3 elements (n uniform in 4..16), polydeg uniform "
                        "in 2..5, seeded smooth random states, curvilinear periodic [-pi,pi]^3, Ranocha + LLF, "
-                       "one dg_batch_rhs (2 launches) per step; inputs larger than L2")
+                       "one dg_batch_rhs (interface launch + one persistent volume launch per degree) per step; "
+                       "inputs larger than L2")
     out["speedup_fp32_vs_fp64"] = out["fp64"]["pid_ns"] / out["fp32"]["pid_ns"]
     return out
 

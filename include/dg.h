@@ -198,9 +198,9 @@ const char* dg_status_string(dg_status s);
  * gamma, and polydeg <= 5 (DG_ERR_UNSUPPORTED otherwise). Uses the contexts' metric terms, interface-flux
  * workspaces and non-physical flags (dg_check_status of each context reports its instance). Allocates small
  * device tables (work lists) and synchronizes.
- * dg_batch_rhs computes du[i] = RHS_i(u[i]) for every instance: it queues one memset and two kernels on `stream`
- * (all instances' interface fluxes, then one persistent volume kernel whose CTAs take element tiles, most
- * expensive first, from a shared counter). It allocates nothing and does not synchronize, so a sequence of calls
+ * dg_batch_rhs computes du[i] = RHS_i(u[i]) for every instance: it queues one memset and 1 + (number of distinct
+ * degrees) kernels on `stream` (all instances' interface fluxes, then per degree one persistent volume kernel
+ * whose CTAs take that degree's element tiles from a shared counter). It allocates nothing and does not synchronize, so a sequence of calls
  * can be captured in a CUDA graph after a first call outside the capture. Plans sharing a context must not run
  * concurrently (they share its workspace).
  * dg_batch_autotune times every tile shape (threads per CTA 128/192/256, which sets the elements per tile of

@@ -4,8 +4,9 @@
 // and their state buffers; dg_batch_rhs then queues one memset and two launches on a stream:
 //   1. one interface-flux launch over the face nodes of all instances (the instance is found by binary search
 //      in the prefix sums of the face-node counts),
-//   2. one persistent volume launch: each CTA repeatedly takes the next element tile from a global work
-//      counter (tiles ordered by decreasing cost) and runs the volume/lift/Jacobian code of that tile's degree.
+//   2. one persistent volume launch per polynomial degree present: each CTA repeatedly takes the next element
+//      tile of its degree from a global work counter and runs the volume/lift/Jacobian code. A kernel per degree
+//      keeps each degree's register allocation (one kernel over all degrees would carry the largest).
 // The work is the same per element as dg_rhs (Eq. fluxdiff-SBP-opDsplit); only the scheduling differs.
 #include <stdio.h>
 #include <string.h>
@@ -139,7 +140,8 @@ __device__ __forceinline__ void batch_tile(const BatchInst& in, int e0, T gamma,
                                                 gamma, in.flag, none, e0, smem, general_variant());
 }
 
-template <typename T, int THREADS>
+// Persistent volume kernel of one degree (N nodes per line): CTAs take tiles of that degree from the counter.
+template <int N, typename T, int THREADS>
 __global__ void __launch_bounds__(THREADS) batch_volume_kernel(const BatchInst* __restrict__ insts,
                                                                const BatchTile* __restrict__ tiles, int ntiles,
                                                                int* counter, T gamma) {
@@ -151,15 +153,7 @@ __global__ void __launch_bounds__(THREADS) batch_volume_kernel(const BatchInst* 
     const int t = s_tile;
     if (t >= ntiles) break;
     const BatchTile tl = tiles[t];
-    const BatchInst& in = insts[tl.inst];
-    switch (in.p) {
-      case 1: batch_tile<2, T, THREADS>(in, tl.e0, gamma, smem); break;
-      case 2: batch_tile<3, T, THREADS>(in, tl.e0, gamma, smem); break;
-      case 3: batch_tile<4, T, THREADS>(in, tl.e0, gamma, smem); break;
-      case 4: batch_tile<5, T, THREADS>(in, tl.e0, gamma, smem); break;
-      case 5: batch_tile<6, T, THREADS>(in, tl.e0, gamma, smem); break;
-      default: break;
-    }
+    batch_tile<N, T, THREADS>(insts[tl.inst], tl.e0, gamma, smem);
     __syncthreads();  // the next tile reuses shared memory and s_tile
   }
 }
@@ -200,46 +194,53 @@ cudaError_t ensure_const_ops(int device) {
   return e;
 }
 
-template <typename T, int THREADS>
-cudaError_t launch_batch_volume_t(const BatchInst* insts, const BatchTile* tiles, int ntiles, int* counter,
-                                  double gamma, size_t smem, int grid, cudaStream_t s) {
-  auto kern = batch_volume_kernel<T, THREADS>;
+// One entry point per (degree, precision, CTA size): its occupancy at a shared-memory size, or its launch.
+template <int N, typename T, int THREADS>
+cudaError_t batch_volume_call(bool launch, const BatchInst* insts, const BatchTile* tiles, int ntiles, int* counter,
+                              double gamma, size_t smem, int grid, cudaStream_t s, int* occupancy) {
+  auto kern = batch_volume_kernel<N, T, THREADS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  if (!launch) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, kern, THREADS, smem);
   kern<<<grid, THREADS, smem, s>>>(insts, tiles, ntiles, counter, (T)gamma);
   return cudaGetLastError();
 }
 
 template <typename T, int THREADS>
-int batch_occupancy(size_t smem) {
-  int blocks = 0;
-  auto kern = batch_volume_kernel<T, THREADS>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, THREADS, smem) != cudaSuccess) return 0;
-  return blocks;
+cudaError_t batch_volume_p(int p, bool launch, const BatchInst* insts, const BatchTile* tiles, int ntiles,
+                           int* counter, double gamma, size_t smem, int grid, cudaStream_t s, int* occupancy) {
+  switch (p) {
+    case 1: return batch_volume_call<2, T, THREADS>(launch, insts, tiles, ntiles, counter, gamma, smem, grid, s, occupancy);
+    case 2: return batch_volume_call<3, T, THREADS>(launch, insts, tiles, ntiles, counter, gamma, smem, grid, s, occupancy);
+    case 3: return batch_volume_call<4, T, THREADS>(launch, insts, tiles, ntiles, counter, gamma, smem, grid, s, occupancy);
+    case 4: return batch_volume_call<5, T, THREADS>(launch, insts, tiles, ntiles, counter, gamma, smem, grid, s, occupancy);
+    case 5: return batch_volume_call<6, T, THREADS>(launch, insts, tiles, ntiles, counter, gamma, smem, grid, s, occupancy);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
-int occupancy_for(int precision, int threads, size_t smem) {
+cudaError_t batch_volume(int precision, int threads, int p, bool launch, const BatchInst* insts,
+                         const BatchTile* tiles, int ntiles, int* counter, double gamma, size_t smem, int grid,
+                         cudaStream_t s, int* occupancy) {
   if (precision == DG_FP32) {
-    if (threads == 128) return batch_occupancy<float, 128>(smem);
-    if (threads == 192) return batch_occupancy<float, 192>(smem);
-    return batch_occupancy<float, 256>(smem);
+    if (threads == 128)
+      return batch_volume_p<float, 128>(p, launch, insts, tiles, ntiles, counter, gamma, smem, grid, s, occupancy);
+    if (threads == 192)
+      return batch_volume_p<float, 192>(p, launch, insts, tiles, ntiles, counter, gamma, smem, grid, s, occupancy);
+    return batch_volume_p<float, 256>(p, launch, insts, tiles, ntiles, counter, gamma, smem, grid, s, occupancy);
   }
-  if (threads == 128) return batch_occupancy<double, 128>(smem);
-  if (threads == 192) return batch_occupancy<double, 192>(smem);
-  return batch_occupancy<double, 256>(smem);
+  if (threads == 128)
+    return batch_volume_p<double, 128>(p, launch, insts, tiles, ntiles, counter, gamma, smem, grid, s, occupancy);
+  if (threads == 192)
+    return batch_volume_p<double, 192>(p, launch, insts, tiles, ntiles, counter, gamma, smem, grid, s, occupancy);
+  return batch_volume_p<double, 256>(p, launch, insts, tiles, ntiles, counter, gamma, smem, grid, s, occupancy);
 }
 
-cudaError_t launch_volume_for(int precision, int threads, const BatchInst* insts, const BatchTile* tiles, int ntiles,
-                              int* counter, double gamma, size_t smem, int grid, cudaStream_t s) {
-  if (precision == DG_FP32) {
-    if (threads == 128) return launch_batch_volume_t<float, 128>(insts, tiles, ntiles, counter, gamma, smem, grid, s);
-    if (threads == 192) return launch_batch_volume_t<float, 192>(insts, tiles, ntiles, counter, gamma, smem, grid, s);
-    return launch_batch_volume_t<float, 256>(insts, tiles, ntiles, counter, gamma, smem, grid, s);
-  }
-  if (threads == 128) return launch_batch_volume_t<double, 128>(insts, tiles, ntiles, counter, gamma, smem, grid, s);
-  if (threads == 192) return launch_batch_volume_t<double, 192>(insts, tiles, ntiles, counter, gamma, smem, grid, s);
-  return launch_batch_volume_t<double, 256>(insts, tiles, ntiles, counter, gamma, smem, grid, s);
+int occupancy_for(int precision, int threads, int p, size_t smem) {
+  int occ = 0;
+  if (batch_volume(precision, threads, p, false, nullptr, nullptr, 0, nullptr, 0.0, smem, 0, 0, &occ) != cudaSuccess)
+    return 0;
+  return occ;
 }
 
 }  // namespace
@@ -253,10 +254,12 @@ struct dg_batch {
   double gamma = 1.4;
   long long total_face_nodes = 0;
   dgk::BatchInst* d_inst = nullptr;
-  dgk::BatchTile* d_tiles[dgk::kNumThreadChoices] = {nullptr, nullptr, nullptr};
-  int ntiles[dgk::kNumThreadChoices] = {0, 0, 0};
-  size_t smem[dgk::kNumThreadChoices] = {0, 0, 0};
-  int* d_counter = nullptr;
+  // element tiles per CTA size and degree (index p), and the shared memory of that degree's kernel
+  dgk::BatchTile* d_tiles[dgk::kNumThreadChoices][dgk::kBatchMaxP + 1] = {};
+  int ntiles[dgk::kNumThreadChoices][dgk::kBatchMaxP + 1] = {};
+  size_t smem[dgk::kNumThreadChoices][dgk::kBatchMaxP + 1] = {};
+  int* d_counter = nullptr;  // one work counter per degree
+  int occ[dgk::kNumThreadChoices][dgk::kBatchMaxP + 1];  // occupancy limits, -1 until queried
   int threads_idx = 1;  // 192 threads per CTA until tuned
   int ctas_per_sm = 0;  // 0: the occupancy limit
   std::string signature;
@@ -267,7 +270,8 @@ namespace {
 void batch_release(dg_batch* b) {
   if (!b) return;
   cudaFree(b->d_inst);
-  for (int i = 0; i < dgk::kNumThreadChoices; ++i) cudaFree(b->d_tiles[i]);
+  for (int i = 0; i < dgk::kNumThreadChoices; ++i)
+    for (int p = 0; p <= dgk::kBatchMaxP; ++p) cudaFree(b->d_tiles[i][p]);
   cudaFree(b->d_counter);
   delete b;
 }
@@ -277,15 +281,22 @@ dg_status to_status(cudaError_t e) {
   return e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
 }
 
-int grid_for(const dg_batch* b, int ti) {
-  const int occ = dgk::occupancy_for(b->precision, dgk::kThreadChoices[ti], b->smem[ti]);
-  if (occ <= 0) return 0;
-  const int per_sm = b->ctas_per_sm > 0 ? std::min(b->ctas_per_sm, occ) : occ;
-  return std::max(1, std::min(per_sm * b->sms, b->ntiles[ti]));
+// persistent grid of degree p's kernel: CTAs per SM (tuned, capped by the occupancy limit) times SMs, at most the
+// number of tiles
+int occupancy_of(dg_batch* b, int ti, int p) {
+  if (b->occ[ti][p] < 0) b->occ[ti][p] = dgk::occupancy_for(b->precision, dgk::kThreadChoices[ti], p, b->smem[ti][p]);
+  return b->occ[ti][p];
 }
 
-dg_status batch_launch(dg_batch* b, int ti, int grid, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), s);
+int grid_for(dg_batch* b, int ti, int p) {
+  const int occ = occupancy_of(b, ti, p);
+  if (occ <= 0) return 0;
+  const int per_sm = b->ctas_per_sm > 0 ? std::min(b->ctas_per_sm, occ) : occ;
+  return std::max(1, std::min(per_sm * b->sms, b->ntiles[ti][p]));
+}
+
+dg_status batch_launch(dg_batch* b, int ti, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int) * (dgk::kBatchMaxP + 1), s);
   if (e != cudaSuccess) return to_status(e);
   if (b->total_face_nodes > 0) {
     const long long blocks = (b->total_face_nodes + 255) / 256;
@@ -307,8 +318,13 @@ dg_status batch_launch(dg_batch* b, int ti, int grid, cudaStream_t s) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return to_status(e);
   }
-  e = dgk::launch_volume_for(b->precision, dgk::kThreadChoices[ti], b->d_inst, b->d_tiles[ti], b->ntiles[ti],
-                             b->d_counter, b->gamma, b->smem[ti], grid, s);
+  for (int p = 1; p <= dgk::kBatchMaxP && e == cudaSuccess; ++p) {
+    if (b->ntiles[ti][p] == 0) continue;
+    const int grid = grid_for(b, ti, p);
+    if (grid <= 0) return DG_ERR_CUDA;
+    e = dgk::batch_volume(b->precision, dgk::kThreadChoices[ti], p, true, b->d_inst, b->d_tiles[ti][p],
+                          b->ntiles[ti][p], b->d_counter + p, b->gamma, b->smem[ti][p], grid, s, nullptr);
+  }
   return to_status(e);
 }
 
@@ -339,6 +355,8 @@ dg_status dg_batch_create(dg_batch** out, dg_ctx* const* ctxs, int n, const doub
   if (cudaGetDevice(&cur) != cudaSuccess || cur != c0->device) return DG_ERR_ARG;
   dg_batch* b = new (std::nothrow) dg_batch();
   if (!b) return DG_ERR_OOM;
+  for (int ti = 0; ti < dgk::kNumThreadChoices; ++ti)
+    for (int p = 0; p <= dgk::kBatchMaxP; ++p) b->occ[ti][p] = -1;
   b->device = c0->device;
   b->n = n;
   b->precision = c0->precision;
@@ -373,33 +391,29 @@ dg_status dg_batch_create(dg_batch** out, dg_ctx* const* ctxs, int n, const doub
   snprintf(sig, sizeof(sig), "%s n=%d E=%lld p1-5=%d,%d,%d,%d,%d", c0->precision == DG_FP32 ? "fp32" : "fp64", n, elems,
            hist[1], hist[2], hist[3], hist[4], hist[5]);
   b->signature = sig;
-  // tile lists per CTA size, most expensive tiles first (pairs per tile ~ elements x p^4) for load balance
+  // tile lists per CTA size and degree; full tiles first, the instances' ragged last tiles at the end
   for (int ti = 0; ti < dgk::kNumThreadChoices && e == cudaSuccess; ++ti) {
     const int threads = dgk::kThreadChoices[ti];
-    std::vector<std::pair<double, dgk::BatchTile>> tl;
-    size_t smem = 0;
-    for (int i = 0; i < n; ++i) {
-      const int p = ctxs[i]->p, N = p + 1;
+    for (int p = 1; p <= dgk::kBatchMaxP && e == cudaSuccess; ++p) {
+      if (hist[p] == 0) continue;
       const int epb = dgk::batch_epb(p, b->precision, threads);
-      smem = std::max(smem, dgk::batch_smem(p, b->precision, threads));
-      const double cost = (double)epb * N * N * N * (double)N * (N - 1);
-      for (int e0 = 0; e0 < ctxs[i]->md.E; e0 += epb) {
-        const int nel = std::min(epb, ctxs[i]->md.E - e0);
-        tl.push_back({cost * nel / epb, dgk::BatchTile{i, e0}});
+      std::vector<dgk::BatchTile> full, ragged;
+      for (int i = 0; i < n; ++i) {
+        if (ctxs[i]->p != p) continue;
+        for (int e0 = 0; e0 < ctxs[i]->md.E; e0 += epb)
+          (ctxs[i]->md.E - e0 >= epb ? full : ragged).push_back(dgk::BatchTile{i, e0});
       }
+      full.insert(full.end(), ragged.begin(), ragged.end());
+      b->ntiles[ti][p] = (int)full.size();
+      b->smem[ti][p] = dgk::batch_smem(p, b->precision, threads);
+      e = cudaMalloc(&b->d_tiles[ti][p], full.size() * sizeof(dgk::BatchTile));
+      if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_tiles[ti][p], full.data(), full.size() * sizeof(dgk::BatchTile), cudaMemcpyHostToDevice);
     }
-    std::stable_sort(tl.begin(), tl.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
-    std::vector<dgk::BatchTile> tiles(tl.size());
-    for (size_t k = 0; k < tl.size(); ++k) tiles[k] = tl[k].second;
-    b->ntiles[ti] = (int)tiles.size();
-    b->smem[ti] = smem;
-    e = cudaMalloc(&b->d_tiles[ti], tiles.size() * sizeof(dgk::BatchTile));
-    if (e == cudaSuccess)
-      e = cudaMemcpy(b->d_tiles[ti], tiles.data(), tiles.size() * sizeof(dgk::BatchTile), cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess) e = cudaMalloc(&b->d_inst, n * sizeof(dgk::BatchInst));
   if (e == cudaSuccess) e = cudaMemcpy(b->d_inst, inst.data(), n * sizeof(dgk::BatchInst), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int) * (dgk::kBatchMaxP + 1));
   if (e != cudaSuccess) {
     batch_release(b);
     return to_status(e);
@@ -410,9 +424,7 @@ dg_status dg_batch_create(dg_batch** out, dg_ctx* const* ctxs, int n, const doub
 
 dg_status dg_batch_rhs(dg_batch* b, dg_stream_t stream) {
   if (!b) return DG_ERR_ARG;
-  const int grid = grid_for(b, b->threads_idx);
-  if (grid <= 0) return DG_ERR_CUDA;
-  return batch_launch(b, b->threads_idx, grid, (cudaStream_t)stream);
+  return batch_launch(b, b->threads_idx, (cudaStream_t)stream);
 }
 
 dg_status dg_batch_autotune(dg_batch* b, const char* cache_path, dg_stream_t stream, int* threads_out,
@@ -456,14 +468,15 @@ dg_status dg_batch_autotune(dg_batch* b, const char* cache_path, dg_stream_t str
   int best_ti = b->threads_idx, best_cps = b->ctas_per_sm;
   dg_status st = DG_OK;
   for (int ti = 0; ti < dgk::kNumThreadChoices && st == DG_OK; ++ti) {
-    const int occ = dgk::occupancy_for(b->precision, dgk::kThreadChoices[ti], b->smem[ti]);
+    int occ = 0;  // the largest occupancy limit over the degrees present (cps is capped per degree)
+    for (int p = 1; p <= dgk::kBatchMaxP; ++p)
+      if (b->ntiles[ti][p] > 0)
+        occ = std::max(occ, occupancy_of(b, ti, p));
     for (int cps = 1; cps <= occ && st == DG_OK; ++cps) {
       b->ctas_per_sm = cps;
-      const int grid = grid_for(b, ti);
-      if (grid <= 0) continue;
-      st = batch_launch(b, ti, grid, s);  // warm-up
+      st = batch_launch(b, ti, s);  // warm-up
       cudaEventRecord(t0, s);
-      for (int r = 0; r < 3 && st == DG_OK; ++r) st = batch_launch(b, ti, grid, s);
+      for (int r = 0; r < 3 && st == DG_OK; ++r) st = batch_launch(b, ti, s);
       cudaEventRecord(t1, s);
       if (st != DG_OK) break;
       if (cudaEventSynchronize(t1) != cudaSuccess) {
