@@ -325,10 +325,11 @@ def run_batch(args, dev):
     out = {}
     specs = batch_specs()
     lo, hi = [-math.pi] * 3, [math.pi] * 3
-    for precision in ("fp64", "fp32"):
+    for precision, logs in (("fp64", False), ("fp32", False), ("fp64", True), ("fp32", True)):
         ctxs, us, dus = [], [], []
         for k, (n, p) in enumerate(specs):
-            ctx = dg.DG(3, [n, n, n], p, lo=lo, hi=hi, mapping="sine", amp=AMP, surface="llf", precision=precision)
+            ctx = dg.DG(3, [n, n, n], p, lo=lo, hi=hi, mapping="sine", amp=AMP, surface="llf", precision=precision,
+                        precompute_logs=logs)
             u = inputs.smooth_random(ctx.node_coords(), seed=1000 + k)
             ctxs.append(ctx)
             us.append(torch.from_numpy(u).to(dev))
@@ -349,8 +350,9 @@ def run_batch(args, dev):
         bad = [i for i, c in enumerate(ctxs) if c.check_status() != dg.DG_OK]
         if bad:
             raise RuntimeError("non-physical state in batch instances %s" % bad)
-        out[precision] = {"pid_ns": ms * 1e6 / batch.ndofs, "ms_per_batch_rhs": ms,
-                          "tuning": {"threads_per_cta": tuning[0], "ctas_per_sm": tuning[1]}}
+        out[precision + ("_precomputed_logs" if logs else "")] = {
+            "pid_ns": ms * 1e6 / batch.ndofs, "ms_per_batch_rhs": ms,
+            "tuning": {"threads_per_cta": tuning[0], "ctas_per_sm": tuning[1]}}
         out["ndofs"] = batch.ndofs
         batch.close()
         del ctxs, us, dus

@@ -103,7 +103,8 @@ typedef struct dg_metrics {
                                       node, which leaves the differences, i.e. the logs of the ratios, unchanged).
    Non-default values need DG_VOL_RANOCHA (else DG_ERR_UNSUPPORTED); the DG_LOGMEAN_ALG* variants run the
    general metric path on an affine mesh and are available in dg_rhs only (dg_step returns DG_ERR_UNSUPPORTED).
-   The interface fluxes always use the default. dg_vjp and dg_batch_* accept the default only.
+   The interface fluxes always use the default. dg_vjp accepts the default only; dg_batch_* the default or
+   precompute_logs (the same for all contexts of a batch).
    nodes: DG_NODES_LGL, the flux-differencing LGL-DGSEM above, or DG_NODES_GAUSS, the Legendre-Gauss collocation
    scheme with entropy projection (Sec. 6, Eq. fluxdiff-GSBP-opDsplit with the hybridized volume terms of Eq.
    hybridized_gauss_formulation): the state lives at the tensor-product Gauss nodes (dg_get_node_coords), face

@@ -71,34 +71,38 @@ DG_BATCH_CONST_GET(5)
 DG_BATCH_CONST_GET(6)
 
 // elements per tile for degree N at a CTA size: as many element line sets as fit, capped by shared memory
-template <int N, typename T, int THREADS>
+template <int N, typename T, int THREADS, int LMK = LM_SHARED_RCP>
 struct BatchEpb {
   static constexpr int kByThreads = THREADS / Geo<3, N>::TPE;
-  static constexpr int kBySmem = (int)(200 * 1024 / VolumeSmem<3, N, T>::bytes(1, false));
+  static constexpr int kBySmem = (int)(200 * 1024 / VolumeSmem<3, N, T>::bytes(1, false, LMK == LM_PRELOG));
   static constexpr int value = kByThreads < kBySmem ? kByThreads : kBySmem;
   static_assert(value >= 1, "CTA too small for this degree");
 };
 
-int batch_epb(int p, int precision, int threads) {
+// shared memory per element of the volume tile (node quantities, metric terms, accumulators; with precomputed
+// logarithms two more values per node and four range slots), as VolumeSmem<3, N, T>::bytes(1, false, logs)
+size_t batch_smem_per_elem(int p, int precision, bool logs) {
+  const int N = p + 1;
+  return (size_t)((6 + 9 + 15) * N * N * N + (logs ? 2 * N * N * N + 4 : 0)) * (precision == DG_FP32 ? 4 : 8);
+}
+
+int batch_epb(int p, int precision, int threads, bool logs) {
   const int N = p + 1;
   const int tpe = 3 * N * N;
-  const size_t per = (size_t)(6 + 9 + 15) * N * N * N * (precision == DG_FP32 ? 4 : 8);
-  const int by_t = threads / tpe, by_s = (int)(200 * 1024 / per);
+  const int by_t = threads / tpe, by_s = (int)(200 * 1024 / batch_smem_per_elem(p, precision, logs));
   return std::max(1, std::min(by_t, by_s));
 }
 
-size_t batch_smem(int p, int precision, int threads) {
-  const int N = p + 1;
-  const size_t per = (size_t)(6 + 9 + 15) * N * N * N * (precision == DG_FP32 ? 4 : 8);
-  return per * batch_epb(p, precision, threads);
+size_t batch_smem(int p, int precision, int threads, bool logs) {
+  return batch_smem_per_elem(p, precision, logs) * batch_epb(p, precision, threads, logs);
 }
 
 // batches use Ranocha's flux on the instances' metric arrays (a compile-time variant, so only that loop is built)
-__device__ __forceinline__ Variant general_variant() {
+__device__ __forceinline__ Variant general_variant(int lm = LM_SHARED_RCP) {
   Variant v;
   v.flux = 0;
   v.cart = 0;
-  v.lm = 0;
+  v.lm = lm;
   v.jn[0] = v.jn[1] = v.jn[2] = 0.0;
   v.invJ = 0.0;
   return v;
@@ -130,18 +134,20 @@ __global__ void __launch_bounds__(256) batch_interface_kernel(const BatchInst* _
   }
 }
 
-template <int N, typename T, int THREADS>
+template <int N, typename T, int THREADS, int LMK>
 __device__ __forceinline__ void batch_tile(const BatchInst& in, int e0, T gamma, unsigned char* smem) {
-  constexpr int EPB = BatchEpb<N, T, THREADS>::value;
+  constexpr int EPB = BatchEpb<N, T, THREADS, LMK>::value;
   Epilogue none{};
   none.mode = EPI_STORE;
-  volume_tile<3, N, T, EPB, EPI_STORE, THREADS>(in.u, static_cast<const T*>(in.Ja), in.invJ,
-                                                static_cast<const T*>(in.face), in.du, in.md, ConstOp<N, T>::get(),
-                                                gamma, in.flag, none, e0, smem, general_variant());
+  volume_tile<3, N, T, EPB, EPI_STORE, THREADS, LMK>(in.u, static_cast<const T*>(in.Ja), in.invJ,
+                                                     static_cast<const T*>(in.face), in.du, in.md,
+                                                     ConstOp<N, T>::get(), gamma, in.flag, none, e0, smem,
+                                                     general_variant(LMK));
 }
 
 // Persistent volume kernel of one degree (N nodes per line): CTAs take tiles of that degree from the counter.
-template <int N, typename T, int THREADS>
+// LMK: the log-mean variant of the batch's contexts (the default, or logarithms precomputed per node).
+template <int N, typename T, int THREADS, int LMK>
 __global__ void __launch_bounds__(THREADS) batch_volume_kernel(const BatchInst* __restrict__ insts,
                                                                const BatchTile* __restrict__ tiles, int ntiles,
                                                                int* counter, T gamma) {
@@ -153,7 +159,7 @@ __global__ void __launch_bounds__(THREADS) batch_volume_kernel(const BatchInst* 
     const int t = s_tile;
     if (t >= ntiles) break;
     const BatchTile tl = tiles[t];
-    batch_tile<N, T, THREADS>(insts[tl.inst], tl.e0, gamma, smem);
+    batch_tile<N, T, THREADS, LMK>(insts[tl.inst], tl.e0, gamma, smem);
     __syncthreads();  // the next tile reuses shared memory and s_tile
   }
 }
@@ -196,9 +202,10 @@ cudaError_t ensure_const_ops(int device) {
 
 // One entry point per (degree, precision, CTA size): its occupancy at a shared-memory size, or its launch.
 template <int N, typename T, int THREADS>
-cudaError_t batch_volume_call(bool launch, const BatchInst* insts, const BatchTile* tiles, int ntiles, int* counter,
-                              double gamma, size_t smem, int grid, cudaStream_t s, int* occupancy) {
-  auto kern = batch_volume_kernel<N, T, THREADS>;
+cudaError_t batch_volume_call(int lm, bool launch, const BatchInst* insts, const BatchTile* tiles, int ntiles,
+                              int* counter, double gamma, size_t smem, int grid, cudaStream_t s, int* occupancy) {
+  auto kern = lm == LM_PRELOG ? batch_volume_kernel<N, T, THREADS, LM_PRELOG>
+                              : batch_volume_kernel<N, T, THREADS, LM_SHARED_RCP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (!launch) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, kern, THREADS, smem);
@@ -206,40 +213,52 @@ cudaError_t batch_volume_call(bool launch, const BatchInst* insts, const BatchTi
   return cudaGetLastError();
 }
 
+// The arguments of one degree's persistent launch (or of its occupancy query).
+struct BatchCall {
+  int lm;
+  bool launch;
+  const BatchInst* insts;
+  const BatchTile* tiles;
+  int ntiles;
+  int* counter;
+  double gamma;
+  size_t smem;
+  int grid;
+  cudaStream_t s;
+  int* occupancy;
+};
+
 template <typename T, int THREADS>
-cudaError_t batch_volume_p(int p, bool launch, const BatchInst* insts, const BatchTile* tiles, int ntiles,
-                           int* counter, double gamma, size_t smem, int grid, cudaStream_t s, int* occupancy) {
+cudaError_t batch_volume_p(int p, const BatchCall& c) {
+#define DG_BATCH_CALL(NN)                                                                                        \
+  batch_volume_call<NN, T, THREADS>(c.lm, c.launch, c.insts, c.tiles, c.ntiles, c.counter, c.gamma, c.smem, c.grid, \
+                                    c.s, c.occupancy)
   switch (p) {
-    case 1: return batch_volume_call<2, T, THREADS>(launch, insts, tiles, ntiles, counter, gamma, smem, grid, s, occupancy);
-    case 2: return batch_volume_call<3, T, THREADS>(launch, insts, tiles, ntiles, counter, gamma, smem, grid, s, occupancy);
-    case 3: return batch_volume_call<4, T, THREADS>(launch, insts, tiles, ntiles, counter, gamma, smem, grid, s, occupancy);
-    case 4: return batch_volume_call<5, T, THREADS>(launch, insts, tiles, ntiles, counter, gamma, smem, grid, s, occupancy);
-    case 5: return batch_volume_call<6, T, THREADS>(launch, insts, tiles, ntiles, counter, gamma, smem, grid, s, occupancy);
+    case 1: return DG_BATCH_CALL(2);
+    case 2: return DG_BATCH_CALL(3);
+    case 3: return DG_BATCH_CALL(4);
+    case 4: return DG_BATCH_CALL(5);
+    case 5: return DG_BATCH_CALL(6);
     default: return cudaErrorInvalidValue;
   }
+#undef DG_BATCH_CALL
 }
 
-cudaError_t batch_volume(int precision, int threads, int p, bool launch, const BatchInst* insts,
-                         const BatchTile* tiles, int ntiles, int* counter, double gamma, size_t smem, int grid,
-                         cudaStream_t s, int* occupancy) {
+cudaError_t batch_volume(int precision, int threads, int p, const BatchCall& c) {
   if (precision == DG_FP32) {
-    if (threads == 128)
-      return batch_volume_p<float, 128>(p, launch, insts, tiles, ntiles, counter, gamma, smem, grid, s, occupancy);
-    if (threads == 192)
-      return batch_volume_p<float, 192>(p, launch, insts, tiles, ntiles, counter, gamma, smem, grid, s, occupancy);
-    return batch_volume_p<float, 256>(p, launch, insts, tiles, ntiles, counter, gamma, smem, grid, s, occupancy);
+    if (threads == 128) return batch_volume_p<float, 128>(p, c);
+    if (threads == 192) return batch_volume_p<float, 192>(p, c);
+    return batch_volume_p<float, 256>(p, c);
   }
-  if (threads == 128)
-    return batch_volume_p<double, 128>(p, launch, insts, tiles, ntiles, counter, gamma, smem, grid, s, occupancy);
-  if (threads == 192)
-    return batch_volume_p<double, 192>(p, launch, insts, tiles, ntiles, counter, gamma, smem, grid, s, occupancy);
-  return batch_volume_p<double, 256>(p, launch, insts, tiles, ntiles, counter, gamma, smem, grid, s, occupancy);
+  if (threads == 128) return batch_volume_p<double, 128>(p, c);
+  if (threads == 192) return batch_volume_p<double, 192>(p, c);
+  return batch_volume_p<double, 256>(p, c);
 }
 
-int occupancy_for(int precision, int threads, int p, size_t smem) {
+int occupancy_for(int precision, int threads, int p, int lm, size_t smem) {
   int occ = 0;
-  if (batch_volume(precision, threads, p, false, nullptr, nullptr, 0, nullptr, 0.0, smem, 0, 0, &occ) != cudaSuccess)
-    return 0;
+  const BatchCall c{lm, false, nullptr, nullptr, 0, nullptr, 0.0, smem, 0, 0, &occ};
+  if (batch_volume(precision, threads, p, c) != cudaSuccess) return 0;
   return occ;
 }
 
@@ -250,7 +269,7 @@ int occupancy_for(int precision, int threads, int p, size_t smem) {
 // The plan
 // ---------------------------------------------------------------------------------------------------------
 struct dg_batch {
-  int device = 0, n = 0, precision = 0, llf = 0, sms = 0;
+  int device = 0, n = 0, precision = 0, llf = 0, sms = 0, lm = 0;
   double gamma = 1.4;
   long long total_face_nodes = 0;
   dgk::BatchInst* d_inst = nullptr;
@@ -284,7 +303,8 @@ dg_status to_status(cudaError_t e) {
 // persistent grid of degree p's kernel: CTAs per SM (tuned, capped by the occupancy limit) times SMs, at most the
 // number of tiles
 int occupancy_of(dg_batch* b, int ti, int p) {
-  if (b->occ[ti][p] < 0) b->occ[ti][p] = dgk::occupancy_for(b->precision, dgk::kThreadChoices[ti], p, b->smem[ti][p]);
+  if (b->occ[ti][p] < 0)
+    b->occ[ti][p] = dgk::occupancy_for(b->precision, dgk::kThreadChoices[ti], p, b->lm, b->smem[ti][p]);
   return b->occ[ti][p];
 }
 
@@ -322,8 +342,9 @@ dg_status batch_launch(dg_batch* b, int ti, cudaStream_t s) {
     if (b->ntiles[ti][p] == 0) continue;
     const int grid = grid_for(b, ti, p);
     if (grid <= 0) return DG_ERR_CUDA;
-    e = dgk::batch_volume(b->precision, dgk::kThreadChoices[ti], p, true, b->d_inst, b->d_tiles[ti][p],
-                          b->ntiles[ti][p], b->d_counter + p, b->gamma, b->smem[ti][p], grid, s, nullptr);
+    const dgk::BatchCall c{b->lm, true, b->d_inst, b->d_tiles[ti][p], b->ntiles[ti][p], b->d_counter + p, b->gamma,
+                           b->smem[ti][p], grid, s, nullptr};
+    e = dgk::batch_volume(b->precision, dgk::kThreadChoices[ti], p, c);
   }
   return to_status(e);
 }
@@ -341,11 +362,11 @@ dg_status dg_batch_create(dg_batch** out, dg_ctx* const* ctxs, int n, const doub
     const dg_ctx* c = ctxs[i];
     if (!c || !u[i] || !du[i]) return DG_ERR_ARG;
     if (c->device != c0->device || c->precision != c0->precision || c->surface_flux != c0->surface_flux ||
-        c->gamma != c0->gamma)
+        c->gamma != c0->gamma || c->var.lm != c0->var.lm)
       return DG_ERR_ARG;
     if (c->nd != 3 || c->p > dgk::kBatchMaxP || c->volume_flux != DG_VOL_RANOCHA ||
-      c->var.lm != 0 || c->nodes != DG_NODES_LGL)
-    return DG_ERR_UNSUPPORTED;
+        (c->var.lm != dgk::LM_SHARED_RCP && c->var.lm != dgk::LM_PRELOG) || c->nodes != DG_NODES_LGL)
+      return DG_ERR_UNSUPPORTED;
     if (((uintptr_t)u[i] | (uintptr_t)du[i]) & 7) return DG_ERR_ARG;
     const size_t bytes = (size_t)c->state_len * sizeof(double);
     const char *ub = (const char*)u[i], *db = (const char*)du[i];
@@ -362,6 +383,7 @@ dg_status dg_batch_create(dg_batch** out, dg_ctx* const* ctxs, int n, const doub
   b->precision = c0->precision;
   b->llf = c0->surface_flux == DG_SURF_EC_LLF;
   b->gamma = c0->gamma;
+  b->lm = c0->var.lm;
   cudaError_t e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
   if (e == cudaSuccess) e = dgk::ensure_const_ops(b->device);
   if (e != cudaSuccess) {
@@ -388,15 +410,16 @@ dg_status dg_batch_create(dg_batch** out, dg_ctx* const* ctxs, int n, const doub
     elems += c->E;
   }
   char sig[256];
-  snprintf(sig, sizeof(sig), "%s n=%d E=%lld p1-5=%d,%d,%d,%d,%d", c0->precision == DG_FP32 ? "fp32" : "fp64", n, elems,
-           hist[1], hist[2], hist[3], hist[4], hist[5]);
+  snprintf(sig, sizeof(sig), "%s%s n=%d E=%lld p1-5=%d,%d,%d,%d,%d", c0->precision == DG_FP32 ? "fp32" : "fp64",
+           b->lm == dgk::LM_PRELOG ? " logs" : "", n, elems, hist[1], hist[2], hist[3], hist[4], hist[5]);
   b->signature = sig;
   // tile lists per CTA size and degree; full tiles first, the instances' ragged last tiles at the end
   for (int ti = 0; ti < dgk::kNumThreadChoices && e == cudaSuccess; ++ti) {
     const int threads = dgk::kThreadChoices[ti];
     for (int p = 1; p <= dgk::kBatchMaxP && e == cudaSuccess; ++p) {
       if (hist[p] == 0) continue;
-      const int epb = dgk::batch_epb(p, b->precision, threads);
+      const bool logs = b->lm == dgk::LM_PRELOG;
+      const int epb = dgk::batch_epb(p, b->precision, threads, logs);
       std::vector<dgk::BatchTile> full, ragged;
       for (int i = 0; i < n; ++i) {
         if (ctxs[i]->p != p) continue;
@@ -405,7 +428,7 @@ dg_status dg_batch_create(dg_batch** out, dg_ctx* const* ctxs, int n, const doub
       }
       full.insert(full.end(), ragged.begin(), ragged.end());
       b->ntiles[ti][p] = (int)full.size();
-      b->smem[ti][p] = dgk::batch_smem(p, b->precision, threads);
+      b->smem[ti][p] = dgk::batch_smem(p, b->precision, threads, logs);
       e = cudaMalloc(&b->d_tiles[ti][p], full.size() * sizeof(dgk::BatchTile));
       if (e == cudaSuccess)
         e = cudaMemcpy(b->d_tiles[ti][p], full.data(), full.size() * sizeof(dgk::BatchTile), cudaMemcpyHostToDevice);

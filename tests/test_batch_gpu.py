@@ -22,11 +22,11 @@ def dgmod():
     return dg
 
 
-def make_batch(dgmod, precision, specs, seed0=100):
+def make_batch(dgmod, precision, specs, seed0=100, ic="smooth", **extra):
     import torch
     scs, ctxs, us, dus = [], [], [], []
     for k, (nelem, p) in enumerate(specs):
-        sc = Scenario(3, nelem, p, mapping="sine", ic="smooth", llf=True, seed=seed0 + k)
+        sc = Scenario(3, nelem, p, mapping="sine", ic=ic, llf=True, seed=seed0 + k, **extra)
         ctx = dgmod.DG(precision=precision, **sc.dg_kwargs())
         scs.append(sc)
         ctxs.append(ctx)
@@ -96,3 +96,27 @@ def test_batch_rejects_mixed_precision_and_high_degree(dgmod):
     with pytest.raises(dgmod.DGError) as ei:
         dgmod.DGBatch(c7, u7, d7)
     assert ei.value.status == dgmod.DG_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_with_precomputed_logarithms(dgmod, precision):
+    # contexts with precompute_logs: the batch runs the per-node-logarithm kernels (Sec. 7.2); rough states take the
+    # log branches
+    import torch
+    scs, ctxs, us, dus = make_batch(dgmod, precision, SPECS, seed0=300, ic="rough", precompute_logs=True)
+    batch = dgmod.DGBatch(ctxs, us, dus)
+    tol = 1e-12 if precision == "fp64" else 4e-6
+    for threads in (128, 256):
+        batch.set_tuning(threads, 0)
+        batch.rhs()
+        torch.cuda.synchronize()
+        for sc, c, u, d in zip(scs, ctxs, us, dus):
+            _, term = parity_errors(d.cpu().numpy(), c.rhs(u).cpu().numpy(), sc.du_scale())
+            assert np.all(term <= tol), (threads, sc.p, term)
+            _, term = parity_errors(d.cpu().numpy(), sc.du_ref(), sc.du_scale())
+            assert np.all(term <= tol), (threads, sc.p, term)
+    # contexts must agree on the log-mean variant
+    _, c1, u1, d1 = make_batch(dgmod, precision, SPECS[:1], seed0=400)
+    with pytest.raises(dgmod.DGError) as ei:
+        dgmod.DGBatch(ctxs[:1] + c1, us[:1] + u1, dus[:1] + d1)
+    assert ei.value.status == dgmod.DG_ERR_ARG

@@ -138,8 +138,9 @@ def test_variant_restrictions(dgmod):
     with pytest.raises(dgmod.DGError) as ei:
         ctx.vjp(u, u.clone())
     assert ei.value.status == dgmod.DG_ERR_UNSUPPORTED
-    with pytest.raises(dgmod.DGError) as ei:
-        dgmod.DGBatch([ctx], [u], [torch.empty_like(u)])
+    alg = dgmod.DG(**scenario(3, [2, 2, 2], 3, "sine_paper", logmean="alg").dg_kwargs())
+    with pytest.raises(dgmod.DGError) as ei:  # batches run the default or the precomputed-logarithm kernels
+        dgmod.DGBatch([alg], [u], [torch.empty_like(u)])
     assert ei.value.status == dgmod.DG_ERR_UNSUPPORTED
     kw = scenario(3, [2, 2, 2], 3, "sine_paper").dg_kwargs()
     kw.update(flux="shima", precompute_logs=True)  # the Shima flux has no logarithmic means
