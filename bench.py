@@ -249,6 +249,23 @@ def run_ours(args, rank, world, local_rank):
         ifc_ms, ifc_n = ctx.profile_read(dg.KERNEL_INTERFACE)
         ctx.profile(False)
         ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps, dev)
+        # the same step captured once in a CUDA graph (8 kernels) and replayed per step: the launch gaps go away
+        # (the library neither allocates nor synchronizes in dg_step); timed separately, same L2 flushes
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(stream)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=side):
+            ctx.step(u, dt, dg.DG_RK4_CLASSIC, scratch=scratch, stream=side)
+        for _ in range(2):
+            graph.replay()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            graph.replay()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        gms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps, dev)
         status = ctx.check_status()
         if status != dg.DG_OK:
             raise RuntimeError("non-physical state during the timed steps")
@@ -257,7 +274,8 @@ def run_ours(args, rank, world, local_rank):
         vol_avg_s = vol_ms / max(vol_n, 1) * 1e-3
         res = {"ms_per_step": ms, "pid_ns": pid, "launches": launches, "clocks": clk,
                "volume_ms_avg": vol_avg_s * 1e3, "interface_ms_avg": ifc_ms / max(ifc_n, 1),
-               "volume_share_of_step": vol_ms / (ms * args.steps) if ms > 0 else None}
+               "volume_share_of_step": vol_ms / (ms * args.steps) if ms > 0 else None,
+               "graph_ms_per_step": gms, "graph_pid_ns": whole_job_pid(gms, ndofs, world)}
         # e2e: the same step through the public API with the state in pinned host memory, copies timed
         if main:
             u_host = torch.from_numpy(u0).pin_memory()
@@ -666,6 +684,10 @@ def main():
             "clocks": r64["clocks"],
             "kernels_ms": {"volume_with_stage_update": r64["volume_ms_avg"], "interface": r64["interface_ms_avg"],
                            "volume_share_of_step": r64["volume_share_of_step"]},
+            "cuda_graph_replay": {
+                "note": "the same timed steps with each dg_step captured once in a CUDA graph and replayed",
+                "fp64_16": r64["graph_pid_ns"], "fp32_16": r32["graph_pid_ns"], "fp64_32": b64["graph_pid_ns"],
+                "fp32_32": b32["graph_pid_ns"], "unit": "ns/DOF/RHS"},
             "fp32": {"value": r32["pid_ns"], "unit": "ns/DOF/RHS", "ms_per_step": r32["ms_per_step"],
                      "workload": "same as value (16^3, p=3)", "dtype": "f32 flux + line sums; f64 state, RK",
                      "speedup_vs_fp64": r64["pid_ns"] / r32["pid_ns"], "gpu_launches": r32["launches"],

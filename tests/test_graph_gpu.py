@@ -1,0 +1,78 @@
+"""dg_rhs and dg_step inside CUDA graphs: the library neither allocates nor synchronizes in these calls, so a
+captured sequence replays the same kernels; replays must equal eager execution bit for bit (LGL FP64 and FP32 with
+both Runge-Kutta schemes, Gauss collocation), and the non-physical flag still reaches dg_check_status."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dgmod():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_10517_gb300 import build
+    build.build()
+    from paper_2112_10517_gb300 import dg
+    return dg
+
+
+def context(dgmod, precision="fp64", nodes="lgl"):
+    from paper_2112_10517_gb300 import inputs
+    mapping = dict(mapping="affine") if nodes == "gauss" else dict(mapping="sine", amp=0.1)
+    ctx = dgmod.DG(3, [4, 3, 5], 3, lo=[-math.pi] * 3, hi=[math.pi] * 3, surface="llf", precision=precision,
+                   nodes=nodes, **mapping)
+    return ctx, inputs.taylor_green(ctx.node_coords(), mach=0.3)
+
+
+@pytest.mark.parametrize("precision,nodes", [("fp64", "lgl"), ("fp32", "lgl"), ("fp64", "gauss")])
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_step_graph_replay_equals_eager(dgmod, precision, nodes, scheme):
+    import torch
+    ctx, u0 = context(dgmod, precision, nodes)
+    u = torch.from_numpy(u0).cuda()
+    scratch = torch.empty((2,) + ctx.shape, dtype=torch.float64, device="cuda")
+    dt, steps = 0.002, 3
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    ctx.step(u, dt, scheme=scheme, scratch=scratch)  # first calls outside the capture
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        for _ in range(steps):
+            ctx.step(u, dt, scheme=scheme, scratch=scratch, stream=side)
+    u.copy_(torch.from_numpy(u0))
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    replayed = u.cpu().numpy()
+    u.copy_(torch.from_numpy(u0))
+    for _ in range(2 * steps):
+        ctx.step(u, dt, scheme=scheme, scratch=scratch)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(replayed, u.cpu().numpy())
+    assert ctx.check_status() == dgmod.DG_OK
+
+
+def test_rhs_graph_replay_and_flag(dgmod):
+    import torch
+    ctx, u0 = context(dgmod)
+    u = torch.from_numpy(u0).cuda()
+    du = torch.empty_like(u)
+    ref = ctx.rhs(u).clone()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        ctx.rhs(u, du, stream=side)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(du, ref)
+    u[1, 0, 3] = -1.0  # a negative density: the replayed kernels raise the flag
+    graph.replay()
+    torch.cuda.synchronize()
+    assert ctx.check_status() == dgmod.DG_ERR_NONPHYSICAL
+    assert ctx.check_status() == dgmod.DG_OK
