@@ -147,6 +147,23 @@ def committed_traffic(precision: str, ndofs: int):
     return float(m.group(1)) * ndofs
 
 
+def committed_utilization(precision: str):
+    """The ncu view of the same kernel (32^3 capture): FP64-pipe activity and DRAM throughput as fractions of
+    their peaks; None unless the capture was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "volume_kernel_tgv32_p3.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    out = {}
+    for key in ("fp64_pipe_active", "dram_throughput"):
+        m = re.search(r"ncu_%s_%s:\s*([0-9.eE+]+)\s+source_digest:\s*([0-9a-f]+)" % (key, precision), text)
+        if not m or m.group(2) != source_digest():
+            return None
+        out[key] = float(m.group(1))
+    out["capture"] = "profiles/volume_kernel_tgv32_p3.md (32^3, p = 3)"
+    return out
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -248,7 +265,9 @@ def run_ours(args, rank, world, local_rank):
         vol_ms, vol_n = ctx.profile_read(dg.KERNEL_VOLUME)
         ifc_ms, ifc_n = ctx.profile_read(dg.KERNEL_INTERFACE)
         ctx.profile(False)
-        ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps, dev)
+        per_step = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        ms = max_over_ranks(sum(per_step) / args.steps, dev)
+        ms_std = statistics.pstdev(per_step) if len(per_step) > 1 else 0.0
         # the same step captured once in a CUDA graph (8 kernels) and replayed per step: the launch gaps go away
         # (the library neither allocates nor synchronizes in dg_step); timed separately, same L2 flushes
         side = torch.cuda.Stream(device=dev)
@@ -272,7 +291,8 @@ def run_ours(args, rank, world, local_rank):
         ndofs = ctx.ndofs
         pid = whole_job_pid(ms, ndofs, world)
         vol_avg_s = vol_ms / max(vol_n, 1) * 1e-3
-        res = {"ms_per_step": ms, "pid_ns": pid, "launches": launches, "clocks": clk,
+        res = {"ms_per_step": ms, "pid_ns": pid, "pid_std_ns": whole_job_pid(ms_std, ndofs, world) if ms_std else 0.0,
+               "launches": launches, "clocks": clk,
                "volume_ms_avg": vol_avg_s * 1e3, "interface_ms_avg": ifc_ms / max(ifc_n, 1),
                "volume_share_of_step": vol_ms / (ms * args.steps) if ms > 0 else None,
                "graph_ms_per_step": gms, "graph_pid_ns": whole_job_pid(gms, ndofs, world)}
@@ -309,7 +329,8 @@ def run_ours(args, rank, world, local_rank):
                                "frac": achieved / (peak / 1e12) if peak else None,
                                "traffic": committed_traffic("fp64", ndofs),
                                "peak_source": "measured live: libdgpeaks fp64 FMA chain x 2 flop",
-                               "algorithmic_flops_per_launch": vflops}
+                               "algorithmic_flops_per_launch": vflops,
+                               "ncu_utilization": committed_utilization("fp64")}
         else:
             hbm = measured_peaks().get("hbm_gbs", 6800.0)
             vbytes = VOLUME_BYTES_PER_DOF_F32 * ndofs
@@ -319,6 +340,7 @@ def run_ours(args, rank, world, local_rank):
                                "frac": achieved / hbm, "traffic": committed_traffic("fp32", ndofs),
                                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
                                "algorithmic_bytes_per_launch": vbytes,
+                               "ncu_utilization": committed_utilization("fp32"),
                                "alu_frac_of_fp32_peak": (vflops / vol_avg_s) / peak32 if peak32 else None}
         res["ndofs"] = ndofs
         results[label] = res
@@ -595,6 +617,35 @@ def oracle_pid(seconds_target: float, elements=None):
     return el / (reps * nd) * 1e9, reps, nd
 
 
+def _oracle_slice(job):
+    """Worker of oracle_pid_all_cores (a spawned process): `reps` oracle RHS evaluations of elements [b, e)."""
+    import oracle as orc
+    Ja, J, u, b, e, reps = job
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        orc.rhs(3, POLYDEG, NELEM, Ja, J, u, llf=True, elem_range=(b, e))
+    return time.perf_counter() - t0
+
+
+def oracle_pid_all_cores(reps: int = 8):
+    """The same oracle RHS split over all host cores by element ranges (spawned processes, one per core): the
+    parallel wall time of `reps` full evaluations, as ns per DOF per RHS; returns (pid_ns, cores)."""
+    import multiprocessing as mp
+    import oracle as orc
+    from paper_2112_10517_gb300 import inputs
+    lo, hi = [-math.pi] * 3, [math.pi] * 3
+    xyz = orc.coords(3, NELEM, lo, hi, POLYDEG, mapping=1, amp=AMP)
+    Ja, J = orc.metrics(3, POLYDEG, xyz)
+    u = inputs.taylor_green(xyz, mach=MACH)
+    E = u.shape[0]
+    cores = max(1, min(os.cpu_count() or 1, E))
+    bounds = [(E * k // cores, E * (k + 1) // cores) for k in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_slice, [(Ja, J, u, b, e, 1) for b, e in bounds])  # warm-up: imports and the library
+        times = pool.map(_oracle_slice, [(Ja, J, u, b, e, reps) for b, e in bounds])
+    return max(times) / (reps * u.shape[0] * u.shape[2]) * 1e9, cores
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -667,8 +718,13 @@ def main():
             pid_cpu, reps, nd = oracle_pid(10.0)
             cpu = {"value": pid_cpu, "unit": "ns/DOF/RHS", "cores": 1, "kind": "oracle",
                    "sample": "%d oracle RHS evaluations of the full 16^3 p=3 mesh (%d DOF each), 1 core" % (reps, nd)}
+            pid_all, cores = oracle_pid_all_cores()
+            cpu["all_cores"] = {"value": pid_all, "unit": "ns/DOF/RHS", "cores": cores,
+                                "sample": "8 oracle RHS evaluations of the full 16^3 p=3 mesh split by element "
+                                          "ranges over %d spawned processes (parallel wall time)" % cores}
         line = {
-            "metric": METRIC, "value": r64["pid_ns"], "unit": "ns/DOF/RHS", "n_gpus": world,
+            "metric": METRIC, "value": r64["pid_ns"], "value_std": r64["pid_std_ns"], "unit": "ns/DOF/RHS",
+            "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": r64["ms_per_step"],
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
