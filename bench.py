@@ -127,10 +127,15 @@ class ClockSampler:
 
 # ------------------------------------------------------------------------------------------------------
 def source_digest() -> str:
+    """sha256 (first 16 hex digits) of the volume kernel's sources with comments and blank lines removed: it changes
+    with the compiled code, not with its comments."""
     h = hashlib.sha256()
     for f in ("dgmath.cuh", "kernels.cuh", "volume.cu", "volume_impl.cuh", "volume_inst.cu"):
-        with open(os.path.join(ROOT, "paper_2112_10517_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2112_10517_gb300", "csrc", f)) as fh:
+            for line in fh:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update((code + "\n").encode())
     return h.hexdigest()[:16]
 
 

@@ -69,7 +69,7 @@ struct OpTable {
 
 // ---------------------------------------------------------------------------------------------------
 // Interface flux (Sec. 2.4: one surface flux per interface node, shared by both elements).
-// Thread per (direction n, lower element e, face node fn). The upper neighbour across +n is e+.
+// Thread per (lower element e, direction n, face node fn). The upper neighbour across +n is e+.
 // f* = f_Ranocha(u_L, u_R, m) - [llf] lambda/2 (u_R - u_L), m = Ja^n at the lower element's face node,
 // lambda = max(|v_L.m| + c_L|m|, |v_R.m| + c_R|m|), c = sqrt(gamma p/rho).
 // face layout [n][E][NV][NL].
