@@ -201,12 +201,27 @@ cudaError_t ensure_const_ops(int device) {
 }
 
 // One entry point per (degree, precision, CTA size): its occupancy at a shared-memory size, or its launch.
+// The kernel's dynamic shared-memory opt-in is raised once to the largest size asked for, so that launches issue
+// no attribute call (a batch's launches can then be captured in a CUDA graph after a first call outside it).
+template <int N, typename T, int THREADS, int LMK>
+cudaError_t batch_volume_optin(size_t smem) {
+  static std::mutex m;
+  static size_t done = 0;
+  std::lock_guard<std::mutex> lock(m);
+  if (smem <= done) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(batch_volume_kernel<N, T, THREADS, LMK>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) done = smem;
+  return e;
+}
+
 template <int N, typename T, int THREADS>
 cudaError_t batch_volume_call(int lm, bool launch, const BatchInst* insts, const BatchTile* tiles, int ntiles,
                               int* counter, double gamma, size_t smem, int grid, cudaStream_t s, int* occupancy) {
   auto kern = lm == LM_PRELOG ? batch_volume_kernel<N, T, THREADS, LM_PRELOG>
                               : batch_volume_kernel<N, T, THREADS, LM_SHARED_RCP>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = lm == LM_PRELOG ? batch_volume_optin<N, T, THREADS, LM_PRELOG>(smem)
+                                  : batch_volume_optin<N, T, THREADS, LM_SHARED_RCP>(smem);
   if (e != cudaSuccess) return e;
   if (!launch) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, kern, THREADS, smem);
   kern<<<grid, THREADS, smem, s>>>(insts, tiles, ntiles, counter, (T)gamma);

@@ -120,3 +120,26 @@ def test_batch_with_precomputed_logarithms(dgmod, precision):
     with pytest.raises(dgmod.DGError) as ei:
         dgmod.DGBatch(ctxs[:1] + c1, us[:1] + u1, dus[:1] + d1)
     assert ei.value.status == dgmod.DG_ERR_ARG
+
+
+def test_batch_rhs_in_a_cuda_graph(dgmod):
+    # dg_batch_rhs issues launches only (no allocation, no synchronization, no attribute calls after the first
+    # call), so a captured batch RHS replays the same kernels: bitwise equal to the eager call
+    import torch
+    scs, ctxs, us, dus = make_batch(dgmod, "fp64", SPECS, seed0=500)
+    batch = dgmod.DGBatch(ctxs, us, dus)
+    batch.set_tuning(192, 0)
+    batch.rhs()
+    torch.cuda.synchronize()
+    eager = [d.clone() for d in dus]
+    for d in dus:
+        d.fill_(float("nan"))
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        batch.rhs(stream=side)
+    graph.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(eager, dus):
+        assert torch.equal(a, b)
