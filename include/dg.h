@@ -199,9 +199,10 @@ const char* dg_status_string(dg_status s);
  * gamma, and polydeg <= 5 (DG_ERR_UNSUPPORTED otherwise). Uses the contexts' metric terms, interface-flux
  * workspaces and non-physical flags (dg_check_status of each context reports its instance). Allocates small
  * device tables (work lists) and synchronizes.
- * dg_batch_rhs computes du[i] = RHS_i(u[i]) for every instance: it queues one memset and 1 + (number of distinct
- * degrees) kernels on `stream` (all instances' interface fluxes, then per degree one persistent volume kernel
- * whose CTAs take that degree's element tiles from a shared counter). It allocates nothing and does not synchronize, so a sequence of calls
+ * dg_batch_rhs computes du[i] = RHS_i(u[i]) for every instance: it queues one memset and the interface fluxes of
+ * all instances on `stream`, then per degree one persistent volume kernel (whose CTAs take that degree's element
+ * tiles from a shared counter) on the plan's own streams, forked from `stream` by an event and joined back into it
+ * before the call returns; work queued later on `stream` follows all of it. It allocates nothing and does not synchronize, so a sequence of calls
  * can be captured in a CUDA graph after a first call outside the capture. Plans sharing a context must not run
  * concurrently (they share its workspace).
  * dg_batch_autotune times every tile shape (threads per CTA 128/192/256, which sets the elements per tile of

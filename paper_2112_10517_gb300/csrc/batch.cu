@@ -293,6 +293,10 @@ struct dg_batch {
   int ntiles[dgk::kNumThreadChoices][dgk::kBatchMaxP + 1] = {};
   size_t smem[dgk::kNumThreadChoices][dgk::kBatchMaxP + 1] = {};
   int* d_counter = nullptr;  // one work counter per degree
+  // the per-degree kernels run concurrently: forked from the caller's stream after the interface launch, joined
+  // before dg_batch_rhs returns (in a captured graph these become parallel branches)
+  cudaStream_t streams[dgk::kBatchMaxP + 1] = {};
+  cudaEvent_t fork = nullptr, join[dgk::kBatchMaxP + 1] = {};
   int occ[dgk::kNumThreadChoices][dgk::kBatchMaxP + 1];  // occupancy limits, -1 until queried
   int threads_idx = 1;  // 192 threads per CTA until tuned
   int ctas_per_sm = 0;  // 0: the occupancy limit
@@ -307,6 +311,11 @@ void batch_release(dg_batch* b) {
   for (int i = 0; i < dgk::kNumThreadChoices; ++i)
     for (int p = 0; p <= dgk::kBatchMaxP; ++p) cudaFree(b->d_tiles[i][p]);
   cudaFree(b->d_counter);
+  for (int p = 0; p <= dgk::kBatchMaxP; ++p) {
+    if (b->streams[p]) cudaStreamDestroy(b->streams[p]);
+    if (b->join[p]) cudaEventDestroy(b->join[p]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   delete b;
 }
 
@@ -353,13 +362,17 @@ dg_status batch_launch(dg_batch* b, int ti, cudaStream_t s) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return to_status(e);
   }
+  if (e == cudaSuccess) e = cudaEventRecord(b->fork, s);
   for (int p = 1; p <= dgk::kBatchMaxP && e == cudaSuccess; ++p) {
     if (b->ntiles[ti][p] == 0) continue;
     const int grid = grid_for(b, ti, p);
     if (grid <= 0) return DG_ERR_CUDA;
+    e = cudaStreamWaitEvent(b->streams[p], b->fork, 0);
     const dgk::BatchCall c{b->lm, true, b->d_inst, b->d_tiles[ti][p], b->ntiles[ti][p], b->d_counter + p, b->gamma,
-                           b->smem[ti][p], grid, s, nullptr};
-    e = dgk::batch_volume(b->precision, dgk::kThreadChoices[ti], p, c);
+                           b->smem[ti][p], grid, b->streams[p], nullptr};
+    if (e == cudaSuccess) e = dgk::batch_volume(b->precision, dgk::kThreadChoices[ti], p, c);
+    if (e == cudaSuccess) e = cudaEventRecord(b->join[p], b->streams[p]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->join[p], 0);
   }
   return to_status(e);
 }
@@ -452,6 +465,12 @@ dg_status dg_batch_create(dg_batch** out, dg_ctx* const* ctxs, int n, const doub
   if (e == cudaSuccess) e = cudaMalloc(&b->d_inst, n * sizeof(dgk::BatchInst));
   if (e == cudaSuccess) e = cudaMemcpy(b->d_inst, inst.data(), n * sizeof(dgk::BatchInst), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int) * (dgk::kBatchMaxP + 1));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int p = 1; p <= dgk::kBatchMaxP && e == cudaSuccess; ++p) {
+    if (hist[p] == 0) continue;
+    e = cudaStreamCreateWithFlags(&b->streams[p], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[p], cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
     batch_release(b);
     return to_status(e);
