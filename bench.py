@@ -62,7 +62,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (debug runs)")
     ap.add_argument("--only", default="", help="comma-separated subset of fp64_16,fp32_16,fp64_32,fp32_32, "
-                    "variants, ablation, gauss (profiling runs; prints one line per configuration instead of the "
+                    "variants, ablation, gauss, staging (profiling runs; prints one line per configuration instead of the "
                     "contract line)")
     return ap.parse_args()
 
@@ -460,6 +460,50 @@ def run_variants(args, dev):
     return out
 
 
+def run_staging(args, dev):
+    """The FP32 RK4 step (dg_step, fused stage update) with the two ways the volume kernel stages a tile: bulk
+    asynchronous copies that overlap the computation of a persistent CTA's tiles (pipelined) and direct loads by
+    one CTA per tile (direct); the default (auto) takes the pipelined kernel at 32^3 and the direct one at 16^3.
+    Taylor-Green vortex, p = 3, 16^3 and 32^3; L2 flushed before every timed step."""
+    import torch
+    from paper_2112_10517_gb300 import dg
+    lo, hi = [-math.pi] * 3, [math.pi] * 3
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for nelem in (NELEM, NELEM_LARGE):
+        for staging in ("pipelined", "direct"):
+            ctx = dg.DG(3, nelem, POLYDEG, lo=lo, hi=hi, mapping="sine", amp=AMP, surface="llf", precision="fp32",
+                        staging=staging)
+            u = torch.from_numpy(make_state(ctx)).to(dev)
+            scratch = torch.empty((2,) + ctx.shape, dtype=torch.float64, device=dev)
+            dt = 0.5 * (2 * math.pi / nelem[0]) / (POLYDEG + 1) ** 2 / (1.0 + 1.0 / MACH)
+            for _ in range(args.warmup):
+                ctx.step(u, dt, dg.DG_RK4_CLASSIC, scratch=scratch)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            ctx.profile(True)
+            for a, b in ev:
+                flush.zero_()
+                a.record(stream)
+                ctx.step(u, dt, dg.DG_RK4_CLASSIC, scratch=scratch)
+                b.record(stream)
+            torch.cuda.synchronize()
+            vol_ms, vol_n = ctx.profile_read(dg.KERNEL_VOLUME)
+            ctx.profile(False)
+            if ctx.check_status() != dg.DG_OK:
+                raise RuntimeError("non-physical state or wait timeout in the staging runs")
+            ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+            out["%d_%s" % (nelem[0], staging)] = {
+                "pid_ns": whole_job_pid(ms, ctx.ndofs, 1), "volume_ms": vol_ms / max(vol_n, 1),
+                "volume_GBps": VOLUME_BYTES_PER_DOF_F32 * ctx.ndofs / (vol_ms / max(vol_n, 1) * 1e-3) / 1e9}
+            del ctx, u, scratch
+    out["workload"] = ("dg_step (RK4, FP32 flux mode) on the Taylor-Green vortex, p = 3, sine-perturbed mesh, 16^3 "
+                       "and 32^3 elements; volume_GBps = algorithmic bytes of the volume kernel / its event time")
+    return out
+
+
 def run_logmean_ablation(args, dev):
     """Volume-term time of the log-mean variants (Sec. 3.1: Algorithms 2/3 with divisions, with the polynomial 1/log
     form; Sec. 7.2: logarithms precomputed per node) against the default (no division, one shared reciprocal),
@@ -710,6 +754,7 @@ def main():
     variants = run_variants(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
     ablation = run_logmean_ablation(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
     gauss = run_gauss(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
+    staging = run_staging(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
     if rank == 0 and args.only:
         for label, res in results.items():
             print(json.dumps({"configuration": label, "pid_ns": res["pid_ns"], "ms_per_step": res["ms_per_step"],
@@ -723,6 +768,8 @@ def main():
             print(json.dumps({"configuration": "ablation", "result": run_logmean_ablation(args, dev)}), flush=True)
         if "gauss" in only:
             print(json.dumps({"configuration": "gauss", "result": run_gauss(args, dev)}), flush=True)
+        if "staging" in only:
+            print(json.dumps({"configuration": "staging", "result": run_staging(args, dev)}), flush=True)
     elif rank == 0:
         r64, r32 = results["fp64_16"], results["fp32_16"]
         b64, b32 = results["fp64_32"], results["fp32_32"]
@@ -776,6 +823,7 @@ def main():
             "flux_and_geometry_variants": variants,
             "logmean_ablation": ablation,
             "gauss_collocation": gauss,
+            "fp32_tile_staging": staging,
             "alu_peaks_measured_tflops": {k: (v / 1e12 if v else None) for k, v in peaks_alu.items()},
         }
         print(json.dumps(line), flush=True)

@@ -111,9 +111,23 @@ typedef struct dg_metrics {
    states are u(R w(u)) of each element, interface fluxes are computed once per face node. DG_NODES_GAUSS needs
    DG_MAP_AFFINE without overrides, DG_VOL_RANOCHA, DG_FP64 and the default log mean (else DG_ERR_UNSUPPORTED);
    dg_vjp and dg_batch_* do not support it. Its face states need the entropy variables interpolated to the faces
-   to stay admissible (rho/p > 0); otherwise the non-physical flag is raised. */
+   to stay admissible (rho/p > 0); otherwise the non-physical flag is raised.
+   staging: how the volume kernel of dg_rhs / dg_step brings an element tile's data into shared memory.
+     DG_STAGING_PIPELINED  DG_FP32 with an even number of nodes per line (odd polydeg), the default log mean and
+                           16-byte-aligned state arrays: persistent CTAs that copy each tile's data (stage input,
+                           metric terms, 1/J, Runge-Kutta operands, interface fluxes) with bulk asynchronous copies,
+                           each group for the next tile as soon as the current tile has read it, so that the copies
+                           overlap computation; otherwise as DG_STAGING_DIRECT.
+     DG_STAGING_AUTO       as DG_STAGING_PIPELINED on meshes with at least 4 tiles per resident CTA (the first
+                           tile's copies are not overlapped), else as DG_STAGING_DIRECT.
+     DG_STAGING_DIRECT     one CTA per tile, loads issued by its threads (always the case for DG_FP64, whose
+                           kernels are bound by the FP64 pipe, not by load latency).
+   All compute the same values (the same arithmetic in the same order). A pipelined kernel whose wait for its own
+   copies runs out (bounded; it cannot under normal operation) skips the rest of its tiles and raises the flag that
+   dg_check_status reports as DG_ERR_TIMEOUT. */
 enum { DG_LOGMEAN_SHARED_RCP = 0, DG_LOGMEAN_ALG = 1, DG_LOGMEAN_ALG_POLY = 2 };
 enum { DG_NODES_LGL = 0, DG_NODES_GAUSS = 1 };
+enum { DG_STAGING_AUTO = 0, DG_STAGING_DIRECT = 1, DG_STAGING_PIPELINED = 2 };
 typedef struct dg_opts {
   double gamma;
   int volume_flux;
@@ -122,7 +136,8 @@ typedef struct dg_opts {
   int precompute_logs; /* 0 or 1 */
   int logmean;         /* DG_LOGMEAN_* */
   int nodes;           /* DG_NODES_* */
-  int reserved[2];     /* must be zero */
+  int staging;         /* DG_STAGING_* */
+  int reserved[1];     /* must be zero */
 } dg_opts;
 
 /* Sizes of a context. */

@@ -23,6 +23,10 @@ struct RefTables {
   double Dt[DG_MAXN * DG_MAXN];  // flux-differencing matrix 2D - M^{-1}B (Eq. opDsplit), zero diagonal
 };
 
+// Bits of the per-context device flag: a non-physical state (set with atomicOr(flag, 1)); a bounded wait of a
+// kernel on its own asynchronous copies that ran out (the kernel then skipped its work).
+enum { FLAG_NONPHYSICAL = 1, FLAG_WAIT_TIMEOUT = 4 };
+
 // Kernel ids for profiling (KID_PROJECT: the entropy projection of the Gauss collocation scheme)
 enum { KID_VOLUME = 0, KID_INTERFACE = 1, KID_PROJECT = 2, KID_COUNT = 3 };
 
@@ -37,6 +41,8 @@ struct Epilogue {
   int stage;       // stage index
   double dt;       // time step
   double a, b;     // CK45: A_s, B_s
+  double ca, cy;   // RK4: the stage's weights of k in acc (b_s dt) and in the next stage state (c_{s+1} dt),
+                   // computed on the host (no FP64 division per node)
   double* u;       // RK4: solution at the start of the step (updated at the last stage); CK45: the state
   double* y;       // RK4: next stage state; CK45: the K register
   double* acc;     // RK4: accumulated sum of b_s dt k_s
@@ -53,6 +59,8 @@ struct Variant {
   int flux;      // DG_VOL_RANOCHA or DG_VOL_SHIMA (volume and surface)
   int cart;      // 1: constant diagonal metrics from jn/invJ, the metric arrays are not read
   int lm;        // log-mean variant of the volume terms (LM_* in dgmath.cuh; Ranocha's flux only)
+  int pipe;      // FP32 volume kernel with bulk asynchronous tile copies (where supported): 0 never, 1 on meshes
+                 // with enough tiles per resident CTA, 2 always
   double jn[3];  // Ja^n_n of a Cartesian mesh
   double invJ;   // 1/J of a Cartesian mesh
 };

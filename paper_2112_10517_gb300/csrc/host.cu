@@ -346,8 +346,8 @@ dg_status dg_init(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metri
   if (opts->volume_flux != DG_VOL_RANOCHA && opts->volume_flux != DG_VOL_SHIMA) return DG_ERR_ARG;
   if (opts->surface_flux != DG_SURF_EC && opts->surface_flux != DG_SURF_EC_LLF) return DG_ERR_ARG;
   if (opts->precision != DG_FP64 && opts->precision != DG_FP32) return DG_ERR_ARG;
-  for (int r = 0; r < 2; ++r)
-    if (opts->reserved[r] != 0) return DG_ERR_ARG;
+  if (opts->reserved[0] != 0) return DG_ERR_ARG;
+  if (opts->staging < DG_STAGING_AUTO || opts->staging > DG_STAGING_PIPELINED) return DG_ERR_ARG;
   if (opts->nodes != DG_NODES_LGL && opts->nodes != DG_NODES_GAUSS) return DG_ERR_ARG;
   const bool gauss = opts->nodes == DG_NODES_GAUSS;
   if (gauss && (mesh->mapping != DG_MAP_AFFINE || (metrics && metrics->Ja_host) || opts->precision != DG_FP64 ||
@@ -393,6 +393,7 @@ dg_status dg_init(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metri
   c->var.cart = (mesh->mapping == DG_MAP_AFFINE && !(metrics && metrics->Ja_host) &&
                  opts->logmean == DG_LOGMEAN_SHARED_RCP) ? 1 : 0;
   c->var.lm = opts->precompute_logs ? dgk::LM_PRELOG : opts->logmean;  // DG_LOGMEAN_* equal LM_* 0..2
+  c->var.pipe = opts->staging == DG_STAGING_AUTO ? 1 : (opts->staging == DG_STAGING_PIPELINED ? 2 : 0);
   {
     double hh[3] = {1.0, 1.0, 1.0}, jac = 1.0;
     for (int d = 0; d < nd; ++d) {
@@ -537,6 +538,8 @@ dg_status dg_step(dg_ctx* c, double* u, double* scratch, double t, double dt, in
     const double* in = (scheme == DG_RK4_CLASSIC && st > 0) ? scratch : u;
     epi.stage = st;
     if (scheme == DG_LSRK45_CK) dgk::ck45_coefficients(st, &epi.a, &epi.b);
+    epi.ca = (st == 0 || st == 3) ? dt / 6.0 : dt / 3.0;
+    epi.cy = st == 2 ? dt : 0.5 * dt;
     if (c->nodes == DG_NODES_GAUSS) {
       const dg_status gs = gauss_rhs(c, in, nullptr, &epi, s);
       if (gs != DG_OK) return gs;
@@ -588,7 +591,8 @@ dg_status dg_check_status(dg_ctx* c) {
   if (flag) {
     e = cudaMemset(c->d_flag, 0, sizeof(int));
     if (e != cudaSuccess) return cuda_status(e);
-    return DG_ERR_NONPHYSICAL;
+    // bit 0: a non-physical state; bit 2 (FLAG_WAIT_TIMEOUT): a kernel's bounded wait on its own copies ran out
+    return (flag & dgk::FLAG_WAIT_TIMEOUT) ? DG_ERR_TIMEOUT : DG_ERR_NONPHYSICAL;
   }
   return DG_OK;
 }

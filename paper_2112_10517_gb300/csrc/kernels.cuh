@@ -168,18 +168,15 @@ __global__ void __launch_bounds__(256) interface_kernel(const double* __restrict
 template <int EPI>
 __device__ __forceinline__ void stage_update(const Epilogue& epi, size_t o, double k, double uo, double yo) {
   if (EPI == EPI_RK4) {
-    const double dt = epi.dt;
+    // weights: ca = dt/6, dt/3, dt/3, dt/6 and cy = dt/2, dt/2, dt for stages 0..3 (set by the host)
     if (epi.stage == 0) {
-      epi.acc[o] = (dt / 6.0) * k;
-      epi.y[o] = uo + (0.5 * dt) * k;
-    } else if (epi.stage == 1) {
-      epi.acc[o] = yo + (dt / 3.0) * k;
-      epi.y[o] = uo + (0.5 * dt) * k;
-    } else if (epi.stage == 2) {
-      epi.acc[o] = yo + (dt / 3.0) * k;
-      epi.y[o] = uo + dt * k;
+      epi.acc[o] = epi.ca * k;
+      epi.y[o] = uo + epi.cy * k;
+    } else if (epi.stage < 3) {
+      epi.acc[o] = yo + epi.ca * k;
+      epi.y[o] = uo + epi.cy * k;
     } else {
-      epi.u[o] = uo + yo + (dt / 6.0) * k;
+      epi.u[o] = uo + yo + epi.ca * k;
     }
   } else {
     const double kk = (epi.stage == 0 ? 0.0 : epi.a * yo) + epi.dt * k;

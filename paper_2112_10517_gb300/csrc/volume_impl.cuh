@@ -3,6 +3,7 @@
 #pragma once
 
 #include "kernels.cuh"
+#include "volume_pipe.cuh"
 
 namespace dgk {
 namespace volume_detail {
@@ -25,9 +26,76 @@ constexpr int elems_per_block() {
   return Geo<ND, N>::TPE >= target ? 1 : target / Geo<ND, N>::TPE;
 }
 
+// Threads per CTA of the pipelined FP32 kernel, and the fewest tiles per resident CTA for which it is used
+// (compile-time tuning parameters, as above). With few tiles per CTA the first tile's copies are not overlapped
+// and the per-tile kernel is faster (measured at 16^3, p = 3: about 2 tiles per CTA, 12 % slower; at 32^3, about
+// 18 tiles per CTA, 10 % faster).
+#ifndef DG_VOLUME_PIPE_TARGET_THREADS
+#define DG_VOLUME_PIPE_TARGET_THREADS 96
+#endif
+#ifndef DG_VOLUME_PIPE_MIN_TILES_PER_CTA
+#define DG_VOLUME_PIPE_MIN_TILES_PER_CTA 4
+#endif
+
+template <int N, typename T>
+OpTable<N, T> op_table() {
+  OpTable<N, T> op;
+  const RefTables& t = ref_tables(N - 1);
+  for (int i = 0; i < N * N; ++i) op.Dt8[i] = (T)(0.125 * t.Dt[i]);
+  op.winv = (T)(1.0 / t.w[0]);
+  op.lift8 = (T)(0.125 / t.w[0]);
+  return op;
+}
+
+inline bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+// The pipelined kernel (volume_pipe.cuh) where it applies: FP32, even N, default log mean, 16-byte-aligned arrays,
+// shared memory within the opt-in limit, and (var.pipe == 1) enough tiles per resident CTA, or (var.pipe == 2)
+// any mesh. Returns cudaErrorNotSupported where it does not apply (the caller then launches the per-tile kernel).
+template <int ND, int N, typename T, int EPI, int LMK>
+cudaError_t launch_volume_pipe(MeshDims md, const double* u, const T* Ja, const double* invJ, const T* face,
+                               double* du, double gamma, int* flag, cudaStream_t s, const Epilogue& epi,
+                               const Variant& var) {
+  if constexpr (sizeof(T) == 4 && N % 2 == 0 && LMK == LM_SHARED_RCP) {
+    constexpr int TPE = Geo<ND, N>::TPE;
+    constexpr int EPB = TPE >= DG_VOLUME_PIPE_TARGET_THREADS ? 1 : DG_VOLUME_PIPE_TARGET_THREADS / TPE;
+    constexpr bool fused = EPI != EPI_STORE;
+    constexpr size_t smem = PipeSmem<ND, N, T>::bytes(EPB, fused);
+    if constexpr (smem <= 227 * 1024) {
+      if (!var.pipe) return cudaErrorNotSupported;
+      bool ok = aligned16(u) && aligned16(face) && (var.cart || (aligned16(Ja) && aligned16(invJ)));
+      if (fused) ok = ok && aligned16(epi.u) && aligned16(EPI == EPI_RK4 ? epi.acc : epi.y);
+      if (!ok) return cudaErrorNotSupported;
+      auto kern = volume_pipe_kernel<ND, N, T, EPB, EPI>;
+      static int ctas = 0;  // resident CTAs on the device (occupancy x SMs); computed once, with the opt-in
+      if (ctas == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, occ = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, EPB * TPE, smem)) != cudaSuccess)
+          return e;
+        if (occ < 1) return cudaErrorNotSupported;
+        ctas = occ * sms;
+      }
+      const int ntiles = (md.E + EPB - 1) / EPB;
+      if (var.pipe == 1 && (long long)ntiles < (long long)DG_VOLUME_PIPE_MIN_TILES_PER_CTA * ctas)
+        return cudaErrorNotSupported;
+      const int grid = ntiles < ctas ? ntiles : ctas;
+      kern<<<grid, EPB * TPE, smem, s>>>(u, Ja, invJ, face, du, md, op_table<N, T>(), (T)gamma, flag, epi, var,
+                                          ntiles);
+      return cudaGetLastError();
+    }
+  }
+  return cudaErrorNotSupported;
+}
+
 template <int ND, int N, typename T, int EPI, int LMK>
 cudaError_t launch_volume_k(MeshDims md, const double* u, const T* Ja, const double* invJ, const T* face, double* du,
                             double gamma, int* flag, cudaStream_t s, const Epilogue& epi, const Variant& var) {
+  const cudaError_t pe = launch_volume_pipe<ND, N, T, EPI, LMK>(md, u, Ja, invJ, face, du, gamma, flag, s, epi, var);
+  if (pe != cudaErrorNotSupported) return pe;
   constexpr int EPB = elems_per_block<ND, N, T>();
   constexpr int threads = EPB * Geo<ND, N>::TPE;
   const size_t smem = VolumeSmem<ND, N, T>::bytes(EPB, EPI != EPI_STORE, LMK == LM_PRELOG);
@@ -38,13 +106,8 @@ cudaError_t launch_volume_k(MeshDims md, const double* u, const T* Ja, const dou
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  OpTable<N, T> op;
-  const RefTables& t = ref_tables(N - 1);
-  for (int i = 0; i < N * N; ++i) op.Dt8[i] = (T)(0.125 * t.Dt[i]);
-  op.winv = (T)(1.0 / t.w[0]);
-  op.lift8 = (T)(0.125 / t.w[0]);
   const int blocks = (md.E + EPB - 1) / EPB;
-  kern<<<blocks, threads, smem, s>>>(u, Ja, invJ, face, du, md, op, (T)gamma, flag, epi, var);
+  kern<<<blocks, threads, smem, s>>>(u, Ja, invJ, face, du, md, op_table<N, T>(), (T)gamma, flag, epi, var);
   return cudaGetLastError();
 }
 

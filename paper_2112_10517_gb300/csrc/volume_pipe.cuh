@@ -1,0 +1,311 @@
+// Pipelined volume kernel for the FP32 flux mode (Eq. fluxdiff-SBP-opDsplit, the same arithmetic as volume_tile):
+// persistent CTAs take element tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...; one thread copies the tiles'
+// data into shared memory with bulk asynchronous copies (cp.async.bulk, the TMA engine), each group of arrays
+// completing on its own mbarrier. A tile runs in three phases -- A: node quantities from the stage input,
+// B: the two-point fluxes along lines (metric terms), C: lift of the interface fluxes, -1/J, store or stage update
+// (1/J, the Runge-Kutta operands, the faces' fluxes) -- and each group is copied for the NEXT tile as soon as the
+// phase that reads it has finished: the stage input during phases B and C, the metric terms during C and the next
+// A, the phase-C group during the next A and B. One buffer per group keeps the shared memory per CTA, and so the
+// number of resident CTAs, close to that of the per-tile kernel, while the loads, whose latency bounds the FP32
+// kernel, overlap computation.
+//
+// Requirements (checked by the launcher): an even number of nodes per line (every element block of every array is
+// then a multiple of 16 bytes), 16-byte-aligned array pointers, the default log mean. Waits on the mbarriers are
+// bounded: on a timeout the CTA raises FLAG_WAIT_TIMEOUT, waits (bounded again) for its copies in flight and
+// returns.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace dgk {
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// make the initialised barriers visible to the asynchronous proxy (the bulk-copy engine)
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// arrive once (the barrier's expected count is 1) and add `bytes` to the transaction count of the current phase
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+// global -> shared bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned), completing on `bar`
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+// true once the phase of parity `parity` has completed (acquire: the copied data are then visible)
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Polls `bar` for the phase of parity `parity` at most kPolls times, about 64 ns apart (about half a second).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  constexpr int kPolls = 1 << 23;
+  for (int i = 0; i < kPolls; ++i) {
+    if (mbar_test(bar, parity)) return true;
+    __nanosleep(64);
+  }
+  return false;
+}
+
+// Shared memory of the pipelined kernel, for EPB elements: the copied groups
+//   IN [EPB][NV][NDOF] f64 (stage input)                                         mbarrier 0
+//   JA [EPB][ND][ND][NDOF] T (metric terms; not copied on Cartesian meshes)       mbarrier 1
+//   IJ [EPB][NDOF] f64 (1/J; not on Cartesian meshes), EU, EY [EPB][NV][NDOF] f64
+//   (fused stage update: u, and acc (RK4) / K (CK45) after stage 0), FC [2][ND][EPB][NV][NL] T (side 0: the upper
+//   face of the lower neighbour, side 1: the element's own)                      mbarrier 2
+// then the tile scratch, node quantities [EPB][NQ][NDOF] T and per-direction sums [EPB][ND][NV][NDOF] T, then the
+// three mbarriers. Every region is a multiple of 16 bytes for even N.
+template <int ND, int N, typename T>
+struct PipeSmem {
+  using G = Geo<ND, N>;
+  static constexpr size_t kIn = (size_t)G::NV * G::NDOF * sizeof(double);
+  static constexpr size_t kJa = (size_t)ND * ND * G::NDOF * sizeof(T);
+  static constexpr size_t kInvJ = (size_t)G::NDOF * sizeof(double);
+  static constexpr size_t kFace = (size_t)G::NV * G::NL * sizeof(T);  // one face of one element
+  static constexpr size_t kPrim = (size_t)NodeQ<ND>::NQ * G::NDOF * sizeof(T);
+  static constexpr size_t kAcc = (size_t)ND * G::NV * G::NDOF * sizeof(T);
+  // byte offsets of the regions for EPB elements
+  __host__ __device__ static constexpr size_t off_ja(int epb) { return (size_t)epb * kIn; }
+  __host__ __device__ static constexpr size_t off_ij(int epb) { return off_ja(epb) + (size_t)epb * kJa; }
+  __host__ __device__ static constexpr size_t off_eu(int epb) { return off_ij(epb) + (size_t)epb * kInvJ; }
+  __host__ __device__ static constexpr size_t off_ey(int epb, bool fused) { return off_eu(epb) + (fused ? epb * kIn : 0); }
+  __host__ __device__ static constexpr size_t off_fc(int epb, bool fused) { return off_ey(epb, fused) + (fused ? epb * kIn : 0); }
+  __host__ __device__ static constexpr size_t off_prim(int epb, bool fused) { return off_fc(epb, fused) + (size_t)2 * ND * epb * kFace; }
+  __host__ __device__ static constexpr size_t off_acc(int epb, bool fused) { return off_prim(epb, fused) + (size_t)epb * kPrim; }
+  __host__ __device__ static constexpr size_t off_bar(int epb, bool fused) { return off_acc(epb, fused) + (size_t)epb * kAcc; }
+  __host__ __device__ static constexpr size_t bytes(int epb, bool fused) { return off_bar(epb, fused) + 32; }
+  static_assert(N % 2 == 0, "element blocks are multiples of 16 bytes only for an even number of nodes per line");
+  static_assert(kIn % 16 == 0 && kJa % 16 == 0 && kInvJ % 16 == 0 && kFace % 16 == 0 && kPrim % 16 == 0 &&
+                    kAcc % 16 == 0,
+                "bulk copies move multiples of 16 bytes");
+};
+
+// True when the lower neighbours across direction n of the consecutive elements e0 .. e0+nel-1 are consecutive
+// too. An element's neighbour is e - s_n (s_n the element stride along n) when its coordinate c_n > 0 and
+// e + (len_n - 1) s_n when c_n = 0: the map is one translation when all elements share the group e / s_n, when
+// len_n = 1, or when no element of the range has c_n = 0.
+__device__ __forceinline__ bool lower_neighbors_consecutive(const MeshDims& md, int e0, int nel, int n) {
+  if (nel == 1) return true;
+  const int s = n == 0 ? 1 : (n == 1 ? md.n1 : md.n1 * md.n2);
+  const int len = n == 0 ? md.n1 : (n == 1 ? md.n2 : md.n3);
+  const int g0 = e0 / s, g1 = (e0 + nel - 1) / s;
+  return g0 == g1 || len == 1 || (g0 % len != 0 && g0 / len == g1 / len);
+}
+
+// Waits (bounded) for the last of `fills` fills of `bar`, if any: the drain of the copies in flight on a timeout.
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, int fills) {
+  if (fills > 0) mbar_wait_bounded(bar, (unsigned)((fills - 1) & 1));
+}
+
+template <int ND, int N, typename T, int EPB, int EPI>
+__global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE)
+    volume_pipe_kernel(const double* __restrict__ in, const T* __restrict__ Ja, const double* __restrict__ invJ,
+                       const T* __restrict__ face, double* du, MeshDims md, OpTable<N, T> op, T gamma, int* flag,
+                       Epilogue epi, Variant var, int ntiles) {
+  using G = Geo<ND, N>;
+  using S = PipeSmem<ND, N, T>;
+  constexpr int NQ = NodeQ<ND>::NQ;
+  constexpr bool kFused = EPI != EPI_STORE;
+  constexpr int kThreads = EPB * G::TPE;
+  constexpr int kFaceT = G::NV * G::NL;  // elements of T in one face block
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // s_ok[j]: thread 0's wait before the j-th barrier of a tile succeeded (0: stage input, at the barrier that
+  // closes the previous tile; 1: metric terms; 2: phase-C group). A slot is rewritten only after every thread has
+  // passed the two barriers that follow its read.
+  __shared__ int s_ok[3];
+  double* s_in = reinterpret_cast<double*>(smem_raw);
+  T* s_ja = reinterpret_cast<T*>(smem_raw + S::off_ja(EPB));
+  double* s_ij = reinterpret_cast<double*>(smem_raw + S::off_ij(EPB));
+  double* s_eu = reinterpret_cast<double*>(smem_raw + S::off_eu(EPB));
+  double* s_ey = reinterpret_cast<double*>(smem_raw + S::off_ey(EPB, kFused));
+  T* s_fc = reinterpret_cast<T*>(smem_raw + S::off_fc(EPB, kFused));
+  T* s_prim = reinterpret_cast<T*>(smem_raw + S::off_prim(EPB, kFused));
+  T* s_acc = reinterpret_cast<T*>(smem_raw + S::off_acc(EPB, kFused));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + S::off_bar(EPB, kFused));
+  const int tid = threadIdx.x;
+  const T gm1 = gamma - T(1);
+  const bool has_ja = !var.cart;
+  const bool need_y = kFused && epi.stage > 0;  // acc (RK4) / K (CK45) are read after stage 0
+  const double* gy = EPI == EPI_RK4 ? epi.acc : epi.y;
+  // locals for the copy lambdas (a kernel parameter captured by reference would be copied to local memory)
+  const double* gu = epi.u;
+  const MeshDims mdl = md;
+  int fill_in = 0, fill_ja = 0, fill_c = 0;  // thread 0: fills issued per mbarrier
+
+  // thread 0: the copies of one group for the tile t (byte count first, then the copies)
+  auto issue_in = [&](int t) {
+    const int e0 = t * EPB, nel = min(EPB, mdl.E - e0);
+    mbar_expect_tx(&bars[0], (unsigned)(nel * S::kIn));
+    bulk_g2s(s_in, in + (size_t)e0 * G::NV * G::NDOF, (unsigned)(nel * S::kIn), &bars[0]);
+    ++fill_in;
+  };
+  auto issue_ja = [&](int t) {
+    const int e0 = t * EPB, nel = min(EPB, mdl.E - e0);
+    mbar_expect_tx(&bars[1], (unsigned)(nel * S::kJa));
+    bulk_g2s(s_ja, Ja + (size_t)e0 * ND * ND * G::NDOF, (unsigned)(nel * S::kJa), &bars[1]);
+    ++fill_ja;
+  };
+  auto issue_c = [&](int t) {
+    const int e0 = t * EPB, nel = min(EPB, mdl.E - e0);
+    const unsigned nin = (unsigned)(nel * S::kIn), nfc = (unsigned)(nel * S::kFace);
+    const unsigned nij = has_ja ? (unsigned)(nel * S::kInvJ) : 0u;
+    mbar_expect_tx(&bars[2], nij + (kFused ? nin : 0u) + (need_y ? nin : 0u) + 2u * ND * nfc);
+    const size_t so = (size_t)e0 * G::NV * G::NDOF;
+    if (has_ja) bulk_g2s(s_ij, invJ + (size_t)e0 * G::NDOF, nij, &bars[2]);
+    if (kFused) bulk_g2s(s_eu, gu + so, nin, &bars[2]);
+    if (need_y) bulk_g2s(s_ey, gy + so, nin, &bars[2]);
+#pragma unroll
+    for (int n = 0; n < ND; ++n) {
+      // the tile's own upper faces along n are consecutive in the face array; the lower neighbours' mostly are
+      const T* fn = face + (size_t)n * mdl.E * kFaceT;
+      bulk_g2s(s_fc + ((1 * ND + n) * EPB) * kFaceT, fn + (size_t)e0 * kFaceT, nfc, &bars[2]);
+      if (lower_neighbors_consecutive(mdl, e0, nel, n)) {
+        bulk_g2s(s_fc + (n * EPB) * kFaceT, fn + (size_t)neighbor(mdl, e0, n, -1) * kFaceT, nfc, &bars[2]);
+      } else {
+        for (int el = 0; el < nel; ++el)
+          bulk_g2s(s_fc + (n * EPB + el) * kFaceT, fn + (size_t)neighbor(mdl, e0 + el, n, -1) * kFaceT,
+                   (unsigned)S::kFace, &bars[2]);
+      }
+    }
+    ++fill_c;
+  };
+
+  int t = blockIdx.x;
+  if (tid == 0) {
+    for (int j = 0; j < 3; ++j) mbar_init(&bars[j], 1);
+    mbar_init_fence();
+    if (t < ntiles) {
+      issue_in(t);
+      if (has_ja) issue_ja(t);
+      issue_c(t);
+      s_ok[0] = mbar_wait_bounded(&bars[0], 0u) ? 1 : 0;
+    }
+  }
+  __syncthreads();
+  bool failed = false;
+  for (int k = 0; t < ntiles; ++k, t += gridDim.x) {
+    const unsigned par = (unsigned)(k & 1);  // every group is copied once per tile
+    const int tn = t + gridDim.x;
+    const int e0 = t * EPB, nel = min(EPB, md.E - e0);
+    if (!s_ok[0]) {  // all threads read the same slot: the whole CTA leaves the loop
+      failed = true;
+      break;
+    }
+    mbar_test(&bars[0], par);  // completed: each thread's own acquire of the copied data
+
+    // ---- A: node quantities from the staged input
+    bool ok = true;
+    for (int idx = tid; idx < nel * G::NDOF; idx += kThreads) {
+      const int el = idx / G::NDOF, i = idx - el * G::NDOF;
+      double uc[G::NV];
+#pragma unroll
+      for (int c = 0; c < G::NV; ++c) uc[c] = s_in[(el * G::NV + c) * G::NDOF + i];
+      T q[NQ];
+      ok &= node_quantities<ND, T>(uc, gm1, T(2) / gm1, q);
+#pragma unroll
+      for (int c = 0; c < NQ; ++c) s_prim[(el * NQ + c) * G::NDOF + i] = q[c];
+    }
+    if (!ok) atomicOr(flag, FLAG_NONPHYSICAL);
+    if (tid == 0) s_ok[1] = has_ja ? (mbar_wait_bounded(&bars[1], par) ? 1 : 0) : 1;
+    __syncthreads();
+    if (!s_ok[1]) {  // all threads read the same slot: the whole CTA leaves the loop
+      failed = true;
+      break;
+    }
+    if (has_ja) mbar_test(&bars[1], par);
+    if (tid == 0 && tn < ntiles) issue_in(tn);  // the stage input has been read
+
+    // ---- B: the pairs i < k of each line, as in volume_tile
+    if (tid < nel * G::TPE) {
+      const int el = tid / G::TPE, r = tid - el * G::TPE;
+      const int n = r / G::NL, l = r - n * G::NL;
+      const int st = G::stride(n), lb = G::line_base(n, l);
+      const T* sp = s_prim + el * NQ * G::NDOF + lb;
+      const T* sj = s_ja + (el * ND + n) * ND * G::NDOF + lb;
+      T* sa = s_acc + (el * ND + n) * G::NV * G::NDOF + lb;
+      const T n2n = T(2) * (T)cart_jn(var, n);
+      switch (var.flux * 2 + var.cart) {
+        case 0: line_pairs<ND, N, T, 0, false>(sp, sj, nullptr, st, n, n2n, op, sa); break;
+        case 1: line_pairs<ND, N, T, 0, true>(sp, sj, nullptr, st, n, n2n, op, sa); break;
+        case 2: line_pairs<ND, N, T, 1, false>(sp, sj, nullptr, st, n, n2n, op, sa); break;
+        default: line_pairs<ND, N, T, 1, true>(sp, sj, nullptr, st, n, n2n, op, sa); break;
+      }
+    }
+    if (tid == 0) s_ok[2] = mbar_wait_bounded(&bars[2], par) ? 1 : 0;
+    __syncthreads();
+    if (!s_ok[2]) {  // all threads read the same slot: the whole CTA leaves the loop
+      failed = true;
+      break;
+    }
+    mbar_test(&bars[2], par);
+    if (tid == 0 && tn < ntiles && has_ja) issue_ja(tn);  // the metric terms have been read
+
+    // ---- C: sum the directions, lift the staged interface fluxes, scale by -1/J, store or update
+    for (int idx = tid; idx < nel * G::NDOF; idx += kThreads) {
+      const int el = idx / G::NDOF, i = idx - el * G::NDOF;
+      T tot[G::NV];
+#pragma unroll
+      for (int c = 0; c < G::NV; ++c) {
+        T s = T(0);
+#pragma unroll
+        for (int n = 0; n < ND; ++n) s += s_acc[((el * ND + n) * G::NV + c) * G::NDOF + i];
+        tot[c] = s;
+      }
+#pragma unroll
+      for (int n = 0; n < ND; ++n) {
+        const int in_ = (i / G::stride(n)) % N;
+        if (in_ == N - 1 || in_ == 0) {
+          const int side = in_ == N - 1 ? 1 : 0;
+          const T sgn = in_ == N - 1 ? op.lift8 : -op.lift8;
+          const T* fp = s_fc + ((side * ND + n) * EPB + el) * kFaceT + G::face_index(n, i);
+#pragma unroll
+          for (int c = 0; c < G::NV; ++c) tot[c] += sgn * fp[c * G::NL];
+        }
+      }
+      const double ij = var.cart ? var.invJ : s_ij[el * G::NDOF + i];
+      const T sjT = -to_flux<T>(ij);
+      const size_t off = (size_t)(e0 + el) * G::NV * G::NDOF + i;
+#pragma unroll
+      for (int c = 0; c < G::NV; ++c) {
+        const size_t o = off + (size_t)c * G::NDOF;
+        const int so = (el * G::NV + c) * G::NDOF + i;
+        // the scaling in FP32 and an exact integer-pipe widening, as in volume_tile
+        const double kv = f2d_int((float)(sjT * tot[c]));
+        if (EPI == EPI_STORE)
+          du[o] = kv;
+        else
+          stage_update<EPI>(epi, o, kv, s_eu[so], need_y ? s_ey[so] : 0.0);
+      }
+    }
+    if (tid == 0 && tn < ntiles) s_ok[0] = mbar_wait_bounded(&bars[0], par ^ 1u) ? 1 : 0;
+    __syncthreads();
+    if (tid == 0 && tn < ntiles) issue_c(tn);  // the phase-C group has been read
+  }
+  if (failed && tid == 0) {  // a wait ran out: raise the flag, wait (bounded) for the copies in flight
+    atomicOr(flag, FLAG_WAIT_TIMEOUT);
+    mbar_drain(&bars[0], fill_in);
+    mbar_drain(&bars[1], fill_ja);
+    mbar_drain(&bars[2], fill_c);
+  }
+}
+
+}  // namespace dgk

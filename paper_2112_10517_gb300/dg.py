@@ -32,6 +32,8 @@ DG_LOGMEAN_SHARED_RCP, DG_LOGMEAN_ALG, DG_LOGMEAN_ALG_POLY = 0, 1, 2
 LOGMEANS = {"rcp": DG_LOGMEAN_SHARED_RCP, "alg": DG_LOGMEAN_ALG, "alg_poly": DG_LOGMEAN_ALG_POLY}
 DG_NODES_LGL, DG_NODES_GAUSS = 0, 1
 NODES = {"lgl": DG_NODES_LGL, "gauss": DG_NODES_GAUSS}
+DG_STAGING_AUTO, DG_STAGING_DIRECT, DG_STAGING_PIPELINED = 0, 1, 2
+STAGINGS = {"auto": DG_STAGING_AUTO, "direct": DG_STAGING_DIRECT, "pipelined": DG_STAGING_PIPELINED}
 DG_RK4_CLASSIC, DG_LSRK45_CK = 0, 1
 KERNEL_VOLUME, KERNEL_INTERFACE, KERNEL_PROJECT = 0, 1, 2
 
@@ -54,7 +56,7 @@ class DgMetrics(ctypes.Structure):
 class DgOpts(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("volume_flux", ctypes.c_int), ("surface_flux", ctypes.c_int),
                 ("precision", ctypes.c_int), ("precompute_logs", ctypes.c_int), ("logmean", ctypes.c_int),
-                ("nodes", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("nodes", ctypes.c_int), ("staging", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class DgInfo(ctypes.Structure):
@@ -131,12 +133,15 @@ class DG:
     means of Ranocha's flux (Sec. 3.1, 7.2; see dg_opts in include/dg.h); the defaults are the fastest.
     nodes: "lgl" (flux-differencing LGL-DGSEM) or "gauss" (Legendre-Gauss collocation with entropy projection,
     Sec. 6; affine meshes, FP64, Ranocha's flux).
+    staging: "pipelined" (the FP32 volume kernel copies tiles with bulk asynchronous copies that overlap
+    computation, where supported), "direct" (one CTA per tile, loads by its threads) or "auto" (pipelined on meshes
+    with enough tiles per CTA); the same values either way.
     """
 
     def __init__(self, ndims: int, nelem, polydeg: int, lo=None, hi=None, mapping: str = "affine", amp: float = 0.0,
                  node_xyz=None, Ja=None, J=None, gamma: float = 1.4, surface: str = "llf",
                  precision: str = "fp64", flux: str = "ranocha", logmean: str = "rcp",
-                 precompute_logs: bool = False, nodes: str = "lgl"):
+                 precompute_logs: bool = False, nodes: str = "lgl", staging: str = "auto"):
         mesh = DgMesh()
         mesh.ndims = ndims
         ne = list(nelem) + [1] * (3 - len(nelem))
@@ -165,6 +170,7 @@ class DG:
         opts.logmean = LOGMEANS[logmean]
         opts.precompute_logs = 1 if precompute_logs else 0
         opts.nodes = NODES[nodes]
+        opts.staging = STAGINGS[staging]
         opts.surface_flux = {"ec": DG_SURF_EC, "llf": DG_SURF_EC_LLF}[surface]
         opts.precision = {"fp64": DG_FP64, "fp32": DG_FP32}[precision]
         ctx = ctypes.c_void_p()

@@ -57,6 +57,9 @@ def test_argument_errors_without_gpu(built):
     opts.reserved[0] = 1
     assert dg.dg_init(ctypes.byref(ctx), ctypes.byref(mesh), 3, None, ctypes.byref(opts)) == dg.DG_ERR_ARG
     opts.reserved[0] = 0
+    opts.staging = 3
+    assert dg.dg_init(ctypes.byref(ctx), ctypes.byref(mesh), 3, None, ctypes.byref(opts)) == dg.DG_ERR_ARG
+    opts.staging = dg.DG_STAGING_DIRECT
     # log-mean options: out of range, or combinations without a kernel, are rejected before any device call
     init = lambda: dg.dg_init(ctypes.byref(ctx), ctypes.byref(mesh), 3, None, ctypes.byref(opts))
     opts.precompute_logs = 2
