@@ -130,7 +130,7 @@ def source_digest() -> str:
     """sha256 (first 16 hex digits) of the volume kernel's sources with comments and blank lines removed: it changes
     with the compiled code, not with its comments."""
     h = hashlib.sha256()
-    for f in ("dgmath.cuh", "kernels.cuh", "volume.cu", "volume_impl.cuh", "volume_inst.cu"):
+    for f in ("dgmath.cuh", "kernels.cuh", "volume.cu", "volume_impl.cuh", "volume_inst.cu", "volume_pipe.cuh"):
         with open(os.path.join(ROOT, "paper_2112_10517_gb300", "csrc", f)) as fh:
             for line in fh:
                 code = line.split("//", 1)[0].rstrip()
@@ -461,19 +461,19 @@ def run_variants(args, dev):
 
 
 def run_staging(args, dev):
-    """The FP32 RK4 step (dg_step, fused stage update) with the two ways the volume kernel stages a tile: bulk
+    """The RK4 step (dg_step, fused stage update) with the two ways the volume kernel stages a tile: bulk
     asynchronous copies that overlap the computation of a persistent CTA's tiles (pipelined) and direct loads by
-    one CTA per tile (direct); the default (auto) takes the pipelined kernel at 32^3 and the direct one at 16^3.
-    Taylor-Green vortex, p = 3, 16^3 and 32^3; L2 flushed before every timed step."""
+    one CTA per tile (direct), FP32 and FP64 flux arithmetic. Taylor-Green vortex, p = 3, 16^3 and 32^3; L2 flushed
+    before every timed step."""
     import torch
     from paper_2112_10517_gb300 import dg
     lo, hi = [-math.pi] * 3, [math.pi] * 3
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     out = {}
-    for nelem in (NELEM, NELEM_LARGE):
+    for precision, nelem in (("fp32", NELEM), ("fp32", NELEM_LARGE), ("fp64", NELEM), ("fp64", NELEM_LARGE)):
         for staging in ("pipelined", "direct"):
-            ctx = dg.DG(3, nelem, POLYDEG, lo=lo, hi=hi, mapping="sine", amp=AMP, surface="llf", precision="fp32",
+            ctx = dg.DG(3, nelem, POLYDEG, lo=lo, hi=hi, mapping="sine", amp=AMP, surface="llf", precision=precision,
                         staging=staging)
             u = torch.from_numpy(make_state(ctx)).to(dev)
             scratch = torch.empty((2,) + ctx.shape, dtype=torch.float64, device=dev)
@@ -495,12 +495,11 @@ def run_staging(args, dev):
             if ctx.check_status() != dg.DG_OK:
                 raise RuntimeError("non-physical state or wait timeout in the staging runs")
             ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-            out["%d_%s" % (nelem[0], staging)] = {
-                "pid_ns": whole_job_pid(ms, ctx.ndofs, 1), "volume_ms": vol_ms / max(vol_n, 1),
-                "volume_GBps": VOLUME_BYTES_PER_DOF_F32 * ctx.ndofs / (vol_ms / max(vol_n, 1) * 1e-3) / 1e9}
+            out["%s_%d_%s" % (precision, nelem[0], staging)] = {
+                "pid_ns": whole_job_pid(ms, ctx.ndofs, 1), "volume_ms": vol_ms / max(vol_n, 1)}
             del ctx, u, scratch
-    out["workload"] = ("dg_step (RK4, FP32 flux mode) on the Taylor-Green vortex, p = 3, sine-perturbed mesh, 16^3 "
-                       "and 32^3 elements; volume_GBps = algorithmic bytes of the volume kernel / its event time")
+    out["workload"] = ("dg_step (RK4) on the Taylor-Green vortex, p = 3, sine-perturbed mesh, 16^3 and 32^3 elements, "
+                       "FP32 and FP64 flux arithmetic; volume_ms = the volume kernel's event time per launch")
     return out
 
 

@@ -171,7 +171,10 @@ cudaError_t upload_const_ops() {
   if (e == cudaSuccess) {                                                      \
     OpTable<NN, T> op;                                                         \
     const RefTables& t = ref_tables(NN - 1);                                   \
-    for (int i = 0; i < NN * NN; ++i) op.Dt8[i] = (T)(0.125 * t.Dt[i]);        \
+    for (int i = 0; i < NN * NN; ++i) {                                        \
+      op.Dt8[i] = (T)(0.125 * t.Dt[i]);                                        \
+      op.D0[i] = (T)(0.25 * t.Dt[i]);                                          \
+    }                                                                          \
     op.winv = (T)(1.0 / t.w[0]);                                               \
     op.lift8 = (T)(0.125 / t.w[0]);                                            \
     e = cudaMemcpyToSymbol(SYM, &op, sizeof(op));                              \

@@ -327,7 +327,9 @@ __device__ __forceinline__ void ranocha_means(const T* a, const T* b, T& L, T& L
 //                                                             + ((p; v.n))))
 // using 1/{{rho/p}}_log = p_a p_b / {{rho_a p_b, rho_b p_a}}_log (Sec. 3.2) and the homogeneity of the mean.
 // ---------------------------------------------------------------------------------------------------
-template <int ND, typename T, int LM = LM_SHARED_RCP>
+// HALF0: return F_rho / 2 (= Q; the volume sums take it with doubled coefficients, which is exact and saves the
+// addition Q + Q per pair).
+template <int ND, typename T, int LM = LM_SHARED_RCP, bool HALF0 = false>
 __device__ __forceinline__ void ranocha_flux8(const T* a, const T* b, const T* n2, T* F,
                                               const LogRef<T>& lg = LogRef<T>{nullptr, nullptr, 0}) {
   using Q = NodeQ<ND>;
@@ -342,7 +344,7 @@ __device__ __forceinline__ void ranocha_flux8(const T* a, const T* b, const T* n
   ranocha_means<ND, T, LM>(a, b, L, Li, lg);
   const T q = L * (A + B);
   const T ps = a[Q::PP] + b[Q::PP];
-  F[0] = q + q;
+  F[0] = HALF0 ? q : q + q;
 #pragma unroll
   for (int j = 0; j < ND; ++j) F[1 + j] = q * (a[1 + j] + b[1 + j]) + ps * n2[j];
   F[ND + 1] = q * (vv + a[Q::PG] * b[Q::PP] * Li) + (a[Q::PP] * B + b[Q::PP] * A);
@@ -356,7 +358,7 @@ __device__ __forceinline__ void ranocha_flux8(const T* a, const T* b, const T* n
 //   F_rhoe = q v_a.v_b/2 + (pg_a + pg_b)(A + B)/2 + pp_a B + pp_b A
 //                                                          (8 (f_rho ((v;v))/2 + {{p}}{{v.n}}/(gamma-1) + ((p; v.n))))
 // ---------------------------------------------------------------------------------------------------
-template <int ND, typename T>
+template <int ND, typename T, bool HALF0 = false>
 __device__ __forceinline__ void shima_flux8(const T* a, const T* b, const T* n2, T* F) {
   using Q = NodeQ<ND>;
   T A = a[1] * n2[0], B = b[1] * n2[0], vv = a[1] * b[1];
@@ -370,7 +372,7 @@ __device__ __forceinline__ void shima_flux8(const T* a, const T* b, const T* n2,
   const T q = (a[Q::RHO] + b[Q::RHO]) * AB;
   const T hq = T(0.5) * q;
   const T ps = a[Q::PP] + b[Q::PP];
-  F[0] = q;
+  F[0] = HALF0 ? hq : q;
 #pragma unroll
   for (int j = 0; j < ND; ++j) F[1 + j] = hq * (a[1 + j] + b[1 + j]) + ps * n2[j];
   F[ND + 1] = hq * vv + T(0.5) * (a[Q::PG] + b[Q::PG]) * AB + (a[Q::PP] * B + b[Q::PP] * A);
@@ -381,7 +383,7 @@ __device__ __forceinline__ void shima_flux8(const T* a, const T* b, const T* n2,
 // has the single component n2n = 2 Ja^n_n along axis n, so v.n2 is one product and the pressure acts on one
 // momentum component (van, vbn: the velocity components along n).
 // ---------------------------------------------------------------------------------------------------
-template <int ND, typename T, int FLUX, int LM = LM_SHARED_RCP>
+template <int ND, typename T, int FLUX, int LM = LM_SHARED_RCP, bool HALF0 = false>
 __device__ __forceinline__ void pair_flux8_cart(const T* a, const T* b, T van, T vbn, T n2n, int n, T* F,
                                                 const LogRef<T>& lg = LogRef<T>{nullptr, nullptr, 0}) {
   using Q = NodeQ<ND>;
@@ -395,14 +397,14 @@ __device__ __forceinline__ void pair_flux8_cart(const T* a, const T* b, T van, T
     T L, Li;
     ranocha_means<ND, T, LM>(a, b, L, Li, lg);
     const T q = L * (A + B);
-    F[0] = q + q;
+    F[0] = HALF0 ? q : q + q;
     qv = q;
     e = q * (vv + a[Q::PG] * b[Q::PP] * Li);
   } else {
     const T AB = A + B;
     const T q = (a[Q::RHO] + b[Q::RHO]) * AB;
-    F[0] = q;
     qv = T(0.5) * q;
+    F[0] = HALF0 ? qv : q;
     e = qv * vv + T(0.5) * (a[Q::PG] + b[Q::PG]) * AB;
   }
 #pragma unroll
@@ -410,13 +412,13 @@ __device__ __forceinline__ void pair_flux8_cart(const T* a, const T* b, T van, T
   F[ND + 1] = e + (a[Q::PP] * B + b[Q::PP] * A);
 }
 
-template <int ND, typename T, int FLUX, int LM = LM_SHARED_RCP>
+template <int ND, typename T, int FLUX, int LM = LM_SHARED_RCP, bool HALF0 = false>
 __device__ __forceinline__ void pair_flux8(const T* a, const T* b, const T* n2, T* F,
                                            const LogRef<T>& lg = LogRef<T>{nullptr, nullptr, 0}) {
   if (FLUX == 0)
-    ranocha_flux8<ND, T, LM>(a, b, n2, F, lg);
+    ranocha_flux8<ND, T, LM, HALF0>(a, b, n2, F, lg);
   else
-    shima_flux8<ND, T>(a, b, n2, F);
+    shima_flux8<ND, T, HALF0>(a, b, n2, F);
 }
 
 }  // namespace dgk

@@ -63,6 +63,7 @@ __device__ __forceinline__ int upper_neighbor(const MeshDims& md, int e, int n) 
 template <int N, typename T>
 struct OpTable {
   T Dt8[N * N];  // flux-differencing matrix 2D - M^{-1}B (Eq. opDsplit), divided by 8 (fluxes come scaled by 8)
+  T D0[N * N];   // 2 Dt8: the coefficients of the mass flux, which the volume sums take halved (exact)
   T winv;        // 1/w_0 = 1/w_p = p(p+1)/2: the lift M^{-1} R^T B at the end nodes
   T lift8;       // winv / 8: the lift of the face buffer, which holds interface fluxes scaled by 8
 };
@@ -261,16 +262,19 @@ __device__ __forceinline__ void line_pairs(const T* sp, const T* sj, const T* sl
       for (int c = 0; c < NQ; ++c) b[c] = sp[c * G::NDOF + k * st];
       const LogRef<T> lg{sl + i * st, sl + k * st, G::NDOF};
       if (CART) {
-        pair_flux8_cart<ND, T, FLUX, LM>(a, b, va_n, sp[(1 + n) * G::NDOF + k * st], n2n, n, f, lg);
+        pair_flux8_cart<ND, T, FLUX, LM, true>(a, b, va_n, sp[(1 + n) * G::NDOF + k * st], n2n, n, f, lg);
       } else {
         T n2[ND];
 #pragma unroll
         for (int j = 0; j < ND; ++j) n2[j] = ja_i[j] + sj[j * G::NDOF + k * st];
-        pair_flux8<ND, T, FLUX, LM>(a, b, n2, f, lg);
+        pair_flux8<ND, T, FLUX, LM, true>(a, b, n2, f, lg);
       }
       const T dik = op.Dt8[i * N + k], dki = op.Dt8[k * N + i];
+      // f[0] is the halved mass flux: 2 dik (f[0]) equals dik (2 f[0]) exactly
+      acc[i][0] += op.D0[i * N + k] * f[0];
+      acc[k][0] += op.D0[k * N + i] * f[0];
 #pragma unroll
-      for (int c = 0; c < G::NV; ++c) {
+      for (int c = 1; c < G::NV; ++c) {
         acc[i][c] += dik * f[c];
         acc[k][c] += dki * f[c];
       }

@@ -261,7 +261,10 @@ cudaError_t launch_vjp_t(int llf, MeshDims md, const double* u, const double* Ja
   }
   OpTable<N, double> op;
   const RefTables& t = ref_tables(N - 1);
-  for (int i = 0; i < N * N; ++i) op.Dt8[i] = 0.125 * t.Dt[i];
+  for (int i = 0; i < N * N; ++i) {
+    op.Dt8[i] = 0.125 * t.Dt[i];
+    op.D0[i] = 0.25 * t.Dt[i];
+  }
   op.winv = 1.0 / t.w[0];
   op.lift8 = 0.125 / t.w[0];
   kern<<<(md.E + EPB - 1) / EPB, EPB * G::TPE, smem, s>>>(u, Ja, invJ, gbar, fadj, ubar, md, op, gamma);

@@ -26,22 +26,28 @@ constexpr int elems_per_block() {
   return Geo<ND, N>::TPE >= target ? 1 : target / Geo<ND, N>::TPE;
 }
 
-// Threads per CTA of the pipelined FP32 kernel, and the fewest tiles per resident CTA for which it is used
-// (compile-time tuning parameters, as above). With few tiles per CTA the first tile's copies are not overlapped
-// and the per-tile kernel is faster (measured at 16^3, p = 3: about 2 tiles per CTA, 12 % slower; at 32^3, about
-// 18 tiles per CTA, 10 % faster).
+// Threads per CTA of the pipelined kernel (FP32, FP64), and the fewest tiles per resident CTA for which
+// DG_STAGING_AUTO uses it (compile-time tuning parameters, as above). With one tile per CTA nothing overlaps;
+// measured at p = 3 on the RK4 step: 16^3 (2.2 tiles per CTA in FP32, 3.4 in FP64) 7 % and 3 % faster than the
+// per-tile kernel, 32^3 26 % and 3 % faster.
 #ifndef DG_VOLUME_PIPE_TARGET_THREADS
 #define DG_VOLUME_PIPE_TARGET_THREADS 96
 #endif
+#ifndef DG_VOLUME_PIPE_TARGET_THREADS_F64
+#define DG_VOLUME_PIPE_TARGET_THREADS_F64 192
+#endif
 #ifndef DG_VOLUME_PIPE_MIN_TILES_PER_CTA
-#define DG_VOLUME_PIPE_MIN_TILES_PER_CTA 4
+#define DG_VOLUME_PIPE_MIN_TILES_PER_CTA 2
 #endif
 
 template <int N, typename T>
 OpTable<N, T> op_table() {
   OpTable<N, T> op;
   const RefTables& t = ref_tables(N - 1);
-  for (int i = 0; i < N * N; ++i) op.Dt8[i] = (T)(0.125 * t.Dt[i]);
+  for (int i = 0; i < N * N; ++i) {
+    op.Dt8[i] = (T)(0.125 * t.Dt[i]);
+    op.D0[i] = (T)(0.25 * t.Dt[i]);
+  }
   op.winv = (T)(1.0 / t.w[0]);
   op.lift8 = (T)(0.125 / t.w[0]);
   return op;
@@ -56,9 +62,11 @@ template <int ND, int N, typename T, int EPI, int LMK>
 cudaError_t launch_volume_pipe(MeshDims md, const double* u, const T* Ja, const double* invJ, const T* face,
                                double* du, double gamma, int* flag, cudaStream_t s, const Epilogue& epi,
                                const Variant& var) {
-  if constexpr (sizeof(T) == 4 && N % 2 == 0 && LMK == LM_SHARED_RCP) {
+  // FP64: p <= 3 (larger elements run one per CTA, where the per-tile kernel keeps more registers)
+  if constexpr (N % 2 == 0 && LMK == LM_SHARED_RCP && (sizeof(T) == 4 || N <= 4)) {
     constexpr int TPE = Geo<ND, N>::TPE;
-    constexpr int EPB = TPE >= DG_VOLUME_PIPE_TARGET_THREADS ? 1 : DG_VOLUME_PIPE_TARGET_THREADS / TPE;
+    constexpr int target = sizeof(T) == 8 ? DG_VOLUME_PIPE_TARGET_THREADS_F64 : DG_VOLUME_PIPE_TARGET_THREADS;
+    constexpr int EPB = TPE >= target ? 1 : target / TPE;
     constexpr bool fused = EPI != EPI_STORE;
     constexpr size_t smem = PipeSmem<ND, N, T>::bytes(EPB, fused);
     if constexpr (smem <= 227 * 1024) {

@@ -1,4 +1,4 @@
-// Pipelined volume kernel for the FP32 flux mode (Eq. fluxdiff-SBP-opDsplit, the same arithmetic as volume_tile):
+// Pipelined volume kernel (Eq. fluxdiff-SBP-opDsplit, the same arithmetic as volume_tile):
 // persistent CTAs take element tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...; one thread copies the tiles'
 // data into shared memory with bulk asynchronous copies (cp.async.bulk, the TMA engine), each group of arrays
 // completing on its own mbarrier. A tile runs in three phases -- A: node quantities from the stage input,
@@ -6,8 +6,8 @@
 // (1/J, the Runge-Kutta operands, the faces' fluxes) -- and each group is copied for the NEXT tile as soon as the
 // phase that reads it has finished: the stage input during phases B and C, the metric terms during C and the next
 // A, the phase-C group during the next A and B. One buffer per group keeps the shared memory per CTA, and so the
-// number of resident CTAs, close to that of the per-tile kernel, while the loads, whose latency bounds the FP32
-// kernel, overlap computation.
+// number of resident CTAs, close to that of the per-tile kernel, while the loads overlap computation: the FP32
+// kernel is bound by their latency, the FP64 kernel by its FP64 pipe, which then also runs through phases A and C.
 //
 // Requirements (checked by the launcher): an even number of nodes per line (every element block of every array is
 // then a multiple of 16 bytes), 16-byte-aligned array pointers, the default log mean. Waits on the mbarriers are
@@ -116,8 +116,20 @@ __device__ __forceinline__ void mbar_drain(uint64_t* bar, int fills) {
   if (fills > 0) mbar_wait_bounded(bar, (unsigned)((fills - 1) & 1));
 }
 
+// Resident CTAs per SM that the register budget is set for (65536 / (CTAs x threads) registers per thread): as
+// many as the shared memory of a fused-update kernel admits (228 KB per SM, 1 KB of it reserved per CTA), at most
+// 2048 threads.
+template <int ND, int N, typename T, int EPB>
+constexpr int pipe_min_ctas() {
+  constexpr size_t smem = PipeSmem<ND, N, T>::bytes(EPB, true) + 1024;
+  constexpr int by_smem = (int)((228 * 1024) / smem);
+  constexpr int by_threads = 2048 / (EPB * Geo<ND, N>::TPE);
+  constexpr int n = by_smem < by_threads ? by_smem : by_threads;
+  return n < 1 ? 1 : n;
+}
+
 template <int ND, int N, typename T, int EPB, int EPI>
-__global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE)
+__global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, EPB>())
     volume_pipe_kernel(const double* __restrict__ in, const T* __restrict__ Ja, const double* __restrict__ invJ,
                        const T* __restrict__ face, double* du, MeshDims md, OpTable<N, T> op, T gamma, int* flag,
                        Epilogue epi, Variant var, int ntiles) {
@@ -146,47 +158,42 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE)
   const bool has_ja = !var.cart;
   const bool need_y = kFused && epi.stage > 0;  // acc (RK4) / K (CK45) are read after stage 0
   const double* gy = EPI == EPI_RK4 ? epi.acc : epi.y;
-  // locals for the copy lambdas (a kernel parameter captured by reference would be copied to local memory)
-  const double* gu = epi.u;
-  const MeshDims mdl = md;
   int fill_in = 0, fill_ja = 0, fill_c = 0;  // thread 0: fills issued per mbarrier
 
-  // thread 0: the copies of one group for the tile t (byte count first, then the copies)
-  auto issue_in = [&](int t) {
-    const int e0 = t * EPB, nel = min(EPB, mdl.E - e0);
+  // thread 0: the copies of one group for the tile t (byte count first, then the copies). Captures by value: a
+  // kernel parameter captured by reference would be copied to local memory.
+  auto issue_in = [=](int t) {
+    const int e0 = t * EPB, nel = min(EPB, md.E - e0);
     mbar_expect_tx(&bars[0], (unsigned)(nel * S::kIn));
     bulk_g2s(s_in, in + (size_t)e0 * G::NV * G::NDOF, (unsigned)(nel * S::kIn), &bars[0]);
-    ++fill_in;
   };
-  auto issue_ja = [&](int t) {
-    const int e0 = t * EPB, nel = min(EPB, mdl.E - e0);
+  auto issue_ja = [=](int t) {
+    const int e0 = t * EPB, nel = min(EPB, md.E - e0);
     mbar_expect_tx(&bars[1], (unsigned)(nel * S::kJa));
     bulk_g2s(s_ja, Ja + (size_t)e0 * ND * ND * G::NDOF, (unsigned)(nel * S::kJa), &bars[1]);
-    ++fill_ja;
   };
-  auto issue_c = [&](int t) {
-    const int e0 = t * EPB, nel = min(EPB, mdl.E - e0);
+  auto issue_c = [=](int t) {
+    const int e0 = t * EPB, nel = min(EPB, md.E - e0);
     const unsigned nin = (unsigned)(nel * S::kIn), nfc = (unsigned)(nel * S::kFace);
     const unsigned nij = has_ja ? (unsigned)(nel * S::kInvJ) : 0u;
     mbar_expect_tx(&bars[2], nij + (kFused ? nin : 0u) + (need_y ? nin : 0u) + 2u * ND * nfc);
     const size_t so = (size_t)e0 * G::NV * G::NDOF;
     if (has_ja) bulk_g2s(s_ij, invJ + (size_t)e0 * G::NDOF, nij, &bars[2]);
-    if (kFused) bulk_g2s(s_eu, gu + so, nin, &bars[2]);
+    if (kFused) bulk_g2s(s_eu, epi.u + so, nin, &bars[2]);
     if (need_y) bulk_g2s(s_ey, gy + so, nin, &bars[2]);
 #pragma unroll
     for (int n = 0; n < ND; ++n) {
       // the tile's own upper faces along n are consecutive in the face array; the lower neighbours' mostly are
-      const T* fn = face + (size_t)n * mdl.E * kFaceT;
+      const T* fn = face + (size_t)n * md.E * kFaceT;
       bulk_g2s(s_fc + ((1 * ND + n) * EPB) * kFaceT, fn + (size_t)e0 * kFaceT, nfc, &bars[2]);
-      if (lower_neighbors_consecutive(mdl, e0, nel, n)) {
-        bulk_g2s(s_fc + (n * EPB) * kFaceT, fn + (size_t)neighbor(mdl, e0, n, -1) * kFaceT, nfc, &bars[2]);
+      if (lower_neighbors_consecutive(md, e0, nel, n)) {
+        bulk_g2s(s_fc + (n * EPB) * kFaceT, fn + (size_t)neighbor(md, e0, n, -1) * kFaceT, nfc, &bars[2]);
       } else {
         for (int el = 0; el < nel; ++el)
-          bulk_g2s(s_fc + (n * EPB + el) * kFaceT, fn + (size_t)neighbor(mdl, e0 + el, n, -1) * kFaceT,
+          bulk_g2s(s_fc + (n * EPB + el) * kFaceT, fn + (size_t)neighbor(md, e0 + el, n, -1) * kFaceT,
                    (unsigned)S::kFace, &bars[2]);
       }
     }
-    ++fill_c;
   };
 
   int t = blockIdx.x;
@@ -197,6 +204,8 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE)
       issue_in(t);
       if (has_ja) issue_ja(t);
       issue_c(t);
+      fill_in = fill_c = 1;
+      fill_ja = has_ja ? 1 : 0;
       s_ok[0] = mbar_wait_bounded(&bars[0], 0u) ? 1 : 0;
     }
   }
@@ -212,9 +221,10 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE)
     }
     mbar_test(&bars[0], par);  // completed: each thread's own acquire of the copied data
 
-    // ---- A: node quantities from the staged input
+    // ---- A: node quantities from the staged input (a partial last round falls to the last warps, not to warp 0,
+    // which also issues the copies)
     bool ok = true;
-    for (int idx = tid; idx < nel * G::NDOF; idx += kThreads) {
+    for (int idx = kThreads - 1 - tid; idx < nel * G::NDOF; idx += kThreads) {
       const int el = idx / G::NDOF, i = idx - el * G::NDOF;
       double uc[G::NV];
 #pragma unroll
@@ -232,7 +242,10 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE)
       break;
     }
     if (has_ja) mbar_test(&bars[1], par);
-    if (tid == 0 && tn < ntiles) issue_in(tn);  // the stage input has been read
+    if (tid == 0 && tn < ntiles) {  // the stage input has been read
+      issue_in(tn);
+      ++fill_in;
+    }
 
     // ---- B: the pairs i < k of each line, as in volume_tile
     if (tid < nel * G::TPE) {
@@ -257,10 +270,14 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE)
       break;
     }
     mbar_test(&bars[2], par);
-    if (tid == 0 && tn < ntiles && has_ja) issue_ja(tn);  // the metric terms have been read
+    if (tid == 0 && tn < ntiles && has_ja) {  // the metric terms have been read
+      issue_ja(tn);
+      ++fill_ja;
+    }
 
-    // ---- C: sum the directions, lift the staged interface fluxes, scale by -1/J, store or update
-    for (int idx = tid; idx < nel * G::NDOF; idx += kThreads) {
+    // ---- C: sum the directions, lift the staged interface fluxes, scale by -1/J, store or update (reversed
+    // thread order as in phase A)
+    for (int idx = kThreads - 1 - tid; idx < nel * G::NDOF; idx += kThreads) {
       const int el = idx / G::NDOF, i = idx - el * G::NDOF;
       T tot[G::NV];
 #pragma unroll
@@ -282,14 +299,15 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE)
         }
       }
       const double ij = var.cart ? var.invJ : s_ij[el * G::NDOF + i];
-      const T sjT = -to_flux<T>(ij);
+      const double sj = -ij;
+      const T sjT = sizeof(T) == 8 ? T(0) : -to_flux<T>(ij);
       const size_t off = (size_t)(e0 + el) * G::NV * G::NDOF + i;
 #pragma unroll
       for (int c = 0; c < G::NV; ++c) {
         const size_t o = off + (size_t)c * G::NDOF;
         const int so = (el * G::NV + c) * G::NDOF + i;
-        // the scaling in FP32 and an exact integer-pipe widening, as in volume_tile
-        const double kv = f2d_int((float)(sjT * tot[c]));
+        // as in volume_tile: FP64 scaling, or the FP32 scaling and an exact integer-pipe widening
+        const double kv = sizeof(T) == 8 ? sj * (double)tot[c] : f2d_int((float)(sjT * tot[c]));
         if (EPI == EPI_STORE)
           du[o] = kv;
         else
@@ -298,7 +316,10 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE)
     }
     if (tid == 0 && tn < ntiles) s_ok[0] = mbar_wait_bounded(&bars[0], par ^ 1u) ? 1 : 0;
     __syncthreads();
-    if (tid == 0 && tn < ntiles) issue_c(tn);  // the phase-C group has been read
+    if (tid == 0 && tn < ntiles) {  // the phase-C group has been read
+      issue_c(tn);
+      ++fill_c;
+    }
   }
   if (failed && tid == 0) {  // a wait ran out: raise the flag, wait (bounded) for the copies in flight
     atomicOr(flag, FLAG_WAIT_TIMEOUT);
