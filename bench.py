@@ -507,7 +507,8 @@ def run_logmean_ablation(args, dev):
     """Volume-term time of the log-mean variants (Sec. 3.1: Algorithms 2/3 with divisions, with the polynomial 1/log
     form; Sec. 7.2: logarithms precomputed per node) against the default (no division, one shared reciprocal),
     on the three initial conditions of the paper's ablation, 2D and 3D, p = 3 and 7, on the sine-perturbed mesh of
-    [-5, 5]^d. FP64; FP32 for 3D p = 3. Each entry is the mean of `steps` dg_rhs calls, L2 flushed before each."""
+    [-5, 5]^d. FP64; FP32 for 3D p = 3. Each entry is the mean of `steps` dg_rhs calls, L2 flushed before each.
+    Every variant runs the per-tile volume kernel, so that the log mean is the only difference."""
     import torch
     from paper_2112_10517_gb300 import dg, inputs
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -522,8 +523,9 @@ def run_logmean_ablation(args, dev):
         states = None
         geo = {}
         for vname, vkw in variants:
+            # all variants on the per-tile kernel (the pipelined one serves the default log mean only)
             ctx = dg.DG(nd, nelem, p, lo=lo, hi=hi, mapping="sine", amp=AMP, surface="llf", precision=precision,
-                        **vkw)
+                        staging="direct", **vkw)
             if states is None:
                 xyz = ctx.node_coords()
                 states = {"vortex": inputs.isentropic_vortex(xyz, eps=20.0), "sine": inputs.sine_paper(xyz),
