@@ -184,9 +184,16 @@ dg_status dg_entropy_rate(dg_ctx* ctx, const double* u, const double* du, double
    (8 nvar (p+1)^(d-1) d bytes per element). FP64 contexts with polydeg <= 5; DG_ERR_UNSUPPORTED otherwise. */
 dg_status dg_vjp(dg_ctx* ctx, const double* u, const double* gbar, double* ubar, dg_stream_t stream);
 
-/* Reads and clears the asynchronous flag of non-physical states. Waits (bounded, 60 s) for the work queued
-   on the stream of the last call; returns DG_OK, DG_ERR_NONPHYSICAL or DG_ERR_TIMEOUT. */
+/* Reads and clears the asynchronous flag of non-physical states and of device-side waits that ran out. Waits
+   (bounded, 60 s) for the work queued on the stream of the last call; returns DG_OK, DG_ERR_NONPHYSICAL or
+   DG_ERR_TIMEOUT (the host wait gave up, or a pipelined kernel's bounded wait on its own copies ran out). */
 dg_status dg_check_status(dg_ctx* ctx);
+
+/* Failure-path self-test of the device-side bounded waits: queues on `stream` one CTA that waits, with the same
+   bounded mbarrier wait the pipelined volume kernel uses, on an mbarrier that nothing completes. The wait gives up
+   after about half a second and sets the context's timeout flag, so that the next dg_check_status returns
+   DG_ERR_TIMEOUT (and clears it; the context stays usable). Nothing faults, traps or hangs. */
+dg_status dg_selftest_wait_timeout(dg_ctx* ctx, dg_stream_t stream);
 
 /* Getters (host copies; synchronize the device). */
 dg_status dg_get_info(const dg_ctx* ctx, dg_info* info);

@@ -77,6 +77,8 @@ cudaError_t launch_volume(int nd, int p, int precision, MeshDims md, const doubl
 cudaError_t launch_entropy_rate(int nd, int p, MeshDims md, const double* u, const double* du, const double* JW,
                                 double gamma, double* partial, int nblocks, double* out, cudaStream_t s);
 int entropy_rate_blocks();
+// One CTA whose bounded mbarrier wait runs out and sets FLAG_WAIT_TIMEOUT in *flag (dg_selftest_wait_timeout).
+cudaError_t launch_wait_probe(int* flag, cudaStream_t s);
 void ck45_coefficients(int stage, double* a, double* b);
 
 // Legendre-Gauss reference tables of degree p (Sec. 6): nodes, weights and derivative matrix in `ref` (ref.Dt is

@@ -597,6 +597,14 @@ dg_status dg_check_status(dg_ctx* c) {
   return DG_OK;
 }
 
+dg_status dg_selftest_wait_timeout(dg_ctx* c, dg_stream_t stream) {
+  if (!c) return DG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  c->launches += 1;
+  return cuda_status(dgk::launch_wait_probe(c->d_flag, s));
+}
+
 dg_status dg_get_info(const dg_ctx* c, dg_info* info) {
   if (!c || !info) return DG_ERR_ARG;
   info->ndims = c->nd;

@@ -1,6 +1,7 @@
 // Runge-Kutta coefficients and the entropy-rate diagnostic (FP64). The stage updates themselves run in the
 // volume kernel's epilogue.
 #include "kernels.cuh"
+#include "volume_pipe.cuh"
 
 namespace dgk {
 namespace {
@@ -112,6 +113,22 @@ cudaError_t launch_entropy_rate(int nd, int p, MeshDims md, const double* u, con
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   reduce_pairs_kernel<<<1, kRedThreads, 0, s>>>(partial, nblocks, out);
+  return cudaGetLastError();
+}
+
+// One thread waits on an mbarrier that expects one arrival and gets none: mbar_wait_bounded gives up and the flag
+// records the timeout, as in the pipelined volume kernel.
+__global__ void wait_probe_kernel(int* flag) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+    if (!mbar_wait_bounded(&bar, 0u)) atomicOr(flag, FLAG_WAIT_TIMEOUT);
+  }
+}
+
+cudaError_t launch_wait_probe(int* flag, cudaStream_t s) {
+  wait_probe_kernel<<<1, 32, 0, s>>>(flag);
   return cudaGetLastError();
 }
 

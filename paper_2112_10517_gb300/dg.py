@@ -40,7 +40,7 @@ KERNEL_VOLUME, KERNEL_INTERFACE, KERNEL_PROJECT = 0, 1, 2
 EXPORTED = ["dg_init", "dg_rhs", "dg_step", "dg_entropy_rate", "dg_check_status", "dg_get_info",
             "dg_get_node_coords", "dg_get_metrics", "dg_profile_enable", "dg_profile_read", "dg_launch_count",
             "dg_free", "dg_status_string", "dg_rhs_noalloc", "dg_batch_create", "dg_batch_rhs",
-            "dg_batch_autotune", "dg_batch_set_tuning", "dg_batch_free", "dg_vjp"]
+            "dg_batch_autotune", "dg_batch_set_tuning", "dg_batch_free", "dg_vjp", "dg_selftest_wait_timeout"]
 
 
 class DgMesh(ctypes.Structure):
@@ -92,6 +92,7 @@ _sig = {
     "dg_batch_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "dg_batch_free": (None, [_vp]),
     "dg_vjp": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "dg_selftest_wait_timeout": (ctypes.c_int, [_vp, _vp]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)

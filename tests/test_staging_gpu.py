@@ -152,3 +152,23 @@ def test_auto_selects_by_tiles_per_cta(dgmod):
     sc = Scenario(3, [32, 32, 32], 3, mapping="sine", ic="tgv", llf=True)
     auto, pipe = rhs_with(dgmod, sc, "auto"), rhs_with(dgmod, sc, "pipelined")
     assert np.array_equal(auto, pipe)
+
+
+def test_device_wait_timeout_is_reported_and_the_context_recovers(dgmod):
+    # the pipelined kernel's waits on its own copies are bounded; a wait that runs out raises the timeout flag.
+    # The self-test waits, with the same bounded wait, on an mbarrier nothing completes (no fault, no hang)
+    import time
+    import torch
+    sc = Scenario(3, [3, 2, 3], 3, mapping="sine", ic="rough", llf=True, seed=670)
+    ctx = dgmod.DG(precision="fp32", staging="pipelined", **sc.dg_kwargs())
+    t0 = time.time()
+    assert dgmod.dg_selftest_wait_timeout(ctx.ctx, None) == dgmod.DG_OK
+    assert ctx.check_status() == dgmod.DG_ERR_TIMEOUT
+    elapsed = time.time() - t0
+    assert 0.1 < elapsed < 30.0, elapsed
+    assert ctx.check_status() == dgmod.DG_OK  # read and cleared
+    du = ctx.rhs(torch.from_numpy(sc.u).cuda())
+    torch.cuda.synchronize()
+    assert ctx.check_status() == dgmod.DG_OK
+    _, term = parity_errors(du.cpu().numpy(), sc.du_ref(), sc.du_scale())
+    assert np.all(term <= TOL32), term
