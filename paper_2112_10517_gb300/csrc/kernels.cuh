@@ -65,7 +65,7 @@ struct OpTable {
   T Dt8[N * N];  // flux-differencing matrix 2D - M^{-1}B (Eq. opDsplit), divided by 8 (fluxes come scaled by 8)
   T D0[N * N];   // 2 Dt8: the coefficients of the mass flux, which the volume sums take halved (exact)
   T winv;        // 1/w_0 = 1/w_p = p(p+1)/2: the lift M^{-1} R^T B at the end nodes
-  T lift8;       // winv / 8: the lift of the face buffer, which holds interface fluxes scaled by 8
+  T lift8;       // winv / 8 (the face buffer holds the interface fluxes already lifted: f* / w_0)
 };
 
 // ---------------------------------------------------------------------------------------------------
@@ -73,7 +73,9 @@ struct OpTable {
 // Thread per (lower element e, direction n, face node fn). The upper neighbour across +n is e+.
 // f* = f_Ranocha(u_L, u_R, m) - [llf] lambda/2 (u_R - u_L), m = Ja^n at the lower element's face node,
 // lambda = max(|v_L.m| + c_L|m|, |v_R.m| + c_R|m|), c = sqrt(gamma p/rho).
-// face layout [n][E][NV][NL].
+// face layout [n][E][NV][NL], holding the lifted flux f* / w_0 (the surface term of the volume kernel: +f* / w_p
+// at i_n = p, -f* / w_0 at i_n = 0, Eq. opDsplit). f* is linear in m (both the two-point flux and the LLF term are
+// homogeneous of degree 1 in m), so the factor 1/w_0 = p(p+1)/2 rides on the metric vector at no cost.
 // ---------------------------------------------------------------------------------------------------
 // Interface flux at face node `idx` of a mesh, idx = (e * ND + n) * NL + fn: the faces on an element's upper side
 // in all directions are neighbours in the launch, so the element's data are fetched once for them and its lower
@@ -100,18 +102,20 @@ __device__ __forceinline__ void interface_node(const double* __restrict__ u, con
     uL[c] = u[((size_t)e * G::NV + c) * G::NDOF + nodeL];
     uR[c] = u[((size_t)eR * G::NV + c) * G::NDOF + nodeR];
   }
+  // the pair flux takes 2 m and returns 8 f: with 2 m scaled by lift8 = N(N-1)/16 the result is f / w_0
+  constexpr double kLift8 = N * (N - 1) / 16.0;
   T m[ND], m2[ND];
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
     m[j] = var.cart ? (j == n ? (T)cart_jn(var, n) : T(0)) : Ja[(((size_t)e * ND + n) * ND + j) * G::NDOF + nodeL];
-    m2[j] = m[j] + m[j];
+    m2[j] = m[j] * T(2.0 * kLift8);
   }
   const T gm1 = gamma - T(1);
   T qL[NodeQ<ND>::NQ], qR[NodeQ<ND>::NQ], f[G::NV], irL, irR;
   const bool ok = node_quantities<ND, T>(uL, gm1, T(2) / gm1, qL, &irL) &
                   node_quantities<ND, T>(uR, gm1, T(2) / gm1, qR, &irR);
   if (!ok) atomicOr(flag, 1);
-  pair_flux8<ND, T, FLUX>(qL, qR, m2, f);  // 8 f(u_L, u_R, m); the face buffer keeps this scale (lift8)
+  pair_flux8<ND, T, FLUX>(qL, qR, m2, f);  // f(u_L, u_R, m) / w_0
   if (LLF) {
     T mm = m[0] * m[0], vnL = qL[1] * m[0], vnR = qR[1] * m[0];
 #pragma unroll
@@ -124,7 +128,7 @@ __device__ __forceinline__ void interface_node(const double* __restrict__ u, con
     const T hgm = T(0.5) * gamma * mm;
     const T lamL = Num<T>::abs(vnL) + Num<T>::sqrt(hgm * qL[NodeQ<ND>::PP] * irL);
     const T lamR = Num<T>::abs(vnR) + Num<T>::sqrt(hgm * qR[NodeQ<ND>::PP] * irR);
-    const T lam4 = T(4) * (lamL > lamR ? lamL : lamR);  // 8 (lambda / 2)
+    const T lam4 = T(4.0 * kLift8) * (lamL > lamR ? lamL : lamR);  // (lambda / 2) / w_0
 #pragma unroll
     for (int c = 0; c < G::NV; ++c) {
       // FP64: the jump in FP64; FP32 mode: both states rounded to FP32 first (no FP64 arithmetic)
@@ -186,6 +190,40 @@ __device__ __forceinline__ void stage_update(const Epilogue& epi, size_t o, doub
   }
 }
 
+// The same update with the node's Jacobian factor s = -1/J folded into the weights (k = s tot; FP64 flux
+// arithmetic): w1 = s b_s dt (RK4: the weight of k in acc, or in u at the last stage) or s dt (CK45), w2 = s c dt
+// (RK4: the weight of k in the next stage state). Two products per node replace one per value.
+template <int EPI>
+__device__ __forceinline__ void stage_weights(const Epilogue& epi, double s, double& w1, double& w2) {
+  if (EPI == EPI_RK4) {
+    w1 = epi.ca * s;
+    w2 = epi.cy * s;
+  } else {
+    w1 = epi.dt * s;
+    w2 = 0.0;
+  }
+}
+
+template <int EPI>
+__device__ __forceinline__ void stage_update_w(const Epilogue& epi, size_t o, double tot, double w1, double w2,
+                                               double uo, double yo) {
+  if (EPI == EPI_RK4) {
+    if (epi.stage == 0) {
+      epi.acc[o] = w1 * tot;
+      epi.y[o] = uo + w2 * tot;
+    } else if (epi.stage < 3) {
+      epi.acc[o] = yo + w1 * tot;
+      epi.y[o] = uo + w2 * tot;
+    } else {
+      epi.u[o] = uo + yo + w1 * tot;
+    }
+  } else {
+    const double kk = (epi.stage == 0 ? 0.0 : epi.a * yo) + w1 * tot;
+    epi.y[o] = kk;
+    epi.u[o] = uo + epi.b * kk;
+  }
+}
+
 // Positive floating-point values order like their bit patterns read as unsigned integers: shared-memory integer
 // atomicMin/atomicMax then give a tile's value range.
 template <typename T>
@@ -234,9 +272,13 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // The pairs i < k of one line (Sec. 2.2): sp/sj point at the line's first node in the node-quantity and metric
 // arrays (stride st), sa at its accumulator slots; each pair's flux is evaluated once and added to both nodes.
 // With LM == LM_PRELOG, sl points at the line's first node in the per-node logarithm array [2][NDOF].
+// fu, fl (optional): the lifted interface fluxes (f* / w_0, component stride NL) of the line's upper and lower face
+// point; the surface term then starts the end nodes' sums (+fu at node N-1, -fl at node 0) instead of being added
+// in the epilogue.
 template <int ND, int N, typename T, int FLUX, bool CART, int LM = LM_SHARED_RCP>
 __device__ __forceinline__ void line_pairs(const T* sp, const T* sj, const T* sl, int st, int n, T n2n,
-                                           const OpTable<N, T>& op, T* sa) {
+                                           const OpTable<N, T>& op, T* sa, const T* fu = nullptr,
+                                           const T* fl = nullptr) {
   using G = Geo<ND, N>;
   constexpr int NQ = NodeQ<ND>::NQ;
   T acc[N][G::NV];
@@ -244,6 +286,13 @@ __device__ __forceinline__ void line_pairs(const T* sp, const T* sj, const T* sl
   for (int i = 0; i < N; ++i)
 #pragma unroll
     for (int c = 0; c < G::NV; ++c) acc[i][c] = T(0);
+  if (fu) {
+#pragma unroll
+    for (int c = 0; c < G::NV; ++c) {
+      acc[N - 1][c] = fu[c * G::NL];
+      acc[0][c] = -fl[c * G::NL];
+    }
+  }
 #pragma unroll
   for (int i = 0; i < N - 1; ++i) {
     T a[NQ], ja_i[ND], va_n = T(0);
@@ -426,16 +475,30 @@ __device__ __forceinline__ void volume_tile(const double* u, const T* __restrict
       if (in == N - 1 || in == 0) {
         const int fn = G::face_index(n, i);
         const int fe = in == N - 1 ? ge : neighbor(md, ge, n, -1);
-        const T sgn = in == N - 1 ? op.lift8 : -op.lift8;
-        const T* fp = face + ((size_t)n * md.E + fe) * G::NV * G::NL + fn;
+        const T* fp = face + ((size_t)n * md.E + fe) * G::NV * G::NL + fn;  // lifted: f* / w_0
+        if (in == N - 1) {
 #pragma unroll
-        for (int c = 0; c < G::NV; ++c) tot[c] += sgn * fp[c * G::NL];
+          for (int c = 0; c < G::NV; ++c) tot[c] += fp[c * G::NL];
+        } else {
+#pragma unroll
+          for (int c = 0; c < G::NV; ++c) tot[c] -= fp[c * G::NL];
+        }
       }
     }
     const double ij = var.cart ? var.invJ : invJ[(size_t)ge * G::NDOF + i];
     const double sj = -ij;
     const T sjT = sizeof(T) == 8 ? T(0) : -to_flux<T>(ij);
     const size_t off = (size_t)ge * G::NV * G::NDOF + i;
+    if constexpr (sizeof(T) == 8 && EPI != EPI_STORE) {  // FP64: -1/J folded into the stage weights
+      double w1, w2;
+      stage_weights<EPI>(epi, sj, w1, w2);
+#pragma unroll
+      for (int c = 0; c < G::NV; ++c) {
+        const int so = (el * G::NV + c) * G::NDOF + i;
+        stage_update_w<EPI>(epi, off + (size_t)c * G::NDOF, (double)tot[c], w1, w2, s_eu[so], s_ey[so]);
+      }
+      continue;
+    }
 #pragma unroll
     for (int c = 0; c < G::NV; ++c) {
       const size_t o = off + (size_t)c * G::NDOF;

@@ -2,8 +2,8 @@
 // persistent CTAs take element tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...; one thread copies the tiles'
 // data into shared memory with bulk asynchronous copies (cp.async.bulk, the TMA engine), each group of arrays
 // completing on its own mbarrier. A tile runs in three phases -- A: node quantities from the stage input,
-// B: the two-point fluxes along lines (metric terms), C: lift of the interface fluxes, -1/J, store or stage update
-// (1/J, the Runge-Kutta operands, the faces' fluxes) -- and each group is copied for the NEXT tile as soon as the
+// B: the two-point fluxes along lines, whose sums start from the lifted interface fluxes (metric terms, faces),
+// C: -1/J, store or stage update (1/J, the Runge-Kutta operands) -- and each group is copied for the NEXT tile as soon as the
 // phase that reads it has finished: the stage input during phases B and C, the metric terms during C and the next
 // A, the phase-C group during the next A and B. One buffer per group keeps the shared memory per CTA, and so the
 // number of resident CTAs, close to that of the per-tile kernel, while the loads overlap computation: the FP32
@@ -68,10 +68,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
 
 // Shared memory of the pipelined kernel, for EPB elements: the copied groups
 //   IN [EPB][NV][NDOF] f64 (stage input)                                         mbarrier 0
-//   JA [EPB][ND][ND][NDOF] T (metric terms; not copied on Cartesian meshes)       mbarrier 1
+//   JA [EPB][ND][ND][NDOF] T (metric terms; not copied on Cartesian meshes), FC [2][ND][EPB][NV][NL] T (the
+//   lifted interface fluxes; side 0: the upper face of the lower neighbour, side 1: the element's own)
+//                                                                                  mbarrier 1
 //   IJ [EPB][NDOF] f64 (1/J; not on Cartesian meshes), EU, EY [EPB][NV][NDOF] f64
-//   (fused stage update: u, and acc (RK4) / K (CK45) after stage 0), FC [2][ND][EPB][NV][NL] T (side 0: the upper
-//   face of the lower neighbour, side 1: the element's own)                      mbarrier 2
+//   (fused stage update: u, and acc (RK4) / K (CK45) after stage 0)              mbarrier 2
 // then the tile scratch, node quantities [EPB][NQ][NDOF] T and per-direction sums [EPB][ND][NV][NDOF] T, then the
 // three mbarriers. Every region is a multiple of 16 bytes for even N.
 template <int ND, int N, typename T>
@@ -167,33 +168,34 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, 
     mbar_expect_tx(&bars[0], (unsigned)(nel * S::kIn));
     bulk_g2s(s_in, in + (size_t)e0 * G::NV * G::NDOF, (unsigned)(nel * S::kIn), &bars[0]);
   };
-  auto issue_ja = [=](int t) {
+  auto issue_ja = [=](int t) {  // metric terms (curvilinear meshes) and the faces' lifted fluxes
     const int e0 = t * EPB, nel = min(EPB, md.E - e0);
-    mbar_expect_tx(&bars[1], (unsigned)(nel * S::kJa));
-    bulk_g2s(s_ja, Ja + (size_t)e0 * ND * ND * G::NDOF, (unsigned)(nel * S::kJa), &bars[1]);
-  };
-  auto issue_c = [=](int t) {
-    const int e0 = t * EPB, nel = min(EPB, md.E - e0);
-    const unsigned nin = (unsigned)(nel * S::kIn), nfc = (unsigned)(nel * S::kFace);
-    const unsigned nij = has_ja ? (unsigned)(nel * S::kInvJ) : 0u;
-    mbar_expect_tx(&bars[2], nij + (kFused ? nin : 0u) + (need_y ? nin : 0u) + 2u * ND * nfc);
-    const size_t so = (size_t)e0 * G::NV * G::NDOF;
-    if (has_ja) bulk_g2s(s_ij, invJ + (size_t)e0 * G::NDOF, nij, &bars[2]);
-    if (kFused) bulk_g2s(s_eu, epi.u + so, nin, &bars[2]);
-    if (need_y) bulk_g2s(s_ey, gy + so, nin, &bars[2]);
+    const unsigned nja = has_ja ? (unsigned)(nel * S::kJa) : 0u, nfc = (unsigned)(nel * S::kFace);
+    mbar_expect_tx(&bars[1], nja + 2u * ND * nfc);
+    if (has_ja) bulk_g2s(s_ja, Ja + (size_t)e0 * ND * ND * G::NDOF, nja, &bars[1]);
 #pragma unroll
     for (int n = 0; n < ND; ++n) {
       // the tile's own upper faces along n are consecutive in the face array; the lower neighbours' mostly are
       const T* fn = face + (size_t)n * md.E * kFaceT;
-      bulk_g2s(s_fc + ((1 * ND + n) * EPB) * kFaceT, fn + (size_t)e0 * kFaceT, nfc, &bars[2]);
+      bulk_g2s(s_fc + ((1 * ND + n) * EPB) * kFaceT, fn + (size_t)e0 * kFaceT, nfc, &bars[1]);
       if (lower_neighbors_consecutive(md, e0, nel, n)) {
-        bulk_g2s(s_fc + (n * EPB) * kFaceT, fn + (size_t)neighbor(md, e0, n, -1) * kFaceT, nfc, &bars[2]);
+        bulk_g2s(s_fc + (n * EPB) * kFaceT, fn + (size_t)neighbor(md, e0, n, -1) * kFaceT, nfc, &bars[1]);
       } else {
         for (int el = 0; el < nel; ++el)
           bulk_g2s(s_fc + (n * EPB + el) * kFaceT, fn + (size_t)neighbor(md, e0 + el, n, -1) * kFaceT,
-                   (unsigned)S::kFace, &bars[2]);
+                   (unsigned)S::kFace, &bars[1]);
       }
     }
+  };
+  auto issue_c = [=](int t) {  // 1/J (curvilinear meshes) and the stage update's operands; may be empty
+    const int e0 = t * EPB, nel = min(EPB, md.E - e0);
+    const unsigned nin = (unsigned)(nel * S::kIn);
+    const unsigned nij = has_ja ? (unsigned)(nel * S::kInvJ) : 0u;
+    mbar_expect_tx(&bars[2], nij + (kFused ? nin : 0u) + (need_y ? nin : 0u));
+    const size_t so = (size_t)e0 * G::NV * G::NDOF;
+    if (has_ja) bulk_g2s(s_ij, invJ + (size_t)e0 * G::NDOF, nij, &bars[2]);
+    if (kFused) bulk_g2s(s_eu, epi.u + so, nin, &bars[2]);
+    if (need_y) bulk_g2s(s_ey, gy + so, nin, &bars[2]);
   };
 
   int t = blockIdx.x;
@@ -202,10 +204,9 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, 
     mbar_init_fence();
     if (t < ntiles) {
       issue_in(t);
-      if (has_ja) issue_ja(t);
+      issue_ja(t);
       issue_c(t);
-      fill_in = fill_c = 1;
-      fill_ja = has_ja ? 1 : 0;
+      fill_in = fill_ja = fill_c = 1;
       s_ok[0] = mbar_wait_bounded(&bars[0], 0u) ? 1 : 0;
     }
   }
@@ -235,19 +236,20 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, 
       for (int c = 0; c < NQ; ++c) s_prim[(el * NQ + c) * G::NDOF + i] = q[c];
     }
     if (!ok) atomicOr(flag, FLAG_NONPHYSICAL);
-    if (tid == 0) s_ok[1] = has_ja ? (mbar_wait_bounded(&bars[1], par) ? 1 : 0) : 1;
+    if (tid == 0) s_ok[1] = mbar_wait_bounded(&bars[1], par) ? 1 : 0;
     __syncthreads();
     if (!s_ok[1]) {  // all threads read the same slot: the whole CTA leaves the loop
       failed = true;
       break;
     }
-    if (has_ja) mbar_test(&bars[1], par);
+    mbar_test(&bars[1], par);
     if (tid == 0 && tn < ntiles) {  // the stage input has been read
       issue_in(tn);
       ++fill_in;
     }
 
-    // ---- B: the pairs i < k of each line, as in volume_tile
+    // ---- B: the pairs i < k of each line, as in volume_tile; the end nodes' sums start from the lifted fluxes of
+    // the line's two face points (face node l of the faces normal to n)
     if (tid < nel * G::TPE) {
       const int el = tid / G::TPE, r = tid - el * G::TPE;
       const int n = r / G::NL, l = r - n * G::NL;
@@ -255,12 +257,14 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, 
       const T* sp = s_prim + el * NQ * G::NDOF + lb;
       const T* sj = s_ja + (el * ND + n) * ND * G::NDOF + lb;
       T* sa = s_acc + (el * ND + n) * G::NV * G::NDOF + lb;
+      const T* fu = s_fc + ((1 * ND + n) * EPB + el) * kFaceT + l;
+      const T* fl = s_fc + ((0 * ND + n) * EPB + el) * kFaceT + l;
       const T n2n = T(2) * (T)cart_jn(var, n);
       switch (var.flux * 2 + var.cart) {
-        case 0: line_pairs<ND, N, T, 0, false>(sp, sj, nullptr, st, n, n2n, op, sa); break;
-        case 1: line_pairs<ND, N, T, 0, true>(sp, sj, nullptr, st, n, n2n, op, sa); break;
-        case 2: line_pairs<ND, N, T, 1, false>(sp, sj, nullptr, st, n, n2n, op, sa); break;
-        default: line_pairs<ND, N, T, 1, true>(sp, sj, nullptr, st, n, n2n, op, sa); break;
+        case 0: line_pairs<ND, N, T, 0, false>(sp, sj, nullptr, st, n, n2n, op, sa, fu, fl); break;
+        case 1: line_pairs<ND, N, T, 0, true>(sp, sj, nullptr, st, n, n2n, op, sa, fu, fl); break;
+        case 2: line_pairs<ND, N, T, 1, false>(sp, sj, nullptr, st, n, n2n, op, sa, fu, fl); break;
+        default: line_pairs<ND, N, T, 1, true>(sp, sj, nullptr, st, n, n2n, op, sa, fu, fl); break;
       }
     }
     if (tid == 0) s_ok[2] = mbar_wait_bounded(&bars[2], par) ? 1 : 0;
@@ -270,13 +274,12 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, 
       break;
     }
     mbar_test(&bars[2], par);
-    if (tid == 0 && tn < ntiles && has_ja) {  // the metric terms have been read
+    if (tid == 0 && tn < ntiles) {  // the metric terms and face fluxes have been read
       issue_ja(tn);
       ++fill_ja;
     }
 
-    // ---- C: sum the directions, lift the staged interface fluxes, scale by -1/J, store or update (reversed
-    // thread order as in phase A)
+    // ---- C: sum the directions, scale by -1/J, store or update (reversed thread order as in phase A)
     for (int idx = kThreads - 1 - tid; idx < nel * G::NDOF; idx += kThreads) {
       const int el = idx / G::NDOF, i = idx - el * G::NDOF;
       T tot[G::NV];
@@ -287,21 +290,21 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, 
         for (int n = 0; n < ND; ++n) s += s_acc[((el * ND + n) * G::NV + c) * G::NDOF + i];
         tot[c] = s;
       }
-#pragma unroll
-      for (int n = 0; n < ND; ++n) {
-        const int in_ = (i / G::stride(n)) % N;
-        if (in_ == N - 1 || in_ == 0) {
-          const int side = in_ == N - 1 ? 1 : 0;
-          const T sgn = in_ == N - 1 ? op.lift8 : -op.lift8;
-          const T* fp = s_fc + ((side * ND + n) * EPB + el) * kFaceT + G::face_index(n, i);
-#pragma unroll
-          for (int c = 0; c < G::NV; ++c) tot[c] += sgn * fp[c * G::NL];
-        }
-      }
       const double ij = var.cart ? var.invJ : s_ij[el * G::NDOF + i];
       const double sj = -ij;
       const T sjT = sizeof(T) == 8 ? T(0) : -to_flux<T>(ij);
       const size_t off = (size_t)(e0 + el) * G::NV * G::NDOF + i;
+      if constexpr (sizeof(T) == 8 && EPI != EPI_STORE) {  // FP64: -1/J folded into the stage weights
+        double w1, w2;
+        stage_weights<EPI>(epi, sj, w1, w2);
+#pragma unroll
+        for (int c = 0; c < G::NV; ++c) {
+          const int so = (el * G::NV + c) * G::NDOF + i;
+          stage_update_w<EPI>(epi, off + (size_t)c * G::NDOF, (double)tot[c], w1, w2, s_eu[so],
+                              need_y ? s_ey[so] : 0.0);
+        }
+        continue;
+      }
 #pragma unroll
       for (int c = 0; c < G::NV; ++c) {
         const size_t o = off + (size_t)c * G::NDOF;

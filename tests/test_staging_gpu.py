@@ -79,13 +79,14 @@ def test_both_stagings_match_oracle(dgmod, precision, nd, nelem, p, mapping, flu
 def test_stagings_agree_on_many_tiles_per_cta(dgmod, nelem, p):
     # thousands of tiles: each persistent CTA loops several times, both stage buffers change parity twice or more
     # (the 16^3 case is also checked against the oracle, element by element, by the FP32 Taylor-Green parity test)
+    # (the two kernels add the surface term at different points of the sums: they agree to FP32 rounding of the
+    # summed terms, the measure of the parity tests)
     sc = Scenario(3, nelem, p, mapping="sine", ic="tgv", llf=True)
     a = rhs_with(dgmod, sc, "pipelined")
     d = rhs_with(dgmod, sc, "direct")
-    scale = np.max(np.abs(d), axis=(0, 2))
-    err = np.max(np.abs(a - d), axis=(0, 2)) / scale
-    print("pipelined vs direct, max abs diff / max |du| per variable", err)
-    assert np.all(err <= 1e-5), err
+    _, term = parity_errors(a, d, sc.du_scale())
+    print("pipelined vs direct, term-relative per variable", term)
+    assert np.all(term <= TOL32), term
 
 
 @pytest.mark.parametrize("nelem,p", [([16, 16, 16], 3), ([16, 16, 16], 1)])
@@ -93,10 +94,9 @@ def test_fp64_stagings_agree_on_many_tiles_per_cta(dgmod, nelem, p):
     sc = Scenario(3, nelem, p, mapping="sine", ic="tgv", llf=True)
     a = rhs_with(dgmod, sc, "pipelined", precision="fp64")
     d = rhs_with(dgmod, sc, "direct", precision="fp64")
-    scale = np.max(np.abs(d), axis=(0, 2))
-    err = np.max(np.abs(a - d), axis=(0, 2)) / scale
-    print("pipelined vs direct (FP64), max abs diff / max |du| per variable", err)
-    assert np.all(err <= 1e-11), err
+    _, term = parity_errors(a, d, sc.du_scale())
+    print("pipelined vs direct (FP64), term-relative per variable", term)
+    assert np.all(term <= TOL64), term
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
