@@ -68,13 +68,34 @@ __device__ __forceinline__ double log_f64(double x) {
   return fma(kd, kLn2Head, fma(kd, kLn2Tail, logm));
 }
 
+// Sign and order tests of doubles on the integer pipe (on GB300 FP64 compares, absolute values and minima/maxima
+// issue on the FP64 pipe, which the kernels saturate): a double's bit pattern read as a signed 64-bit integer
+// orders like the value for non-negative values, and +inf is 0x7FF0000000000000 with the NaNs above it.
+//   pos_f64(x):   0 < x <= +inf (false for NaN and zero), as x > 0
+//   posfin_f64(x): 0 < x < +inf
+//   abs_f64(x):   |x| by clearing the sign bit of the high word
+//   maxnn_f64(a, b): max(a, b) for non-negative a, b (b when equal)
+__device__ __forceinline__ bool pos_f64(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && b <= 0x7FF0000000000000LL;
+}
+__device__ __forceinline__ bool posfin_f64(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && b < 0x7FF0000000000000LL;
+}
+__device__ __forceinline__ double abs_f64(double x) {
+  return __hiloint2double(__double2hiint(x) & 0x7FFFFFFF, __double2loint(x));
+}
+__device__ __forceinline__ double maxnn_f64(double a, double b) {
+  return __double_as_longlong(a) > __double_as_longlong(b) ? a : b;
+}
+
 // sqrt x for positive normal x by Goldschmidt's iteration for the square root: from r ~ 1/sqrt(x)
 // (rsqrt.approx.ftz.f64), g = x r ~ sqrt(x) and h = r/2 are refined together by e = 1/2 - g h,
 // g <- g + g e, h <- h + h e, which doubles the number of correct bits per step; two steps reach the rounding
 // limit (about 1 ulp). x = 0 gives 0; other non-positive or non-finite x give NaN or inf.
 __device__ __forceinline__ double sqrt_f64(double x) {
-  if (!(x > 0.0) || x == __longlong_as_double(0x7FF0000000000000LL))
-    return x == 0.0 ? x : (x > 0.0 ? x : __longlong_as_double(0x7FF8000000000000LL));
+  if (!posfin_f64(x)) return x == 0.0 ? x : (x > 0.0 ? x : __longlong_as_double(0x7FF8000000000000LL));
   double r;
   asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
   double g = x * r, h = 0.5 * r;
@@ -104,7 +125,9 @@ struct Num<double> {
   __device__ static __forceinline__ double log(double x) { return log_f64(x); }
   __device__ static __forceinline__ double log1p(double x) { return ::log1p(x); }
   __device__ static __forceinline__ double sqrt(double x) { return sqrt_f64(x); }
-  __device__ static __forceinline__ double abs(double x) { return ::fabs(x); }
+  __device__ static __forceinline__ double abs(double x) { return abs_f64(x); }
+  __device__ static __forceinline__ bool pos(double x) { return pos_f64(x); }
+  __device__ static __forceinline__ double maxnn(double a, double b) { return maxnn_f64(a, b); }
   // u < 1e-4, the threshold of the series branch of Algorithms 2 and 3 for 64-bit floats (Sec. 3.1), tested on
   // the high 32 bits of u >= 0 (an integer comparison): the effective threshold is the largest double whose
   // high word is below that of 1e-4, 1e-4 to within a relative 1e-6; both branches are accurate there.
@@ -127,6 +150,8 @@ struct Num<float> {
   __device__ static __forceinline__ float log1p(float x) { return ::log1pf(x); }
   __device__ static __forceinline__ float sqrt(float x) { return ::sqrtf(x); }
   __device__ static __forceinline__ float abs(float x) { return ::fabsf(x); }
+  __device__ static __forceinline__ bool pos(float x) { return x > 0.0f; }
+  __device__ static __forceinline__ float maxnn(float a, float b) { return a > b ? a : b; }
   // The paper states the threshold for 64-bit floats only. In FP32 the truncated series is accurate to about
   // 0.03 u^4 relative and the log branch loses about eps32/(2 sqrt(u)); 1e-2 keeps both near 1 ulp.
   // values within this ratio give u <= 7.6e-3: the series branch with margin
@@ -248,7 +273,7 @@ __device__ __forceinline__ bool node_quantities(const double* uc, T gm1, T two_o
   q[0] = rho;
   q[NodeQ<ND>::PP] = p + p;
   q[NodeQ<ND>::PG] = p * two_over_gm1;
-  return rho > T(0) && p > T(0);
+  return Num<T>::pos(rho) && Num<T>::pos(p);
 }
 
 // ---------------------------------------------------------------------------------------------------

@@ -128,7 +128,7 @@ __device__ __forceinline__ void interface_node(const double* __restrict__ u, con
     const T hgm = T(0.5) * gamma * mm;
     const T lamL = Num<T>::abs(vnL) + Num<T>::sqrt(hgm * qL[NodeQ<ND>::PP] * irL);
     const T lamR = Num<T>::abs(vnR) + Num<T>::sqrt(hgm * qR[NodeQ<ND>::PP] * irR);
-    const T lam4 = T(4.0 * kLift8) * (lamL > lamR ? lamL : lamR);  // (lambda / 2) / w_0
+    const T lam4 = T(4.0 * kLift8) * Num<T>::maxnn(lamL, lamR);  // (lambda / 2) / w_0
 #pragma unroll
     for (int c = 0; c < G::NV; ++c) {
       // FP64: the jump in FP64; FP32 mode: both states rounded to FP32 first (no FP64 arithmetic)
