@@ -47,6 +47,11 @@ int dgpk_eval_log(long long n, const double* x, double* log_own, double* log_ref
    cudaError_t value. */
 int dgpk_eval_sqrt(long long n, const double* x, double* own, double* ref);
 
+/* Self-test of the LLF wave speed's square root (an FP32 root refined by one FP64 Newton step, about 46 bits;
+   sqrt_f64 outside [2^-100, 2^100]): out receives sqrt_wave_f64(x[i]). Device arrays; synchronizes; returns 0 or a
+   cudaError_t value. */
+int dgpk_eval_sqrt_wave(long long n, const double* x, double* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -190,6 +190,20 @@ __device__ __forceinline__ double f2d_int(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// sqrt x to about 46 bits, for the local Lax-Friedrichs wave speed: the correctly rounded FP32 root g of x and
+// h ~ 1/(2g) in FP32 (integer-pipe conversions), then one Newton (Heron) step in FP64, g + h (x - g^2), which
+// squares the relative error of g (2^-24 -> 2^-48; h's own error adds about 2^-47). Two FP64 operations instead
+// of the seven of sqrt_f64; x outside [2^-100, 2^100] (beyond the FP32 seed's range) takes sqrt_f64.
+__device__ __forceinline__ double sqrt_wave_f64(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x);
+  if (hi - 0x39B00000u >= 0x0C800000u) return sqrt_f64(x);  // not in [2^-100, 2^100): sign, 0, NaN, inf, range
+  const float xf = d2f_int(x);
+  const float gf = sqrtf(xf);
+  const double g = f2d_int(gf);
+  const double h = f2d_int(__fdividef(0.5f, gf));
+  return fma(fma(-g, g, x), h, g);
+}
+
 // FP32 value of a double x in [0, 1) from its high word alone: the exponent and 20 of the 52 mantissa bits
 // (truncated, relative error below 2^-20); x below 2^-100 gives 0. Four integer operations.
 __device__ __forceinline__ float d2f_hi(double x) {
@@ -255,6 +269,25 @@ struct NodeQ {
   static constexpr int NQ = ND + 3;
   static constexpr int RHO = 0, V = 1, PP = ND + 1, PG = ND + 2;
 };
+
+// The same with 1/rho given (ir), for callers that share one reciprocal between two states.
+template <int ND, typename T>
+__device__ __forceinline__ bool node_quantities_ir(const double* uc, T ir, T gm1, T two_over_gm1, T* q) {
+  const T rho = to_flux<T>(uc[0]);
+  T ke = T(0);
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    const T m = to_flux<T>(uc[1 + j]);
+    const T v = m * ir;
+    q[1 + j] = v;
+    ke += m * v;
+  }
+  const T p = gm1 * (to_flux<T>(uc[ND + 1]) - T(0.5) * ke);
+  q[0] = rho;
+  q[NodeQ<ND>::PP] = p + p;
+  q[NodeQ<ND>::PG] = p * two_over_gm1;
+  return Num<T>::pos(rho) && Num<T>::pos(p);
+}
 
 template <int ND, typename T>
 __device__ __forceinline__ bool node_quantities(const double* uc, T gm1, T two_over_gm1, T* q, T* ir_out = nullptr) {

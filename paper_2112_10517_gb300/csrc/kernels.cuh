@@ -112,8 +112,15 @@ __device__ __forceinline__ void interface_node(const double* __restrict__ u, con
   }
   const T gm1 = gamma - T(1);
   T qL[NodeQ<ND>::NQ], qR[NodeQ<ND>::NQ], f[G::NV], irL, irR;
-  const bool ok = node_quantities<ND, T>(uL, gm1, T(2) / gm1, qL, &irL) &
-                  node_quantities<ND, T>(uR, gm1, T(2) / gm1, qR, &irR);
+  bool ok;
+  if constexpr (sizeof(T) == 8) {  // one Newton reciprocal for both densities: 1/rho_L = rho_R R, R = 1/(rho_L rho_R)
+    const T R = Num<T>::rcp(uL[0] * uR[0]);
+    irL = uR[0] * R;
+    irR = uL[0] * R;
+    ok = node_quantities_ir<ND, T>(uL, irL, gm1, T(2) / gm1, qL) & node_quantities_ir<ND, T>(uR, irR, gm1, T(2) / gm1, qR);
+  } else {
+    ok = node_quantities<ND, T>(uL, gm1, T(2) / gm1, qL, &irL) & node_quantities<ND, T>(uR, gm1, T(2) / gm1, qR, &irR);
+  }
   if (!ok) atomicOr(flag, 1);
   pair_flux8<ND, T, FLUX>(qL, qR, m2, f);  // f(u_L, u_R, m) / w_0
   if (LLF) {
@@ -124,10 +131,19 @@ __device__ __forceinline__ void interface_node(const double* __restrict__ u, con
       vnL += qL[1 + j] * m[j];
       vnR += qR[1 + j] * m[j];
     }
-    // c |m| = sqrt(gamma p |m|^2 / rho) with p = pp/2: one root per side
+    // c |m| = sqrt(gamma p |m|^2 / rho) with p = pp/2: one root per side (FP64: to about 46 bits, sqrt_wave_f64)
     const T hgm = T(0.5) * gamma * mm;
-    const T lamL = Num<T>::abs(vnL) + Num<T>::sqrt(hgm * qL[NodeQ<ND>::PP] * irL);
-    const T lamR = Num<T>::abs(vnR) + Num<T>::sqrt(hgm * qR[NodeQ<ND>::PP] * irR);
+    const T aL = hgm * qL[NodeQ<ND>::PP] * irL, aR = hgm * qR[NodeQ<ND>::PP] * irR;
+    T cL, cR;
+    if constexpr (sizeof(T) == 8) {
+      cL = sqrt_wave_f64(aL);
+      cR = sqrt_wave_f64(aR);
+    } else {
+      cL = Num<T>::sqrt(aL);
+      cR = Num<T>::sqrt(aR);
+    }
+    const T lamL = Num<T>::abs(vnL) + cL;
+    const T lamR = Num<T>::abs(vnR) + cR;
     const T lam4 = T(4.0 * kLift8) * Num<T>::maxnn(lamL, lamR);  // (lambda / 2) / w_0
 #pragma unroll
     for (int c = 0; c < G::NV; ++c) {
@@ -497,19 +513,19 @@ __device__ __forceinline__ void volume_tile(const double* u, const T* __restrict
         const int so = (el * G::NV + c) * G::NDOF + i;
         stage_update_w<EPI>(epi, off + (size_t)c * G::NDOF, (double)tot[c], w1, w2, s_eu[so], s_ey[so]);
       }
-      continue;
-    }
+    } else {
 #pragma unroll
-    for (int c = 0; c < G::NV; ++c) {
-      const size_t o = off + (size_t)c * G::NDOF;
-      const int so = (el * G::NV + c) * G::NDOF + i;  // same value, prefetched into shared memory
-      // FP64: k = -(1/J) tot in FP64. FP32 mode: the scaling in FP32 and an exact integer-pipe widening, so the
-      // FP64 pipe only carries the RK accumulation below.
-      const double k = sizeof(T) == 8 ? sj * (double)tot[c] : f2d_int((float)(sjT * tot[c]));
-      if (EPI == EPI_STORE)
-        du[o] = k;
-      else
-        stage_update<EPI>(epi, o, k, s_eu[so], s_ey[so]);
+      for (int c = 0; c < G::NV; ++c) {
+        const size_t o = off + (size_t)c * G::NDOF;
+        const int so = (el * G::NV + c) * G::NDOF + i;  // same value, prefetched into shared memory
+        // FP64: k = -(1/J) tot in FP64. FP32 mode: the scaling in FP32 and an exact integer-pipe widening, so the
+        // FP64 pipe only carries the RK accumulation below.
+        const double k = sizeof(T) == 8 ? sj * (double)tot[c] : f2d_int((float)(sjT * tot[c]));
+        if (EPI == EPI_STORE)
+          du[o] = k;
+        else
+          stage_update<EPI>(epi, o, k, s_eu[so], s_ey[so]);
+      }
     }
   }
 }

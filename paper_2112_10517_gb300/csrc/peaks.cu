@@ -151,6 +151,20 @@ __global__ void sqrt_kernel(long long n, const double* x, double* own, double* r
 
 extern "C" {
 
+__global__ void sqrt_wave_kernel(long long n, const double* x, double* out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[i] = dgk::sqrt_wave_f64(x[i]);
+}
+
+int dgpk_eval_sqrt_wave(long long n, const double* x, double* out) {
+  if (n <= 0) return 0;
+  sqrt_wave_kernel<<<(unsigned)((n + 255) / 256), 256>>>(n, x, out);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return (int)e;
+}
+
 // Self-test of the RHS kernels' FP64 square root against CUDA's sqrt: own/ref = sqrt_f64(x[i]) / sqrt(x[i]).
 int dgpk_eval_sqrt(long long n, const double* x, double* own, double* ref) {
   if (n <= 0) return 0;

@@ -303,18 +303,18 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, 
           stage_update_w<EPI>(epi, off + (size_t)c * G::NDOF, (double)tot[c], w1, w2, s_eu[so],
                               need_y ? s_ey[so] : 0.0);
         }
-        continue;
-      }
+      } else {
 #pragma unroll
-      for (int c = 0; c < G::NV; ++c) {
-        const size_t o = off + (size_t)c * G::NDOF;
-        const int so = (el * G::NV + c) * G::NDOF + i;
-        // as in volume_tile: FP64 scaling, or the FP32 scaling and an exact integer-pipe widening
-        const double kv = sizeof(T) == 8 ? sj * (double)tot[c] : f2d_int((float)(sjT * tot[c]));
-        if (EPI == EPI_STORE)
-          du[o] = kv;
-        else
-          stage_update<EPI>(epi, o, kv, s_eu[so], need_y ? s_ey[so] : 0.0);
+        for (int c = 0; c < G::NV; ++c) {
+          const size_t o = off + (size_t)c * G::NDOF;
+          const int so = (el * G::NV + c) * G::NDOF + i;
+          // as in volume_tile: FP64 scaling, or the FP32 scaling and an exact integer-pipe widening
+          const double kv = sizeof(T) == 8 ? sj * (double)tot[c] : f2d_int((float)(sjT * tot[c]));
+          if (EPI == EPI_STORE)
+            du[o] = kv;
+          else
+            stage_update<EPI>(epi, o, kv, s_eu[so], need_y ? s_ey[so] : 0.0);
+        }
       }
     }
     if (tid == 0 && tn < ntiles) s_ok[0] = mbar_wait_bounded(&bars[0], par ^ 1u) ? 1 : 0;
