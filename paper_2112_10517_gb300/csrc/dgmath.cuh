@@ -222,9 +222,11 @@ __device__ __forceinline__ T series_inner(T u, float c2, float c3) {
     return c2 + u * c3;
 }
 
-// state value (FP64 in memory) in the flux precision T
+// state value (FP64 in memory) in the flux precision T; a float is already in the FP32 flux precision
 template <typename T>
 __device__ __forceinline__ T to_flux(double x);
+template <typename T>
+__device__ __forceinline__ T to_flux(float x) { return (T)x; }
 template <>
 __device__ __forceinline__ double to_flux<double>(double x) { return x; }
 template <>
@@ -270,9 +272,10 @@ struct NodeQ {
   static constexpr int RHO = 0, V = 1, PP = ND + 1, PG = ND + 2;
 };
 
-// The same with 1/rho given (ir), for callers that share one reciprocal between two states.
-template <int ND, typename T>
-__device__ __forceinline__ bool node_quantities_ir(const double* uc, T ir, T gm1, T two_over_gm1, T* q) {
+// The same with 1/rho given (ir), for callers that share one reciprocal between two states; uc is the state in
+// FP64 (U = double) or already in the flux precision (U = T).
+template <int ND, typename T, typename U>
+__device__ __forceinline__ bool node_quantities_ir(const U* uc, T ir, T gm1, T two_over_gm1, T* q) {
   const T rho = to_flux<T>(uc[0]);
   T ke = T(0);
 #pragma unroll

@@ -105,22 +105,31 @@ __device__ __forceinline__ void interface_node(const double* __restrict__ u, con
   // the pair flux takes 2 m and returns 8 f: with 2 m scaled by lift8 = N(N-1)/16 the result is f / w_0
   constexpr double kLift8 = N * (N - 1) / 16.0;
   T m[ND], m2[ND];
+  const T jn = var.cart ? to_flux<T>(cart_jn(var, n)) : T(0);  // (integer-pipe conversion in FP32 mode)
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
-    m[j] = var.cart ? (j == n ? (T)cart_jn(var, n) : T(0)) : Ja[(((size_t)e * ND + n) * ND + j) * G::NDOF + nodeL];
+    m[j] = var.cart ? (j == n ? jn : T(0)) : Ja[(((size_t)e * ND + n) * ND + j) * G::NDOF + nodeL];
     m2[j] = m[j] * T(2.0 * kLift8);
   }
   const T gm1 = gamma - T(1);
-  T qL[NodeQ<ND>::NQ], qR[NodeQ<ND>::NQ], f[G::NV], irL, irR;
-  bool ok;
-  if constexpr (sizeof(T) == 8) {  // one Newton reciprocal for both densities: 1/rho_L = rho_R R, R = 1/(rho_L rho_R)
-    const T R = Num<T>::rcp(uL[0] * uR[0]);
-    irL = uR[0] * R;
-    irR = uL[0] * R;
-    ok = node_quantities_ir<ND, T>(uL, irL, gm1, T(2) / gm1, qL) & node_quantities_ir<ND, T>(uR, irR, gm1, T(2) / gm1, qR);
-  } else {
-    ok = node_quantities<ND, T>(uL, gm1, T(2) / gm1, qL, &irL) & node_quantities<ND, T>(uR, gm1, T(2) / gm1, qR, &irR);
+  // the states in the flux precision, converted once (FP32 mode: also the LLF jump below)
+  T uLt[G::NV], uRt[G::NV];
+#pragma unroll
+  for (int c = 0; c < G::NV; ++c) {
+    uLt[c] = to_flux<T>(uL[c]);
+    uRt[c] = to_flux<T>(uR[c]);
   }
+  T qL[NodeQ<ND>::NQ], qR[NodeQ<ND>::NQ], f[G::NV], irL, irR;
+  if constexpr (sizeof(T) == 8) {  // one Newton reciprocal for both densities: 1/rho_L = rho_R R, R = 1/(rho_L rho_R)
+    const T R = Num<T>::rcp(uLt[0] * uRt[0]);
+    irL = uRt[0] * R;
+    irR = uLt[0] * R;
+  } else {
+    irL = Num<T>::rcp(uLt[0]);
+    irR = Num<T>::rcp(uRt[0]);
+  }
+  const bool ok = node_quantities_ir<ND, T>(uLt, irL, gm1, T(2) / gm1, qL) &
+                  node_quantities_ir<ND, T>(uRt, irR, gm1, T(2) / gm1, qR);
   if (!ok) atomicOr(flag, 1);
   pair_flux8<ND, T, FLUX>(qL, qR, m2, f);  // f(u_L, u_R, m) / w_0
   if (LLF) {
@@ -148,7 +157,7 @@ __device__ __forceinline__ void interface_node(const double* __restrict__ u, con
 #pragma unroll
     for (int c = 0; c < G::NV; ++c) {
       // FP64: the jump in FP64; FP32 mode: both states rounded to FP32 first (no FP64 arithmetic)
-      const T jump = sizeof(T) == 8 ? (T)(uR[c] - uL[c]) : to_flux<T>(uR[c]) - to_flux<T>(uL[c]);
+      const T jump = uRt[c] - uLt[c];
       f[c] -= lam4 * jump;
     }
   }
@@ -450,7 +459,7 @@ __device__ __forceinline__ void volume_tile(const double* u, const T* __restrict
     const T* sj = s_ja + (el * ND + n) * ND * G::NDOF + base;
     const T* sl = s_log + el * 2 * G::NDOF + base;
     T* sa = s_acc + (el * ND + n) * G::NV * G::NDOF + base;
-    const T n2n = T(2) * (T)cart_jn(var, n);
+    const T n2n = T(2) * to_flux<T>(cart_jn(var, n));
     if constexpr (LMK == LM_SHARED_RCP) {
       switch (var.flux * 2 + var.cart) {
         case 0: line_pairs<ND, N, T, 0, false>(sp, sj, sl, st, n, n2n, op, sa); break;

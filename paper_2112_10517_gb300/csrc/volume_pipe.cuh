@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, 
       T* sa = s_acc + (el * ND + n) * G::NV * G::NDOF + lb;
       const T* fu = s_fc + ((1 * ND + n) * EPB + el) * kFaceT + l;
       const T* fl = s_fc + ((0 * ND + n) * EPB + el) * kFaceT + l;
-      const T n2n = T(2) * (T)cart_jn(var, n);
+      const T n2n = T(2) * to_flux<T>(cart_jn(var, n));
       switch (var.flux * 2 + var.cart) {
         case 0: line_pairs<ND, N, T, 0, false>(sp, sj, nullptr, st, n, n2n, op, sa, fu, fl); break;
         case 1: line_pairs<ND, N, T, 0, true>(sp, sj, nullptr, st, n, n2n, op, sa, fu, fl); break;
