@@ -463,21 +463,26 @@ def run_variants(args, dev):
 def run_staging(args, dev):
     """The RK4 step (dg_step, fused stage update) with the two ways the volume kernel stages a tile: bulk
     asynchronous copies that overlap the computation of a persistent CTA's tiles (pipelined) and direct loads by
-    one CTA per tile (direct), FP32 and FP64 flux arithmetic. Taylor-Green vortex, p = 3, 16^3 and 32^3; L2 flushed
-    before every timed step."""
+    one CTA per tile (direct), FP32 and FP64 flux arithmetic. Taylor-Green vortex, p = 3 at 16^3 and 32^3, and
+    p = 1, 5, 7 at about 2M DOF; L2 flushed before every timed step."""
     import torch
     from paper_2112_10517_gb300 import dg
     lo, hi = [-math.pi] * 3, [math.pi] * 3
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     out = {}
-    for precision, nelem in (("fp32", NELEM), ("fp32", NELEM_LARGE), ("fp64", NELEM), ("fp64", NELEM_LARGE)):
+    # (precision, p, elements per direction): p = 3 on the bench meshes, and the other odd degrees (even node
+    # counts, the ones the pipelined kernel serves) at about 2M DOF
+    cases = [("fp32", 3, NELEM[0]), ("fp32", 3, NELEM_LARGE[0]), ("fp64", 3, NELEM[0]), ("fp64", 3, NELEM_LARGE[0]),
+             ("fp32", 1, 64), ("fp32", 5, 18), ("fp32", 7, 16), ("fp64", 1, 64), ("fp64", 5, 18), ("fp64", 7, 16)]
+    for precision, p, ne in cases:
+        nelem = [ne] * 3
         for staging in ("pipelined", "direct"):
-            ctx = dg.DG(3, nelem, POLYDEG, lo=lo, hi=hi, mapping="sine", amp=AMP, surface="llf", precision=precision,
+            ctx = dg.DG(3, nelem, p, lo=lo, hi=hi, mapping="sine", amp=AMP, surface="llf", precision=precision,
                         staging=staging)
             u = torch.from_numpy(make_state(ctx)).to(dev)
             scratch = torch.empty((2,) + ctx.shape, dtype=torch.float64, device=dev)
-            dt = 0.5 * (2 * math.pi / nelem[0]) / (POLYDEG + 1) ** 2 / (1.0 + 1.0 / MACH)
+            dt = 0.5 * (2 * math.pi / ne) / (p + 1) ** 2 / (1.0 + 1.0 / MACH)
             for _ in range(args.warmup):
                 ctx.step(u, dt, dg.DG_RK4_CLASSIC, scratch=scratch)
             torch.cuda.synchronize()
@@ -495,11 +500,12 @@ def run_staging(args, dev):
             if ctx.check_status() != dg.DG_OK:
                 raise RuntimeError("non-physical state or wait timeout in the staging runs")
             ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-            out["%s_%d_%s" % (precision, nelem[0], staging)] = {
-                "pid_ns": whole_job_pid(ms, ctx.ndofs, 1), "volume_ms": vol_ms / max(vol_n, 1)}
+            key = "%s_%d_%s" % (precision, ne, staging) if p == POLYDEG else "%s_p%d_%d_%s" % (precision, p, ne, staging)
+            out[key] = {"pid_ns": whole_job_pid(ms, ctx.ndofs, 1), "volume_ms": vol_ms / max(vol_n, 1)}
             del ctx, u, scratch
-    out["workload"] = ("dg_step (RK4) on the Taylor-Green vortex, p = 3, sine-perturbed mesh, 16^3 and 32^3 elements, "
-                       "FP32 and FP64 flux arithmetic; volume_ms = the volume kernel's event time per launch")
+    out["workload"] = ("dg_step (RK4) on the Taylor-Green vortex, sine-perturbed mesh: p = 3 at 16^3 and 32^3 elements "
+                       "(keys fp32_16 ...), p = 1 at 64^3, p = 5 at 18^3, p = 7 at 16^3 (keys fp32_p7_16 ...); FP32 and "
+                       "FP64 flux arithmetic; volume_ms = the volume kernel's event time per launch")
     return out
 
 

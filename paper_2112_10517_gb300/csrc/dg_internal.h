@@ -59,7 +59,7 @@ struct Variant {
   int flux;      // DG_VOL_RANOCHA or DG_VOL_SHIMA (volume and surface)
   int cart;      // 1: constant diagonal metrics from jn/invJ, the metric arrays are not read
   int lm;        // log-mean variant of the volume terms (LM_* in dgmath.cuh; Ranocha's flux only)
-  int pipe;      // FP32 volume kernel with bulk asynchronous tile copies (where supported): 0 never, 1 on meshes
+  int pipe;      // volume kernel with bulk asynchronous tile copies (where supported): 0 never, 1 on meshes
                  // with enough tiles per resident CTA, 2 always
   double jn[3];  // Ja^n_n of a Cartesian mesh
   double invJ;   // 1/J of a Cartesian mesh

@@ -27,9 +27,10 @@ constexpr int elems_per_block() {
 }
 
 // Threads per CTA of the pipelined kernel (FP32, FP64), and the fewest tiles per resident CTA for which
-// DG_STAGING_AUTO uses it (compile-time tuning parameters, as above). With one tile per CTA nothing overlaps;
-// measured at p = 3 on the RK4 step: 16^3 (2.2 tiles per CTA in FP32, 3.4 in FP64) 7 % and 3 % faster than the
-// per-tile kernel, 32^3 26 % and 3 % faster.
+// DG_STAGING_AUTO uses it (compile-time tuning parameters, as above). With one tile per CTA nothing overlaps.
+// Measured on the RK4 step (volume kernel, pipelined vs per-tile): p = 3 at 16^3 (2.2 tiles per CTA in FP32, 3.4 in
+// FP64) -15 % / -10 %, at 32^3 -34 % / -9 %; at about 2M DOF p = 1 -13 % / -14 %, p = 5 -27 % / -6 %, p = 7 0 % /
+// -11 %.
 #ifndef DG_VOLUME_PIPE_TARGET_THREADS
 #define DG_VOLUME_PIPE_TARGET_THREADS 96
 #endif
@@ -62,8 +63,7 @@ template <int ND, int N, typename T, int EPI, int LMK>
 cudaError_t launch_volume_pipe(MeshDims md, const double* u, const T* Ja, const double* invJ, const T* face,
                                double* du, double gamma, int* flag, cudaStream_t s, const Epilogue& epi,
                                const Variant& var) {
-  // FP64: p <= 3 (larger elements run one per CTA, where the per-tile kernel keeps more registers)
-  if constexpr (N % 2 == 0 && LMK == LM_SHARED_RCP && (sizeof(T) == 4 || N <= 4)) {
+  if constexpr (N % 2 == 0 && LMK == LM_SHARED_RCP) {
     constexpr int TPE = Geo<ND, N>::TPE;
     constexpr int target = sizeof(T) == 8 ? DG_VOLUME_PIPE_TARGET_THREADS_F64 : DG_VOLUME_PIPE_TARGET_THREADS;
     constexpr int EPB = TPE >= target ? 1 : target / TPE;

@@ -134,8 +134,8 @@ class DG:
     means of Ranocha's flux (Sec. 3.1, 7.2; see dg_opts in include/dg.h); the defaults are the fastest.
     nodes: "lgl" (flux-differencing LGL-DGSEM) or "gauss" (Legendre-Gauss collocation with entropy projection,
     Sec. 6; affine meshes, FP64, Ranocha's flux).
-    staging: "pipelined" (the FP32 volume kernel copies tiles with bulk asynchronous copies that overlap
-    computation, where supported), "direct" (one CTA per tile, loads by its threads) or "auto" (pipelined on meshes
+    staging: "pipelined" (the volume kernel copies tiles with bulk asynchronous copies that overlap computation,
+    for odd degrees), "direct" (one CTA per tile, loads by its threads) or "auto" (pipelined on meshes
     with enough tiles per CTA); the same values either way.
     """
 

@@ -60,7 +60,7 @@ CASES = [
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 @pytest.mark.parametrize("nd,nelem,p,mapping,flux,ic", CASES)
 def test_both_stagings_match_oracle(dgmod, precision, nd, nelem, p, mapping, flux, ic):
-    # FP64: the pipelined kernel serves p <= 3 (the others fall back to the per-tile kernel)
+    # the pipelined kernel serves odd p (even node counts); even p falls back to the per-tile kernel
     sc = Scenario(nd, nelem, p, mapping=mapping, ic=ic, llf=True, seed=600 + 10 * nd + p, flux=flux)
     ref, scale = sc.du_ref(), sc.du_scale()
     tol = TOL32 if precision == "fp32" else TOL64
