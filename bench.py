@@ -830,7 +830,7 @@ def main():
             "flux_and_geometry_variants": variants,
             "logmean_ablation": ablation,
             "gauss_collocation": gauss,
-            "fp32_tile_staging": staging,
+            "tile_staging": staging,
             "alu_peaks_measured_tflops": {k: (v / 1e12 if v else None) for k, v in peaks_alu.items()},
         }
         print(json.dumps(line), flush=True)
