@@ -137,6 +137,7 @@ struct dg_ctx {
   cudaStream_t last_stream;
   // profiling
   int prof_on;
+  unsigned prof_mask;    // kernels timed while profiling is on (bit k: kernel id k)
   cudaEvent_t* prof_ev;  // pairs
   int prof_cap, prof_n[dgk::KID_COUNT];
   int* prof_kid;

@@ -6,6 +6,8 @@ import math
 import numpy as np
 import pytest
 
+from cases import Scenario
+
 pytestmark = pytest.mark.gpu
 
 
@@ -76,3 +78,28 @@ def test_rhs_graph_replay_and_flag(dgmod):
     torch.cuda.synchronize()
     assert ctx.check_status() == dgmod.DG_ERR_NONPHYSICAL
     assert ctx.check_status() == dgmod.DG_OK
+
+
+def test_profiling_counts_the_selected_kernels_only(dgmod):
+    # dg_profile_enable times every kernel; dg_profile_enable_kernels only those of its mask (the bench's timed
+    # region carries events around the volume kernel alone); every launch is counted either way
+    import torch
+    sc = Scenario(3, [3, 2, 3], 3, mapping="sine", ic="smooth", llf=True, seed=710)
+    ctx = dgmod.DG(**sc.dg_kwargs())
+    u = torch.from_numpy(sc.u).cuda()
+    du = torch.empty_like(u)
+    n0 = ctx.launch_count()
+    ctx.profile(True)
+    for _ in range(3):
+        ctx.rhs(u, du)
+    assert ctx.profile_read(dgmod.KERNEL_VOLUME)[1] == 3 and ctx.profile_read(dgmod.KERNEL_INTERFACE)[1] == 3
+    ctx.profile(True, kernels=[dgmod.KERNEL_VOLUME])
+    for _ in range(2):
+        ctx.rhs(u, du)
+    vol_ms, vol_n = ctx.profile_read(dgmod.KERNEL_VOLUME)
+    assert vol_n == 2 and vol_ms > 0.0
+    assert ctx.profile_read(dgmod.KERNEL_INTERFACE)[1] == 0
+    ctx.profile(False)
+    ctx.rhs(u, du)
+    assert ctx.profile_read(dgmod.KERNEL_VOLUME)[1] == 0
+    assert ctx.launch_count() - n0 == 12
