@@ -54,6 +54,10 @@ CASES = [
     (2, [4, 3], 3, "sine", "shima", "rough"),
     (2, [3, 3], 5, "sine", "ranocha", "rough"),
     (2, [2, 3], 7, "sine", "ranocha", "rough"),
+    (3, [1, 3, 2], 1, "sine", "ranocha", "rough"),   # one element along x: every x-neighbour is the element itself
+    (3, [3, 1, 1], 3, "affine", "ranocha", "rough"),  # one element along y and z
+    (2, [1, 5], 3, "affine", "shima", "random"),
+    (3, [1, 1, 1], 5, "sine", "ranocha", "rough"),    # a single element, its own neighbour in every direction
 ]
 
 
