@@ -482,17 +482,17 @@ def run_staging(args, dev):
     """The RK4 step (dg_step, fused stage update) with the two ways the volume kernel stages a tile: bulk
     asynchronous copies that overlap the computation of a persistent CTA's tiles (pipelined) and direct loads by
     one CTA per tile (direct), FP32 and FP64 flux arithmetic. Taylor-Green vortex, p = 3 at 16^3 and 32^3, and
-    p = 1, 5, 7 at about 2M DOF; L2 flushed before every timed step."""
+    p = 1, 2, 4, 5, 6, 7 at about 2M DOF; L2 flushed before every timed step."""
     import torch
     from paper_2112_10517_gb300 import dg
     lo, hi = [-math.pi] * 3, [math.pi] * 3
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     out = {}
-    # (precision, p, elements per direction): p = 3 on the bench meshes, and the other odd degrees (even node
-    # counts, the ones the pipelined kernel serves) at about 2M DOF
+    # (precision, p, elements per direction): p = 3 on the bench meshes, and p = 1, 2, 4, 5, 6, 7 at about 2M DOF
     cases = [("fp32", 3, NELEM[0]), ("fp32", 3, NELEM_LARGE[0]), ("fp64", 3, NELEM[0]), ("fp64", 3, NELEM_LARGE[0]),
-             ("fp32", 1, 64), ("fp32", 5, 18), ("fp32", 7, 16), ("fp64", 1, 64), ("fp64", 5, 18), ("fp64", 7, 16)]
+             ("fp32", 1, 64), ("fp32", 5, 18), ("fp32", 7, 16), ("fp64", 1, 64), ("fp64", 5, 18), ("fp64", 7, 16),
+             ("fp32", 2, 43), ("fp32", 4, 26), ("fp32", 6, 18), ("fp64", 2, 43), ("fp64", 4, 26), ("fp64", 6, 18)]
     for precision, p, ne in cases:
         nelem = [ne] * 3
         for staging in ("pipelined", "direct"):
@@ -522,7 +522,8 @@ def run_staging(args, dev):
             out[key] = {"pid_ns": whole_job_pid(ms, ctx.ndofs, 1), "volume_ms": vol_ms / max(vol_n, 1)}
             del ctx, u, scratch
     out["workload"] = ("dg_step (RK4) on the Taylor-Green vortex, sine-perturbed mesh: p = 3 at 16^3 and 32^3 elements "
-                       "(keys fp32_16 ...), p = 1 at 64^3, p = 5 at 18^3, p = 7 at 16^3 (keys fp32_p7_16 ...); FP32 and "
+                       "(keys fp32_16 ...), p = 1 at 64^3, 2 at 43^3, 4 at 26^3, 5 at 18^3, 6 at 18^3, 7 at 16^3 (keys "
+                       "fp32_p7_16 ...); FP32 and "
                        "FP64 flux arithmetic; volume_ms = the volume kernel's event time per launch")
     return out
 

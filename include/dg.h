@@ -113,13 +113,14 @@ typedef struct dg_metrics {
    dg_vjp and dg_batch_* do not support it. Its face states need the entropy variables interpolated to the faces
    to stay admissible (rho/p > 0); otherwise the non-physical flag is raised.
    staging: how the volume kernel of dg_rhs / dg_step brings an element tile's data into shared memory.
-     DG_STAGING_PIPELINED  an even number of nodes per line (odd polydeg), the default log mean and
-                           16-byte-aligned state arrays: persistent CTAs that copy each tile's data (stage input,
-                           metric terms, 1/J, Runge-Kutta operands, interface fluxes) with bulk asynchronous copies,
-                           each group for the next tile as soon as the current tile has read it, so that the copies
-                           overlap computation; otherwise as DG_STAGING_DIRECT.
-     DG_STAGING_AUTO       as DG_STAGING_PIPELINED on meshes with at least 4 tiles per resident CTA (the first
-                           tile's copies are not overlapped), else as DG_STAGING_DIRECT.
+     DG_STAGING_PIPELINED  the default log mean: persistent CTAs that copy each tile's data (stage input, metric
+                           terms, 1/J, Runge-Kutta operands, interface fluxes) with asynchronous copies, each group
+                           for the next tile as soon as the current tile has read it, so that the copies overlap
+                           computation (bulk copies for an even number of nodes per line, which then needs
+                           16-byte-aligned state arrays; per-thread copies otherwise); else as DG_STAGING_DIRECT.
+     DG_STAGING_AUTO       as DG_STAGING_PIPELINED on meshes with at least 2 tiles per resident CTA (the first
+                           tile's copies are not overlapped), except DG_FP32 at polydeg 2 (measured slower); else
+                           as DG_STAGING_DIRECT.
      DG_STAGING_DIRECT     one CTA per tile, loads issued by its threads.
    All compute the same values (the same arithmetic in the same order). A pipelined kernel whose wait for its own
    copies runs out (bounded; it cannot under normal operation) skips the rest of its tiles and raises the flag that

@@ -28,9 +28,9 @@ constexpr int elems_per_block() {
 
 // Threads per CTA of the pipelined kernel (FP32, FP64), and the fewest tiles per resident CTA for which
 // DG_STAGING_AUTO uses it (compile-time tuning parameters, as above). With one tile per CTA nothing overlaps.
-// Measured on the RK4 step (volume kernel, pipelined vs per-tile): p = 3 at 16^3 (2.2 tiles per CTA in FP32, 3.4 in
-// FP64) -15 % / -10 %, at 32^3 -34 % / -9 %; at about 2M DOF p = 1 -13 % / -14 %, p = 5 -27 % / -6 %, p = 7 0 % /
-// -11 %.
+// Measured on the RK4 step (volume kernel, pipelined vs per-tile, FP32 / FP64): p = 3 at 16^3 (2.2 tiles per CTA in
+// FP32, 3.4 in FP64) -15 % / -10 %, at 32^3 -34 % / -9 %; at about 2M DOF p = 1 -13 % / -14 %, p = 2 +25 % / -15 %,
+// p = 4 -16 % / -7 %, p = 5 -27 % / -6 %, p = 6 -8 % / -9 %, p = 7 0 % / -11 %.
 #ifndef DG_VOLUME_PIPE_TARGET_THREADS
 #define DG_VOLUME_PIPE_TARGET_THREADS 96
 #endif
@@ -56,14 +56,15 @@ OpTable<N, T> op_table() {
 
 inline bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
-// The pipelined kernel (volume_pipe.cuh) where it applies: FP32, even N, default log mean, 16-byte-aligned arrays,
-// shared memory within the opt-in limit, and (var.pipe == 1) enough tiles per resident CTA, or (var.pipe == 2)
-// any mesh. Returns cudaErrorNotSupported where it does not apply (the caller then launches the per-tile kernel).
+// The pipelined kernel (volume_pipe.cuh) where it applies: the default log mean, shared memory within the opt-in
+// limit, for even N 16-byte-aligned arrays (bulk copies), and (var.pipe == 1) enough tiles per resident CTA, or
+// (var.pipe == 2) any mesh. Returns cudaErrorNotSupported where it does not apply (the caller then launches the
+// per-tile kernel).
 template <int ND, int N, typename T, int EPI, int LMK>
 cudaError_t launch_volume_pipe(MeshDims md, const double* u, const T* Ja, const double* invJ, const T* face,
                                double* du, double gamma, int* flag, cudaStream_t s, const Epilogue& epi,
                                const Variant& var) {
-  if constexpr (N % 2 == 0 && LMK == LM_SHARED_RCP) {
+  if constexpr (LMK == LM_SHARED_RCP) {
     constexpr int TPE = Geo<ND, N>::TPE;
     constexpr int target = sizeof(T) == 8 ? DG_VOLUME_PIPE_TARGET_THREADS_F64 : DG_VOLUME_PIPE_TARGET_THREADS;
     constexpr int EPB = TPE >= target ? 1 : target / TPE;
@@ -71,9 +72,11 @@ cudaError_t launch_volume_pipe(MeshDims md, const double* u, const T* Ja, const 
     constexpr size_t smem = PipeSmem<ND, N, T>::bytes(EPB, fused);
     if constexpr (smem <= 227 * 1024) {
       if (!var.pipe) return cudaErrorNotSupported;
-      bool ok = aligned16(u) && aligned16(face) && (var.cart || (aligned16(Ja) && aligned16(invJ)));
-      if (fused) ok = ok && aligned16(epi.u) && aligned16(EPI == EPI_RK4 ? epi.acc : epi.y);
-      if (!ok) return cudaErrorNotSupported;
+      if constexpr (PipeSmem<ND, N, T>::kBulk) {  // bulk copies start on 16-byte boundaries
+        bool ok = aligned16(u) && aligned16(face) && (var.cart || (aligned16(Ja) && aligned16(invJ)));
+        if (fused) ok = ok && aligned16(epi.u) && aligned16(EPI == EPI_RK4 ? epi.acc : epi.y);
+        if (!ok) return cudaErrorNotSupported;
+      }
       auto kern = volume_pipe_kernel<ND, N, T, EPB, EPI>;
       static int ctas = 0;  // resident CTAs on the device (occupancy x SMs); computed once, with the opt-in
       if (ctas == 0) {
@@ -88,7 +91,10 @@ cudaError_t launch_volume_pipe(MeshDims md, const double* u, const T* Ja, const 
         ctas = occ * sms;
       }
       const int ntiles = (md.E + EPB - 1) / EPB;
-      if (var.pipe == 1 && (long long)ntiles < (long long)DG_VOLUME_PIPE_MIN_TILES_PER_CTA * ctas)
+      // auto: enough tiles per CTA, and not FP32 at p = 2 (3 elements of 27 threads per CTA, each thread issuing
+      // many small copies: measured 25 % slower than the per-tile kernel; every other degree and precision gains)
+      constexpr bool kAutoOk = !(sizeof(T) == 4 && N == 3);
+      if (var.pipe == 1 && (!kAutoOk || (long long)ntiles < (long long)DG_VOLUME_PIPE_MIN_TILES_PER_CTA * ctas))
         return cudaErrorNotSupported;
       const int grid = ntiles < ctas ? ntiles : ctas;
       kern<<<grid, EPB * TPE, smem, s>>>(u, Ja, invJ, face, du, md, op_table<N, T>(), (T)gamma, flag, epi, var,

@@ -9,10 +9,12 @@
 // number of resident CTAs, close to that of the per-tile kernel, while the loads overlap computation: the FP32
 // kernel is bound by their latency, the FP64 kernel by its FP64 pipe, which then also runs through phases A and C.
 //
-// Requirements (checked by the launcher): an even number of nodes per line (every element block of every array is
-// then a multiple of 16 bytes), 16-byte-aligned array pointers, the default log mean. Waits on the mbarriers are
-// bounded: on a timeout the CTA raises FLAG_WAIT_TIMEOUT, waits (bounded again) for its copies in flight and
-// returns.
+// With an even number of nodes per line every element block of every array is a multiple of 16 bytes, and thread
+// 0 moves each group with a few bulk copies (16-byte-aligned arrays, checked by the launcher). With an odd number
+// every thread copies part of the group with 4- or 8-byte asynchronous copies (cp.async), which the same
+// mbarrier tracks (cp.async.mbarrier.arrive, one arrival per thread). The default log mean only. Waits on the
+// mbarriers are bounded: on a timeout the CTA raises FLAG_WAIT_TIMEOUT, waits (bounded again, or for its own
+// copies) for the copies in flight and returns.
 #pragma once
 
 #include "kernels.cuh"
@@ -35,6 +37,17 @@ __device__ __forceinline__ void mbar_init_fence() {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                : "memory");
+}
+
+// 4-byte asynchronous copy (cp.async; the 8-byte form is cp_async8)
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
+}
+
+// the executing thread's cp.async copies issued so far arrive on `bar` once complete (the barrier's expected
+// count includes this thread)
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 // global -> shared bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned), completing on `bar`
@@ -74,10 +87,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
 //   IJ [EPB][NDOF] f64 (1/J; not on Cartesian meshes), EU, EY [EPB][NV][NDOF] f64
 //   (fused stage update: u, and acc (RK4) / K (CK45) after stage 0)              mbarrier 2
 // then the tile scratch, node quantities [EPB][NQ][NDOF] T and per-direction sums [EPB][ND][NV][NDOF] T, then the
-// three mbarriers. Every region is a multiple of 16 bytes for even N.
+// three mbarriers. Each region starts on a 16-byte boundary (for even N every element block is a multiple of 16
+// bytes already).
 template <int ND, int N, typename T>
 struct PipeSmem {
   using G = Geo<ND, N>;
+  static constexpr bool kBulk = N % 2 == 0;  // bulk (TMA) copies; else per-thread cp.async
+  __host__ __device__ static constexpr size_t r16(size_t x) { return (x + 15) / 16 * 16; }
   static constexpr size_t kIn = (size_t)G::NV * G::NDOF * sizeof(double);
   static constexpr size_t kJa = (size_t)ND * ND * G::NDOF * sizeof(T);
   static constexpr size_t kInvJ = (size_t)G::NDOF * sizeof(double);
@@ -85,18 +101,16 @@ struct PipeSmem {
   static constexpr size_t kPrim = (size_t)NodeQ<ND>::NQ * G::NDOF * sizeof(T);
   static constexpr size_t kAcc = (size_t)ND * G::NV * G::NDOF * sizeof(T);
   // byte offsets of the regions for EPB elements
-  __host__ __device__ static constexpr size_t off_ja(int epb) { return (size_t)epb * kIn; }
-  __host__ __device__ static constexpr size_t off_ij(int epb) { return off_ja(epb) + (size_t)epb * kJa; }
-  __host__ __device__ static constexpr size_t off_eu(int epb) { return off_ij(epb) + (size_t)epb * kInvJ; }
-  __host__ __device__ static constexpr size_t off_ey(int epb, bool fused) { return off_eu(epb) + (fused ? epb * kIn : 0); }
-  __host__ __device__ static constexpr size_t off_fc(int epb, bool fused) { return off_ey(epb, fused) + (fused ? epb * kIn : 0); }
-  __host__ __device__ static constexpr size_t off_prim(int epb, bool fused) { return off_fc(epb, fused) + (size_t)2 * ND * epb * kFace; }
-  __host__ __device__ static constexpr size_t off_acc(int epb, bool fused) { return off_prim(epb, fused) + (size_t)epb * kPrim; }
-  __host__ __device__ static constexpr size_t off_bar(int epb, bool fused) { return off_acc(epb, fused) + (size_t)epb * kAcc; }
+  __host__ __device__ static constexpr size_t off_ja(int epb) { return r16((size_t)epb * kIn); }
+  __host__ __device__ static constexpr size_t off_ij(int epb) { return off_ja(epb) + r16((size_t)epb * kJa); }
+  __host__ __device__ static constexpr size_t off_eu(int epb) { return off_ij(epb) + r16((size_t)epb * kInvJ); }
+  __host__ __device__ static constexpr size_t off_ey(int epb, bool fused) { return off_eu(epb) + (fused ? r16(epb * kIn) : 0); }
+  __host__ __device__ static constexpr size_t off_fc(int epb, bool fused) { return off_ey(epb, fused) + (fused ? r16(epb * kIn) : 0); }
+  __host__ __device__ static constexpr size_t off_prim(int epb, bool fused) { return off_fc(epb, fused) + r16((size_t)2 * ND * epb * kFace); }
+  __host__ __device__ static constexpr size_t off_acc(int epb, bool fused) { return off_prim(epb, fused) + r16((size_t)epb * kPrim); }
+  __host__ __device__ static constexpr size_t off_bar(int epb, bool fused) { return off_acc(epb, fused) + r16((size_t)epb * kAcc); }
   __host__ __device__ static constexpr size_t bytes(int epb, bool fused) { return off_bar(epb, fused) + 32; }
-  static_assert(N % 2 == 0, "element blocks are multiples of 16 bytes only for an even number of nodes per line");
-  static_assert(kIn % 16 == 0 && kJa % 16 == 0 && kInvJ % 16 == 0 && kFace % 16 == 0 && kPrim % 16 == 0 &&
-                    kAcc % 16 == 0,
+  static_assert(!kBulk || (kIn % 16 == 0 && kJa % 16 == 0 && kInvJ % 16 == 0 && kFace % 16 == 0),
                 "bulk copies move multiples of 16 bytes");
 };
 
@@ -161,55 +175,75 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, 
   const double* gy = EPI == EPI_RK4 ? epi.acc : epi.y;
   int fill_in = 0, fill_ja = 0, fill_c = 0;  // thread 0: fills issued per mbarrier
 
-  // thread 0: the copies of one group for the tile t (byte count first, then the copies). Captures by value: a
-  // kernel parameter captured by reference would be copied to local memory.
+  // The copies of one group for the tile t: bulk mode, by thread 0 (byte count first, then the copies); cp.async
+  // mode, by every thread (its share of each array, then its arrival on the group's barrier). Captures by value:
+  // a kernel parameter captured by reference would be copied to local memory.
+  auto copy = [=](auto* dst, const auto* src, int count, uint64_t* bar) {  // count values of src's type
+    if constexpr (S::kBulk) {
+      bulk_g2s(dst, src, (unsigned)(count * sizeof(*src)), bar);
+    } else {
+      for (int w = tid; w < count; w += kThreads) {
+        if constexpr (sizeof(*src) == 8)
+          cp_async8(dst + w, src + w);
+        else
+          cp_async4(dst + w, src + w);
+      }
+    }
+  };
   auto issue_in = [=](int t) {
     const int e0 = t * EPB, nel = min(EPB, md.E - e0);
-    mbar_expect_tx(&bars[0], (unsigned)(nel * S::kIn));
-    bulk_g2s(s_in, in + (size_t)e0 * G::NV * G::NDOF, (unsigned)(nel * S::kIn), &bars[0]);
+    if constexpr (S::kBulk) mbar_expect_tx(&bars[0], (unsigned)(nel * S::kIn));
+    copy(s_in, in + (size_t)e0 * G::NV * G::NDOF, nel * G::NV * G::NDOF, &bars[0]);
+    if constexpr (!S::kBulk) cp_async_arrive(&bars[0]);
   };
   auto issue_ja = [=](int t) {  // metric terms (curvilinear meshes) and the faces' lifted fluxes
     const int e0 = t * EPB, nel = min(EPB, md.E - e0);
-    const unsigned nja = has_ja ? (unsigned)(nel * S::kJa) : 0u, nfc = (unsigned)(nel * S::kFace);
-    mbar_expect_tx(&bars[1], nja + 2u * ND * nfc);
-    if (has_ja) bulk_g2s(s_ja, Ja + (size_t)e0 * ND * ND * G::NDOF, nja, &bars[1]);
+    if constexpr (S::kBulk)
+      mbar_expect_tx(&bars[1], (has_ja ? (unsigned)(nel * S::kJa) : 0u) + 2u * ND * (unsigned)(nel * S::kFace));
+    if (has_ja) copy(s_ja, Ja + (size_t)e0 * ND * ND * G::NDOF, nel * ND * ND * G::NDOF, &bars[1]);
 #pragma unroll
     for (int n = 0; n < ND; ++n) {
       // the tile's own upper faces along n are consecutive in the face array; the lower neighbours' mostly are
       const T* fn = face + (size_t)n * md.E * kFaceT;
-      bulk_g2s(s_fc + ((1 * ND + n) * EPB) * kFaceT, fn + (size_t)e0 * kFaceT, nfc, &bars[1]);
+      copy(s_fc + ((1 * ND + n) * EPB) * kFaceT, fn + (size_t)e0 * kFaceT, nel * kFaceT, &bars[1]);
       if (lower_neighbors_consecutive(md, e0, nel, n)) {
-        bulk_g2s(s_fc + (n * EPB) * kFaceT, fn + (size_t)neighbor(md, e0, n, -1) * kFaceT, nfc, &bars[1]);
+        copy(s_fc + (n * EPB) * kFaceT, fn + (size_t)neighbor(md, e0, n, -1) * kFaceT, nel * kFaceT, &bars[1]);
       } else {
         for (int el = 0; el < nel; ++el)
-          bulk_g2s(s_fc + (n * EPB + el) * kFaceT, fn + (size_t)neighbor(md, e0 + el, n, -1) * kFaceT,
-                   (unsigned)S::kFace, &bars[1]);
+          copy(s_fc + (n * EPB + el) * kFaceT, fn + (size_t)neighbor(md, e0 + el, n, -1) * kFaceT, kFaceT,
+               &bars[1]);
       }
     }
+    if constexpr (!S::kBulk) cp_async_arrive(&bars[1]);
   };
   auto issue_c = [=](int t) {  // 1/J (curvilinear meshes) and the stage update's operands; may be empty
     const int e0 = t * EPB, nel = min(EPB, md.E - e0);
-    const unsigned nin = (unsigned)(nel * S::kIn);
-    const unsigned nij = has_ja ? (unsigned)(nel * S::kInvJ) : 0u;
-    mbar_expect_tx(&bars[2], nij + (kFused ? nin : 0u) + (need_y ? nin : 0u));
+    const int nin = nel * G::NV * G::NDOF;
+    if constexpr (S::kBulk)
+      mbar_expect_tx(&bars[2], (has_ja ? (unsigned)(nel * S::kInvJ) : 0u) + (kFused ? (unsigned)(nel * S::kIn) : 0u) +
+                                   (need_y ? (unsigned)(nel * S::kIn) : 0u));
     const size_t so = (size_t)e0 * G::NV * G::NDOF;
-    if (has_ja) bulk_g2s(s_ij, invJ + (size_t)e0 * G::NDOF, nij, &bars[2]);
-    if (kFused) bulk_g2s(s_eu, epi.u + so, nin, &bars[2]);
-    if (need_y) bulk_g2s(s_ey, gy + so, nin, &bars[2]);
+    if (has_ja) copy(s_ij, invJ + (size_t)e0 * G::NDOF, nel * G::NDOF, &bars[2]);
+    if (kFused) copy(s_eu, epi.u + so, nin, &bars[2]);
+    if (need_y) copy(s_ey, gy + so, nin, &bars[2]);
+    if constexpr (!S::kBulk) cp_async_arrive(&bars[2]);
   };
+  // the threads that issue copies: thread 0 in bulk mode, all in cp.async mode
+  const bool issuer = S::kBulk ? tid == 0 : true;
 
   int t = blockIdx.x;
   if (tid == 0) {
-    for (int j = 0; j < 3; ++j) mbar_init(&bars[j], 1);
+    for (int j = 0; j < 3; ++j) mbar_init(&bars[j], S::kBulk ? 1 : kThreads);
     mbar_init_fence();
-    if (t < ntiles) {
-      issue_in(t);
-      issue_ja(t);
-      issue_c(t);
-      fill_in = fill_ja = fill_c = 1;
-      s_ok[0] = mbar_wait_bounded(&bars[0], 0u) ? 1 : 0;
-    }
   }
+  __syncthreads();
+  if (issuer && t < ntiles) {
+    issue_in(t);
+    issue_ja(t);
+    issue_c(t);
+    fill_in = fill_ja = fill_c = 1;
+  }
+  if (tid == 0 && t < ntiles) s_ok[0] = mbar_wait_bounded(&bars[0], 0u) ? 1 : 0;
   __syncthreads();
   bool failed = false;
   for (int k = 0; t < ntiles; ++k, t += gridDim.x) {
@@ -243,7 +277,7 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, 
       break;
     }
     mbar_test(&bars[1], par);
-    if (tid == 0 && tn < ntiles) {  // the stage input has been read
+    if (issuer && tn < ntiles) {  // the stage input has been read
       issue_in(tn);
       ++fill_in;
     }
@@ -274,7 +308,7 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, 
       break;
     }
     mbar_test(&bars[2], par);
-    if (tid == 0 && tn < ntiles) {  // the metric terms and face fluxes have been read
+    if (issuer && tn < ntiles) {  // the metric terms and face fluxes have been read
       issue_ja(tn);
       ++fill_ja;
     }
@@ -319,16 +353,22 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, 
     }
     if (tid == 0 && tn < ntiles) s_ok[0] = mbar_wait_bounded(&bars[0], par ^ 1u) ? 1 : 0;
     __syncthreads();
-    if (tid == 0 && tn < ntiles) {  // the phase-C group has been read
+    if (issuer && tn < ntiles) {  // the phase-C group has been read
       issue_c(tn);
       ++fill_c;
     }
   }
-  if (failed && tid == 0) {  // a wait ran out: raise the flag, wait (bounded) for the copies in flight
-    atomicOr(flag, FLAG_WAIT_TIMEOUT);
-    mbar_drain(&bars[0], fill_in);
-    mbar_drain(&bars[1], fill_ja);
-    mbar_drain(&bars[2], fill_c);
+  if (failed) {  // a wait ran out: raise the flag, wait (bounded, or for the own copies) for the copies in flight
+    if (tid == 0) atomicOr(flag, FLAG_WAIT_TIMEOUT);
+    if constexpr (S::kBulk) {
+      if (tid == 0) {
+        mbar_drain(&bars[0], fill_in);
+        mbar_drain(&bars[1], fill_ja);
+        mbar_drain(&bars[2], fill_c);
+      }
+    } else {
+      cp_async_wait_all();
+    }
   }
 }
 

@@ -136,9 +136,9 @@ class DG:
     means of Ranocha's flux (Sec. 3.1, 7.2; see dg_opts in include/dg.h); the defaults are the fastest.
     nodes: "lgl" (flux-differencing LGL-DGSEM) or "gauss" (Legendre-Gauss collocation with entropy projection,
     Sec. 6; affine meshes, FP64, Ranocha's flux).
-    staging: "pipelined" (the volume kernel copies tiles with bulk asynchronous copies that overlap computation,
-    for odd degrees), "direct" (one CTA per tile, loads by its threads) or "auto" (pipelined on meshes
-    with enough tiles per CTA); the same values either way.
+    staging: "pipelined" (the volume kernel copies tiles with asynchronous copies that overlap computation),
+    "direct" (one CTA per tile, loads by its threads) or "auto" (pipelined on meshes with enough tiles per CTA,
+    except FP32 at p = 2); the same values either way.
     """
 
     def __init__(self, ndims: int, nelem, polydeg: int, lo=None, hi=None, mapping: str = "affine", amp: float = 0.0,

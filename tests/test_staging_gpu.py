@@ -1,7 +1,7 @@
-"""The two ways the FP32 volume kernel stages an element tile (dg_opts.staging): bulk asynchronous copies into
-shared memory that overlap the computation of a persistent CTA's tiles (DG_STAGING_PIPELINED; even node counts per
-line), and direct loads by one CTA per tile (DG_STAGING_DIRECT); DG_STAGING_AUTO picks the first on meshes with
-enough tiles per CTA. The pipelined kernel evaluates the same arithmetic in the same order, so it
+"""The two ways the volume kernel stages an element tile (dg_opts.staging): asynchronous copies into shared memory
+that overlap the computation of a persistent CTA's tiles (DG_STAGING_PIPELINED: bulk copies for even node counts
+per line, per-thread cp.async for odd ones), and direct loads by one CTA per tile (DG_STAGING_DIRECT);
+DG_STAGING_AUTO picks the first on meshes with enough tiles per CTA. The pipelined kernel evaluates the same arithmetic in the same order, so it
 must meet the FP32 parity bound against the oracle (4e-6 of the term magnitude) and agree with the direct kernel
 to rounding; the cases cover ragged last tiles, lower-neighbour faces that wrap around the periodic mesh (copied
 element by element), tiles that are smaller than the grid and grids that loop over a tile count several times
@@ -58,13 +58,19 @@ CASES = [
     (3, [3, 1, 1], 3, "affine", "ranocha", "rough"),  # one element along y and z
     (2, [1, 5], 3, "affine", "shima", "random"),
     (3, [1, 1, 1], 5, "sine", "ranocha", "rough"),    # a single element, its own neighbour in every direction
+    # odd node counts (even p): per-thread cp.async copies instead of bulk copies
+    (3, [3, 3, 2], 2, "sine", "ranocha", "rough"),
+    (3, [2, 3, 2], 4, "sine", "shima", "rough"),
+    (3, [2, 1, 2], 6, "affine", "ranocha", "rough"),
+    (2, [4, 3], 2, "sine", "ranocha", "rough"),
+    (2, [3, 2], 4, "affine", "ranocha", "random"),
+    (2, [2, 3], 6, "sine", "shima", "rough"),
 ]
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 @pytest.mark.parametrize("nd,nelem,p,mapping,flux,ic", CASES)
 def test_both_stagings_match_oracle(dgmod, precision, nd, nelem, p, mapping, flux, ic):
-    # the pipelined kernel serves odd p (even node counts); even p falls back to the per-tile kernel
     sc = Scenario(nd, nelem, p, mapping=mapping, ic=ic, llf=True, seed=600 + 10 * nd + p, flux=flux)
     ref, scale = sc.du_ref(), sc.du_scale()
     tol = TOL32 if precision == "fp32" else TOL64
@@ -79,7 +85,8 @@ def test_both_stagings_match_oracle(dgmod, precision, nd, nelem, p, mapping, flu
     assert np.all(term <= tol), term
 
 
-@pytest.mark.parametrize("nelem,p", [([32, 32, 32], 1), ([16, 16, 16], 3), ([8, 8, 8], 5)])
+@pytest.mark.parametrize("nelem,p", [([32, 32, 32], 1), ([16, 16, 16], 3), ([8, 8, 8], 5), ([16, 16, 16], 2),
+                                     ([8, 8, 8], 4)])
 def test_stagings_agree_on_many_tiles_per_cta(dgmod, nelem, p):
     # thousands of tiles: each persistent CTA loops several times, both stage buffers change parity twice or more
     # (the 16^3 case is also checked against the oracle, element by element, by the FP32 Taylor-Green parity test)
@@ -93,7 +100,7 @@ def test_stagings_agree_on_many_tiles_per_cta(dgmod, nelem, p):
     assert np.all(term <= TOL32), term
 
 
-@pytest.mark.parametrize("nelem,p", [([16, 16, 16], 3), ([16, 16, 16], 1)])
+@pytest.mark.parametrize("nelem,p", [([16, 16, 16], 3), ([16, 16, 16], 1), ([12, 12, 12], 2)])
 def test_fp64_stagings_agree_on_many_tiles_per_cta(dgmod, nelem, p):
     sc = Scenario(3, nelem, p, mapping="sine", ic="tgv", llf=True)
     a = rhs_with(dgmod, sc, "pipelined", precision="fp64")
