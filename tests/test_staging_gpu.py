@@ -163,6 +163,11 @@ def test_auto_selects_by_tiles_per_cta(dgmod):
     sc = Scenario(3, [32, 32, 32], 3, mapping="sine", ic="tgv", llf=True)
     auto, pipe = rhs_with(dgmod, sc, "auto"), rhs_with(dgmod, sc, "pipelined")
     assert np.array_equal(auto, pipe)
+    # FP32 at p = 2 stays on the per-tile kernel (measured faster there) even with many tiles; FP64 does not
+    sc = Scenario(3, [24, 24, 24], 2, mapping="sine", ic="tgv", llf=True)
+    assert np.array_equal(rhs_with(dgmod, sc, "auto"), rhs_with(dgmod, sc, "direct"))
+    assert np.array_equal(rhs_with(dgmod, sc, "auto", precision="fp64"),
+                          rhs_with(dgmod, sc, "pipelined", precision="fp64"))
 
 
 def test_device_wait_timeout_is_reported_and_the_context_recovers(dgmod):
