@@ -62,7 +62,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (debug runs)")
     ap.add_argument("--only", default="", help="comma-separated subset of fp64_16,fp32_16,fp64_32,fp32_32, "
-                    "variants, ablation, gauss, staging (profiling runs; prints one line per configuration instead of the "
+                    "variants, ablation, gauss, staging, batch (profiling runs; prints one line per configuration instead of the "
                     "contract line)")
     return ap.parse_args()
 
@@ -797,6 +797,8 @@ def main():
             print(json.dumps({"configuration": "gauss", "result": run_gauss(args, dev)}), flush=True)
         if "staging" in only:
             print(json.dumps({"configuration": "staging", "result": run_staging(args, dev)}), flush=True)
+        if "batch" in only:
+            print(json.dumps({"configuration": "batch", "result": run_batch(args, dev)}), flush=True)
     elif rank == 0:
         r64, r32 = results["fp64_16"], results["fp32_16"]
         b64, b32 = results["fp64_32"], results["fp32_32"]

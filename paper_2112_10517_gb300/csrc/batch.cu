@@ -6,7 +6,10 @@
 //      in the prefix sums of the face-node counts),
 //   2. one persistent volume launch per polynomial degree present: each CTA repeatedly takes the next element
 //      tile of its degree from a global work counter and runs the volume/lift/Jacobian code. A kernel per degree
-//      keeps each degree's register allocation (one kernel over all degrees would carry the largest).
+//      keeps each degree's register allocation (one kernel over all degrees would carry the largest). With the
+//      default log mean and pipelined staging (the contexts' dg_opts.staging) the kernel is the pipelined one of
+//      volume_pipe.cuh: a CTA takes its next tile from the counter while the current one computes and copies
+//      that tile's data from its instance's arrays with asynchronous copies.
 // The work is the same per element as dg_rhs (Eq. fluxdiff-SBP-opDsplit); only the scheduling differs.
 #include <stdio.h>
 #include <string.h>
@@ -18,6 +21,7 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "volume_pipe.cuh"
 
 namespace dgk {
 namespace {
@@ -164,6 +168,47 @@ __global__ void __launch_bounds__(THREADS) batch_volume_kernel(const BatchInst* 
   }
 }
 
+// The batch's tiles for the pipelined kernel: taken from the degree's work counter one ahead (thread 0 fetches the
+// next index while the current tile computes), each tile from its instance's arrays.
+template <typename T>
+struct BatchTileSource {
+  const BatchInst* insts;
+  const BatchTile* tiles;
+  int ntiles;
+  int* counter;
+  __device__ __forceinline__ int first() const { return atomicAdd(counter, 1); }
+  __device__ __forceinline__ int next(int) const { return atomicAdd(counter, 1); }
+  __device__ __forceinline__ bool valid(int t) const { return t < ntiles; }
+  __device__ __forceinline__ PipeTile<T> tile(int t) const {
+    const BatchTile bt = tiles[t];
+    const BatchInst& in = insts[bt.inst];
+    return PipeTile<T>{in.u, static_cast<const T*>(in.Ja), in.invJ, static_cast<const T*>(in.face), in.du,
+                       in.flag, in.md, bt.e0};
+  }
+};
+
+// The pipelined batch kernel of degree N at a CTA size: the tile of the direct kernel (elements per tile of the
+// tile table), one thread per element line set.
+template <int N, typename T, int THREADS>
+struct BatchPipe {
+  static constexpr int EPB = BatchEpb<N, T, THREADS, LM_SHARED_RCP>::value;
+  static constexpr int kThreads = EPB * Geo<3, N>::TPE;
+  static constexpr size_t kSmem = PipeSmem<3, N, T>::bytes(EPB, false);
+  static constexpr bool kFits = kSmem <= 227 * 1024;
+};
+
+template <int N, typename T, int THREADS>
+__global__ void __launch_bounds__(BatchPipe<N, T, THREADS>::kThreads,
+                                  pipe_min_ctas<3, N, T, BatchPipe<N, T, THREADS>::EPB>())
+    batch_pipe_kernel(const BatchInst* __restrict__ insts, const BatchTile* __restrict__ tiles, int ntiles,
+                      int* counter, T gamma) {
+  const BatchTileSource<T> src{insts, tiles, ntiles, counter};
+  Epilogue none{};
+  none.mode = EPI_STORE;
+  pipe_tiles<3, N, T, BatchPipe<N, T, THREADS>::EPB, EPI_STORE>(src, ConstOp<N, T>::get(), gamma, none,
+                                                                general_variant());
+}
+
 template <typename T>
 cudaError_t upload_const_ops() {
   cudaError_t e = cudaSuccess;
@@ -219,8 +264,37 @@ cudaError_t batch_volume_optin(size_t smem) {
 }
 
 template <int N, typename T, int THREADS>
-cudaError_t batch_volume_call(int lm, bool launch, const BatchInst* insts, const BatchTile* tiles, int ntiles,
-                              int* counter, double gamma, size_t smem, int grid, cudaStream_t s, int* occupancy) {
+cudaError_t batch_pipe_optin() {
+  static std::mutex m;
+  static bool done = false;
+  std::lock_guard<std::mutex> lock(m);
+  if (done) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(batch_pipe_kernel<N, T, THREADS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)BatchPipe<N, T, THREADS>::kSmem);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+// pipe: the pipelined kernel (its own CTA size and shared memory); else the per-tile kernel with `smem`.
+template <int N, typename T, int THREADS>
+cudaError_t batch_volume_call(int lm, bool pipe, bool launch, const BatchInst* insts, const BatchTile* tiles,
+                              int ntiles, int* counter, double gamma, size_t smem, int grid, cudaStream_t s,
+                              int* occupancy) {
+  if (pipe) {
+    using BP = BatchPipe<N, T, THREADS>;
+    if constexpr (BP::kFits) {
+      cudaError_t e = batch_pipe_optin<N, T, THREADS>();
+      if (e != cudaSuccess) return e;
+      if (!launch)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, batch_pipe_kernel<N, T, THREADS>,
+                                                             BP::kThreads, BP::kSmem);
+      batch_pipe_kernel<N, T, THREADS><<<grid, BP::kThreads, BP::kSmem, s>>>(insts, tiles, ntiles, counter, (T)gamma);
+      return cudaGetLastError();
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  }
   auto kern = lm == LM_PRELOG ? batch_volume_kernel<N, T, THREADS, LM_PRELOG>
                               : batch_volume_kernel<N, T, THREADS, LM_SHARED_RCP>;
   cudaError_t e = lm == LM_PRELOG ? batch_volume_optin<N, T, THREADS, LM_PRELOG>(smem)
@@ -234,6 +308,7 @@ cudaError_t batch_volume_call(int lm, bool launch, const BatchInst* insts, const
 // The arguments of one degree's persistent launch (or of its occupancy query).
 struct BatchCall {
   int lm;
+  bool pipe;
   bool launch;
   const BatchInst* insts;
   const BatchTile* tiles;
@@ -249,8 +324,8 @@ struct BatchCall {
 template <typename T, int THREADS>
 cudaError_t batch_volume_p(int p, const BatchCall& c) {
 #define DG_BATCH_CALL(NN)                                                                                        \
-  batch_volume_call<NN, T, THREADS>(c.lm, c.launch, c.insts, c.tiles, c.ntiles, c.counter, c.gamma, c.smem, c.grid, \
-                                    c.s, c.occupancy)
+  batch_volume_call<NN, T, THREADS>(c.lm, c.pipe, c.launch, c.insts, c.tiles, c.ntiles, c.counter, c.gamma, c.smem, \
+                                    c.grid, c.s, c.occupancy)
   switch (p) {
     case 1: return DG_BATCH_CALL(2);
     case 2: return DG_BATCH_CALL(3);
@@ -273,9 +348,30 @@ cudaError_t batch_volume(int precision, int threads, int p, const BatchCall& c) 
   return batch_volume_p<double, 256>(p, c);
 }
 
-int occupancy_for(int precision, int threads, int p, int lm, size_t smem) {
+// Whether the pipelined kernel fits degree p's tile at a CTA size (its shared memory within the opt-in limit).
+template <typename T, int THREADS>
+bool batch_pipe_fits_t(int p) {
+  switch (p) {
+    case 1: return BatchPipe<2, T, THREADS>::kFits;
+    case 2: return BatchPipe<3, T, THREADS>::kFits;
+    case 3: return BatchPipe<4, T, THREADS>::kFits;
+    case 4: return BatchPipe<5, T, THREADS>::kFits;
+    case 5: return BatchPipe<6, T, THREADS>::kFits;
+    default: return false;
+  }
+}
+
+bool batch_pipe_fits(int precision, int threads, int p) {
+  if (precision == DG_FP32)
+    return threads == 128 ? batch_pipe_fits_t<float, 128>(p)
+                          : (threads == 192 ? batch_pipe_fits_t<float, 192>(p) : batch_pipe_fits_t<float, 256>(p));
+  return threads == 128 ? batch_pipe_fits_t<double, 128>(p)
+                        : (threads == 192 ? batch_pipe_fits_t<double, 192>(p) : batch_pipe_fits_t<double, 256>(p));
+}
+
+int occupancy_for(int precision, int threads, int p, int lm, bool pipe, size_t smem) {
   int occ = 0;
-  const BatchCall c{lm, false, nullptr, nullptr, 0, nullptr, 0.0, smem, 0, 0, &occ};
+  const BatchCall c{lm, pipe, false, nullptr, nullptr, 0, nullptr, 0.0, smem, 0, 0, &occ};
   if (batch_volume(precision, threads, p, c) != cudaSuccess) return 0;
   return occ;
 }
@@ -301,6 +397,7 @@ struct dg_batch {
   cudaStream_t streams[dgk::kBatchMaxP + 1] = {};
   cudaEvent_t fork = nullptr, join[dgk::kBatchMaxP + 1] = {};
   int occ[dgk::kNumThreadChoices][dgk::kBatchMaxP + 1];  // occupancy limits, -1 until queried
+  bool pipe[dgk::kNumThreadChoices][dgk::kBatchMaxP + 1] = {};  // the pipelined kernel for this CTA size and degree
   int threads_idx = 1;  // 192 threads per CTA until tuned
   int ctas_per_sm = 0;  // 0: the occupancy limit
   std::string signature;
@@ -331,7 +428,8 @@ dg_status to_status(cudaError_t e) {
 // number of tiles
 int occupancy_of(dg_batch* b, int ti, int p) {
   if (b->occ[ti][p] < 0)
-    b->occ[ti][p] = dgk::occupancy_for(b->precision, dgk::kThreadChoices[ti], p, b->lm, b->smem[ti][p]);
+    b->occ[ti][p] = dgk::occupancy_for(b->precision, dgk::kThreadChoices[ti], p, b->lm, b->pipe[ti][p],
+                                       b->smem[ti][p]);
   return b->occ[ti][p];
 }
 
@@ -371,8 +469,8 @@ dg_status batch_launch(dg_batch* b, int ti, cudaStream_t s) {
     const int grid = grid_for(b, ti, p);
     if (grid <= 0) return DG_ERR_CUDA;
     e = cudaStreamWaitEvent(b->streams[p], b->fork, 0);
-    const dgk::BatchCall c{b->lm, true, b->d_inst, b->d_tiles[ti][p], b->ntiles[ti][p], b->d_counter + p, b->gamma,
-                           b->smem[ti][p], grid, b->streams[p], nullptr};
+    const dgk::BatchCall c{b->lm,  b->pipe[ti][p], true, b->d_inst, b->d_tiles[ti][p], b->ntiles[ti][p],
+                           b->d_counter + p, b->gamma, b->smem[ti][p], grid, b->streams[p], nullptr};
     if (e == cudaSuccess) e = dgk::batch_volume(b->precision, dgk::kThreadChoices[ti], p, c);
     if (e == cudaSuccess) e = cudaEventRecord(b->join[p], b->streams[p]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->join[p], 0);
@@ -393,7 +491,7 @@ dg_status dg_batch_create(dg_batch** out, dg_ctx* const* ctxs, int n, const doub
     const dg_ctx* c = ctxs[i];
     if (!c || !u[i] || !du[i]) return DG_ERR_ARG;
     if (c->device != c0->device || c->precision != c0->precision || c->surface_flux != c0->surface_flux ||
-        c->gamma != c0->gamma || c->var.lm != c0->var.lm)
+        c->gamma != c0->gamma || c->var.lm != c0->var.lm || (c->var.pipe != 0) != (c0->var.pipe != 0))
       return DG_ERR_ARG;
     if (c->nd != 3 || c->p > dgk::kBatchMaxP || c->volume_flux != DG_VOL_RANOCHA ||
         (c->var.lm != dgk::LM_SHARED_RCP && c->var.lm != dgk::LM_PRELOG) || c->nodes != DG_NODES_LGL)
@@ -460,6 +558,9 @@ dg_status dg_batch_create(dg_batch** out, dg_ctx* const* ctxs, int n, const doub
       full.insert(full.end(), ragged.begin(), ragged.end());
       b->ntiles[ti][p] = (int)full.size();
       b->smem[ti][p] = dgk::batch_smem(p, b->precision, threads, logs);
+      // the pipelined kernel with the default log mean and pipelined staging, except FP32 at p = 2 (slower there)
+      b->pipe[ti][p] = c0->var.pipe != 0 && !logs && !(b->precision == DG_FP32 && p == 2) &&
+                       dgk::batch_pipe_fits(b->precision, threads, p);
       e = cudaMalloc(&b->d_tiles[ti][p], full.size() * sizeof(dgk::BatchTile));
       if (e == cudaSuccess)
         e = cudaMemcpy(b->d_tiles[ti][p], full.data(), full.size() * sizeof(dgk::BatchTile), cudaMemcpyHostToDevice);

@@ -143,11 +143,39 @@ constexpr int pipe_min_ctas() {
   return n < 1 ? 1 : n;
 }
 
-template <int ND, int N, typename T, int EPB, int EPI>
-__global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, EPB>())
-    volume_pipe_kernel(const double* __restrict__ in, const T* __restrict__ Ja, const double* __restrict__ invJ,
-                       const T* __restrict__ face, double* du, MeshDims md, OpTable<N, T> op, T gamma, int* flag,
-                       Epilogue epi, Variant var, int ntiles) {
+// Where a tile's data live: the arrays of its mesh and its first element.
+template <typename T>
+struct PipeTile {
+  const double* in;   // stage input [E][NV][NDOF]
+  const T* Ja;        // metric terms [E][ND][ND][NDOF]
+  const double* invJ;  // 1/J [E][NDOF]
+  const T* face;      // lifted interface fluxes [ND][E][NV][NL]
+  double* du;         // output (stored RHS)
+  int* flag;          // the mesh's status flag
+  MeshDims md;
+  int e0;
+};
+
+// The tiles of one mesh, round-robin over the persistent grid: t = blockIdx.x, blockIdx.x + gridDim.x, ...
+// (first and next are called by thread 0, which passes the index on through shared memory).
+template <typename T, int EPB>
+struct MeshTileSource {
+  PipeTile<T> mesh;
+  int ntiles;
+  __device__ __forceinline__ int first() const { return blockIdx.x; }
+  __device__ __forceinline__ int next(int t) const { return t + gridDim.x; }
+  __device__ __forceinline__ bool valid(int t) const { return t < ntiles; }
+  __device__ __forceinline__ PipeTile<T> tile(int t) const {
+    PipeTile<T> r = mesh;
+    r.e0 = t * EPB;
+    return r;
+  }
+};
+
+// The tile loop of the pipelined kernel over the tiles of `src` (MeshTileSource, or the batch's dynamic source).
+template <int ND, int N, typename T, int EPB, int EPI, class Src>
+__device__ __forceinline__ void pipe_tiles(const Src& src, const OpTable<N, T>& op, T gamma, const Epilogue& epi,
+                                           const Variant& var) {
   using G = Geo<ND, N>;
   using S = PipeSmem<ND, N, T>;
   constexpr int NQ = NodeQ<ND>::NQ;
@@ -159,6 +187,8 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, 
   // closes the previous tile; 1: metric terms; 2: phase-C group). A slot is rewritten only after every thread has
   // passed the two barriers that follow its read.
   __shared__ int s_ok[3];
+  __shared__ int s_tile[2];  // thread 0's tile indices: [0] the first, [1] the next (read after the tile's first
+                             // barrier, rewritten after its third)
   double* s_in = reinterpret_cast<double*>(smem_raw);
   T* s_ja = reinterpret_cast<T*>(smem_raw + S::off_ja(EPB));
   double* s_ij = reinterpret_cast<double*>(smem_raw + S::off_ij(EPB));
@@ -173,7 +203,7 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, 
   const bool has_ja = !var.cart;
   const bool need_y = kFused && epi.stage > 0;  // acc (RK4) / K (CK45) are read after stage 0
   const double* gy = EPI == EPI_RK4 ? epi.acc : epi.y;
-  int fill_in = 0, fill_ja = 0, fill_c = 0;  // thread 0: fills issued per mbarrier
+  int fill_in = 0, fill_ja = 0, fill_c = 0;  // issuing threads: fills issued per mbarrier
 
   // The copies of one group for the tile t: bulk mode, by thread 0 (byte count first, then the copies); cp.async
   // mode, by every thread (its share of each array, then its arrival on the group's barrier). Captures by value:
@@ -190,21 +220,22 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, 
       }
     }
   };
-  auto issue_in = [=](int t) {
-    const int e0 = t * EPB, nel = min(EPB, md.E - e0);
+  auto issue_in = [=](const PipeTile<T>& tt) {
+    const int e0 = tt.e0, nel = min(EPB, tt.md.E - e0);
     if constexpr (S::kBulk) mbar_expect_tx(&bars[0], (unsigned)(nel * S::kIn));
-    copy(s_in, in + (size_t)e0 * G::NV * G::NDOF, nel * G::NV * G::NDOF, &bars[0]);
+    copy(s_in, tt.in + (size_t)e0 * G::NV * G::NDOF, nel * G::NV * G::NDOF, &bars[0]);
     if constexpr (!S::kBulk) cp_async_arrive(&bars[0]);
   };
-  auto issue_ja = [=](int t) {  // metric terms (curvilinear meshes) and the faces' lifted fluxes
-    const int e0 = t * EPB, nel = min(EPB, md.E - e0);
+  auto issue_ja = [=](const PipeTile<T>& tt) {  // metric terms (curvilinear meshes) and the faces' lifted fluxes
+    const int e0 = tt.e0, nel = min(EPB, tt.md.E - e0);
+    const MeshDims& md = tt.md;
     if constexpr (S::kBulk)
       mbar_expect_tx(&bars[1], (has_ja ? (unsigned)(nel * S::kJa) : 0u) + 2u * ND * (unsigned)(nel * S::kFace));
-    if (has_ja) copy(s_ja, Ja + (size_t)e0 * ND * ND * G::NDOF, nel * ND * ND * G::NDOF, &bars[1]);
+    if (has_ja) copy(s_ja, tt.Ja + (size_t)e0 * ND * ND * G::NDOF, nel * ND * ND * G::NDOF, &bars[1]);
 #pragma unroll
     for (int n = 0; n < ND; ++n) {
       // the tile's own upper faces along n are consecutive in the face array; the lower neighbours' mostly are
-      const T* fn = face + (size_t)n * md.E * kFaceT;
+      const T* fn = tt.face + (size_t)n * md.E * kFaceT;
       copy(s_fc + ((1 * ND + n) * EPB) * kFaceT, fn + (size_t)e0 * kFaceT, nel * kFaceT, &bars[1]);
       if (lower_neighbors_consecutive(md, e0, nel, n)) {
         copy(s_fc + (n * EPB) * kFaceT, fn + (size_t)neighbor(md, e0, n, -1) * kFaceT, nel * kFaceT, &bars[1]);
@@ -216,14 +247,14 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, 
     }
     if constexpr (!S::kBulk) cp_async_arrive(&bars[1]);
   };
-  auto issue_c = [=](int t) {  // 1/J (curvilinear meshes) and the stage update's operands; may be empty
-    const int e0 = t * EPB, nel = min(EPB, md.E - e0);
+  auto issue_c = [=](const PipeTile<T>& tt) {  // 1/J (curvilinear meshes) and the stage update's operands; may be empty
+    const int e0 = tt.e0, nel = min(EPB, tt.md.E - e0);
     const int nin = nel * G::NV * G::NDOF;
     if constexpr (S::kBulk)
       mbar_expect_tx(&bars[2], (has_ja ? (unsigned)(nel * S::kInvJ) : 0u) + (kFused ? (unsigned)(nel * S::kIn) : 0u) +
                                    (need_y ? (unsigned)(nel * S::kIn) : 0u));
     const size_t so = (size_t)e0 * G::NV * G::NDOF;
-    if (has_ja) copy(s_ij, invJ + (size_t)e0 * G::NDOF, nel * G::NDOF, &bars[2]);
+    if (has_ja) copy(s_ij, tt.invJ + (size_t)e0 * G::NDOF, nel * G::NDOF, &bars[2]);
     if (kFused) copy(s_eu, epi.u + so, nin, &bars[2]);
     if (need_y) copy(s_ey, gy + so, nin, &bars[2]);
     if constexpr (!S::kBulk) cp_async_arrive(&bars[2]);
@@ -231,25 +262,30 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, 
   // the threads that issue copies: thread 0 in bulk mode, all in cp.async mode
   const bool issuer = S::kBulk ? tid == 0 : true;
 
-  int t = blockIdx.x;
   if (tid == 0) {
     for (int j = 0; j < 3; ++j) mbar_init(&bars[j], S::kBulk ? 1 : kThreads);
     mbar_init_fence();
+    s_tile[0] = src.first();
   }
   __syncthreads();
-  if (issuer && t < ntiles) {
-    issue_in(t);
-    issue_ja(t);
-    issue_c(t);
+  int t = s_tile[0];
+  if (issuer && src.valid(t)) {
+    const PipeTile<T> ft = src.tile(t);
+    issue_in(ft);
+    issue_ja(ft);
+    issue_c(ft);
     fill_in = fill_ja = fill_c = 1;
   }
-  if (tid == 0 && t < ntiles) s_ok[0] = mbar_wait_bounded(&bars[0], 0u) ? 1 : 0;
+  if (tid == 0 && src.valid(t)) s_ok[0] = mbar_wait_bounded(&bars[0], 0u) ? 1 : 0;
   __syncthreads();
   bool failed = false;
-  for (int k = 0; t < ntiles; ++k, t += gridDim.x) {
+  int* flag = nullptr;  // the current tile's mesh flag (a wait that ran out is reported there)
+  for (int k = 0; src.valid(t); ++k) {
     const unsigned par = (unsigned)(k & 1);  // every group is copied once per tile
-    const int tn = t + gridDim.x;
-    const int e0 = t * EPB, nel = min(EPB, md.E - e0);
+    const PipeTile<T> cur = src.tile(t);
+    const int e0 = cur.e0, nel = min(EPB, cur.md.E - e0);
+    flag = cur.flag;
+    if (tid == 0) s_tile[1] = src.next(t);
     if (!s_ok[0]) {  // all threads read the same slot: the whole CTA leaves the loop
       failed = true;
       break;
@@ -277,8 +313,11 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, 
       break;
     }
     mbar_test(&bars[1], par);
-    if (issuer && tn < ntiles) {  // the stage input has been read
-      issue_in(tn);
+    const int tn = s_tile[1];
+    const bool has_next = src.valid(tn);
+    const PipeTile<T> nxt = src.tile(has_next ? tn : t);
+    if (issuer && has_next) {  // the stage input has been read
+      issue_in(nxt);
       ++fill_in;
     }
 
@@ -308,8 +347,8 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, 
       break;
     }
     mbar_test(&bars[2], par);
-    if (issuer && tn < ntiles) {  // the metric terms and face fluxes have been read
-      issue_ja(tn);
+    if (issuer && has_next) {  // the metric terms and face fluxes have been read
+      issue_ja(nxt);
       ++fill_ja;
     }
 
@@ -345,21 +384,22 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, 
           // as in volume_tile: FP64 scaling, or the FP32 scaling and an exact integer-pipe widening
           const double kv = sizeof(T) == 8 ? sj * (double)tot[c] : f2d_int((float)(sjT * tot[c]));
           if (EPI == EPI_STORE)
-            du[o] = kv;
+            cur.du[o] = kv;
           else
             stage_update<EPI>(epi, o, kv, s_eu[so], need_y ? s_ey[so] : 0.0);
         }
       }
     }
-    if (tid == 0 && tn < ntiles) s_ok[0] = mbar_wait_bounded(&bars[0], par ^ 1u) ? 1 : 0;
+    if (tid == 0 && has_next) s_ok[0] = mbar_wait_bounded(&bars[0], par ^ 1u) ? 1 : 0;
     __syncthreads();
-    if (issuer && tn < ntiles) {  // the phase-C group has been read
-      issue_c(tn);
+    if (issuer && has_next) {  // the phase-C group has been read
+      issue_c(nxt);
       ++fill_c;
     }
+    t = tn;
   }
   if (failed) {  // a wait ran out: raise the flag, wait (bounded, or for the own copies) for the copies in flight
-    if (tid == 0) atomicOr(flag, FLAG_WAIT_TIMEOUT);
+    if (tid == 0 && flag) atomicOr(flag, FLAG_WAIT_TIMEOUT);
     if constexpr (S::kBulk) {
       if (tid == 0) {
         mbar_drain(&bars[0], fill_in);
@@ -370,6 +410,15 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, 
       cp_async_wait_all();
     }
   }
+}
+
+template <int ND, int N, typename T, int EPB, int EPI>
+__global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, EPB>())
+    volume_pipe_kernel(const double* __restrict__ in, const T* __restrict__ Ja, const double* __restrict__ invJ,
+                       const T* __restrict__ face, double* du, MeshDims md, OpTable<N, T> op, T gamma, int* flag,
+                       Epilogue epi, Variant var, int ntiles) {
+  const MeshTileSource<T, EPB> src{{in, Ja, invJ, face, du, flag, md, 0}, ntiles};
+  pipe_tiles<ND, N, T, EPB, EPI>(src, op, gamma, epi, var);
 }
 
 }  // namespace dgk
