@@ -204,11 +204,13 @@ dg_status dg_get_metrics(const dg_ctx* ctx, double* Ja_host /* [E][d][d][Nd] */,
    (0 = volume term with surface lift and Jacobian, which in dg_step also applies the RK stage update;
    1 = interface flux; 2 = entropy projection of DG_NODES_GAUSS) while enabled. dg_profile_enable times every
    kernel (on != 0) or none; dg_profile_enable_kernels times the kernels of `mask` (bit k: kernel k; 0 = off), so
-   that a timed region carries events around the kernel of interest only. dg_profile_read returns the summed
-   milliseconds and the launch count since the last enable, and synchronizes. dg_launch_count counts every kernel
-   the context has launched since dg_init. */
+   that a timed region carries events around the kernel of interest only; dg_profile_enable_sampled times every
+   `every`-th launch (>= 1) of each of them (with `every` coprime to the launches per step, every Runge-Kutta stage
+   is sampled). dg_profile_read returns the summed milliseconds and the number of timed launches since the last
+   enable, and synchronizes. dg_launch_count counts every kernel the context has launched since dg_init. */
 dg_status dg_profile_enable(dg_ctx* ctx, int on);
 dg_status dg_profile_enable_kernels(dg_ctx* ctx, unsigned mask);
+dg_status dg_profile_enable_sampled(dg_ctx* ctx, unsigned mask, int every);
 dg_status dg_profile_read(dg_ctx* ctx, int which, double* total_ms, long long* launches);
 long long dg_launch_count(const dg_ctx* ctx);
 

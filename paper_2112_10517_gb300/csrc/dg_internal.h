@@ -138,6 +138,8 @@ struct dg_ctx {
   // profiling
   int prof_on;
   unsigned prof_mask;    // kernels timed while profiling is on (bit k: kernel id k)
+  int prof_every;        // time every prof_every-th launch of each of them
+  long long prof_seen[dgk::KID_COUNT];  // launches of each kernel since the enable
   cudaEvent_t* prof_ev;  // pairs
   int prof_cap, prof_n[dgk::KID_COUNT];
   int* prof_kid;

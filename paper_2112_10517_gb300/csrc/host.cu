@@ -303,6 +303,7 @@ void prof_begin(dg_ctx* c, int kid, cudaStream_t s, int* slot) {
   *slot = -1;
   c->launches++;
   if (!c->prof_on || !((c->prof_mask >> kid) & 1u) || c->prof_used >= c->prof_cap) return;
+  if (c->prof_seen[kid]++ % c->prof_every != 0) return;  // every prof_every-th launch of the kernel
   *slot = c->prof_used++;
   c->prof_kid[*slot] = kid;
   cudaEventRecord(c->prof_ev[2 * *slot], s);
@@ -632,15 +633,19 @@ dg_status dg_get_metrics(const dg_ctx* c, double* Ja, double* J) {
   return DG_OK;
 }
 
-dg_status dg_profile_enable_kernels(dg_ctx* c, unsigned mask) {
-  if (!c) return DG_ERR_ARG;
+dg_status dg_profile_enable_sampled(dg_ctx* c, unsigned mask, int every) {
+  if (!c || every < 1) return DG_ERR_ARG;
   c->prof_mask = mask;
+  c->prof_every = every;
   c->prof_on = mask ? 1 : 0;
   c->prof_used = 0;
+  for (int k = 0; k < dgk::KID_COUNT; ++k) c->prof_seen[k] = 0;
   return DG_OK;
 }
 
-dg_status dg_profile_enable(dg_ctx* c, int on) { return dg_profile_enable_kernels(c, on ? ~0u : 0u); }
+dg_status dg_profile_enable_kernels(dg_ctx* c, unsigned mask) { return dg_profile_enable_sampled(c, mask, 1); }
+
+dg_status dg_profile_enable(dg_ctx* c, int on) { return dg_profile_enable_sampled(c, on ? ~0u : 0u, 1); }
 
 dg_status dg_profile_read(dg_ctx* c, int which, double* total_ms, long long* launches) {
   if (!c || which < 0 || which >= dgk::KID_COUNT || !total_ms) return DG_ERR_ARG;

@@ -41,7 +41,7 @@ EXPORTED = ["dg_init", "dg_rhs", "dg_step", "dg_entropy_rate", "dg_check_status"
             "dg_get_node_coords", "dg_get_metrics", "dg_profile_enable", "dg_profile_read", "dg_launch_count",
             "dg_free", "dg_status_string", "dg_rhs_noalloc", "dg_batch_create", "dg_batch_rhs",
             "dg_batch_autotune", "dg_batch_set_tuning", "dg_batch_free", "dg_vjp", "dg_selftest_wait_timeout",
-            "dg_profile_enable_kernels"]
+            "dg_profile_enable_kernels", "dg_profile_enable_sampled"]
 
 
 class DgMesh(ctypes.Structure):
@@ -80,6 +80,7 @@ _sig = {
     "dg_get_metrics": (ctypes.c_int, [_vp, _dp, _dp]),
     "dg_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "dg_profile_enable_kernels": (ctypes.c_int, [_vp, ctypes.c_uint]),
+    "dg_profile_enable_sampled": (ctypes.c_int, [_vp, ctypes.c_uint, ctypes.c_int]),
     "dg_profile_read": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_longlong)]),
     "dg_launch_count": (ctypes.c_longlong, [_vp]),
     "dg_free": (None, [_vp]),
@@ -260,15 +261,18 @@ class DG:
         check(dg_get_metrics(self.ctx, _dptr(Ja), _dptr(J)), "dg_get_metrics")
         return Ja, J
 
-    def profile(self, on: bool, kernels=None):
-        """Time every kernel (kernels=None) or only the given kernel ids (KERNEL_*) while on."""
-        if kernels is None or not on:
-            check(dg_profile_enable(self.ctx, int(bool(on))), "dg_profile_enable")
-        else:
+    def profile(self, on: bool, kernels=None, every: int = 1):
+        """Time every kernel (kernels=None) or only the given kernel ids (KERNEL_*) while on; every: time each
+        every-th launch of them."""
+        if not on:
+            check(dg_profile_enable(self.ctx, 0), "dg_profile_enable")
+            return
+        mask = 0xFFFFFFFF
+        if kernels is not None:
             mask = 0
             for k in kernels:
                 mask |= 1 << int(k)
-            check(dg_profile_enable_kernels(self.ctx, mask), "dg_profile_enable_kernels")
+        check(dg_profile_enable_sampled(self.ctx, mask, int(every)), "dg_profile_enable_sampled")
 
     def profile_read(self, kernel: int = KERNEL_VOLUME):
         ms = ctypes.c_double()

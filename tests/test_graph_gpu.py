@@ -99,7 +99,11 @@ def test_profiling_counts_the_selected_kernels_only(dgmod):
     vol_ms, vol_n = ctx.profile_read(dgmod.KERNEL_VOLUME)
     assert vol_n == 2 and vol_ms > 0.0
     assert ctx.profile_read(dgmod.KERNEL_INTERFACE)[1] == 0
+    ctx.profile(True, kernels=[dgmod.KERNEL_VOLUME], every=3)  # launches 0, 3, 6 of the volume kernel
+    for _ in range(7):
+        ctx.rhs(u, du)
+    assert ctx.profile_read(dgmod.KERNEL_VOLUME)[1] == 3
     ctx.profile(False)
     ctx.rhs(u, du)
     assert ctx.profile_read(dgmod.KERNEL_VOLUME)[1] == 0
-    assert ctx.launch_count() - n0 == 12
+    assert ctx.launch_count() - n0 == 26
