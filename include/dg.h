@@ -168,6 +168,14 @@ dg_status dg_rhs(dg_ctx* ctx, const double* u, double* du, double t, dg_stream_t
    2 kernels: the interface fluxes, then the volume term whose epilogue applies the stage update in FP64. */
 dg_status dg_step(dg_ctx* ctx, double* u, double* scratch, double t, double dt, int scheme, dg_stream_t stream);
 
+/* The same with the state in host memory: queue on `stream` the host->device copy of u_host, dg_step (or dg_rhs)
+   on device copies owned by the context, and the device->host copy of the result (the new state into u_host, or
+   du into du_host). Pinned host memory makes the copies asynchronous; the caller synchronizes the stream before
+   reading the result. The first call allocates three state arrays of device memory held by the context until
+   dg_free. Errors as dg_step / dg_rhs. */
+dg_status dg_step_host(dg_ctx* ctx, double* u_host, double t, double dt, int scheme, dg_stream_t stream);
+dg_status dg_rhs_host(dg_ctx* ctx, const double* u_host, double* du_host, double t, dg_stream_t stream);
+
 /* Entropy rate dS/dt = sum_e sum_i J_i W_i w(u_i) . du_i (Sec. 2: EC/ED semidiscretizations; W the tensor
    LGL weights, w the entropy variables of U = -rho s/(gamma-1)). FP64, deterministic order. Writes the value
    to *out_host and, when abs_out_host is not NULL, the magnitude sum_e sum_i sum_c |J_i W_i w_c(u_i) du_c,i| to

@@ -132,6 +132,7 @@ struct dg_ctx {
   void* d_face;    // face fluxes [nd][E][nv][N^(nd-1)], FP64 or FP32
   double* d_fadj;  // dg_vjp: face adjoint contributions [nd][E][2][nv][N^(nd-1)] (allocated at the first dg_vjp)
   double* d_gface;  // Gauss collocation: projected face states [nd][E][2][nv][N^(nd-1)]
+  double* d_hstage;  // dg_step_host / dg_rhs_host: device copies of the host state (3 state arrays, first call)
   double* d_red;   // entropy-rate partials + result
   int* d_flag;     // non-physical-state flag
   cudaStream_t last_stream;

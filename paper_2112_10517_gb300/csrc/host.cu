@@ -201,6 +201,7 @@ void release(dg_ctx* c) {
   cudaFree(c->d_face);
   cudaFree(c->d_fadj);
   cudaFree(c->d_gface);
+  cudaFree(c->d_hstage);
   cudaFree(c->d_red);
   cudaFree(c->d_flag);
   if (c->prof_ev) {
@@ -560,6 +561,41 @@ dg_status dg_step(dg_ctx* c, double* u, double* scratch, double t, double dt, in
     if (e != cudaSuccess) return cuda_status(e);
   }
   return DG_OK;
+}
+
+// Device staging of dg_step_host / dg_rhs_host: three state arrays, allocated at the first call.
+static dg_status ensure_host_staging(dg_ctx* c) {
+  if (c->d_hstage) return DG_OK;
+  return cuda_status(dev_alloc(&c->d_hstage, (size_t)c->state_len * 3));
+}
+
+dg_status dg_step_host(dg_ctx* c, double* u_host, double t, double dt, int scheme, dg_stream_t stream) {
+  if (!c || !u_host) return DG_ERR_ARG;
+  dg_status st = ensure_host_staging(c);
+  if (st != DG_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)c->state_len * sizeof(double);
+  double* u = c->d_hstage;
+  cudaError_t e = cudaMemcpyAsync(u, u_host, bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  st = dg_step(c, u, u + c->state_len, t, dt, scheme, stream);
+  if (st != DG_OK) return st;
+  return cuda_status(cudaMemcpyAsync(u_host, u, bytes, cudaMemcpyDeviceToHost, s));
+}
+
+dg_status dg_rhs_host(dg_ctx* c, const double* u_host, double* du_host, double t, dg_stream_t stream) {
+  if (!c || !u_host || !du_host) return DG_ERR_ARG;
+  dg_status st = ensure_host_staging(c);
+  if (st != DG_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)c->state_len * sizeof(double);
+  double* u = c->d_hstage;
+  double* du = u + c->state_len;
+  cudaError_t e = cudaMemcpyAsync(u, u_host, bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  st = dg_rhs(c, u, du, t, stream);
+  if (st != DG_OK) return st;
+  return cuda_status(cudaMemcpyAsync(du_host, du, bytes, cudaMemcpyDeviceToHost, s));
 }
 
 dg_status dg_entropy_rate(dg_ctx* c, const double* u, const double* du, double* out_host, double* abs_out_host,

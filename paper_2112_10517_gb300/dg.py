@@ -41,7 +41,7 @@ EXPORTED = ["dg_init", "dg_rhs", "dg_step", "dg_entropy_rate", "dg_check_status"
             "dg_get_node_coords", "dg_get_metrics", "dg_profile_enable", "dg_profile_read", "dg_launch_count",
             "dg_free", "dg_status_string", "dg_rhs_noalloc", "dg_batch_create", "dg_batch_rhs",
             "dg_batch_autotune", "dg_batch_set_tuning", "dg_batch_free", "dg_vjp", "dg_selftest_wait_timeout",
-            "dg_profile_enable_kernels", "dg_profile_enable_sampled"]
+            "dg_profile_enable_kernels", "dg_profile_enable_sampled", "dg_step_host", "dg_rhs_host"]
 
 
 class DgMesh(ctypes.Structure):
@@ -81,6 +81,8 @@ _sig = {
     "dg_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "dg_profile_enable_kernels": (ctypes.c_int, [_vp, ctypes.c_uint]),
     "dg_profile_enable_sampled": (ctypes.c_int, [_vp, ctypes.c_uint, ctypes.c_int]),
+    "dg_step_host": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, _vp]),
+    "dg_rhs_host": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, _vp]),
     "dg_profile_read": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_longlong)]),
     "dg_launch_count": (ctypes.c_longlong, [_vp]),
     "dg_free": (None, [_vp]),
@@ -246,6 +248,27 @@ class DG:
         check(dg_entropy_rate(self.ctx, self._state(u, "u"), self._state(du, "du"), ctypes.byref(out),
                               ctypes.byref(ab), _stream_handle(stream)), "dg_entropy_rate")
         return out.value, ab.value
+
+    # ---- host-resident state: the library copies in and out (asynchronous for pinned tensors) ----
+    def _host_state(self, t, name):
+        import torch
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or t.is_cuda:
+            raise TypeError("%s must be a CPU float64 tensor" % name)
+        if tuple(t.shape) != self.shape or not t.is_contiguous():
+            raise ValueError("%s must be contiguous with shape %s, got %s" % (name, self.shape, tuple(t.shape)))
+        return ctypes.c_void_p(t.data_ptr())
+
+    def step_host(self, u_host, dt: float, scheme: int = DG_RK4_CLASSIC, stream=None):
+        """One time step of the host state u_host (dg_step_host); synchronize the stream before reading it."""
+        check(dg_step_host(self.ctx, self._host_state(u_host, "u_host"), 0.0, float(dt), int(scheme),
+                           _stream_handle(stream)), "dg_step_host")
+        return u_host
+
+    def rhs_host(self, u_host, du_host, stream=None):
+        """du_host = RHS(u_host) through device copies (dg_rhs_host); synchronize the stream before reading."""
+        check(dg_rhs_host(self.ctx, self._host_state(u_host, "u_host"), self._host_state(du_host, "du_host"), 0.0,
+                          _stream_handle(stream)), "dg_rhs_host")
+        return du_host
 
     def check_status(self) -> int:
         return dg_check_status(self.ctx)

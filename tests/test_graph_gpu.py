@@ -107,3 +107,30 @@ def test_profiling_counts_the_selected_kernels_only(dgmod):
     ctx.rhs(u, du)
     assert ctx.profile_read(dgmod.KERNEL_VOLUME)[1] == 0
     assert ctx.launch_count() - n0 == 26
+
+
+def test_host_buffer_entry_points_match_device_calls(dgmod):
+    # dg_rhs_host / dg_step_host: the same kernels on device copies of a host state, bit for bit; pinned host
+    # memory (asynchronous copies) and pageable memory (synchronous copies)
+    import torch
+    sc = Scenario(3, [3, 2, 3], 3, mapping="sine", ic="smooth", llf=True, seed=720)
+    ctx = dgmod.DG(**sc.dg_kwargs())
+    du_dev = ctx.rhs(torch.from_numpy(sc.u).cuda()).cpu()
+    uh = torch.from_numpy(sc.u.copy()).pin_memory()
+    duh = torch.empty_like(uh).pin_memory()
+    ctx.rhs_host(uh, duh)
+    torch.cuda.synchronize()
+    assert torch.equal(duh, du_dev)
+    up, dup = torch.from_numpy(sc.u.copy()), torch.empty(uh.shape, dtype=torch.float64)
+    ctx.rhs_host(up, dup)
+    torch.cuda.synchronize()
+    assert torch.equal(dup, du_dev)
+    ud = torch.from_numpy(sc.u).cuda()
+    for _ in range(2):
+        ctx.step(ud, 1e-3)
+        ctx.step_host(uh, 1e-3)
+    torch.cuda.synchronize()
+    assert torch.equal(uh, ud.cpu())
+    assert ctx.check_status() == dgmod.DG_OK
+    with pytest.raises(TypeError):
+        ctx.rhs_host(ud, duh)  # a device tensor is not a host state
