@@ -62,7 +62,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (debug runs)")
     ap.add_argument("--only", default="", help="comma-separated subset of fp64_16,fp32_16,fp64_32,fp32_32, "
-                    "variants, ablation, gauss, staging, batch (profiling runs; prints one line per configuration instead of the "
+                    "variants, ablation, gauss, staging, launch, batch (profiling runs; prints one line per configuration instead of the "
                     "contract line)")
     return ap.parse_args()
 
@@ -524,6 +524,61 @@ def run_staging(args, dev):
     return out
 
 
+def run_launch_modes(args, dev):
+    """The RK4 step (dg_step) with the interface and pipelined volume kernels launched as programmatic dependents
+    of the kernel before them (overlap, the default) and as ordinary launches (serial): eager steps without
+    profiling events, and the same step captured in a CUDA graph and replayed. Taylor-Green vortex, p = 3 at 16^3
+    and 32^3 elements, FP64 and FP32; L2 flushed before every timed step."""
+    import torch
+    from paper_2112_10517_gb300 import dg
+    lo, hi = [-math.pi] * 3, [math.pi] * 3
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for precision, ne in (("fp64", NELEM[0]), ("fp32", NELEM[0]), ("fp64", NELEM_LARGE[0]), ("fp32", NELEM_LARGE[0])):
+        for launch in ("overlap", "serial"):
+            ctx = dg.DG(3, [ne] * 3, POLYDEG, lo=lo, hi=hi, mapping="sine", amp=AMP, surface="llf",
+                        precision=precision, launch=launch)
+            u = torch.from_numpy(make_state(ctx)).to(dev)
+            scratch = torch.empty((2,) + ctx.shape, dtype=torch.float64, device=dev)
+            dt = 0.5 * (2 * math.pi / ne) / (POLYDEG + 1) ** 2 / (1.0 + 1.0 / MACH)
+            for _ in range(args.warmup):
+                ctx.step(u, dt, dg.DG_RK4_CLASSIC, scratch=scratch)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            for a, b in ev:
+                flush.zero_()
+                a.record(stream)
+                ctx.step(u, dt, dg.DG_RK4_CLASSIC, scratch=scratch)
+                b.record(stream)
+            torch.cuda.synchronize()
+            eager = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+            side = torch.cuda.Stream(device=dev)
+            side.wait_stream(stream)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=side):
+                ctx.step(u, dt, dg.DG_RK4_CLASSIC, scratch=scratch, stream=side)
+            for _ in range(2):
+                graph.replay()
+            torch.cuda.synchronize()
+            for a, b in ev:
+                flush.zero_()
+                a.record(stream)
+                graph.replay()
+                b.record(stream)
+            torch.cuda.synchronize()
+            gms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+            if ctx.check_status() != dg.DG_OK:
+                raise RuntimeError("non-physical state or wait timeout in the launch-mode runs")
+            out["%s_%d_%s" % (precision, ne, launch)] = {"pid_ns": whole_job_pid(eager, ctx.ndofs, 1),
+                                                        "graph_pid_ns": whole_job_pid(gms, ctx.ndofs, 1)}
+            del ctx, u, scratch, graph
+    out["workload"] = ("dg_step (RK4) on the Taylor-Green vortex, sine-perturbed mesh, p = 3 at 16^3 and 32^3 "
+                       "elements; pid_ns eager without profiling events, graph_pid_ns as graph replays")
+    return out
+
+
 def run_logmean_ablation(args, dev):
     """Volume-term time of the log-mean variants (Sec. 3.1: Algorithms 2/3 with divisions, with the polynomial 1/log
     form; Sec. 7.2: logarithms precomputed per node) against the default (no division, one shared reciprocal),
@@ -777,6 +832,7 @@ def main():
     ablation = run_logmean_ablation(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
     gauss = run_gauss(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
     staging = run_staging(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
+    launch_modes = run_launch_modes(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
     if rank == 0 and args.only:
         for label, res in results.items():
             print(json.dumps({"configuration": label, "pid_ns": res["pid_ns"], "noprof_pid_ns": res["noprof_pid_ns"],
@@ -793,6 +849,8 @@ def main():
             print(json.dumps({"configuration": "gauss", "result": run_gauss(args, dev)}), flush=True)
         if "staging" in only:
             print(json.dumps({"configuration": "staging", "result": run_staging(args, dev)}), flush=True)
+        if "launch" in only:
+            print(json.dumps({"configuration": "launch", "result": run_launch_modes(args, dev)}), flush=True)
         if "batch" in only:
             print(json.dumps({"configuration": "batch", "result": run_batch(args, dev)}), flush=True)
     elif rank == 0:
@@ -816,6 +874,7 @@ def main():
             "config": {"workload": WORKLOAD, "time_step": "4-stage low-storage RK4 (4 RHS + 4 stage updates)",
                        "pid_per": "RHS evaluation", "surface_flux": "Ranocha + LLF", "volume_flux": "Ranocha",
                        "l2": "flushed (512 MB write) before every timed step",
+                       "launch": "programmatic dependent launches (dg_opts.launch = DG_LAUNCH_OVERLAP)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": r64["roofline"],
             "cpu_baseline": cpu,
@@ -854,6 +913,7 @@ def main():
             "logmean_ablation": ablation,
             "gauss_collocation": gauss,
             "tile_staging": staging,
+            "launch_modes": launch_modes,
             "alu_peaks_measured_tflops": {k: (v / 1e12 if v else None) for k, v in peaks_alu.items()},
         }
         print(json.dumps(line), flush=True)

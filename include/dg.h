@@ -124,10 +124,20 @@ typedef struct dg_metrics {
      DG_STAGING_DIRECT     one CTA per tile, loads issued by its threads.
    All compute the same values (the same arithmetic in the same order). A pipelined kernel whose wait for its own
    copies runs out (bounded; it cannot under normal operation) skips the rest of its tiles and raises the flag that
-   dg_check_status reports as DG_ERR_TIMEOUT. */
+   dg_check_status reports as DG_ERR_TIMEOUT.
+   launch: how dg_rhs / dg_step queue the interface kernel and the pipelined volume kernel.
+     DG_LAUNCH_OVERLAP     (default) each as a programmatic dependent of the kernel before it in the stream: it is
+                           scheduled ahead and its CTAs start as those of that kernel exit, set up, and copy the
+                           metric terms of their first tile (written only by dg_init); every read of the state, the
+                           interface fluxes and the Runge-Kutta operands, and every write, waits until the kernels
+                           before it have completed and their writes are visible. Work queued on the stream by other
+                           code is ordered as usual.
+     DG_LAUNCH_SERIAL      ordinary launches: each kernel starts after the one before it has completed.
+   Both compute the same values. */
 enum { DG_LOGMEAN_SHARED_RCP = 0, DG_LOGMEAN_ALG = 1, DG_LOGMEAN_ALG_POLY = 2 };
 enum { DG_NODES_LGL = 0, DG_NODES_GAUSS = 1 };
 enum { DG_STAGING_AUTO = 0, DG_STAGING_DIRECT = 1, DG_STAGING_PIPELINED = 2 };
+enum { DG_LAUNCH_OVERLAP = 0, DG_LAUNCH_SERIAL = 1 };
 typedef struct dg_opts {
   double gamma;
   int volume_flux;
@@ -137,7 +147,7 @@ typedef struct dg_opts {
   int logmean;         /* DG_LOGMEAN_* */
   int nodes;           /* DG_NODES_* */
   int staging;         /* DG_STAGING_* */
-  int reserved[1];     /* must be zero */
+  int launch;          /* DG_LAUNCH_* */
 } dg_opts;
 
 /* Sizes of a context. */

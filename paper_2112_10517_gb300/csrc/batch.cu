@@ -169,7 +169,8 @@ __global__ void __launch_bounds__(THREADS) batch_volume_kernel(const BatchInst* 
 }
 
 // The batch's tiles for the pipelined kernel: taken from the degree's work counter one ahead (thread 0 fetches the
-// next index while the current tile computes), each tile from its instance's arrays.
+// next index while the current tile computes), each tile from its instance's arrays. (The batch kernel is launched
+// without the programmatic-dependence attribute, so the counter it takes before pdl_wait is already reset.)
 template <typename T>
 struct BatchTileSource {
   const BatchInst* insts;

@@ -61,6 +61,8 @@ struct Variant {
   int lm;        // log-mean variant of the volume terms (LM_* in dgmath.cuh; Ranocha's flux only)
   int pipe;      // volume kernel with bulk asynchronous tile copies (where supported): 0 never, 1 on meshes
                  // with enough tiles per resident CTA, 2 always
+  int overlap;   // 1: the interface and pipelined volume kernels are launched as programmatic dependents of the
+                 // kernel before them in the stream (they start while it drains; dg_opts.launch)
   double jn[3];  // Ja^n_n of a Cartesian mesh
   double invJ;   // 1/J of a Cartesian mesh
 };

@@ -348,7 +348,7 @@ dg_status dg_init(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metri
   if (opts->volume_flux != DG_VOL_RANOCHA && opts->volume_flux != DG_VOL_SHIMA) return DG_ERR_ARG;
   if (opts->surface_flux != DG_SURF_EC && opts->surface_flux != DG_SURF_EC_LLF) return DG_ERR_ARG;
   if (opts->precision != DG_FP64 && opts->precision != DG_FP32) return DG_ERR_ARG;
-  if (opts->reserved[0] != 0) return DG_ERR_ARG;
+  if (opts->launch != DG_LAUNCH_OVERLAP && opts->launch != DG_LAUNCH_SERIAL) return DG_ERR_ARG;
   if (opts->staging < DG_STAGING_AUTO || opts->staging > DG_STAGING_PIPELINED) return DG_ERR_ARG;
   if (opts->nodes != DG_NODES_LGL && opts->nodes != DG_NODES_GAUSS) return DG_ERR_ARG;
   const bool gauss = opts->nodes == DG_NODES_GAUSS;
@@ -396,6 +396,7 @@ dg_status dg_init(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metri
                  opts->logmean == DG_LOGMEAN_SHARED_RCP) ? 1 : 0;
   c->var.lm = opts->precompute_logs ? dgk::LM_PRELOG : opts->logmean;  // DG_LOGMEAN_* equal LM_* 0..2
   c->var.pipe = opts->staging == DG_STAGING_AUTO ? 1 : (opts->staging == DG_STAGING_PIPELINED ? 2 : 0);
+  c->var.overlap = opts->launch == DG_LAUNCH_OVERLAP ? 1 : 0;
   {
     double hh[3] = {1.0, 1.0, 1.0}, jac = 1.0;
     for (int d = 0; d < nd; ++d) {

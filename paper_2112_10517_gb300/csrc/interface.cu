@@ -10,11 +10,10 @@ cudaError_t launch_interface_t(int llf, MeshDims md, const double* u, const T* J
   const long long total = (long long)ND * md.E * Geo<ND, N>::NL;
   const int threads = 256;
   const long long blocks = (total + threads - 1) / threads;
-  if (llf)
-    interface_kernel<ND, N, T, true><<<(unsigned)blocks, threads, 0, s>>>(u, Ja, face, md, (T)gamma, flag, var);
-  else
-    interface_kernel<ND, N, T, false><<<(unsigned)blocks, threads, 0, s>>>(u, Ja, face, md, (T)gamma, flag, var);
-  return cudaGetLastError();
+  auto kern = llf ? interface_kernel<ND, N, T, true> : interface_kernel<ND, N, T, false>;
+  const cudaError_t e = launch_kernel(kern, dim3((unsigned)blocks), dim3(threads), 0, s, var.overlap != 0, u, Ja, face,
+                                      md, (T)gamma, flag, var);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int ND, typename T>

@@ -97,9 +97,9 @@ cudaError_t launch_volume_pipe(MeshDims md, const double* u, const T* Ja, const 
       if (var.pipe == 1 && (!kAutoOk || (long long)ntiles < (long long)DG_VOLUME_PIPE_MIN_TILES_PER_CTA * ctas))
         return cudaErrorNotSupported;
       const int grid = ntiles < ctas ? ntiles : ctas;
-      kern<<<grid, EPB * TPE, smem, s>>>(u, Ja, invJ, face, du, md, op_table<N, T>(), (T)gamma, flag, epi, var,
-                                          ntiles);
-      return cudaGetLastError();
+      const cudaError_t e = launch_kernel(kern, dim3(grid), dim3(EPB * TPE), smem, s, var.overlap != 0, u, Ja, invJ,
+                                          face, du, md, op_table<N, T>(), (T)gamma, flag, epi, var, ntiles);
+      return e != cudaSuccess ? e : cudaGetLastError();
     }
   }
   return cudaErrorNotSupported;

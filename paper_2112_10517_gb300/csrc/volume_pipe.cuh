@@ -226,12 +226,17 @@ __device__ __forceinline__ void pipe_tiles(const Src& src, const OpTable<N, T>& 
     copy(s_in, tt.in + (size_t)e0 * G::NV * G::NDOF, nel * G::NV * G::NDOF, &bars[0]);
     if constexpr (!S::kBulk) cp_async_arrive(&bars[0]);
   };
-  auto issue_ja = [=](const PipeTile<T>& tt) {  // metric terms (curvilinear meshes) and the faces' lifted fluxes
+  // The metric group in two parts: the metric terms (curvilinear meshes; written once, at set-up), with the byte
+  // count of the whole group, then the faces' lifted fluxes (written by the interface kernel before this one).
+  auto issue_ja_geo = [=](const PipeTile<T>& tt) {
     const int e0 = tt.e0, nel = min(EPB, tt.md.E - e0);
-    const MeshDims& md = tt.md;
     if constexpr (S::kBulk)
       mbar_expect_tx(&bars[1], (has_ja ? (unsigned)(nel * S::kJa) : 0u) + 2u * ND * (unsigned)(nel * S::kFace));
     if (has_ja) copy(s_ja, tt.Ja + (size_t)e0 * ND * ND * G::NDOF, nel * ND * ND * G::NDOF, &bars[1]);
+  };
+  auto issue_ja_dep = [=](const PipeTile<T>& tt) {
+    const int e0 = tt.e0, nel = min(EPB, tt.md.E - e0);
+    const MeshDims& md = tt.md;
 #pragma unroll
     for (int n = 0; n < ND; ++n) {
       // the tile's own upper faces along n are consecutive in the face array; the lower neighbours' mostly are
@@ -247,17 +252,30 @@ __device__ __forceinline__ void pipe_tiles(const Src& src, const OpTable<N, T>& 
     }
     if constexpr (!S::kBulk) cp_async_arrive(&bars[1]);
   };
-  auto issue_c = [=](const PipeTile<T>& tt) {  // 1/J (curvilinear meshes) and the stage update's operands; may be empty
+  // The phase-C group (may be empty), likewise: 1/J (curvilinear meshes) with the group's byte count, then the
+  // stage update's operands.
+  auto issue_c_geo = [=](const PipeTile<T>& tt) {
     const int e0 = tt.e0, nel = min(EPB, tt.md.E - e0);
-    const int nin = nel * G::NV * G::NDOF;
     if constexpr (S::kBulk)
       mbar_expect_tx(&bars[2], (has_ja ? (unsigned)(nel * S::kInvJ) : 0u) + (kFused ? (unsigned)(nel * S::kIn) : 0u) +
                                    (need_y ? (unsigned)(nel * S::kIn) : 0u));
-    const size_t so = (size_t)e0 * G::NV * G::NDOF;
     if (has_ja) copy(s_ij, tt.invJ + (size_t)e0 * G::NDOF, nel * G::NDOF, &bars[2]);
+  };
+  auto issue_c_dep = [=](const PipeTile<T>& tt) {
+    const int e0 = tt.e0, nel = min(EPB, tt.md.E - e0);
+    const int nin = nel * G::NV * G::NDOF;
+    const size_t so = (size_t)e0 * G::NV * G::NDOF;
     if (kFused) copy(s_eu, epi.u + so, nin, &bars[2]);
     if (need_y) copy(s_ey, gy + so, nin, &bars[2]);
     if constexpr (!S::kBulk) cp_async_arrive(&bars[2]);
+  };
+  auto issue_ja = [=](const PipeTile<T>& tt) {
+    issue_ja_geo(tt);
+    issue_ja_dep(tt);
+  };
+  auto issue_c = [=](const PipeTile<T>& tt) {
+    issue_c_geo(tt);
+    issue_c_dep(tt);
   };
   // the threads that issue copies: thread 0 in bulk mode, all in cp.async mode
   const bool issuer = S::kBulk ? tid == 0 : true;
@@ -269,11 +287,19 @@ __device__ __forceinline__ void pipe_tiles(const Src& src, const OpTable<N, T>& 
   }
   __syncthreads();
   int t = s_tile[0];
+  // The first tile: its geometry is copied before the wait for the kernels before this one in the stream (with a
+  // programmatic launch, while the interface kernel's writes are made visible), its state and fluxes after it.
+  if (issuer && src.valid(t)) {
+    const PipeTile<T> ft = src.tile(t);
+    issue_ja_geo(ft);
+    issue_c_geo(ft);
+  }
+  pdl_wait();
   if (issuer && src.valid(t)) {
     const PipeTile<T> ft = src.tile(t);
     issue_in(ft);
-    issue_ja(ft);
-    issue_c(ft);
+    issue_ja_dep(ft);
+    issue_c_dep(ft);
     fill_in = fill_ja = fill_c = 1;
   }
   if (tid == 0 && src.valid(t)) s_ok[0] = mbar_wait_bounded(&bars[0], 0u) ? 1 : 0;

@@ -33,7 +33,9 @@ LOGMEANS = {"rcp": DG_LOGMEAN_SHARED_RCP, "alg": DG_LOGMEAN_ALG, "alg_poly": DG_
 DG_NODES_LGL, DG_NODES_GAUSS = 0, 1
 NODES = {"lgl": DG_NODES_LGL, "gauss": DG_NODES_GAUSS}
 DG_STAGING_AUTO, DG_STAGING_DIRECT, DG_STAGING_PIPELINED = 0, 1, 2
+DG_LAUNCH_OVERLAP, DG_LAUNCH_SERIAL = 0, 1
 STAGINGS = {"auto": DG_STAGING_AUTO, "direct": DG_STAGING_DIRECT, "pipelined": DG_STAGING_PIPELINED}
+LAUNCHES = {"overlap": DG_LAUNCH_OVERLAP, "serial": DG_LAUNCH_SERIAL}
 DG_RK4_CLASSIC, DG_LSRK45_CK = 0, 1
 KERNEL_VOLUME, KERNEL_INTERFACE, KERNEL_PROJECT = 0, 1, 2
 
@@ -57,7 +59,7 @@ class DgMetrics(ctypes.Structure):
 class DgOpts(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("volume_flux", ctypes.c_int), ("surface_flux", ctypes.c_int),
                 ("precision", ctypes.c_int), ("precompute_logs", ctypes.c_int), ("logmean", ctypes.c_int),
-                ("nodes", ctypes.c_int), ("staging", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("nodes", ctypes.c_int), ("staging", ctypes.c_int), ("launch", ctypes.c_int)]
 
 
 class DgInfo(ctypes.Structure):
@@ -142,12 +144,15 @@ class DG:
     staging: "pipelined" (the volume kernel copies tiles with asynchronous copies that overlap computation),
     "direct" (one CTA per tile, loads by its threads) or "auto" (pipelined on meshes with enough tiles per CTA,
     except FP32 at p = 2); the same values either way.
+    launch: "overlap" (each interface and pipelined volume kernel is scheduled ahead and starts as the kernel
+    before it ends, waiting for its writes before reading them) or "serial" (ordinary launches); the same values.
     """
 
     def __init__(self, ndims: int, nelem, polydeg: int, lo=None, hi=None, mapping: str = "affine", amp: float = 0.0,
                  node_xyz=None, Ja=None, J=None, gamma: float = 1.4, surface: str = "llf",
                  precision: str = "fp64", flux: str = "ranocha", logmean: str = "rcp",
-                 precompute_logs: bool = False, nodes: str = "lgl", staging: str = "auto"):
+                 precompute_logs: bool = False, nodes: str = "lgl", staging: str = "auto",
+                 launch: str = "overlap"):
         mesh = DgMesh()
         mesh.ndims = ndims
         ne = list(nelem) + [1] * (3 - len(nelem))
@@ -177,6 +182,7 @@ class DG:
         opts.precompute_logs = 1 if precompute_logs else 0
         opts.nodes = NODES[nodes]
         opts.staging = STAGINGS[staging]
+        opts.launch = LAUNCHES[launch]
         opts.surface_flux = {"ec": DG_SURF_EC, "llf": DG_SURF_EC_LLF}[surface]
         opts.precision = {"fp64": DG_FP64, "fp32": DG_FP32}[precision]
         ctx = ctypes.c_void_p()

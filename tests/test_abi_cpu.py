@@ -54,9 +54,11 @@ def test_argument_errors_without_gpu(built):
     opts.gamma = 1.0
     assert dg.dg_init(ctypes.byref(ctx), ctypes.byref(mesh), 3, None, ctypes.byref(opts)) == dg.DG_ERR_ARG
     opts.gamma = 1.4
-    opts.reserved[0] = 1
+    opts.launch = 2
     assert dg.dg_init(ctypes.byref(ctx), ctypes.byref(mesh), 3, None, ctypes.byref(opts)) == dg.DG_ERR_ARG
-    opts.reserved[0] = 0
+    opts.launch = -1
+    assert dg.dg_init(ctypes.byref(ctx), ctypes.byref(mesh), 3, None, ctypes.byref(opts)) == dg.DG_ERR_ARG
+    opts.launch = dg.DG_LAUNCH_SERIAL
     opts.staging = 3
     assert dg.dg_init(ctypes.byref(ctx), ctypes.byref(mesh), 3, None, ctypes.byref(opts)) == dg.DG_ERR_ARG
     opts.staging = dg.DG_STAGING_DIRECT

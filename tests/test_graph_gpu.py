@@ -134,3 +134,38 @@ def test_host_buffer_entry_points_match_device_calls(dgmod):
     assert ctx.check_status() == dgmod.DG_OK
     with pytest.raises(TypeError):
         ctx.rhs_host(ud, duh)  # a device tensor is not a host state
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("staging,p,nelem", [("pipelined", 3, [16, 16, 16]), ("direct", 3, [4, 3, 5]),
+                                             ("pipelined", 2, [9, 8, 10])])
+def test_overlapped_launches_equal_serial_launches(dgmod, precision, staging, p, nelem):
+    # DG_LAUNCH_OVERLAP schedules each interface and pipelined volume kernel ahead, as a programmatic dependent of
+    # the kernel before it; reads of the state, the fluxes and the RK operands wait for that kernel's writes.
+    # Back-to-back dg_rhs calls on different
+    # states (the second interface kernel rewrites the flux buffer the first volume kernel reads) and RK steps
+    # (each stage reads what the previous one wrote) must equal ordinary launches bit for bit.
+    import torch
+    from paper_2112_10517_gb300 import inputs
+    res = {}
+    for launch in ("overlap", "serial"):
+        ctx = dgmod.DG(3, nelem, p, lo=[-math.pi] * 3, hi=[math.pi] * 3, mapping="sine", amp=0.1, surface="llf",
+                       precision=precision, staging=staging, launch=launch)
+        u0 = inputs.taylor_green(ctx.node_coords(), mach=0.3)
+        ua = torch.from_numpy(u0).cuda()
+        ub = (ua * 1.01).contiguous()
+        torch.cuda.synchronize()
+        dus = [torch.empty_like(ua) for _ in range(4)]
+        for k in range(4):
+            ctx.rhs(ua if k % 2 == 0 else ub, du=dus[k])
+        u = ua.clone()
+        scratch = torch.empty((2,) + ctx.shape, dtype=torch.float64, device="cuda")
+        for scheme in (0, 1, 0):
+            ctx.step(u, 0.002, scheme=scheme, scratch=scratch)
+        torch.cuda.synchronize()
+        assert ctx.check_status() == dgmod.DG_OK
+        res[launch] = [d.cpu().numpy() for d in dus] + [u.cpu().numpy()]
+    for a, b in zip(res["overlap"], res["serial"]):
+        np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(res["overlap"][0], res["overlap"][2])
+    np.testing.assert_array_equal(res["overlap"][1], res["overlap"][3])
