@@ -62,7 +62,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (debug runs)")
     ap.add_argument("--only", default="", help="comma-separated subset of fp64_16,fp32_16,fp64_32,fp32_32, "
-                    "variants, ablation, gauss, staging, launch, batch (profiling runs; prints one line per configuration instead of the "
+                    "variants, ablation, gauss, staging, launch, rhs, batch (profiling runs; prints one line per configuration instead of the "
                     "contract line)")
     return ap.parse_args()
 
@@ -524,6 +524,58 @@ def run_staging(args, dev):
     return out
 
 
+def run_rhs_pid(args, dev, runs: int = 5, calls: int = 20):
+    """The PID of one dg_rhs evaluation (Sec. 4.1, Def. PID: time of one RHS / #DOF), mean and standard deviation
+    over `runs` runs, each the mean of `calls` calls with L2 flushed before every call and CUDA events around the
+    call alone; with the volume and interface kernels' own event times per DOF. Taylor-Green vortex, p = 3,
+    sine-perturbed mesh at 16^3 and 32^3 elements, FP64 and FP32."""
+    import statistics
+    import torch
+    from paper_2112_10517_gb300 import dg
+    lo, hi = [-math.pi] * 3, [math.pi] * 3
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for precision, ne in (("fp64", NELEM[0]), ("fp32", NELEM[0]), ("fp64", NELEM_LARGE[0]), ("fp32", NELEM_LARGE[0])):
+        ctx = dg.DG(3, [ne] * 3, POLYDEG, lo=lo, hi=hi, mapping="sine", amp=AMP, surface="llf", precision=precision)
+        u = torch.from_numpy(make_state(ctx)).to(dev)
+        du = torch.empty_like(u)
+        for _ in range(max(args.warmup, 3)):
+            ctx.rhs(u, du)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(calls)]
+        means = []
+        for _ in range(runs):
+            for a, b in ev:
+                flush.zero_()
+                a.record(stream)
+                ctx.rhs(u, du)
+                b.record(stream)
+            torch.cuda.synchronize()
+            means.append(sum(a.elapsed_time(b) for a, b in ev) / calls)
+        # the kernels' own times: a separate pass with events around each kernel
+        ctx.profile(True)
+        for _ in range(calls):
+            flush.zero_()
+            ctx.rhs(u, du)
+        torch.cuda.synchronize()
+        vol_ms, vol_n = ctx.profile_read(dg.KERNEL_VOLUME)
+        ifc_ms, ifc_n = ctx.profile_read(dg.KERNEL_INTERFACE)
+        ctx.profile(False)
+        if ctx.check_status() != dg.DG_OK:
+            raise RuntimeError("non-physical state in the RHS runs")
+        nd = ctx.ndofs
+        out["%s_%d" % (precision, ne)] = {
+            "pid_ns": statistics.mean(means) * 1e6 / nd, "pid_std_ns": statistics.pstdev(means) * 1e6 / nd,
+            "volume_pid_ns": vol_ms / max(vol_n, 1) * 1e6 / nd, "interface_pid_ns": ifc_ms / max(ifc_n, 1) * 1e6 / nd}
+        del ctx, u, du
+    out["workload"] = ("dg_rhs (interface kernel + volume kernel storing du) on the Taylor-Green vortex, sine-perturbed "
+                       "mesh, p = 3 at 16^3 and 32^3 elements; %d runs of %d calls, L2 flushed before every call; "
+                       "pid_std_ns over the runs' means; volume/interface_pid_ns from the kernels' own events"
+                       % (runs, calls))
+    return out
+
+
 def run_launch_modes(args, dev):
     """The RK4 step (dg_step) with the interface and pipelined volume kernels launched as programmatic dependents
     of the kernel before them (overlap, the default) and as ordinary launches (serial): eager steps without
@@ -833,6 +885,7 @@ def main():
     gauss = run_gauss(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
     staging = run_staging(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
     launch_modes = run_launch_modes(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
+    rhs_pid = run_rhs_pid(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
     if rank == 0 and args.only:
         for label, res in results.items():
             print(json.dumps({"configuration": label, "pid_ns": res["pid_ns"], "noprof_pid_ns": res["noprof_pid_ns"],
@@ -849,6 +902,8 @@ def main():
             print(json.dumps({"configuration": "gauss", "result": run_gauss(args, dev)}), flush=True)
         if "staging" in only:
             print(json.dumps({"configuration": "staging", "result": run_staging(args, dev)}), flush=True)
+        if "rhs" in only:
+            print(json.dumps({"configuration": "rhs", "result": run_rhs_pid(args, dev)}), flush=True)
         if "launch" in only:
             print(json.dumps({"configuration": "launch", "result": run_launch_modes(args, dev)}), flush=True)
         if "batch" in only:
@@ -913,6 +968,7 @@ def main():
             "logmean_ablation": ablation,
             "gauss_collocation": gauss,
             "tile_staging": staging,
+            "rhs_pid": rhs_pid,
             "launch_modes": launch_modes,
             "alu_peaks_measured_tflops": {k: (v / 1e12 if v else None) for k, v in peaks_alu.items()},
         }
