@@ -17,6 +17,7 @@ workload, one oracle RHS evaluation per step.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import math
@@ -92,6 +93,7 @@ class ClockSampler:
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        time.sleep(0.3)  # nvidia-smi's first sample
 
     def _read(self):
         for line in self.proc.stdout:
@@ -122,7 +124,85 @@ class ClockSampler:
                 if val.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi -lms 200 around the timed region"}
+
+
+class NvmlClockSampler:
+    """SM clock and clock-event reasons read through NVML (libnvidia-ml, ctypes) every 5 ms from a thread while the
+    timed region runs (a region of tens of milliseconds sees no nvidia-smi sample at its 200 ms period). Reads only.
+    The device is found by the UUID CUDA reports for it."""
+    NVML_CLOCK_SM = 1
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, lib, handle):
+        self.lib, self.handle = lib, handle
+        self.samples = []
+        self.thread = None
+        self.stop_event = threading.Event()
+        self.reasons_fn = None
+        for name in ("nvmlDeviceGetCurrentClocksEventReasons", "nvmlDeviceGetCurrentClocksThrottleReasons"):
+            fn = getattr(lib, name, None)
+            if fn is not None:
+                fn.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_ulonglong)]
+                fn.restype = ctypes.c_int
+                self.reasons_fn = fn
+                break
+        lib.nvmlDeviceGetClockInfo.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_uint)]
+        lib.nvmlDeviceGetClockInfo.restype = ctypes.c_int
+        lib.nvmlDeviceGetMaxClockInfo.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_uint)]
+        lib.nvmlDeviceGetMaxClockInfo.restype = ctypes.c_int
+        mx = ctypes.c_uint(0)
+        self.max_mhz = mx.value if lib.nvmlDeviceGetMaxClockInfo(handle, self.NVML_CLOCK_SM, ctypes.byref(mx)) == 0 \
+            else None
+
+    @classmethod
+    def open(cls, device):
+        """A sampler for the torch device, or None when NVML or the device cannot be had."""
+        try:
+            import torch
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            lib.nvmlInit_v2.restype = ctypes.c_int
+            if lib.nvmlInit_v2() != 0:
+                return None
+            handle = ctypes.c_void_p()
+            uuid = str(torch.cuda.get_device_properties(device).uuid)
+            uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+            lib.nvmlDeviceGetHandleByUUID.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]
+            lib.nvmlDeviceGetHandleByUUID.restype = ctypes.c_int
+            if lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(handle)) != 0 or not handle.value:
+                return None
+            return cls(lib, handle)
+        except (OSError, AttributeError, RuntimeError, ValueError):
+            return None
+
+    def _poll(self):
+        clk, rs = ctypes.c_uint(0), ctypes.c_ulonglong(0)
+        while not self.stop_event.is_set():
+            if self.lib.nvmlDeviceGetClockInfo(self.handle, self.NVML_CLOCK_SM, ctypes.byref(clk)) == 0:
+                bits = rs.value if self.reasons_fn is not None and self.reasons_fn(self.handle, ctypes.byref(rs)) == 0 \
+                    else 0
+                self.samples.append((clk.value, bits))
+            time.sleep(0.005)
+
+    def start(self):
+        self.thread = threading.Thread(target=self._poll, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        self.stop_event.set()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = [c for c, _ in self.samples]
+        reasons = sorted({name for _, bits in self.samples for bit, name in self.REASONS.items() if bits & bit})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.max_mhz, "reasons": reasons,
+                "samples": len(sm), "source": "NVML, every 5 ms during the timed region"}
+
+
+def clock_sampler(local_rank: int, device):
+    """NVML sampling during the timed region where NVML is available, else nvidia-smi at its 200 ms period."""
+    s = NvmlClockSampler.open(device)
+    return s if s is not None else ClockSampler(local_rank)
 
 
 # ------------------------------------------------------------------------------------------------------
@@ -248,13 +328,12 @@ def run_ours(args, rank, world, local_rank):
             raise RuntimeError("non-physical state during warm-up")
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        clocks = ClockSampler(local_rank) if main else None
+        clocks = clock_sampler(local_rank, dev) if main else None
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
         if clocks:
             clocks.start()
-            time.sleep(0.3)
         # CUDA events around every third launch of the dominant (volume) kernel only: the roofline's kernel time
         # (3 is coprime to the 4 stages per step, so every stage is sampled); the interface kernel is timed in a
         # second pass below, so that the timed region carries no more events than needed
