@@ -428,6 +428,30 @@ def test_pressure_equilibrium(nd, nelem, p, curved):
         np.testing.assert_allclose(du[:, -1], 0.5 * np.dot(v, v) * du[:, 0], rtol=0, atol=1e-12 * scale)
 
 
+@pytest.mark.parametrize("nd,nelem,p", [(2, [4, 3], 3), (3, [3, 2, 3], 3)])
+@pytest.mark.parametrize("curved", [False, True])
+def test_mass_and_momentum_rhs_ignore_a_constant_pressure_shift(nd, nelem, p, curved):
+    # Ranocha's mass flux rho_log {{v}}.n does not involve p and its momentum flux f_rho {{v}} + {{p}} n changes by
+    # dp {{n}} when p -> p + dp: with the EC surface flux that part of the RHS is dp times the free-stream
+    # residual (volume terms and lifted surface terms of a constant, cancelled by the discrete metric identities),
+    # so the mass and momentum RHS stay the same up to rounding. The energy RHS changes (p {{v.n}} terms), and the
+    # LLF dissipation changes with the sound speed: both must differ (controls).
+    xyz, Ja, J = mesh(nd, nelem, p, curved)
+    u = inputs.smooth_random(xyz, seed=21) + 0.01 * inputs.random_state(xyz, seed=22)  # jumps at interfaces
+    dp = 25.0
+    v = u.copy()
+    v[:, -1] += dp / (G - 1.0)  # E = p/(gamma - 1) + rho |v|^2 / 2: p -> p + dp at fixed rho, v
+    du = orc.rhs(nd, p, nelem, Ja, J, u, llf=False)
+    dv = orc.rhs(nd, p, nelem, Ja, J, v, llf=False)
+    scale = orc.rhs(nd, p, nelem, Ja, J, v, llf=False, scale=True)
+    for c in range(nd + 1):
+        assert np.max(np.abs(dv[:, c] - du[:, c])) <= 1e-13 * np.max(scale[:, c]), c
+    assert np.max(np.abs(dv[:, -1] - du[:, -1])) > 1e-6 * np.max(scale[:, -1])
+    du = orc.rhs(nd, p, nelem, Ja, J, u, llf=True)
+    dv = orc.rhs(nd, p, nelem, Ja, J, v, llf=True)
+    assert np.max(np.abs(dv[:, 0] - du[:, 0])) > 1e-6 * np.max(scale[:, 0])
+
+
 def test_scale_mode_bounds_the_rhs():
     # scale = (1/J) sum |terms| >= |(1/J) sum terms| = |du| at every node (triangle inequality), and it is
     # equal for a single term: free stream on an affine mesh makes every term cancel against another one
