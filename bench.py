@@ -206,12 +206,12 @@ def clock_sampler(local_rank: int, device):
 
 
 # ------------------------------------------------------------------------------------------------------
-def source_digest() -> str:
+def source_digest(root: str = ROOT) -> str:
     """sha256 (first 16 hex digits) of the volume kernel's sources with comments and blank lines removed: it changes
     with the compiled code, not with its comments."""
     h = hashlib.sha256()
     for f in ("dgmath.cuh", "kernels.cuh", "volume.cu", "volume_impl.cuh", "volume_inst.cu", "volume_pipe.cuh"):
-        with open(os.path.join(ROOT, "paper_2112_10517_gb300", "csrc", f)) as fh:
+        with open(os.path.join(root, "paper_2112_10517_gb300", "csrc", f)) as fh:
             for line in fh:
                 code = line.split("//", 1)[0].rstrip()
                 if code:
@@ -219,15 +219,15 @@ def source_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def committed_traffic(precision: str, ndofs: int):
+def committed_traffic(precision: str, ndofs: int, root: str = ROOT):
     """DRAM bytes per volume-kernel launch: bytes per DOF from the committed ncu capture (32^3 case, inputs larger
     than L2) times the DOF of this launch; None unless the capture was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "volume_kernel_tgv32_p3.md")
+    path = os.path.join(root, "profiles", "volume_kernel_tgv32_p3.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m = re.search(r"traffic_bytes_per_dof_%s:\s*([0-9.eE+]+)\s+source_digest:\s*([0-9a-f]+)" % precision, text)
-    if not m or m.group(2) != source_digest():
+    if not m or m.group(2) != source_digest(root):
         return None
     return float(m.group(1)) * ndofs
 
