@@ -5,7 +5,6 @@ import os
 import shutil
 import time
 
-import pytest
 
 import bench
 
