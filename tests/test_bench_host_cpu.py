@@ -5,7 +5,6 @@ import os
 import shutil
 import time
 
-
 import bench
 
 CSRC = ("dgmath.cuh", "kernels.cuh", "volume.cu", "volume_impl.cuh", "volume_inst.cu", "volume_pipe.cuh")
