@@ -168,14 +168,16 @@ dg_status dg_init(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metri
 
 /* du = RHS(u) (Eq. fluxdiff-SBP-opDsplit). u, du: device [E][nvar][Nd], distinct, not overlapping.
    t is accepted for interface completeness and unused (autonomous, periodic problem). u is not modified.
-   Queues 2 kernels (interface flux, then volume + surface lift + Jacobian) on `stream`. */
+   Queues 2 kernels (interface flux, then volume + surface lift + Jacobian) on `stream`, by default as programmatic
+   dependent launches (dg_opts.launch). */
 dg_status dg_rhs(dg_ctx* ctx, const double* u, double* du, double t, dg_stream_t stream);
 
 /* One explicit time step u <- u + dt * (...) of the low-storage Runge-Kutta method `scheme` (Sec. 4.1):
    DG_RK4_CLASSIC  classical four-stage RK4 in low-storage form; scratch = 2 state arrays (2*state_len);
    DG_LSRK45_CK    five-stage fourth-order 2N method of Carpenter and Kennedy; scratch = 1 state array.
    u and scratch are device memory, not overlapping; scratch contents on entry are ignored. Each stage queues
-   2 kernels: the interface fluxes, then the volume term whose epilogue applies the stage update in FP64. */
+   2 kernels: the interface fluxes, then the volume term whose epilogue applies the stage update in FP64 (launched
+   as in dg_rhs). */
 dg_status dg_step(dg_ctx* ctx, double* u, double* scratch, double t, double dt, int scheme, dg_stream_t stream);
 
 /* The same with the state in host memory: queue on `stream` the host->device copy of u_host, dg_step (or dg_rhs)
