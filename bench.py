@@ -22,7 +22,6 @@ import hashlib
 import json
 import math
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -39,6 +38,7 @@ AMP = 0.1
 STAGES = 4  # classical RK4, low-storage form (per stage: interface kernel + volume kernel with fused update)
 METRIC = "PID (ns per DOF per RHS eval), FP64 vs FP32, 1xGB300, with roofline fraction"
 WORKLOAD = "3D Euler inviscid Taylor-Green vortex M=0.1, curvilinear periodic [-pi,pi]^3 16^3 hex, p=3 (262,144 DOF)"
+WORKLOAD_SHORT = "TGV M=0.1, curved periodic 16^3 hex, p=3 (262,144 DOF), RK4 step, Ranocha+LLF"
 L2_FLUSH_BYTES = 512 << 20
 
 # Algorithmic FLOPs of the volume kernel per DOF (3D, p = 3, series branch of both logarithmic means, a
@@ -55,7 +55,7 @@ VOLUME_BYTES_PER_DOF_F32 = 40 + 36 + 8 + 1.5 * 5 * 4 + 130
 NELEM_LARGE = [32, 32, 32]  # the precision workload: 2,097,152 DOF, inputs larger than L2
 
 
-def parse_args():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -63,9 +63,12 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (debug runs)")
     ap.add_argument("--only", default="", help="comma-separated subset of fp64_16,fp32_16,fp64_32,fp32_32, "
-                    "variants, ablation, gauss, staging, launch, rhs, batch (profiling runs; prints one line per configuration instead of the "
-                    "contract line)")
-    return ap.parse_args()
+                    "variants, ablation, gauss, staging, launch, rhs, batch, diff (profiling runs; prints one line per "
+                    "configuration instead of the contract line)")
+    ap.add_argument("--extras", default="", help="comma-separated sub-benchmarks to run before the contract line "
+                    "(%s, or all); each prints its own line" % ",".join(EXTRAS))
+    ap.add_argument("--details", default="", help="also write every result of the run to this JSON file")
+    return ap.parse_args(argv)
 
 
 # ------------------------------------------------------------------------------------------------------
@@ -219,34 +222,39 @@ def source_digest(root: str = ROOT) -> str:
     return h.hexdigest()[:16]
 
 
+PROFILE_JSON = os.path.join("profiles", "volume_kernel_tgv32_p3.json")
+
+
+def committed_capture(root: str = ROOT):
+    """The keyed figures of the committed ncu capture of the volume kernel (32^3, p = 3; inputs larger than L2), or
+    None unless the capture was taken on the current kernel source (its source digest matches)."""
+    path = os.path.join(root, PROFILE_JSON)
+    if not os.path.exists(path):
+        return None
+    try:
+        cap = json.load(open(path))
+    except ValueError:
+        return None
+    return cap if cap.get("source_digest") == source_digest(root) else None
+
+
 def committed_traffic(precision: str, ndofs: int, root: str = ROOT):
-    """DRAM bytes per volume-kernel launch: bytes per DOF from the committed ncu capture (32^3 case, inputs larger
-    than L2) times the DOF of this launch; None unless the capture was taken on the current kernel source."""
-    path = os.path.join(root, "profiles", "volume_kernel_tgv32_p3.md")
-    if not os.path.exists(path):
+    """DRAM bytes per volume-kernel launch: bytes per DOF from the committed capture times the DOF of this launch;
+    None unless the capture was taken on the current kernel source."""
+    cap = committed_capture(root)
+    if cap is None or precision not in cap:
         return None
-    text = open(path).read()
-    m = re.search(r"traffic_bytes_per_dof_%s:\s*([0-9.eE+]+)\s+source_digest:\s*([0-9a-f]+)" % precision, text)
-    if not m or m.group(2) != source_digest(root):
-        return None
-    return float(m.group(1)) * ndofs
+    return float(cap[precision]["traffic_bytes_per_dof"]) * ndofs
 
 
-def committed_utilization(precision: str):
-    """The ncu view of the same kernel (32^3 capture): FP64-pipe activity and DRAM throughput as fractions of
-    their peaks; None unless the capture was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "volume_kernel_tgv32_p3.md")
-    if not os.path.exists(path):
+def committed_utilization(precision: str, root: str = ROOT):
+    """The ncu view of the same kernel: FP64-pipe activity and DRAM throughput as fractions of their peaks; None
+    unless the capture was taken on the current kernel source."""
+    cap = committed_capture(root)
+    if cap is None or precision not in cap:
         return None
-    text = open(path).read()
-    out = {}
-    for key in ("fp64_pipe_active", "dram_throughput"):
-        m = re.search(r"ncu_%s_%s:\s*([0-9.eE+]+)\s+source_digest:\s*([0-9a-f]+)" % (key, precision), text)
-        if not m or m.group(2) != source_digest():
-            return None
-        out[key] = float(m.group(1))
-    out["capture"] = "profiles/volume_kernel_tgv32_p3.md (32^3, p = 3)"
-    return out
+    return {"fp64_pipe_active": cap[precision]["fp64_pipe_active"],
+            "dram_throughput": cap[precision]["dram_throughput"], "capture": PROFILE_JSON}
 
 
 def measured_peaks():
@@ -257,6 +265,18 @@ def measured_peaks():
         except ValueError:
             pass
     return {}
+
+
+# HBM bandwidth when MEASURED_PEAKS.json is absent: an earlier STREAM-style copy on a GB300 of this pool
+HBM_FALLBACK_GBS = 6800.0
+
+
+def hbm_peak():
+    """(GB/s, source): the measured copy bandwidth of MEASURED_PEAKS.json, else the fallback figure."""
+    v = measured_peaks().get("hbm_gbs")
+    if isinstance(v, (int, float)) and v > 0:
+        return float(v), "measured hbm_gbs"
+    return HBM_FALLBACK_GBS, "fallback 6.8 TB/s"
 
 
 def alu_peaks():
@@ -426,17 +446,17 @@ def run_ours(args, rank, world, local_rank):
                                "peak": peak / 1e12 if peak else None, "unit": "TFLOP/s",
                                "frac": achieved / (peak / 1e12) if peak else None,
                                "traffic": committed_traffic("fp64", ndofs),
-                               "peak_source": "measured live: libdgpeaks fp64 FMA chain x 2 flop",
+                               "peak_src": "measured FP64 FMA x2 (libdgpeaks)",
                                "algorithmic_flops_per_launch": vflops,
                                "ncu_utilization": committed_utilization("fp64")}
         else:
-            hbm = measured_peaks().get("hbm_gbs", 6800.0)
+            hbm, hbm_src = hbm_peak()
             vbytes = VOLUME_BYTES_PER_DOF_F32 * ndofs
             achieved = vbytes / vol_avg_s / 1e9
             peak32 = peaks_alu.get("fp32")
             res["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                                "frac": achieved / hbm, "traffic": committed_traffic("fp32", ndofs),
-                               "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                               "peak_src": hbm_src,
                                "algorithmic_bytes_per_launch": vbytes,
                                "ncu_utilization": committed_utilization("fp32"),
                                "alu_frac_of_fp32_peak": (vflops / vol_avg_s) / peak32 if peak32 else None}
@@ -944,8 +964,70 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def main():
-    args = parse_args()
+# The sub-benchmarks beyond the headline (--extras): each prints its own line before the contract line.
+EXTRAS = ("batch", "diff", "variants", "ablation", "gauss", "staging", "launch", "rhs")
+CONTRACT_LINE_MAX_BYTES = 1200
+
+
+def sig(x, digits: int = 4):
+    """x rounded to `digits` significant digits (None stays None): keeps the contract line short."""
+    if x is None or not isinstance(x, float) or x == 0.0 or not math.isfinite(x):
+        return x
+    return round(x, digits - 1 - int(math.floor(math.log10(abs(x)))))
+
+
+def contract_line(args, world: int, results: dict, cpu) -> dict:
+    """The one JSON line the benchmark contract asks for, printed last: the FP64 headline (16^3, p = 3 RK4 step),
+    its roofline, the CPU oracle, the end-to-end figure through the host-state entry point, clocks, and the FP32
+    mode and the 32^3 precision workload as single numbers. Everything else goes to earlier lines."""
+    r64, r32 = results["fp64_16"], results.get("fp32_16")
+    b64, b32 = results.get("fp64_32"), results.get("fp32_32")
+    rf = r64["roofline"]
+    clk = r64.get("clocks") or {}
+    line = {
+        "metric": METRIC, "value": sig(r64["pid_ns"]), "value_std": sig(r64["pid_std_ns"], 2), "unit": "ns/DOF/RHS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sig(r64["ms_per_step"]),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_SHORT, "l2": "flushed each step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": rf["bound"], "achieved": sig(rf["achieved"]), "peak": sig(rf["peak"]),
+                     "unit": rf["unit"], "frac": sig(rf["frac"], 3), "traffic": sig(rf["traffic"]),
+                     "peak_src": rf["peak_src"]},
+        "cpu_baseline": cpu,
+        "e2e": {"value": sig(r64.get("e2e_pid_ns")), "unit": "ns/DOF/RHS",
+                "h2d_bytes_per_step": r64.get("e2e_bytes"), "d2h_bytes_per_step": r64.get("e2e_bytes")},
+        "gpu_launches": r64["launches"],
+        "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"), "reasons": clk.get("reasons")},
+    }
+    if r32:
+        line["fp32"] = {"value": sig(r32["pid_ns"]), "ms_per_step": sig(r32["ms_per_step"]),
+                        "hbm_frac": sig(r32["roofline"]["frac"], 3)}
+    if b64 and b32:
+        line["p3_32cubed"] = {"fp64": sig(b64["pid_ns"]), "fp32": sig(b32["pid_ns"]),
+                              "fp64_frac": sig(b64["roofline"]["frac"], 3), "fp32_frac": sig(b32["roofline"]["frac"], 3)}
+    return line
+
+
+def compact_cpu_baseline(cpu):
+    """The cpu_baseline object of the contract line (the full record goes to a detail line)."""
+    if cpu is None:
+        return None
+    out = {"value": sig(cpu["value"]), "unit": cpu["unit"], "cores": cpu["cores"], "kind": cpu["kind"],
+           "sample": "full 16^3 mesh RHS x%d, 1 core" % cpu["reps"]}
+    if cpu.get("all_cores"):
+        out["all_cores_value"] = sig(cpu["all_cores"]["value"])
+        out["all_cores"] = cpu["all_cores"]["cores"]
+    return out
+
+
+def emit(name: str, payload, sink: dict):
+    """One detail line (printed before the contract line) and its entry in the details file."""
+    sink[name] = payload
+    print(json.dumps({"bench_detail": name, "result": payload}), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -957,101 +1039,44 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
     results, peaks_alu = run_ours(args, rank, world, local_rank)
-    batch = run_batch(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
-    diff = run_diff_and_scale(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
-    variants = run_variants(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
-    ablation = run_logmean_ablation(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
-    gauss = run_gauss(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
-    staging = run_staging(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
-    launch_modes = run_launch_modes(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
-    rhs_pid = run_rhs_pid(args, torch.device("cuda", local_rank)) if rank == 0 and not args.only else None
+    dev = torch.device("cuda", local_rank)
+    runners = {"batch": run_batch, "diff": run_diff_and_scale, "variants": run_variants,
+               "ablation": run_logmean_ablation, "gauss": run_gauss, "staging": run_staging,
+               "launch": run_launch_modes, "rhs": run_rhs_pid}
     if rank == 0 and args.only:
         for label, res in results.items():
             print(json.dumps({"configuration": label, "pid_ns": res["pid_ns"], "noprof_pid_ns": res["noprof_pid_ns"],
                               "graph_pid_ns": res["graph_pid_ns"], "ms_per_step": res["ms_per_step"],
                               "volume_ms": res["volume_ms_avg"], "interface_ms": res["interface_ms_avg"]}),
                   flush=True)
-        only = args.only.split(",")
-        dev = torch.device("cuda", local_rank)
-        if "variants" in only:
-            print(json.dumps({"configuration": "variants", "result": run_variants(args, dev)}), flush=True)
-        if "ablation" in only:
-            print(json.dumps({"configuration": "ablation", "result": run_logmean_ablation(args, dev)}), flush=True)
-        if "gauss" in only:
-            print(json.dumps({"configuration": "gauss", "result": run_gauss(args, dev)}), flush=True)
-        if "staging" in only:
-            print(json.dumps({"configuration": "staging", "result": run_staging(args, dev)}), flush=True)
-        if "rhs" in only:
-            print(json.dumps({"configuration": "rhs", "result": run_rhs_pid(args, dev)}), flush=True)
-        if "launch" in only:
-            print(json.dumps({"configuration": "launch", "result": run_launch_modes(args, dev)}), flush=True)
-        if "batch" in only:
-            print(json.dumps({"configuration": "batch", "result": run_batch(args, dev)}), flush=True)
+        for name in args.only.split(","):
+            if name in runners:
+                print(json.dumps({"configuration": name, "result": runners[name](args, dev)}), flush=True)
     elif rank == 0:
-        r64, r32 = results["fp64_16"], results["fp32_16"]
-        b64, b32 = results["fp64_32"], results["fp32_32"]
+        details = {}
+        for label, res in results.items():
+            emit(label, res, details)
+        emit("alu_peaks_measured_tflops", {k: (v / 1e12 if v else None) for k, v in peaks_alu.items()}, details)
+        wanted = EXTRAS if args.extras == "all" else [x for x in args.extras.split(",") if x]
+        for name in wanted:
+            if name not in runners:
+                raise SystemExit("unknown --extras entry %r (choose from %s)" % (name, ", ".join(EXTRAS)))
+            emit(name, runners[name](args, dev), details)
         cpu = None
         if not args.no_cpu_baseline:
             pid_cpu, reps, nd = oracle_pid(10.0)
-            cpu = {"value": pid_cpu, "unit": "ns/DOF/RHS", "cores": 1, "kind": "oracle",
+            cpu = {"value": pid_cpu, "unit": "ns/DOF/RHS", "cores": 1, "kind": "oracle", "reps": reps,
                    "sample": "%d oracle RHS evaluations of the full 16^3 p=3 mesh (%d DOF each), 1 core" % (reps, nd)}
             pid_all, cores = oracle_pid_all_cores()
             cpu["all_cores"] = {"value": pid_all, "unit": "ns/DOF/RHS", "cores": cores,
                                 "sample": "8 oracle RHS evaluations of the full 16^3 p=3 mesh split by element "
                                           "ranges over %d spawned processes (parallel wall time)" % cores}
-        line = {
-            "metric": METRIC, "value": r64["pid_ns"], "value_std": r64["pid_std_ns"], "unit": "ns/DOF/RHS",
-            "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r64["ms_per_step"],
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD, "time_step": "4-stage low-storage RK4 (4 RHS + 4 stage updates)",
-                       "pid_per": "RHS evaluation", "surface_flux": "Ranocha + LLF", "volume_flux": "Ranocha",
-                       "l2": "flushed (512 MB write) before every timed step",
-                       "launch": "programmatic dependent launches (dg_opts.launch = DG_LAUNCH_OVERLAP)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": r64["roofline"],
-            "cpu_baseline": cpu,
-            "e2e": {"value": r64.get("e2e_pid_ns"), "unit": "ns/DOF/RHS",
-                    "h2d_bytes_per_step": r64.get("e2e_bytes"), "d2h_bytes_per_step": r64.get("e2e_bytes")},
-            "gpu_launches": r64["launches"],
-            "clocks": r64["clocks"],
-            "kernels_ms": {"volume_with_stage_update": r64["volume_ms_avg"], "interface": r64["interface_ms_avg"],
-                           "volume_share_of_step": r64["volume_share_of_step"]},
-            "cuda_graph_replay": {
-                "note": "the same timed steps with each dg_step captured once in a CUDA graph and replayed",
-                "fp64_16": r64["graph_pid_ns"], "fp32_16": r32["graph_pid_ns"], "fp64_32": b64["graph_pid_ns"],
-                "fp32_32": b32["graph_pid_ns"], "unit": "ns/DOF/RHS"},
-            "eager_without_profiling_events": {
-                "note": "the same eager steps, timed again without the library's per-launch CUDA events (the headline "
-                        "keeps those around every third volume launch: they give the roofline's kernel time)",
-                "fp64_16": r64["noprof_pid_ns"], "fp32_16": r32["noprof_pid_ns"], "fp64_32": b64["noprof_pid_ns"],
-                "fp32_32": b32["noprof_pid_ns"], "unit": "ns/DOF/RHS"},
-            "fp32": {"value": r32["pid_ns"], "unit": "ns/DOF/RHS", "ms_per_step": r32["ms_per_step"],
-                     "workload": "same as value (16^3, p=3)", "dtype": "f32 flux + line sums; f64 state, RK",
-                     "speedup_vs_fp64": r64["pid_ns"] / r32["pid_ns"], "gpu_launches": r32["launches"],
-                     "kernels_ms": {"volume_with_stage_update": r32["volume_ms_avg"],
-                                    "interface": r32["interface_ms_avg"]}},
-            "precision_workload_32cubed": {
-                "workload": "same TGV on 32^3 elements, p=3 (2,097,152 DOF; inputs larger than L2)",
-                "fp64": {"value": b64["pid_ns"], "ms_per_step": b64["ms_per_step"], "roofline": b64["roofline"],
-                         "kernels_ms": {"volume_with_stage_update": b64["volume_ms_avg"],
-                                        "interface": b64["interface_ms_avg"]}},
-                "fp32": {"value": b32["pid_ns"], "ms_per_step": b32["ms_per_step"], "roofline": b32["roofline"],
-                         "kernels_ms": {"volume_with_stage_update": b32["volume_ms_avg"],
-                                        "interface": b32["interface_ms_avg"]}},
-                "speedup_fp32_vs_fp64": b64["pid_ns"] / b32["pid_ns"]},
-            "batch_64": batch,
-            "differentiation_and_scale": diff,
-            "flux_and_geometry_variants": variants,
-            "logmean_ablation": ablation,
-            "gauss_collocation": gauss,
-            "tile_staging": staging,
-            "rhs_pid": rhs_pid,
-            "launch_modes": launch_modes,
-            "alu_peaks_measured_tflops": {k: (v / 1e12 if v else None) for k, v in peaks_alu.items()},
-        }
-        print(json.dumps(line), flush=True)
+            emit("cpu_baseline", cpu, details)
+        line = contract_line(args, world, results, compact_cpu_baseline(cpu))
+        if args.details:
+            with open(args.details, "w") as fh:
+                json.dump({"contract": line, "details": details}, fh, indent=1)
+        print(json.dumps(line, separators=(",", ":")), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
