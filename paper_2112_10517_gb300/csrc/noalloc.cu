@@ -64,7 +64,10 @@ extern "C" dg_status dg_rhs_noalloc(int ndims, const int* nelem, int polydeg, in
   const size_t state_bytes = (size_t)E * nv * Nd * sizeof(double);
   const char *ub = (const char*)u, *db = (const char*)du;
   if (ub < db + state_bytes && db < ub + state_bytes) return DG_ERR_ARG;  // u and du overlap
+  // every array is read or written in whole elements: misaligned pointers are rejected before any launch
   if (((uintptr_t)u | (uintptr_t)du | (uintptr_t)invJ) & 7) return DG_ERR_ARG;
+  if ((uintptr_t)Ja & (precision == DG_FP32 ? 3 : 7)) return DG_ERR_ARG;
+  if ((uintptr_t)flag & 3) return DG_ERR_ARG;
 
   unsigned char* scratch = nullptr;
   cudaError_t e = scratch_address(&scratch);

@@ -87,3 +87,24 @@ def test_argument_errors_without_gpu(built):
     assert dg.dg_check_status(None) == dg.DG_ERR_ARG
     assert dg.dg_launch_count(None) == -1
     dg.dg_free(None)  # no-op
+
+
+def test_noalloc_rejects_misaligned_arrays_before_any_device_call(built):
+    """dg_rhs_noalloc reads u, invJ and the metric terms and writes du and the flag in whole elements: a pointer
+    that is not a multiple of its element size is refused before the library touches a device (the fake
+    addresses below are never dereferenced)."""
+    from paper_2112_10517_gb300 import dg
+    nelem = (ctypes.c_int * 3)(2, 2, 2)
+    state = 2 * 2 * 2 * 5 * 64 * 8  # bytes of one state array: 8 elements, 5 variables, 64 nodes
+    u, du, invJ = 0x100000, 0x100000 + 2 * state, 0x100000 + 4 * state
+    ja64, ja32, flag = 0x100000 + 6 * state, 0x100000 + 6 * state + 4, 0x100000 + 8 * state
+
+    def call(precision, ja, fl, uu=u):
+        return dg.dg_rhs_noalloc(3, nelem, 3, precision, dg.DG_SURF_EC_LLF, 1.4, ctypes.c_void_p(uu),
+                                 ctypes.c_void_p(ja), ctypes.c_void_p(invJ), ctypes.c_void_p(du),
+                                 ctypes.c_void_p(fl), None)
+
+    assert call(dg.DG_FP64, ja32, flag) == dg.DG_ERR_ARG      # FP64 metric terms 4 bytes off an 8-byte boundary
+    assert call(dg.DG_FP32, ja32 + 2, flag) == dg.DG_ERR_ARG  # FP32 metric terms 2 bytes off
+    assert call(dg.DG_FP64, ja64, flag + 2) == dg.DG_ERR_ARG  # the int flag 2 bytes off
+    assert call(dg.DG_FP64, ja64, flag, uu=u + 4) == dg.DG_ERR_ARG  # the state 4 bytes off
