@@ -252,29 +252,32 @@ cudaError_t ensure_const_ops(int device) {
 // One entry point per (degree, precision, CTA size): its occupancy at a shared-memory size, or its launch.
 // The kernel's dynamic shared-memory opt-in is raised once to the largest size asked for, so that launches issue
 // no attribute call (a batch's launches can then be captured in a CUDA graph after a first call outside it).
+// (Function attributes are per device: the largest size set so far is kept per device.)
 template <int N, typename T, int THREADS, int LMK>
 cudaError_t batch_volume_optin(size_t smem) {
   static std::mutex m;
-  static size_t done = 0;
+  static size_t done[kMaxDevices] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(m);
-  if (smem <= done) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(batch_volume_kernel<N, T, THREADS, LMK>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) done = smem;
+  if (smem <= done[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(batch_volume_kernel<N, T, THREADS, LMK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+  if (e == cudaSuccess) done[dev] = smem;
   return e;
 }
 
 template <int N, typename T, int THREADS>
 cudaError_t batch_pipe_optin() {
-  static std::mutex m;
-  static bool done = false;
-  std::lock_guard<std::mutex> lock(m);
-  if (done) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(batch_pipe_kernel<N, T, THREADS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)BatchPipe<N, T, THREADS>::kSmem);
-  if (e == cudaSuccess) done = true;
-  return e;
+  static PerDeviceCache cache;
+  long long done = 0;
+  return per_device(cache, &done, [](long long* v) {
+    *v = 1;
+    return cudaFuncSetAttribute(batch_pipe_kernel<N, T, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)BatchPipe<N, T, THREADS>::kSmem);
+  });
 }
 
 // pipe: the pipelined kernel (its own CTA size and shared memory); else the per-tile kernel with `smem`.

@@ -4,11 +4,39 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "../../include/dg.h"
 
 #define DG_MAXN 8  // polydeg <= 7
 
 namespace dgk {
+
+// A launch setting of one kernel that holds per device: the dynamic shared-memory opt-in is a function attribute
+// of each device, and the resident CTAs (occupancy x SM count) may differ between devices. per_device runs
+// init(&v) once for the current device (under the cache's lock, so concurrent host threads do not race) and
+// returns the cached v (> 0) afterwards.
+constexpr int kMaxDevices = 64;
+struct PerDeviceCache {
+  std::mutex m;
+  long long value[kMaxDevices] = {};  // 0: not computed yet on that device
+};
+template <class F>
+cudaError_t per_device(PerDeviceCache& c, long long* out, F&& init) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(c.m);
+  if (c.value[dev] <= 0) {
+    long long v = 0;
+    e = init(&v);
+    if (e != cudaSuccess) return e;
+    c.value[dev] = v;
+  }
+  *out = c.value[dev];
+  return cudaSuccess;
+}
 
 // Per-launch geometry of a structured periodic mesh.
 struct MeshDims {

@@ -456,12 +456,13 @@ cudaError_t launch_gauss_volume(const GaussLaunch& L, const GaussOps<N>& op, int
   constexpr int EPB = gauss_epb<ND, N>();
   const size_t smem = volume_smem<ND, N>();
   auto kern = gauss_volume_kernel<ND, N, EPB, EPI>;
-  static bool attr_set = false;  // idempotent; a benign race sets the same value twice
-  if (!attr_set) {
-    const cudaError_t a = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (a != cudaSuccess) return a;
-    attr_set = true;
-  }
+  static PerDeviceCache cache;  // the shared-memory opt-in, once per device
+  long long done = 0;
+  const cudaError_t a = per_device(cache, &done, [&](long long* v) {
+    *v = 1;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (a != cudaSuccess) return a;
   const Epilogue epi = L.epi ? *L.epi : Epilogue{};
   kern<<<blocks, EPB * Geo<ND, N>::TPE, smem, L.s>>>(L.u, L.gface, L.fstar, L.du, L.md, op, L.c[0], L.c[1], L.c[2],
                                                      L.gamma, L.flag, epi);

@@ -253,12 +253,13 @@ cudaError_t launch_vjp_t(int llf, MeshDims md, const double* u, const double* Ja
   constexpr int EPB = vjp_epb<ND, N>();
   const size_t smem = VjpSmem<ND, N>::bytes(EPB);
   auto kern = volume_vjp_kernel<ND, N, EPB>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static PerDeviceCache cache;  // the shared-memory opt-in, once per device
+  long long done = 0;
+  e = per_device(cache, &done, [&](long long* v) {
+    *v = 1;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (e != cudaSuccess) return e;
   OpTable<N, double> op;
   const RefTables& t = ref_tables(N - 1);
   for (int i = 0; i < N * N; ++i) {

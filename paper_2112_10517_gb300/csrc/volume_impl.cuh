@@ -78,8 +78,10 @@ cudaError_t launch_volume_pipe(MeshDims md, const double* u, const T* Ja, const 
         if (!ok) return cudaErrorNotSupported;
       }
       auto kern = volume_pipe_kernel<ND, N, T, EPB, EPI>;
-      static int ctas = 0;  // resident CTAs on the device (occupancy x SMs); computed once, with the opt-in
-      if (ctas == 0) {
+      // resident CTAs on the device (occupancy x SMs), computed once per device together with the opt-in
+      static PerDeviceCache cache;
+      long long ctas = 0;
+      cudaError_t ce = per_device(cache, &ctas, [&](long long* v) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int dev = 0, sms = 0, occ = 0;
@@ -88,15 +90,17 @@ cudaError_t launch_volume_pipe(MeshDims md, const double* u, const T* Ja, const 
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, EPB * TPE, smem)) != cudaSuccess)
           return e;
         if (occ < 1) return cudaErrorNotSupported;
-        ctas = occ * sms;
-      }
+        *v = (long long)occ * sms;
+        return cudaSuccess;
+      });
+      if (ce != cudaSuccess) return ce;
       const int ntiles = (md.E + EPB - 1) / EPB;
       // auto: enough tiles per CTA, and not FP32 at p = 2 (3 elements of 27 threads per CTA, each thread issuing
       // many small copies: measured 25 % slower than the per-tile kernel; every other degree and precision gains)
       constexpr bool kAutoOk = !(sizeof(T) == 4 && N == 3);
       if (var.pipe == 1 && (!kAutoOk || (long long)ntiles < (long long)DG_VOLUME_PIPE_MIN_TILES_PER_CTA * ctas))
         return cudaErrorNotSupported;
-      const int grid = ntiles < ctas ? ntiles : ctas;
+      const int grid = ntiles < ctas ? ntiles : (int)ctas;
       const cudaError_t e = launch_kernel(kern, dim3(grid), dim3(EPB * TPE), smem, s, var.overlap != 0, u, Ja, invJ,
                                           face, du, md, op_table<N, T>(), (T)gamma, flag, epi, var, ntiles);
       return e != cudaSuccess ? e : cudaGetLastError();
@@ -114,12 +118,14 @@ cudaError_t launch_volume_k(MeshDims md, const double* u, const T* Ja, const dou
   constexpr int threads = EPB * Geo<ND, N>::TPE;
   const size_t smem = VolumeSmem<ND, N, T>::bytes(EPB, EPI != EPI_STORE, LMK == LM_PRELOG);
   auto kern = volume_kernel<ND, N, T, EPB, EPI, LMK>;
-  static bool attr_set = false;  // idempotent; a benign race sets the same value twice
-  if (!attr_set) {
+  static PerDeviceCache cache;  // the shared-memory opt-in, once per device
+  long long done = 0;
+  cudaError_t ae = per_device(cache, &done, [&](long long* v) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+    *v = 1;
+    return e;
+  });
+  if (ae != cudaSuccess) return ae;
   const int blocks = (md.E + EPB - 1) / EPB;
   kern<<<blocks, threads, smem, s>>>(u, Ja, invJ, face, du, md, op_table<N, T>(), (T)gamma, flag, epi, var);
   return cudaGetLastError();
