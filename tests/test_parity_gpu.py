@@ -5,11 +5,15 @@ The oracle evaluates the strong form with all ordered pairs and Cartesian fluxes
 the flux-differencing operator Dt with each pair once and directional fluxes (Sec. 2.1-2.3). The two are
 algebraically identical, so they agree to round-off.
 
-FP64 tolerance: 1e-12 relative, per variable, normwise, measured against the magnitude of the terms the RHS
-sums, max_i (1/J_i) sum |terms_i| (the oracle's scale mode). Rounding of any FP64 evaluation is proportional to
-that magnitude; the RHS itself can be many orders smaller (the Mach 0.1 Taylor-Green vortex sums pressure
-terms ~1e5 times larger than its RHS), where the plain relative error of two correct FP64 evaluations is
-~1e-8. The plain error is computed too and bounded separately where the data are well conditioned.
+FP64 tolerances, per variable, normwise (cases.assert_parity):
+- 1e-12 relative to the magnitude of the terms the RHS sums, max_i (1/J_i) sum |terms_i| (the oracle's scale
+  mode), in every case. Rounding of any FP64 evaluation is proportional to that magnitude.
+- plain relative, max|du_gpu - du_ref| / max|du_ref| <= max(1e-12, 1e-13 kappa), for every variable whose
+  cancellation factor kappa = max scale / max|du_ref| is at most 1e3 (every state here but the Taylor-Green
+  vortex): 1e-12 where kappa <= 10, else a term-relative bar ten times stricter than the first. The Mach 0.1
+  Taylor-Green vortex sums pressure terms 1e3 .. 3e4 times larger than its RHS, so the plain relative difference of
+  two correct FP64 evaluations is ~1e-8 there (the FP64 oracle is 3e-8 from a long-double build of itself at
+  16^3); those variables are held to the term-relative bar.
 """
 import math
 
@@ -17,11 +21,9 @@ import numpy as np
 import pytest
 
 import oracle as orc
-from cases import Scenario, parity_errors, rel_err_per_var
+from cases import TOL64, Scenario, assert_parity, parity_errors, rel_err_per_var
 
 pytestmark = pytest.mark.gpu
-
-TOL64 = 1e-12
 
 
 @pytest.fixture(scope="module")
@@ -43,15 +45,6 @@ def gpu_rhs(dgmod, sc, precision="fp64"):
     torch.cuda.synchronize()
     assert ctx.check_status() == dgmod.DG_OK
     return ctx, du.cpu().numpy()
-
-
-def assert_parity(got, sc, tol=TOL64, plain_tol=None):
-    plain, term = parity_errors(got, sc.du_ref(), sc.du_scale())
-    print("parity plain %s | term %s" % (" ".join("%.1e" % x for x in plain), " ".join("%.1e" % x for x in term)))
-    assert np.all(term <= tol), (term, plain)
-    if plain_tol is not None:
-        assert np.all(plain <= plain_tol), (term, plain)
-    return plain, term
 
 
 # ------------------------------------------------------------------------------------------------
@@ -78,7 +71,7 @@ def test_rhs_2d_cartesian_noisy_sine_8x8_p3(dgmod):
     # plus seeded uniform(-1e-2, 1e-2) noise on the primitives; Ranocha volume flux, Ranocha + LLF surface
     sc = Scenario(2, [8, 8], 3, mapping="affine", box=([-1.0, -1.0], [1.0, 1.0]), ic="noisy_sine", llf=True)
     _, du = gpu_rhs(dgmod, sc)
-    assert_parity(du, sc, plain_tol=1e-12)
+    assert_parity(du, sc, plain_tol=1e-12)  # both bars (kappa 9 .. 64)
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6, 7])
@@ -130,9 +123,11 @@ def test_rhs_single_element_periodic_self_coupling(dgmod, nd, nelem):
 
 def test_rhs_tgv_16cubed_p3_full_size(dgmod):
     # the 3D curvilinear Taylor-Green workload at full size: 16^3 elements, p = 3, 262,144 DOF, Mach 0.1
+    # (kappa 1e3 .. 3e4: the term-relative bar; assert_parity skips the plain bar for those variables)
     sc = Scenario(3, [16, 16, 16], 3, mapping="sine", ic="tgv", llf=True)
     _, du = gpu_rhs(dgmod, sc)
-    assert_parity(du, sc)
+    _, _, kappa = assert_parity(du, sc)
+    assert np.all(kappa > 1e3)  # the reason the plain bar does not apply here
 
 
 def test_rhs_64cubed_p3_sampled_elements(dgmod):
@@ -153,8 +148,7 @@ def test_rhs_64cubed_p3_sampled_elements(dgmod):
     for s, e in enumerate(sample):
         ref[s] = orc.rhs(3, p, nelem, Ja, J, u, llf=True, elem_range=(int(e), int(e) + 1))[0]
         scale[s] = orc.rhs(3, p, nelem, Ja, J, u, llf=True, elem_range=(int(e), int(e) + 1), scale=True)[0]
-    plain, term = parity_errors(du[sample], ref, scale)
-    assert np.all(term <= TOL64), (term, plain)
+    assert_parity(du[sample], ref, scale=scale)  # low Mach: kappa > 1e3, the term-relative bar
 
 
 # ------------------------------------------------------------------------------------------------
