@@ -730,6 +730,45 @@ def run_launch_modes(args, dev):
     return out
 
 
+def run_reference_pressure(args, dev):
+    """The FP32 flux mode's RK4 step (dg_step) without and with the reference pressure p_ref = 1/(gamma M^2)
+    (dg_opts.p_ref: the momentum equations' pressure terms on p - p_ref), Taylor-Green vortex p = 3 at 16^3 and
+    32^3 elements; eager steps without profiling events, L2 flushed before every timed step."""
+    import torch
+    from paper_2112_10517_gb300 import dg
+    lo, hi = [-math.pi] * 3, [math.pi] * 3
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    p0 = 1.0 / (1.4 * MACH ** 2)
+    out = {}
+    for ne in (NELEM[0], NELEM_LARGE[0]):
+        for name, pref in (("plain", 0.0), ("p_ref", p0)):
+            ctx = dg.DG(3, [ne] * 3, POLYDEG, lo=lo, hi=hi, mapping="sine", amp=AMP, surface="llf", precision="fp32",
+                        p_ref=pref)
+            u = torch.from_numpy(make_state(ctx)).to(dev)
+            scratch = torch.empty((2,) + ctx.shape, dtype=torch.float64, device=dev)
+            dt = 0.5 * (2 * math.pi / ne) / (POLYDEG + 1) ** 2 / (1.0 + 1.0 / MACH)
+            for _ in range(args.warmup):
+                ctx.step(u, dt, dg.DG_RK4_CLASSIC, scratch=scratch)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            torch.cuda.synchronize()
+            for a, b in ev:
+                flush.zero_()
+                a.record(stream)
+                ctx.step(u, dt, dg.DG_RK4_CLASSIC, scratch=scratch)
+                b.record(stream)
+            torch.cuda.synchronize()
+            if ctx.check_status() != dg.DG_OK:
+                raise RuntimeError("non-physical state in the reference-pressure runs")
+            ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+            out["fp32_%d_%s" % (ne, name)] = {"pid_ns": whole_job_pid(ms, ctx.ndofs, 1), "ms_per_step": ms}
+            del ctx, u, scratch
+    out["workload"] = ("dg_step (RK4), FP32 flux mode, Taylor-Green vortex Mach 0.1, sine-perturbed mesh, p = 3 at "
+                       "16^3 and 32^3 elements, without and with p_ref = 1/(gamma M^2)")
+    return out
+
+
 def run_logmean_ablation(args, dev):
     """Volume-term time of the log-mean variants (Sec. 3.1: Algorithms 2/3 with divisions, with the polynomial 1/log
     form; Sec. 7.2: logarithms precomputed per node) against the default (no division, one shared reciprocal),
@@ -965,7 +1004,7 @@ def run_reference(args, rank, world):
 
 
 # The sub-benchmarks beyond the headline (--extras): each prints its own line before the contract line.
-EXTRAS = ("batch", "diff", "variants", "ablation", "gauss", "staging", "launch", "rhs")
+EXTRAS = ("batch", "diff", "variants", "ablation", "gauss", "staging", "launch", "rhs", "pref")
 CONTRACT_LINE_MAX_BYTES = 1200
 
 
@@ -1042,7 +1081,7 @@ def main(argv=None):
     dev = torch.device("cuda", local_rank)
     runners = {"batch": run_batch, "diff": run_diff_and_scale, "variants": run_variants,
                "ablation": run_logmean_ablation, "gauss": run_gauss, "staging": run_staging,
-               "launch": run_launch_modes, "rhs": run_rhs_pid}
+               "launch": run_launch_modes, "rhs": run_rhs_pid, "pref": run_reference_pressure}
     if rank == 0 and args.only:
         for label, res in results.items():
             print(json.dumps({"configuration": label, "pid_ns": res["pid_ns"], "noprof_pid_ns": res["noprof_pid_ns"],

@@ -133,7 +133,17 @@ typedef struct dg_metrics {
                            before it have completed and their writes are visible. Work queued on the stream by other
                            code is ordered as usual.
      DG_LAUNCH_SERIAL      ordinary launches: each kernel starts after the one before it has completed.
-   Both compute the same values. */
+   Both compute the same values.
+   p_ref: a reference pressure for the FP32 flux mode (>= 0, finite; 0: none; ignored in FP64). The momentum
+   equations' pressure terms, {{p}} n of the two-point fluxes in the volume and at the interfaces, are then
+   evaluated on p - p_ref, formed from the FP64 state's energy minus p_ref/(gamma-1) on the integer and FP32
+   pipes, and the LLF dissipation's energy jump on the same relative energies. A constant pressure contributes
+   nothing to the momentum RHS (its volume and lifted surface terms cancel by the discrete metric identities of
+   Sec. 2.3, the property behind free-stream preservation), so the shift leaves the scheme's values unchanged up to
+   rounding and removes the cancellation of large pressure terms that FP32 rounding would otherwise leave in the
+   momentum RHS of a low-Mach flow (choose p_ref near the flow's mean pressure, e.g. 1/(gamma M^2) for a
+   nondimensional flow at Mach M). p_ref is rounded to FP32. Needs the default log mean (DG_ERR_UNSUPPORTED
+   otherwise); dg_batch_* reject contexts with p_ref != 0 in FP32 mode (DG_ERR_UNSUPPORTED). */
 enum { DG_LOGMEAN_SHARED_RCP = 0, DG_LOGMEAN_ALG = 1, DG_LOGMEAN_ALG_POLY = 2 };
 enum { DG_NODES_LGL = 0, DG_NODES_GAUSS = 1 };
 enum { DG_STAGING_AUTO = 0, DG_STAGING_DIRECT = 1, DG_STAGING_PIPELINED = 2 };
@@ -148,6 +158,7 @@ typedef struct dg_opts {
   int nodes;           /* DG_NODES_* */
   int staging;         /* DG_STAGING_* */
   int launch;          /* DG_LAUNCH_* */
+  double p_ref;        /* FP32 flux mode: reference pressure of the momentum pressure terms (0: none) */
 } dg_opts;
 
 /* Sizes of a context. */

@@ -37,6 +37,12 @@ int dgpk_eval_logmeans(long long n, int precision, const double* a1, const doubl
    float. Device arrays of n elements; synchronizes; returns 0 or a cudaError_t value. */
 int dgpk_eval_convert(long long n, const double* x, unsigned* f_int, unsigned* f_hw, double* d_int, double* d_hw);
 
+/* Self-test of the two-float split that the FP32 flux mode's reference pressure uses (integer pipe): hi = the
+   round-to-nearest float of x[i], lo = the float of x[i] - hi (to within 2^-22 of itself), and rel = x[i] - ref[i]
+   in FP32 from the two splits (energy_rel). Device arrays of n elements; synchronizes; returns 0 or a cudaError_t
+   value. */
+int dgpk_eval_split(long long n, const double* x, const double* ref, float* hi, float* lo, float* rel);
+
 /* Self-test of the RHS kernels' FP64 natural logarithm (Cody and Waite's argument reduction with an atanh series;
    used by the logarithmic means and the entropy projection) against CUDA's log: log_own/log_ref receive
    log_f64(x[i]) / log(x[i]). Device arrays of n elements; synchronizes; returns 0 or a cudaError_t value. */

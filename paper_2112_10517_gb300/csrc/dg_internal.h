@@ -93,6 +93,10 @@ struct Variant {
                  // kernel before them in the stream (they start while it drains; dg_opts.launch)
   double jn[3];  // Ja^n_n of a Cartesian mesh
   double invJ;   // 1/J of a Cartesian mesh
+  // FP32 flux mode with a reference pressure (dg_opts.p_ref): the momentum equations' pressure terms are evaluated
+  // on 2 (p - p_ref), with p - p_ref formed from the FP64 state. sh_eh + sh_el = p_ref / (gamma - 1), the energy of
+  // the reference pressure split into two floats; sh_pp = 2 p_ref (a float). All zero: no shift (and in FP64).
+  float sh_eh, sh_el, sh_pp;
 };
 
 // RHS kernels. Each returns the launch error. Ja is FP64 for precision DG_FP64 and FP32 for DG_FP32; the face

@@ -190,6 +190,37 @@ __device__ __forceinline__ double f2d_int(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// The rounding remainder of d2f_int, on the integer pipe: for x in the normal FP32 range and hi = d2f_int(x),
+// lo = x - hi to within 2^-22 of itself, so that hi + lo equals x to about 2^-46 relative. The 29 mantissa bits that
+// d2f_int drops, less 2^29 where it rounded up, give x - hi in units of 2^(e-52) (e the exponent of x); their top 23
+// bits convert exactly to a float (the 1.5 * 2^23 bias trick) and a power of two scales them. lo is 0 where that
+// scale leaves the float range (|x| below about 2^-80 or above 2^170) and where hi flushed to zero.
+__device__ __forceinline__ float split_lo_f64(double x, float hi) {
+  const unsigned h = (unsigned)__double2hiint(x), l = (unsigned)__double2loint(x);
+  const int L = (int)(l & 0x1FFFFFFFu);
+  const bool up = L > 0x10000000 || (L == 0x10000000 && ((l >> 29) & 1u));  // d2f_int's round-to-nearest-even
+  int r = up ? L - 0x20000000 : L;                                          // in [-2^28, 2^28]
+  if (h & 0x80000000u) r = -r;
+  const float fr = __int_as_float(0x4B400000 + (r >> 6)) - 12582912.0f;  // r / 64, exact
+  const int se = (int)((h >> 20) & 0x7FFu) - 1023 + 81;                 // FP32 biased exponent of 2^(e-46)
+  return (se >= 1 && se <= 254 && hi != 0.0f) ? fr * __int_as_float(se << 23) : 0.0f;
+}
+
+// The energy of a state in the flux precision, relative to a reference (FP32 mode with a reference pressure):
+// E - E_ref with E_ref = eh + el, from the FP64 state value E without FP64 instructions. With E and E_ref within a
+// factor 2 the difference of the leading floats is exact (Sterbenz), so the result carries the rounding of the small
+// difference, not that of E (|E| 2^-24). eh = el = 0 gives d2f_int(E) itself (no reference).
+template <typename T>
+__device__ __forceinline__ T energy_rel(double E, float eh, float el) {
+  if constexpr (sizeof(T) == 8) {
+    return E;
+  } else {
+    const float hi = d2f_int(E);
+    if (eh == 0.0f && el == 0.0f) return hi;
+    return (hi - eh) + (split_lo_f64(E, hi) - el);
+  }
+}
+
 // sqrt x to about 46 bits, for the local Lax-Friedrichs wave speed: the correctly rounded FP32 root g of x and
 // h ~ 1/(2g) in FP32 (integer-pipe conversions), then one Newton (Heron) step in FP64, g + h (x - g^2), which
 // squares the relative error of g (2^-24 -> 2^-48; h's own error adds about 2^-47). Two FP64 operations instead
@@ -265,6 +296,10 @@ __device__ __forceinline__ void log_means(T a1, T b1, T a2, T b2, T& L, T& Li) {
 // Per-node quantities for the pair flux (Sec. 7.1: computed once per node, not once per pair):
 //   q = (rho, v_1..v_d, pp = 2p, pg = 2p/(gamma - 1))                            NQ = d + 3 values
 // from conserved u; returns false for rho <= 0, p <= 0 or NaN.
+// FP32 mode with a reference pressure (shift pp0 = 2 p_ref != 0): the state's energy arrives as E - p_ref/(gamma-1)
+// (energy_rel), and q[PP] holds pp - pp0 = 2 (p - p_ref), the form the momentum equations' pressure terms take
+// (a constant pressure contributes nothing to them: its volume and surface terms cancel by the discrete metric
+// identities). The flux recovers pp = q[PP] + pp0 where it needs the pressure itself; q[PG] is unshifted.
 // ---------------------------------------------------------------------------------------------------
 template <int ND>
 struct NodeQ {
@@ -273,9 +308,9 @@ struct NodeQ {
 };
 
 // The same with 1/rho given (ir), for callers that share one reciprocal between two states; uc is the state in
-// FP64 (U = double) or already in the flux precision (U = T).
+// FP64 (U = double) or already in the flux precision (U = T, with the energy relative to the reference, if any).
 template <int ND, typename T, typename U>
-__device__ __forceinline__ bool node_quantities_ir(const U* uc, T ir, T gm1, T two_over_gm1, T* q) {
+__device__ __forceinline__ bool node_quantities_ir(const U* uc, T ir, T gm1, T two_over_gm1, T* q, T pp0 = T(0)) {
   const T rho = to_flux<T>(uc[0]);
   T ke = T(0);
 #pragma unroll
@@ -286,14 +321,17 @@ __device__ __forceinline__ bool node_quantities_ir(const U* uc, T ir, T gm1, T t
     ke += m * v;
   }
   const T p = gm1 * (to_flux<T>(uc[ND + 1]) - T(0.5) * ke);
+  const T pt = sizeof(T) == 8 ? p : p + T(0.5) * pp0;  // the pressure itself (pp0 = 0: p)
   q[0] = rho;
   q[NodeQ<ND>::PP] = p + p;
-  q[NodeQ<ND>::PG] = p * two_over_gm1;
-  return Num<T>::pos(rho) && Num<T>::pos(p);
+  q[NodeQ<ND>::PG] = pt * two_over_gm1;
+  return Num<T>::pos(rho) && Num<T>::pos(pt);
 }
 
+// From the FP64 state; sh (FP32 mode) the reference pressure's split energy and pp0 (all zero: none).
 template <int ND, typename T>
-__device__ __forceinline__ bool node_quantities(const double* uc, T gm1, T two_over_gm1, T* q, T* ir_out = nullptr) {
+__device__ __forceinline__ bool node_quantities(const double* uc, T gm1, T two_over_gm1, T* q, T* ir_out = nullptr,
+                                                float sh_eh = 0.0f, float sh_el = 0.0f, float sh_pp = 0.0f) {
   const T rho = to_flux<T>(uc[0]);
   const T ir = Num<T>::rcp(rho);
   if (ir_out) *ir_out = ir;  // 1/rho, for callers that need it again (the LLF wave speed)
@@ -305,11 +343,12 @@ __device__ __forceinline__ bool node_quantities(const double* uc, T gm1, T two_o
     q[1 + j] = v;
     ke += m * v;
   }
-  const T p = gm1 * (to_flux<T>(uc[ND + 1]) - T(0.5) * ke);
+  const T p = gm1 * (energy_rel<T>(uc[ND + 1], sh_eh, sh_el) - T(0.5) * ke);
+  const T pt = sizeof(T) == 8 ? p : p + T(0.5) * T(sh_pp);  // the pressure itself (no shift: p)
   q[0] = rho;
   q[NodeQ<ND>::PP] = p + p;
-  q[NodeQ<ND>::PG] = p * two_over_gm1;
-  return Num<T>::pos(rho) && Num<T>::pos(p);
+  q[NodeQ<ND>::PG] = pt * two_over_gm1;
+  return Num<T>::pos(rho) && Num<T>::pos(pt);
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -385,10 +424,12 @@ struct LogRef {
   int ls;
 };
 
+// ppa, ppb: the two nodes' 2p (unshifted)
 template <int ND, typename T, int LM>
-__device__ __forceinline__ void ranocha_means(const T* a, const T* b, T& L, T& Li, const LogRef<T>& lg) {
+__device__ __forceinline__ void ranocha_means(const T* a, const T* b, T ppa, T ppb, T& L, T& Li,
+                                              const LogRef<T>& lg) {
   using Q = NodeQ<ND>;
-  const T a2 = a[Q::RHO] * b[Q::PP], b2 = b[Q::RHO] * a[Q::PP];
+  const T a2 = a[Q::RHO] * ppb, b2 = b[Q::RHO] * ppa;
   if constexpr (LM == LM_PRELOG)
     log_means_prelog<T>(a[Q::RHO], b[Q::RHO], a2, b2, lg.la, lg.lb, lg.ls, L, Li);
   else if constexpr (LM == LM_ALG || LM == LM_ALG_POLY)
@@ -409,9 +450,19 @@ __device__ __forceinline__ void ranocha_means(const T* a, const T* b, T& L, T& L
 // ---------------------------------------------------------------------------------------------------
 // HALF0: return F_rho / 2 (= Q; the volume sums take it with doubled coefficients, which is exact and saves the
 // addition Q + Q per pair).
+// pp0 (FP32 mode with a reference pressure): the nodes' q[PP] hold pp - pp0; the momentum flux takes the shifted sum,
+// everything else the pressure itself (pp0 = 0 and FP64: unshifted values, the same arithmetic as without it).
+template <typename T>
+__device__ __forceinline__ T unshift_pp(T pp, T pp0) {
+  if constexpr (sizeof(T) == 8)
+    return pp;
+  else
+    return pp + pp0;
+}
+
 template <int ND, typename T, int LM = LM_SHARED_RCP, bool HALF0 = false>
 __device__ __forceinline__ void ranocha_flux8(const T* a, const T* b, const T* n2, T* F,
-                                              const LogRef<T>& lg = LogRef<T>{nullptr, nullptr, 0}) {
+                                              const LogRef<T>& lg = LogRef<T>{nullptr, nullptr, 0}, T pp0 = T(0)) {
   using Q = NodeQ<ND>;
   T A = a[1] * n2[0], B = b[1] * n2[0], vv = a[1] * b[1];
 #pragma unroll
@@ -420,14 +471,15 @@ __device__ __forceinline__ void ranocha_flux8(const T* a, const T* b, const T* n
     B += b[1 + j] * n2[j];
     vv += a[1 + j] * b[1 + j];
   }
+  const T ppa = unshift_pp(a[Q::PP], pp0), ppb = unshift_pp(b[Q::PP], pp0);
   T L, Li;
-  ranocha_means<ND, T, LM>(a, b, L, Li, lg);
+  ranocha_means<ND, T, LM>(a, b, ppa, ppb, L, Li, lg);
   const T q = L * (A + B);
   const T ps = a[Q::PP] + b[Q::PP];
   F[0] = HALF0 ? q : q + q;
 #pragma unroll
   for (int j = 0; j < ND; ++j) F[1 + j] = q * (a[1 + j] + b[1 + j]) + ps * n2[j];
-  F[ND + 1] = q * (vv + a[Q::PG] * b[Q::PP] * Li) + (a[Q::PP] * B + b[Q::PP] * A);
+  F[ND + 1] = q * (vv + a[Q::PG] * ppb * Li) + (ppa * B + ppb * A);
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -439,7 +491,7 @@ __device__ __forceinline__ void ranocha_flux8(const T* a, const T* b, const T* n
 //                                                          (8 (f_rho ((v;v))/2 + {{p}}{{v.n}}/(gamma-1) + ((p; v.n))))
 // ---------------------------------------------------------------------------------------------------
 template <int ND, typename T, bool HALF0 = false>
-__device__ __forceinline__ void shima_flux8(const T* a, const T* b, const T* n2, T* F) {
+__device__ __forceinline__ void shima_flux8(const T* a, const T* b, const T* n2, T* F, T pp0 = T(0)) {
   using Q = NodeQ<ND>;
   T A = a[1] * n2[0], B = b[1] * n2[0], vv = a[1] * b[1];
 #pragma unroll
@@ -455,7 +507,8 @@ __device__ __forceinline__ void shima_flux8(const T* a, const T* b, const T* n2,
   F[0] = HALF0 ? hq : q;
 #pragma unroll
   for (int j = 0; j < ND; ++j) F[1 + j] = hq * (a[1 + j] + b[1 + j]) + ps * n2[j];
-  F[ND + 1] = hq * vv + T(0.5) * (a[Q::PG] + b[Q::PG]) * AB + (a[Q::PP] * B + b[Q::PP] * A);
+  F[ND + 1] = hq * vv + T(0.5) * (a[Q::PG] + b[Q::PG]) * AB + (unshift_pp(a[Q::PP], pp0) * B +
+                                                               unshift_pp(b[Q::PP], pp0) * A);
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -465,21 +518,22 @@ __device__ __forceinline__ void shima_flux8(const T* a, const T* b, const T* n2,
 // ---------------------------------------------------------------------------------------------------
 template <int ND, typename T, int FLUX, int LM = LM_SHARED_RCP, bool HALF0 = false>
 __device__ __forceinline__ void pair_flux8_cart(const T* a, const T* b, T van, T vbn, T n2n, int n, T* F,
-                                                const LogRef<T>& lg = LogRef<T>{nullptr, nullptr, 0}) {
+                                                const LogRef<T>& lg = LogRef<T>{nullptr, nullptr, 0}, T pp0 = T(0)) {
   using Q = NodeQ<ND>;
   const T A = van * n2n, B = vbn * n2n;
   T vv = a[1] * b[1];
 #pragma unroll
   for (int j = 1; j < ND; ++j) vv += a[1 + j] * b[1 + j];
   const T pn = (a[Q::PP] + b[Q::PP]) * n2n;
+  const T ppa = unshift_pp(a[Q::PP], pp0), ppb = unshift_pp(b[Q::PP], pp0);
   T qv, e;
   if (FLUX == 0) {
     T L, Li;
-    ranocha_means<ND, T, LM>(a, b, L, Li, lg);
+    ranocha_means<ND, T, LM>(a, b, ppa, ppb, L, Li, lg);
     const T q = L * (A + B);
     F[0] = HALF0 ? q : q + q;
     qv = q;
-    e = q * (vv + a[Q::PG] * b[Q::PP] * Li);
+    e = q * (vv + a[Q::PG] * ppb * Li);
   } else {
     const T AB = A + B;
     const T q = (a[Q::RHO] + b[Q::RHO]) * AB;
@@ -489,16 +543,16 @@ __device__ __forceinline__ void pair_flux8_cart(const T* a, const T* b, T van, T
   }
 #pragma unroll
   for (int j = 0; j < ND; ++j) F[1 + j] = qv * (a[1 + j] + b[1 + j]) + (j == n ? pn : T(0));
-  F[ND + 1] = e + (a[Q::PP] * B + b[Q::PP] * A);
+  F[ND + 1] = e + (ppa * B + ppb * A);
 }
 
 template <int ND, typename T, int FLUX, int LM = LM_SHARED_RCP, bool HALF0 = false>
 __device__ __forceinline__ void pair_flux8(const T* a, const T* b, const T* n2, T* F,
-                                           const LogRef<T>& lg = LogRef<T>{nullptr, nullptr, 0}) {
+                                           const LogRef<T>& lg = LogRef<T>{nullptr, nullptr, 0}, T pp0 = T(0)) {
   if (FLUX == 0)
-    ranocha_flux8<ND, T, LM, HALF0>(a, b, n2, F, lg);
+    ranocha_flux8<ND, T, LM, HALF0>(a, b, n2, F, lg, pp0);
   else
-    shima_flux8<ND, T, HALF0>(a, b, n2, F);
+    shima_flux8<ND, T, HALF0>(a, b, n2, F, pp0);
 }
 
 }  // namespace dgk

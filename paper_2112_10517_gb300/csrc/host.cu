@@ -359,6 +359,9 @@ dg_status dg_init(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metri
   if (opts->logmean < DG_LOGMEAN_SHARED_RCP || opts->logmean > DG_LOGMEAN_ALG_POLY) return DG_ERR_ARG;
   if ((opts->precompute_logs || opts->logmean) && opts->volume_flux != DG_VOL_RANOCHA) return DG_ERR_UNSUPPORTED;
   if (opts->precompute_logs && opts->logmean != DG_LOGMEAN_SHARED_RCP) return DG_ERR_UNSUPPORTED;
+  if (!(opts->p_ref >= 0.0) || !isfinite(opts->p_ref)) return DG_ERR_ARG;
+  if (opts->p_ref != 0.0 && opts->precision == DG_FP32 && (opts->precompute_logs || opts->logmean))
+    return DG_ERR_UNSUPPORTED;
   if (metrics && ((metrics->Ja_host == nullptr) != (metrics->J_host == nullptr))) return DG_ERR_ARG;
   const long long n3 = nd == 3 ? mesh->nelem[2] : 1;
   const long long E = (long long)mesh->nelem[0] * mesh->nelem[1] * n3;
@@ -397,6 +400,16 @@ dg_status dg_init(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metri
   c->var.lm = opts->precompute_logs ? dgk::LM_PRELOG : opts->logmean;  // DG_LOGMEAN_* equal LM_* 0..2
   c->var.pipe = opts->staging == DG_STAGING_AUTO ? 1 : (opts->staging == DG_STAGING_PIPELINED ? 2 : 0);
   c->var.overlap = opts->launch == DG_LAUNCH_OVERLAP ? 1 : 0;
+  if (opts->precision == DG_FP32 && opts->p_ref > 0.0) {
+    // the kernels form p - p_ref = (gamma-1)_f (E - E_ref - ke/2) with their FP32 gamma - 1: E_ref = p_ref/(gamma-1)_f
+    // (FP64) makes (gamma-1)_f E_ref = p_ref exactly in exact arithmetic; p_ref and 2 p_ref are floats
+    const float pr = (float)opts->p_ref;
+    const float gm1f = (float)opts->gamma - 1.0f;
+    const double er = (double)pr / (double)gm1f;
+    c->var.sh_eh = (float)er;
+    c->var.sh_el = (float)(er - (double)c->var.sh_eh);
+    c->var.sh_pp = 2.0f * pr;
+  }
   {
     double hh[3] = {1.0, 1.0, 1.0}, jac = 1.0;
     for (int d = 0; d < nd; ++d) {

@@ -141,13 +141,18 @@ __device__ __forceinline__ void interface_node(const double* __restrict__ u, con
 #pragma unroll
   for (int j = 0; j < ND; ++j) m2[j] = m[j] * T(2.0 * kLift8);
   const T gm1 = gamma - T(1);
-  // the states in the flux precision, converted once (FP32 mode: also the LLF jump below)
+  // the states in the flux precision, converted once (FP32 mode: also the LLF jump below); with a reference
+  // pressure (FP32 mode) the energies relative to that of p_ref, so that their jump, and the pressure terms of the
+  // momentum flux, carry the rounding of the small differences
   T uLt[G::NV], uRt[G::NV];
 #pragma unroll
-  for (int c = 0; c < G::NV; ++c) {
+  for (int c = 0; c < G::NV - 1; ++c) {
     uLt[c] = to_flux<T>(uL[c]);
     uRt[c] = to_flux<T>(uR[c]);
   }
+  uLt[G::NV - 1] = energy_rel<T>(uL[G::NV - 1], var.sh_eh, var.sh_el);
+  uRt[G::NV - 1] = energy_rel<T>(uR[G::NV - 1], var.sh_eh, var.sh_el);
+  const T pp0 = T(var.sh_pp);  // 2 p_ref (FP32 mode), else 0
   T qL[NodeQ<ND>::NQ], qR[NodeQ<ND>::NQ], f[G::NV], irL, irR;
   if constexpr (sizeof(T) == 8) {  // one Newton reciprocal for both densities: 1/rho_L = rho_R R, R = 1/(rho_L rho_R)
     const T R = Num<T>::rcp(uLt[0] * uRt[0]);
@@ -157,10 +162,10 @@ __device__ __forceinline__ void interface_node(const double* __restrict__ u, con
     irL = Num<T>::rcp(uLt[0]);
     irR = Num<T>::rcp(uRt[0]);
   }
-  const bool ok = node_quantities_ir<ND, T>(uLt, irL, gm1, T(2) / gm1, qL) &
-                  node_quantities_ir<ND, T>(uRt, irR, gm1, T(2) / gm1, qR);
+  const bool ok = node_quantities_ir<ND, T>(uLt, irL, gm1, T(2) / gm1, qL, pp0) &
+                  node_quantities_ir<ND, T>(uRt, irR, gm1, T(2) / gm1, qR, pp0);
   if (!ok) atomicOr(flag, 1);
-  pair_flux8<ND, T, FLUX>(qL, qR, m2, f);  // f(u_L, u_R, m) / w_0
+  pair_flux8<ND, T, FLUX>(qL, qR, m2, f, LogRef<T>{nullptr, nullptr, 0}, pp0);  // f(u_L, u_R, m) / w_0
   if (LLF) {
     T mm = m[0] * m[0], vnL = qL[1] * m[0], vnR = qR[1] * m[0];
 #pragma unroll
@@ -171,7 +176,7 @@ __device__ __forceinline__ void interface_node(const double* __restrict__ u, con
     }
     // c |m| = sqrt(gamma p |m|^2 / rho) with p = pp/2: one root per side (FP64: to about 46 bits, sqrt_wave_f64)
     const T hgm = T(0.5) * gamma * mm;
-    const T aL = hgm * qL[NodeQ<ND>::PP] * irL, aR = hgm * qR[NodeQ<ND>::PP] * irR;
+    const T aL = hgm * unshift_pp(qL[NodeQ<ND>::PP], pp0) * irL, aR = hgm * unshift_pp(qR[NodeQ<ND>::PP], pp0) * irR;
     T cL, cR;
     if constexpr (sizeof(T) == 8) {
       cL = sqrt_wave_f64(aL);
@@ -329,10 +334,11 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // fu, fl (optional): the lifted interface fluxes (f* / w_0, component stride NL) of the line's upper and lower face
 // point; the surface term then starts the end nodes' sums (+fu at node N-1, -fl at node 0) instead of being added
 // in the epilogue.
+// pp0: 2 p_ref of the FP32 mode's reference pressure (the node quantities' pp is shifted by it), else 0.
 template <int ND, int N, typename T, int FLUX, bool CART, int LM = LM_SHARED_RCP>
 __device__ __forceinline__ void line_pairs(const T* sp, const T* sj, const T* sl, int st, int n, T n2n,
                                            const OpTable<N, T>& op, T* sa, const T* fu = nullptr,
-                                           const T* fl = nullptr) {
+                                           const T* fl = nullptr, T pp0 = T(0)) {
   using G = Geo<ND, N>;
   constexpr int NQ = NodeQ<ND>::NQ;
   T acc[N][G::NV];
@@ -365,12 +371,12 @@ __device__ __forceinline__ void line_pairs(const T* sp, const T* sj, const T* sl
       for (int c = 0; c < NQ; ++c) b[c] = sp[c * G::NDOF + k * st];
       const LogRef<T> lg{sl + i * st, sl + k * st, G::NDOF};
       if (CART) {
-        pair_flux8_cart<ND, T, FLUX, LM, true>(a, b, va_n, sp[(1 + n) * G::NDOF + k * st], n2n, n, f, lg);
+        pair_flux8_cart<ND, T, FLUX, LM, true>(a, b, va_n, sp[(1 + n) * G::NDOF + k * st], n2n, n, f, lg, pp0);
       } else {
         T n2[ND];
 #pragma unroll
         for (int j = 0; j < ND; ++j) n2[j] = ja_i[j] + sj[j * G::NDOF + k * st];
-        pair_flux8<ND, T, FLUX, LM, true>(a, b, n2, f, lg);
+        pair_flux8<ND, T, FLUX, LM, true>(a, b, n2, f, lg, pp0);
       }
       const T dik = op.Dt8[i * N + k], dki = op.Dt8[k * N + i];
       // f[0] is the halved mass flux: 2 dik (f[0]) equals dik (2 f[0]) exactly
@@ -439,7 +445,7 @@ __device__ __forceinline__ void volume_tile(const double* u, const T* __restrict
 #pragma unroll
     for (int c = 0; c < G::NV; ++c) uc[c] = ue[c * G::NDOF];
     T q[NQ];
-    ok &= node_quantities<ND, T>(uc, gm1, T(2) / gm1, q);
+    ok &= node_quantities<ND, T>(uc, gm1, T(2) / gm1, q, nullptr, var.sh_eh, var.sh_el, var.sh_pp);
 #pragma unroll
     for (int c = 0; c < NQ; ++c) s_prim[(el * NQ + c) * G::NDOF + i] = q[c];
     if constexpr (LMK == LM_PRELOG) {  // the element's range of rho and w = pp/rho (positive floats order as integers)
@@ -490,11 +496,12 @@ __device__ __forceinline__ void volume_tile(const double* u, const T* __restrict
     T* sa = s_acc + (el * ND + n) * G::NV * G::NDOF + base;
     const T n2n = T(2) * to_flux<T>(cart_jn(var, n));
     if constexpr (LMK == LM_SHARED_RCP) {
+      const T pp0 = T(var.sh_pp);
       switch (var.flux * 2 + var.cart) {
-        case 0: line_pairs<ND, N, T, 0, false>(sp, sj, sl, st, n, n2n, op, sa); break;
-        case 1: line_pairs<ND, N, T, 0, true>(sp, sj, sl, st, n, n2n, op, sa); break;
-        case 2: line_pairs<ND, N, T, 1, false>(sp, sj, sl, st, n, n2n, op, sa); break;
-        default: line_pairs<ND, N, T, 1, true>(sp, sj, sl, st, n, n2n, op, sa); break;
+        case 0: line_pairs<ND, N, T, 0, false>(sp, sj, sl, st, n, n2n, op, sa, nullptr, nullptr, pp0); break;
+        case 1: line_pairs<ND, N, T, 0, true>(sp, sj, sl, st, n, n2n, op, sa, nullptr, nullptr, pp0); break;
+        case 2: line_pairs<ND, N, T, 1, false>(sp, sj, sl, st, n, n2n, op, sa, nullptr, nullptr, pp0); break;
+        default: line_pairs<ND, N, T, 1, true>(sp, sj, sl, st, n, n2n, op, sa, nullptr, nullptr, pp0); break;
       }
     } else if constexpr (LMK == LM_PRELOG) {
       if (var.cart)

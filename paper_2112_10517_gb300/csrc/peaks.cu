@@ -133,6 +133,16 @@ __global__ void convert_kernel(long long n, const double* x, unsigned* f_int, un
   d_hw[i] = (double)hw;
 }
 
+__global__ void split_kernel(long long n, const double* x, const double* ref, float* hi, float* lo, float* rel) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float h = dgk::d2f_int(x[i]);
+  hi[i] = h;
+  lo[i] = dgk::split_lo_f64(x[i], h);
+  const float rh = dgk::d2f_int(ref[i]);
+  rel[i] = dgk::energy_rel<float>(x[i], rh, dgk::split_lo_f64(ref[i], rh));
+}
+
 __global__ void log_kernel(long long n, const double* x, double* log_own, double* log_ref) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -187,6 +197,14 @@ int dgpk_eval_log(long long n, const double* x, double* log_own, double* log_ref
 // Self-test of the integer-pipe format conversions of the RHS kernels against the hardware conversions: for
 // i < n, f_int[i] / f_hw[i] = bits of d2f_int(x[i]) / __double2float_rn(x[i]); d_int[i] / d_hw[i] = f2d_int and
 // the hardware widening of that float. Device arrays; synchronizes; returns 0 or a cudaError_t value.
+int dgpk_eval_split(long long n, const double* x, const double* ref, float* hi, float* lo, float* rel) {
+  if (n <= 0) return 0;
+  split_kernel<<<(unsigned)((n + 255) / 256), 256>>>(n, x, ref, hi, lo, rel);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return (int)e;
+}
+
 int dgpk_eval_convert(long long n, const double* x, unsigned* f_int, unsigned* f_hw, double* d_int, double* d_hw) {
   if (n <= 0) return 0;
   convert_kernel<<<(unsigned)((n + 255) / 256), 256>>>(n, x, f_int, f_hw, d_int, d_hw);

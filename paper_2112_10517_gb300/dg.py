@@ -59,7 +59,8 @@ class DgMetrics(ctypes.Structure):
 class DgOpts(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("volume_flux", ctypes.c_int), ("surface_flux", ctypes.c_int),
                 ("precision", ctypes.c_int), ("precompute_logs", ctypes.c_int), ("logmean", ctypes.c_int),
-                ("nodes", ctypes.c_int), ("staging", ctypes.c_int), ("launch", ctypes.c_int)]
+                ("nodes", ctypes.c_int), ("staging", ctypes.c_int), ("launch", ctypes.c_int),
+                ("p_ref", ctypes.c_double)]
 
 
 class DgInfo(ctypes.Structure):
@@ -146,13 +147,15 @@ class DG:
     except FP32 at p = 2); the same values either way.
     launch: "overlap" (each interface and pipelined volume kernel is scheduled ahead and starts as the kernel
     before it ends, waiting for its writes before reading them) or "serial" (ordinary launches); the same values.
+    p_ref: FP32 mode only, a reference pressure (0: none) on which the momentum equations' pressure terms are
+    evaluated as p - p_ref (the same scheme up to rounding; for low-Mach flows, the flow's mean pressure).
     """
 
     def __init__(self, ndims: int, nelem, polydeg: int, lo=None, hi=None, mapping: str = "affine", amp: float = 0.0,
                  node_xyz=None, Ja=None, J=None, gamma: float = 1.4, surface: str = "llf",
                  precision: str = "fp64", flux: str = "ranocha", logmean: str = "rcp",
                  precompute_logs: bool = False, nodes: str = "lgl", staging: str = "auto",
-                 launch: str = "overlap"):
+                 launch: str = "overlap", p_ref: float = 0.0):
         mesh = DgMesh()
         mesh.ndims = ndims
         ne = list(nelem) + [1] * (3 - len(nelem))
@@ -183,6 +186,7 @@ class DG:
         opts.nodes = NODES[nodes]
         opts.staging = STAGINGS[staging]
         opts.launch = LAUNCHES[launch]
+        opts.p_ref = float(p_ref)
         opts.surface_flux = {"ec": DG_SURF_EC, "llf": DG_SURF_EC_LLF}[surface]
         opts.precision = {"fp64": DG_FP64, "fp32": DG_FP32}[precision]
         ctx = ctypes.c_void_p()
