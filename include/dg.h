@@ -249,6 +249,72 @@ void dg_free(dg_ctx* ctx);
 const char* dg_status_string(dg_status s);
 
 /* ---------------------------------------------------------------------------------------------------------
+ * Partitioned meshes: one periodic mesh split into slabs, one context per slab (one GPU or one process each).
+ *
+ * The volume terms are element-local and the interface fluxes couple face neighbours only (Sec. 2.4; the
+ * surface flux is evaluated once per interface node from the two adjacent elements' face states), so a slab needs,
+ * besides its own elements, one plane of face states from each neighbouring slab per RHS: N^(d-1) nvar values per
+ * element face on the cut. The cut runs along the LAST direction (xi_3 in 3D, xi_2 in 2D), between element layers.
+ *
+ * dg_init_part creates the context of the element layers [begin, end) of the GLOBAL mesh `mesh` along the last
+ * direction (0 <= begin < end <= nelem[last]); the other directions stay periodic within the slab, the last is
+ * periodic across slabs (the slab of layer 0 is the upper neighbour of the slab ending at nelem[last]). Mappings
+ * DG_MAP_AFFINE and DG_MAP_SINE only (the node coordinates and metric terms of every element are those the global
+ * context computes, bit for bit); no metric override; DG_NODES_LGL. Its state arrays (u, du, RK scratch) hold
+ * E = layer * (1 + end - begin) elements, layer = nelem[0] (2D) or nelem[0] nelem[1] (3D): first a GHOST layer of
+ * `layer` elements, then the slab's own layers in the global element order. Only two planes of the ghost layer are
+ * read: its node plane i_last = p, which must hold the lower neighbour slab's last layer's plane i_last = p, and its
+ * plane i_last = 0, which must hold the upper neighbour slab's first layer's plane i_last = 0. The kernels compute
+ * the slab's own elements; the ghost layer of du and of the RK arrays is never written.
+ *
+ * Per RHS (and per Runge-Kutta stage, on that stage's input state):
+ *   1. dg_part_pack(ctx, state, send_lo, send_hi): send_lo <- plane i_last = 0 of the first own layer, send_hi <-
+ *      plane i_last = p of the last own layer (device buffers of dg_part_info.halo_len doubles each, layout
+ *      [layer][nvar][N^(d-1)], layer elements in element order, face nodes in node order);
+ *   2. the caller moves send_lo to the LOWER neighbour's recv_hi and send_hi to the UPPER neighbour's recv_lo (any
+ *      transport: NCCL send/recv, peer copies, or, for a slab that is its own neighbour, local copies);
+ *   3. dg_part_unpack(ctx, state, recv_lo, recv_hi) writes them into the ghost layer of `state`;
+ *   4. dg_rhs(ctx, state, du) or dg_step_stage(ctx, u, scratch, ..., stage).
+ * Each call queues on `stream` and synchronizes nothing. The result equals, bit for bit, the same elements of the
+ * global context's result when both use the same volume-kernel staging. dg_step, dg_step_host, dg_rhs_host,
+ * dg_vjp and dg_batch_* return DG_ERR_UNSUPPORTED for a partitioned context (they cannot exchange halos between
+ * stages); dg_entropy_rate and dg_conserved_totals sum the slab's own elements (sum them over the slabs: one
+ * all-reduce of nvar + 2 scalars). dg_get_node_coords / dg_get_metrics return all E elements, the ghost layer
+ * included; dg_get_info reports nelem_total = E and state_len for the arrays, ndofs for the slab's own elements.
+ * --------------------------------------------------------------------------------------------------------- */
+typedef struct dg_part {
+  int begin;  /* first element layer along the last direction owned by this slab */
+  int end;    /* one past the last */
+} dg_part;
+
+typedef struct dg_part_info {
+  long long layer;       /* elements per element layer (ghost layer and halo planes) */
+  long long own_elems;   /* elements the slab computes: layer * (end - begin) */
+  long long ghost_elems; /* elements before them in the state arrays: layer */
+  long long halo_len;    /* doubles in each of send_lo, send_hi, recv_lo, recv_hi: layer * nvar * N^(d-1) */
+  int begin, end;
+} dg_part_info;
+
+dg_status dg_init_part(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_opts* opts, const dg_part* part);
+dg_status dg_part_get_info(const dg_ctx* ctx, dg_part_info* info);
+/* DG_ERR_ARG for an ordinary context or null pointers; buffers are device memory, distinct from the state. */
+dg_status dg_part_pack(dg_ctx* ctx, const double* state, double* send_lo, double* send_hi, dg_stream_t stream);
+dg_status dg_part_unpack(dg_ctx* ctx, double* state, const double* recv_lo, const double* recv_hi, dg_stream_t stream);
+
+/* One stage of dg_step's scheme (stage 0 .. 3 for DG_RK4_CLASSIC, 0 .. 4 for DG_LSRK45_CK; arguments as dg_step):
+   running stages 0, 1, ... in order on the same u and scratch is dg_step. Stage `stage` reads the state that
+   dg_stage_input names: 0 = u, 1 = scratch (its first state array). Partitioned contexts exchange halos on that
+   state before each stage. Ordinary contexts accept it too. */
+dg_status dg_step_stage(dg_ctx* ctx, double* u, double* scratch, double t, double dt, int scheme, int stage,
+                        dg_stream_t stream);
+int dg_stage_input(int scheme, int stage); /* 0: u, 1: scratch, -1: invalid scheme or stage */
+
+/* Conserved totals sum_e sum_i J_i W_i q_i per variable (Sec. 2: discrete conservation; q a device state array, W
+   the tensor LGL weights), FP64 in a fixed order, into out_host[nvar]; the slab's own elements for a partitioned
+   context. Synchronizes `stream`. */
+dg_status dg_conserved_totals(dg_ctx* ctx, const double* q, double* out_host, dg_stream_t stream);
+
+/* ---------------------------------------------------------------------------------------------------------
  * Batched RHS: many independent meshes of uneven size and degree in one persistent launch.
  * The per-element work is that of dg_rhs (Eq. fluxdiff-SBP-opDsplit); only the scheduling differs.
  *

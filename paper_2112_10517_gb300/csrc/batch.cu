@@ -110,6 +110,7 @@ __device__ __forceinline__ Variant general_variant(int lm = LM_SHARED_RCP) {
   v.jn[0] = v.jn[1] = v.jn[2] = 0.0;
   v.invJ = 0.0;
   v.sh_eh = v.sh_el = v.sh_pp = 0.0f;  // batches take no reference pressure
+  v.ghost = 0;                         // nor partitioned contexts
   return v;
 }
 
@@ -499,6 +500,7 @@ dg_status dg_batch_create(dg_batch** out, dg_ctx* const* ctxs, int n, const doub
         c->gamma != c0->gamma || c->var.lm != c0->var.lm || (c->var.pipe != 0) != (c0->var.pipe != 0))
       return DG_ERR_ARG;
     if (c->nd != 3 || c->p > dgk::kBatchMaxP || c->volume_flux != DG_VOL_RANOCHA || c->var.sh_pp != 0.0f ||
+        c->var.ghost != 0 ||
         (c->var.lm != dgk::LM_SHARED_RCP && c->var.lm != dgk::LM_PRELOG) || c->nodes != DG_NODES_LGL)
       return DG_ERR_UNSUPPORTED;
     if (((uintptr_t)u[i] | (uintptr_t)du[i]) & 7) return DG_ERR_ARG;

@@ -97,6 +97,11 @@ struct Variant {
   // on 2 (p - p_ref), with p - p_ref formed from the FP64 state. sh_eh + sh_el = p_ref / (gamma - 1), the energy of
   // the reference pressure split into two floats; sh_pp = 2 p_ref (a float). All zero: no shift (and in FP64).
   float sh_eh, sh_el, sh_pp;
+  // Partitioned context (dg_init_part): the first `ghost` elements of the element range are the ghost layer (one
+  // element layer along the last direction, standing for the neighbouring partitions). The volume kernel computes
+  // elements [ghost, E) only; the interface kernel computes only the last direction's faces of ghost elements (the
+  // partition's lower boundary). 0: an ordinary context.
+  int ghost;
 };
 
 // RHS kernels. Each returns the launch error. Ja is FP64 for precision DG_FP64 and FP32 for DG_FP32; the face
@@ -111,6 +116,16 @@ cudaError_t launch_volume(int nd, int p, int precision, MeshDims md, const doubl
 cudaError_t launch_entropy_rate(int nd, int p, MeshDims md, const double* u, const double* du, const double* JW,
                                 double gamma, double* partial, int nblocks, double* out, cudaStream_t s);
 int entropy_rate_blocks();
+// Conserved totals sum J W q per variable over nelem elements: partials into partial[nblocks][nvar] (nblocks <=
+// entropy_rate_blocks()), the totals into out[nvar]. Deterministic order.
+cudaError_t launch_totals(int nd, int p, long long nelem, const double* q, const double* JW, double* partial,
+                          int nblocks, double* out, cudaStream_t s);
+// Halo planes of a partitioned context (see misc.cu): pack copies the owned boundary planes of state u into
+// send_lo/send_hi; unpack copies recv_lo/recv_hi into the ghost layer's two planes. layer: elements per layer;
+// first_owned, last_owned: the first elements of the first and last owned layers.
+cudaError_t launch_halo(int nd, int p, int layer, long long first_owned, long long last_owned, double* u,
+                        const double* recv_lo, const double* recv_hi, double* send_lo, double* send_hi, bool pack,
+                        cudaStream_t s);
 // One CTA whose bounded mbarrier wait runs out and sets FLAG_WAIT_TIMEOUT in *flag (dg_selftest_wait_timeout).
 cudaError_t launch_wait_probe(int* flag, cudaStream_t s);
 void ck45_coefficients(int stage, double* a, double* b);
@@ -167,6 +182,10 @@ struct dg_ctx {
   double* d_fadj;  // dg_vjp: face adjoint contributions [nd][E][2][nv][N^(nd-1)] (allocated at the first dg_vjp)
   double* d_gface;  // Gauss collocation: projected face states [nd][E][2][nv][N^(nd-1)]
   double* d_hstage;  // dg_step_host / dg_rhs_host: device copies of the host state (3 state arrays, first call)
+  // partitioned context (dg_init_part): ghost layer of `layer` elements first, then `owned` layers; 0 otherwise
+  int part_dir, part_begin, part_end;
+  long long layer;       // elements per layer (the ghost layer and each halo plane's element count)
+  long long owned_elems;  // elements computed (E minus the ghost layer)
   double* d_red;   // entropy-rate partials + result
   int* d_flag;     // non-physical-state flag
   cudaStream_t last_stream;

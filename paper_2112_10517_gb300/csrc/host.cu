@@ -83,12 +83,18 @@ int ipow(int b, int e) {
 // Geometry (Sec. 2.3)
 // ---------------------------------------------------------------------------------------------------
 
-void node_coords(const dg_mesh* m, int p, const dgk::RefTables& t, double* xyz) {
+// Node coordinates of `nlayers` element layers along the last direction, local layer l being the mesh's layer
+// (layer0 + l) mod nelem[last] (periodic): the whole mesh for layer0 = 0, nlayers = nelem[last]; a partitioned
+// context's ghost layer and own layers otherwise. Each element's nodes follow from its global element indices, so a
+// slab's geometry is bit for bit that of the same elements of the whole mesh.
+void node_coords(const dg_mesh* m, int p, const dgk::RefTables& t, double* xyz, int layer0, int nlayers) {
   const int nd = m->ndims, N = p + 1, Nd = ipow(N, nd);
-  const int n1 = m->nelem[0], n2 = m->nelem[1], n3 = nd == 3 ? m->nelem[2] : 1;
+  const int last = nd - 1, nlast = m->nelem[last];
+  const int n1 = m->nelem[0], n2 = nd == 3 ? m->nelem[1] : nlayers, n3 = nd == 3 ? nlayers : 1;
   const double twopi = 6.283185307179586476925286766559;
   for (int e = 0; e < n1 * n2 * n3; ++e) {
-    const int ei[3] = {e % n1, (e / n1) % n2, e / (n1 * n2)};
+    int ei[3] = {e % n1, (e / n1) % n2, e / (n1 * n2)};
+    ei[last] = ((layer0 + ei[last]) % nlast + nlast) % nlast;
     for (int i = 0; i < Nd; ++i) {
       const int ii[3] = {i % N, (i / N) % N, i / (N * N)};
       double xi[3];
@@ -332,7 +338,13 @@ const char* dg_status_string(dg_status s) {
   return "unknown status";
 }
 
-dg_status dg_init(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metrics* metrics, const dg_opts* opts) {
+}  // extern "C"
+
+namespace {
+// dg_init and dg_init_part: part == nullptr builds the context of the whole mesh; otherwise that of the slab of
+// element layers [part->begin, part->end) along the last direction, with a ghost layer in front.
+dg_status init_ctx(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metrics* metrics, const dg_opts* opts,
+                   const dg_part* part) {
   if (!out || !mesh || !opts) return DG_ERR_ARG;
   *out = nullptr;
   const int nd = mesh->ndims;
@@ -363,8 +375,16 @@ dg_status dg_init(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metri
   if (opts->p_ref != 0.0 && opts->precision == DG_FP32 && (opts->precompute_logs || opts->logmean))
     return DG_ERR_UNSUPPORTED;
   if (metrics && ((metrics->Ja_host == nullptr) != (metrics->J_host == nullptr))) return DG_ERR_ARG;
-  const long long n3 = nd == 3 ? mesh->nelem[2] : 1;
-  const long long E = (long long)mesh->nelem[0] * mesh->nelem[1] * n3;
+  // local element counts: a slab has its own layers plus the ghost layer along the last direction
+  int nloc[3] = {mesh->nelem[0], mesh->nelem[1], nd == 3 ? mesh->nelem[2] : 1};
+  if (part) {
+    const int nlast = mesh->nelem[nd - 1];
+    if (part->begin < 0 || part->end <= part->begin || part->end > nlast) return DG_ERR_ARG;
+    if (mesh->mapping == DG_MAP_NODES || (metrics && metrics->Ja_host) || gauss) return DG_ERR_UNSUPPORTED;
+    nloc[nd - 1] = part->end - part->begin + 1;
+  }
+  const long long n3 = nd == 3 ? nloc[2] : 1;
+  const long long E = (long long)nloc[0] * nloc[1] * n3;
   const int N = polydeg + 1, Nd = ipow(N, nd), nv = nd + 2;
   if (E * Nd * nv > (1LL << 31) - 1) return DG_ERR_UNSUPPORTED;  // 32-bit node offsets in the kernels
 
@@ -381,12 +401,19 @@ dg_status dg_init(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metri
   c->N = N;
   c->Nd = Nd;
   c->nv = nv;
-  c->md.n1 = mesh->nelem[0];
-  c->md.n2 = mesh->nelem[1];
+  c->md.n1 = nloc[0];
+  c->md.n2 = nloc[1];
   c->md.n3 = (int)n3;
+  c->layer = part ? (nd == 3 ? (long long)nloc[0] * nloc[1] : nloc[0]) : 0;
+  c->owned_elems = E - c->layer;
+  c->part_dir = part ? nd - 1 : -1;
+  c->part_begin = part ? part->begin : 0;
+  c->part_end = part ? part->end : 0;
+  c->var.ghost = (int)c->layer;
+  c->ndofs = c->owned_elems * Nd;  // the DOF the context computes (a slab: its own elements)
   c->md.E = (int)E;
   c->E = E;
-  c->ndofs = E * Nd;
+  // (c->ndofs is set above: the DOF of the elements the context computes)
   c->state_len = E * Nd * nv;
   c->gamma = opts->gamma;
   c->precision = opts->precision;
@@ -434,7 +461,7 @@ dg_status dg_init(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metri
   if (mesh->mapping == DG_MAP_NODES)
     memcpy(c->h_xyz, mesh->node_xyz_host, nx * sizeof(double));
   else
-    node_coords(mesh, polydeg, t, c->h_xyz);
+    node_coords(mesh, polydeg, t, c->h_xyz, part ? part->begin - 1 : 0, nloc[nd - 1]);
   if (metrics && metrics->Ja_host) {
     memcpy(c->h_Ja, metrics->Ja_host, nja * sizeof(double));
     memcpy(c->h_J, metrics->J_host, nj * sizeof(double));
@@ -467,7 +494,8 @@ dg_status dg_init(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metri
   if (ce == cudaSuccess) ce = dev_alloc(&c->d_invJ, nj);
   if (ce == cudaSuccess) ce = dev_alloc(&c->d_JW, nj);
   if (ce == cudaSuccess) ce = cudaMalloc(&c->d_face, face_bytes + 16);
-  if (ce == cudaSuccess) ce = dev_alloc(&c->d_red, (size_t)2 * dgk::entropy_rate_blocks() + 2);
+  // reduction scratch: entropy-rate pairs or conserved totals (nvar per block), then the result
+  if (ce == cudaSuccess) ce = dev_alloc(&c->d_red, (size_t)(nv + 2) * dgk::entropy_rate_blocks() + nv + 2);
   if (ce == cudaSuccess) ce = dev_alloc(&c->d_flag, 1);
   if (ce == cudaSuccess && c->precision == DG_FP32) ce = dev_alloc(&c->d_Ja32, nja);
   if (ce == cudaSuccess && gauss) ce = dev_alloc(&c->d_gface, 2 * nface);
@@ -501,6 +529,72 @@ dg_status dg_init(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metri
   *out = c;
   return DG_OK;
 }
+}  // namespace
+
+extern "C" {
+
+dg_status dg_init(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metrics* metrics, const dg_opts* opts) {
+  return init_ctx(out, mesh, polydeg, metrics, opts, nullptr);
+}
+
+dg_status dg_init_part(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_opts* opts, const dg_part* part) {
+  if (!part) return DG_ERR_ARG;
+  return init_ctx(out, mesh, polydeg, nullptr, opts, part);
+}
+
+dg_status dg_part_get_info(const dg_ctx* c, dg_part_info* info) {
+  if (!c || !info || c->layer == 0) return DG_ERR_ARG;
+  info->layer = c->layer;
+  info->own_elems = c->owned_elems;
+  info->ghost_elems = c->layer;
+  info->halo_len = c->layer * c->nv * (c->Nd / c->N);
+  info->begin = c->part_begin;
+  info->end = c->part_end;
+  return DG_OK;
+}
+
+dg_status dg_part_pack(dg_ctx* c, const double* state, double* send_lo, double* send_hi, dg_stream_t stream) {
+  if (!c || c->layer == 0 || !state || !send_lo || !send_hi || send_lo == send_hi) return DG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  c->launches += 1;
+  return cuda_status(dgk::launch_halo(c->nd, c->p, (int)c->layer, c->layer, c->E - c->layer, const_cast<double*>(state),
+                                      nullptr, nullptr, send_lo, send_hi, true, s));
+}
+
+dg_status dg_part_unpack(dg_ctx* c, double* state, const double* recv_lo, const double* recv_hi, dg_stream_t stream) {
+  if (!c || c->layer == 0 || !state || !recv_lo || !recv_hi) return DG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  c->launches += 1;
+  return cuda_status(dgk::launch_halo(c->nd, c->p, (int)c->layer, c->layer, c->E - c->layer, state, recv_lo, recv_hi,
+                                      nullptr, nullptr, false, s));
+}
+
+int dg_stage_input(int scheme, int stage) {
+  if (scheme == DG_RK4_CLASSIC) return stage >= 0 && stage < 4 ? (stage > 0 ? 1 : 0) : -1;
+  if (scheme == DG_LSRK45_CK) return stage >= 0 && stage < 5 ? 0 : -1;
+  return -1;
+}
+
+dg_status dg_conserved_totals(dg_ctx* c, const double* q, double* out_host, dg_stream_t stream) {
+  if (!c || !q || !out_host) return DG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  const int nb = dgk::entropy_rate_blocks();
+  c->launches += 2;
+  const size_t g = (size_t)c->layer;  // a slab's own elements follow its ghost layer
+  cudaError_t e = dgk::launch_totals(c->nd, c->p, c->E - c->layer, q + g * c->nv * c->Nd, c->d_JW + g * c->Nd,
+                                     c->d_red, nb, c->d_red + (size_t)c->nv * nb, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  std::vector<double> res(c->nv);
+  e = cudaMemcpyAsync(res.data(), c->d_red + (size_t)c->nv * nb, c->nv * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  const dg_status st = bounded_sync(s, 60.0);
+  if (st != DG_OK) return st;
+  for (int k = 0; k < c->nv; ++k) out_host[k] = res[k];
+  return DG_OK;
+}
 
 void dg_free(dg_ctx* ctx) { release(ctx); }
 
@@ -528,8 +622,11 @@ dg_status dg_rhs(dg_ctx* c, const double* u, double* du, double t, dg_stream_t s
   return cuda_status(e);
 }
 
-dg_status dg_step(dg_ctx* c, double* u, double* scratch, double t, double dt, int scheme, dg_stream_t stream) {
-  (void)t;
+}  // extern "C"
+
+namespace {
+// Argument checks shared by dg_step and dg_step_stage.
+dg_status check_step_args(const dg_ctx* c, const double* u, const double* scratch, double dt, int scheme) {
   if (!c || !u || !scratch) return DG_ERR_ARG;
   if (scheme != DG_RK4_CLASSIC && scheme != DG_LSRK45_CK) return DG_ERR_ARG;
   if (!(dt == dt)) return DG_ERR_ARG;
@@ -539,9 +636,13 @@ dg_status dg_step(dg_ctx* c, double* u, double* scratch, double t, double dt, in
   const size_t bytes = n * sizeof(double) * (scheme == DG_RK4_CLASSIC ? 2 : 1);
   const char *ub = (const char*)u, *sb = (const char*)scratch;
   if (ub < sb + bytes && sb < ub + n * sizeof(double)) return DG_ERR_ARG;  // u overlaps the scratch
-  cudaStream_t s = (cudaStream_t)stream;
-  c->last_stream = s;
-  const int stages = scheme == DG_RK4_CLASSIC ? 4 : 5;
+  return DG_OK;
+}
+
+// Stage `st` of the scheme: the interface fluxes of the stage state, then the volume term whose epilogue applies
+// the stage update (no du round trip, no update kernel).
+dg_status run_stage(dg_ctx* c, double* u, double* scratch, double dt, int scheme, int st, cudaStream_t s) {
+  const size_t n = (size_t)c->state_len;
   const void* ja = c->precision == DG_FP32 ? (const void*)c->d_Ja32 : (const void*)c->d_Ja;
   dgk::Epilogue epi{};
   epi.mode = scheme == DG_RK4_CLASSIC ? dgk::EPI_RK4 : dgk::EPI_CK45;
@@ -549,32 +650,53 @@ dg_status dg_step(dg_ctx* c, double* u, double* scratch, double t, double dt, in
   epi.u = u;
   epi.y = scratch;
   epi.acc = scheme == DG_RK4_CLASSIC ? scratch + n : nullptr;
-  for (int st = 0; st < stages; ++st) {
-    // stage state: RK4 evaluates u, then y; CK45 evaluates u (updated in place)
-    const double* in = (scheme == DG_RK4_CLASSIC && st > 0) ? scratch : u;
-    epi.stage = st;
-    if (scheme == DG_LSRK45_CK) dgk::ck45_coefficients(st, &epi.a, &epi.b);
-    epi.ca = (st == 0 || st == 3) ? dt / 6.0 : dt / 3.0;
-    epi.cy = st == 2 ? dt : 0.5 * dt;
-    if (c->nodes == DG_NODES_GAUSS) {
-      const dg_status gs = gauss_rhs(c, in, nullptr, &epi, s);
-      if (gs != DG_OK) return gs;
-      continue;
-    }
-    int slot;
-    dgk::prof_begin(c, dgk::KID_INTERFACE, s, &slot);
-    cudaError_t e = dgk::launch_interface(c->nd, c->p, c->precision, c->surface_flux == DG_SURF_EC_LLF, c->md, in,
-                                          ja, c->d_face, c->gamma, c->d_flag, s, &c->var);
-    dgk::prof_end(c, s, slot);
-    if (e != cudaSuccess) return cuda_status(e);
-    // volume term with the stage update fused into its epilogue (no du round trip, no update kernel)
-    dgk::prof_begin(c, dgk::KID_VOLUME, s, &slot);
-    e = dgk::launch_volume(c->nd, c->p, c->precision, c->md, in, ja, c->d_invJ, c->d_face, nullptr, c->gamma,
-                           c->d_flag, s, &epi, &c->var);
-    dgk::prof_end(c, s, slot);
-    if (e != cudaSuccess) return cuda_status(e);
+  // stage state: RK4 evaluates u, then y; CK45 evaluates u (updated in place)
+  const double* in = dg_stage_input(scheme, st) == 1 ? scratch : u;
+  epi.stage = st;
+  if (scheme == DG_LSRK45_CK) dgk::ck45_coefficients(st, &epi.a, &epi.b);
+  epi.ca = (st == 0 || st == 3) ? dt / 6.0 : dt / 3.0;
+  epi.cy = st == 2 ? dt : 0.5 * dt;
+  if (c->nodes == DG_NODES_GAUSS) return gauss_rhs(c, in, nullptr, &epi, s);
+  int slot;
+  dgk::prof_begin(c, dgk::KID_INTERFACE, s, &slot);
+  cudaError_t e = dgk::launch_interface(c->nd, c->p, c->precision, c->surface_flux == DG_SURF_EC_LLF, c->md, in,
+                                        ja, c->d_face, c->gamma, c->d_flag, s, &c->var);
+  dgk::prof_end(c, s, slot);
+  if (e != cudaSuccess) return cuda_status(e);
+  dgk::prof_begin(c, dgk::KID_VOLUME, s, &slot);
+  e = dgk::launch_volume(c->nd, c->p, c->precision, c->md, in, ja, c->d_invJ, c->d_face, nullptr, c->gamma,
+                         c->d_flag, s, &epi, &c->var);
+  dgk::prof_end(c, s, slot);
+  return cuda_status(e);
+}
+}  // namespace
+
+extern "C" {
+
+dg_status dg_step(dg_ctx* c, double* u, double* scratch, double t, double dt, int scheme, dg_stream_t stream) {
+  (void)t;
+  dg_status st = check_step_args(c, u, scratch, dt, scheme);
+  if (st != DG_OK) return st;
+  if (c->layer) return DG_ERR_UNSUPPORTED;  // a slab exchanges halos between stages: dg_step_stage
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  const int stages = scheme == DG_RK4_CLASSIC ? 4 : 5;
+  for (int k = 0; k < stages; ++k) {
+    st = run_stage(c, u, scratch, dt, scheme, k, s);
+    if (st != DG_OK) return st;
   }
   return DG_OK;
+}
+
+dg_status dg_step_stage(dg_ctx* c, double* u, double* scratch, double t, double dt, int scheme, int stage,
+                        dg_stream_t stream) {
+  (void)t;
+  const dg_status st = check_step_args(c, u, scratch, dt, scheme);
+  if (st != DG_OK) return st;
+  if (dg_stage_input(scheme, stage) < 0) return DG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  return run_stage(c, u, scratch, dt, scheme, stage, s);
 }
 
 // Device staging of dg_step_host / dg_rhs_host: three state arrays, allocated at the first call.
@@ -585,6 +707,7 @@ static dg_status ensure_host_staging(dg_ctx* c) {
 
 dg_status dg_step_host(dg_ctx* c, double* u_host, double t, double dt, int scheme, dg_stream_t stream) {
   if (!c || !u_host) return DG_ERR_ARG;
+  if (c->layer) return DG_ERR_UNSUPPORTED;
   dg_status st = ensure_host_staging(c);
   if (st != DG_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
@@ -599,6 +722,7 @@ dg_status dg_step_host(dg_ctx* c, double* u_host, double t, double dt, int schem
 
 dg_status dg_rhs_host(dg_ctx* c, const double* u_host, double* du_host, double t, dg_stream_t stream) {
   if (!c || !u_host || !du_host) return DG_ERR_ARG;
+  if (c->layer) return DG_ERR_UNSUPPORTED;
   dg_status st = ensure_host_staging(c);
   if (st != DG_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
@@ -619,8 +743,11 @@ dg_status dg_entropy_rate(dg_ctx* c, const double* u, const double* du, double* 
   c->last_stream = s;
   const int nb = dgk::entropy_rate_blocks();
   c->launches += 2;
-  cudaError_t e = dgk::launch_entropy_rate(c->nd, c->p, c->md, u, du, c->d_JW, c->gamma, c->d_red, nb,
-                                           c->d_red + 2 * nb, s);
+  dgk::MeshDims own = c->md;  // a slab's own elements follow its ghost layer
+  own.E = (int)(c->E - c->layer);
+  const size_t g = (size_t)c->layer;
+  cudaError_t e = dgk::launch_entropy_rate(c->nd, c->p, own, u + g * c->nv * c->Nd, du + g * c->nv * c->Nd,
+                                           c->d_JW + g * c->Nd, c->gamma, c->d_red, nb, c->d_red + 2 * nb, s);
   if (e != cudaSuccess) return cuda_status(e);
   double res[2];
   e = cudaMemcpyAsync(res, c->d_red + 2 * nb, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);

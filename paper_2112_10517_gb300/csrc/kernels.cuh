@@ -207,6 +207,10 @@ __global__ void __launch_bounds__(256) interface_kernel(const double* __restrict
   const long long total = (long long)ND * md.E * Geo<ND, N>::NL;  // < 2^31 (checked at dg_init)
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= total) return;
+  if (var.ghost) {  // a partition's ghost layer: only its faces along the last direction (the lower boundary)
+    const int t = (int)(idx / Geo<ND, N>::NL);
+    if (t / ND < var.ghost && t % ND != ND - 1) return;
+  }
   if (var.flux == 0)
     interface_node<ND, N, T, LLF, 0>(u, Ja, face, md, gamma, flag, (int)idx, var);
   else
@@ -585,7 +589,7 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE)
                   Epilogue epi, Variant var) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   volume_tile<ND, N, T, EPB, EPI, EPB * Geo<ND, N>::TPE, LMK>(u, Ja, invJ, face, du, md, op, gamma, flag, epi,
-                                                              blockIdx.x * EPB, smem_raw, var);
+                                                              var.ghost + blockIdx.x * EPB, smem_raw, var);
 }
 
 }  // namespace dgk

@@ -92,7 +92,124 @@ __global__ void __launch_bounds__(kRedThreads) reduce_pairs_kernel(const double*
   }
 }
 
+// Conserved totals (the c scalars of discrete conservation, Sec. 2): sum over nodes of J W q per variable; the same
+// fixed-order reduction as the entropy rate.
+template <int NV>
+__global__ void __launch_bounds__(kRedThreads)
+    totals_partial_kernel(const double* __restrict__ q, const double* __restrict__ JW, long long nodes, int ndof,
+                          double* __restrict__ partial) {
+  double s[NV];
+#pragma unroll
+  for (int c = 0; c < NV; ++c) s[c] = 0.0;
+  for (long long g = (long long)blockIdx.x * kRedThreads + threadIdx.x; g < nodes; g += (long long)gridDim.x * kRedThreads) {
+    const long long e = g / ndof;
+    const int i = (int)(g - e * ndof);
+    const double jw = JW[g];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) s[c] += jw * q[((size_t)e * NV + c) * ndof + i];
+  }
+  __shared__ double sh[NV][kRedThreads];
+#pragma unroll
+  for (int c = 0; c < NV; ++c) sh[c][threadIdx.x] = s[c];
+  __syncthreads();
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+#pragma unroll
+      for (int c = 0; c < NV; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int c = 0; c < NV; ++c) partial[(size_t)blockIdx.x * NV + c] = sh[c][0];
+  }
+}
+
+template <int NV>
+__global__ void __launch_bounds__(kRedThreads) reduce_totals_kernel(const double* __restrict__ partial, int nb,
+                                                                    double* __restrict__ out) {
+  __shared__ double sh[NV][kRedThreads];
+  double s[NV];
+#pragma unroll
+  for (int c = 0; c < NV; ++c) s[c] = 0.0;
+  for (int b = threadIdx.x; b < nb; b += kRedThreads) {
+#pragma unroll
+    for (int c = 0; c < NV; ++c) s[c] += partial[(size_t)b * NV + c];
+  }
+#pragma unroll
+  for (int c = 0; c < NV; ++c) sh[c][threadIdx.x] = s[c];
+  __syncthreads();
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+#pragma unroll
+      for (int c = 0; c < NV; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int c = 0; c < NV; ++c) out[c] = sh[c][0];
+  }
+}
+
+// Halo planes of a partitioned context (the cut runs along the last direction, whose node stride is NL = N^(ND-1)):
+// plane k of element e holds the nodes k NL .. k NL + NL - 1 of each variable. A halo buffer is [layer][NV][NL] for
+// the `layer` elements of one element layer (consecutive in the element order).
+//   pack:   send_lo <- plane 0 of the first owned layer, send_hi <- plane N-1 of the last owned layer
+//   unpack: plane N-1 of the ghost layer <- recv_lo (the lower neighbour's last layer's plane N-1),
+//           plane 0 of the ghost layer <- recv_hi (the upper neighbour's first layer's plane 0)
+__global__ void halo_kernel(double* u, const double* recv_lo, const double* recv_hi, double* send_lo,
+                            double* send_hi, int layer, int nv, int nl, int ndof, long long first_owned,
+                            long long last_owned, int pack) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long count = (long long)layer * nv * nl;
+  if (g >= count) return;
+  const int fn = (int)(g % nl);
+  const long long t = g / nl;
+  const int c = (int)(t % nv);
+  const long long pos = t / nv;
+  const int top = (ndof / nl - 1) * nl;  // first node of plane N-1
+  if (pack) {
+    send_lo[g] = u[((first_owned + pos) * nv + c) * ndof + fn];
+    send_hi[g] = u[((last_owned + pos) * nv + c) * ndof + top + fn];
+  } else {
+    u[(pos * nv + c) * ndof + top + fn] = recv_lo[g];
+    u[(pos * nv + c) * ndof + fn] = recv_hi[g];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_halo(int nd, int p, int layer, long long first_owned, long long last_owned, double* u,
+                        const double* recv_lo, const double* recv_hi, double* send_lo, double* send_hi, bool pack,
+                        cudaStream_t s) {
+  const int N = p + 1, nv = nd + 2;
+  const int nl = nd == 3 ? N * N : N;
+  const long long count = (long long)layer * nv * nl;
+  if (count <= 0) return cudaSuccess;
+  const int threads = 256;
+  halo_kernel<<<(unsigned)((count + threads - 1) / threads), threads, 0, s>>>(
+      u, recv_lo, recv_hi, send_lo, send_hi, layer, nv, nl, nl * N, first_owned, last_owned, pack ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_totals(int nd, int p, long long nelem, const double* q, const double* JW, double* partial,
+                          int nblocks, double* out, cudaStream_t s) {
+  const int N = p + 1;
+  const int ndof = nd == 3 ? N * N * N : N * N;
+  const long long nodes = nelem * ndof;
+  cudaError_t e;
+  if (nd == 2) {
+    totals_partial_kernel<4><<<nblocks, kRedThreads, 0, s>>>(q, JW, nodes, ndof, partial);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) reduce_totals_kernel<4><<<1, kRedThreads, 0, s>>>(partial, nblocks, out);
+  } else {
+    totals_partial_kernel<5><<<nblocks, kRedThreads, 0, s>>>(q, JW, nodes, ndof, partial);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) reduce_totals_kernel<5><<<1, kRedThreads, 0, s>>>(partial, nblocks, out);
+  }
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
 
 int entropy_rate_blocks() { return kRedBlocks; }
 

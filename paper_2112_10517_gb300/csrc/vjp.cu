@@ -291,7 +291,7 @@ cudaError_t dispatch_vjp(int p, int llf, MeshDims md, const double* u, const dou
 extern "C" dg_status dg_vjp(dg_ctx* c, const double* u, const double* gbar, double* ubar, dg_stream_t stream) {
   if (!c || !u || !gbar || !ubar) return DG_ERR_ARG;
   if (c->precision != DG_FP64 || c->p > 5 || c->volume_flux != DG_VOL_RANOCHA ||
-      c->var.lm != 0 || c->nodes != DG_NODES_LGL)
+      c->var.lm != 0 || c->nodes != DG_NODES_LGL || c->layer != 0)
     return DG_ERR_UNSUPPORTED;
   if (((uintptr_t)u | (uintptr_t)gbar | (uintptr_t)ubar) & 7) return DG_ERR_ARG;
   const size_t bytes = (size_t)c->state_len * sizeof(double);

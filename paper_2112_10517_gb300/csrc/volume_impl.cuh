@@ -94,7 +94,7 @@ cudaError_t launch_volume_pipe(MeshDims md, const double* u, const T* Ja, const 
         return cudaSuccess;
       });
       if (ce != cudaSuccess) return ce;
-      const int ntiles = (md.E + EPB - 1) / EPB;
+      const int ntiles = (md.E - var.ghost + EPB - 1) / EPB;  // from element var.ghost on
       // auto: enough tiles per CTA, and not FP32 at p = 2 (3 elements of 27 threads per CTA, each thread issuing
       // many small copies: measured 25 % slower than the per-tile kernel; every other degree and precision gains)
       constexpr bool kAutoOk = !(sizeof(T) == 4 && N == 3);
@@ -126,7 +126,7 @@ cudaError_t launch_volume_k(MeshDims md, const double* u, const T* Ja, const dou
     return e;
   });
   if (ae != cudaSuccess) return ae;
-  const int blocks = (md.E + EPB - 1) / EPB;
+  const int blocks = (md.E - var.ghost + EPB - 1) / EPB;  // from element var.ghost on
   kern<<<blocks, threads, smem, s>>>(u, Ja, invJ, face, du, md, op_table<N, T>(), (T)gamma, flag, epi, var);
   return cudaGetLastError();
 }

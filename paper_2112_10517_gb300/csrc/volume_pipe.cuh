@@ -157,7 +157,8 @@ struct PipeTile {
 };
 
 // The tiles of one mesh, round-robin over the persistent grid: t = blockIdx.x, blockIdx.x + gridDim.x, ...
-// (first and next are called by thread 0, which passes the index on through shared memory).
+// (first and next are called by thread 0, which passes the index on through shared memory). Tile t starts at element
+// mesh.e0 + t EPB (mesh.e0: the first element computed, past a partition's ghost layer).
 template <typename T, int EPB>
 struct MeshTileSource {
   PipeTile<T> mesh;
@@ -167,7 +168,7 @@ struct MeshTileSource {
   __device__ __forceinline__ bool valid(int t) const { return t < ntiles; }
   __device__ __forceinline__ PipeTile<T> tile(int t) const {
     PipeTile<T> r = mesh;
-    r.e0 = t * EPB;
+    r.e0 = mesh.e0 + t * EPB;
     return r;
   }
 };
@@ -444,7 +445,7 @@ __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, 
     volume_pipe_kernel(const double* __restrict__ in, const T* __restrict__ Ja, const double* __restrict__ invJ,
                        const T* __restrict__ face, double* du, MeshDims md, OpTable<N, T> op, T gamma, int* flag,
                        Epilogue epi, Variant var, int ntiles) {
-  const MeshTileSource<T, EPB> src{{in, Ja, invJ, face, du, flag, md, 0}, ntiles};
+  const MeshTileSource<T, EPB> src{{in, Ja, invJ, face, du, flag, md, var.ghost}, ntiles};
   pipe_tiles<ND, N, T, EPB, EPI>(src, op, gamma, epi, var);
 }
 

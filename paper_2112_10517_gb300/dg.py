@@ -43,7 +43,9 @@ EXPORTED = ["dg_init", "dg_rhs", "dg_step", "dg_entropy_rate", "dg_check_status"
             "dg_get_node_coords", "dg_get_metrics", "dg_profile_enable", "dg_profile_read", "dg_launch_count",
             "dg_free", "dg_status_string", "dg_rhs_noalloc", "dg_batch_create", "dg_batch_rhs",
             "dg_batch_autotune", "dg_batch_set_tuning", "dg_batch_free", "dg_vjp", "dg_selftest_wait_timeout",
-            "dg_profile_enable_kernels", "dg_profile_enable_sampled", "dg_step_host", "dg_rhs_host"]
+            "dg_profile_enable_kernels", "dg_profile_enable_sampled", "dg_step_host", "dg_rhs_host",
+            "dg_init_part", "dg_part_get_info", "dg_part_pack", "dg_part_unpack", "dg_step_stage", "dg_stage_input",
+            "dg_conserved_totals"]
 
 
 class DgMesh(ctypes.Structure):
@@ -61,6 +63,15 @@ class DgOpts(ctypes.Structure):
                 ("precision", ctypes.c_int), ("precompute_logs", ctypes.c_int), ("logmean", ctypes.c_int),
                 ("nodes", ctypes.c_int), ("staging", ctypes.c_int), ("launch", ctypes.c_int),
                 ("p_ref", ctypes.c_double)]
+
+
+class DgPart(ctypes.Structure):
+    _fields_ = [("begin", ctypes.c_int), ("end", ctypes.c_int)]
+
+
+class DgPartInfo(ctypes.Structure):
+    _fields_ = [("layer", ctypes.c_longlong), ("own_elems", ctypes.c_longlong), ("ghost_elems", ctypes.c_longlong),
+                ("halo_len", ctypes.c_longlong), ("begin", ctypes.c_int), ("end", ctypes.c_int)]
 
 
 class DgInfo(ctypes.Structure):
@@ -100,6 +111,15 @@ _sig = {
     "dg_batch_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "dg_batch_free": (None, [_vp]),
     "dg_vjp": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "dg_init_part": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(DgMesh), ctypes.c_int, ctypes.POINTER(DgOpts),
+                                    ctypes.POINTER(DgPart)]),
+    "dg_part_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(DgPartInfo)]),
+    "dg_part_pack": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "dg_part_unpack": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "dg_step_stage": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                     _vp]),
+    "dg_stage_input": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
+    "dg_conserved_totals": (ctypes.c_int, [_vp, _vp, _dp, _vp]),
     "dg_selftest_wait_timeout": (ctypes.c_int, [_vp, _vp]),
 }
 for _name, (_res, _args) in _sig.items():
@@ -149,13 +169,16 @@ class DG:
     before it ends, waiting for its writes before reading them) or "serial" (ordinary launches); the same values.
     p_ref: FP32 mode only, a reference pressure (0: none) on which the momentum equations' pressure terms are
     evaluated as p - p_ref (the same scheme up to rounding; for low-Mach flows, the flow's mean pressure).
+    part: (begin, end) makes the context of the slab of element layers [begin, end) of the mesh along its last
+    direction (dg_init_part): state tensors then hold a ghost layer in front of the slab's elements, filled by
+    unpack() from the neighbouring slabs' pack() buffers before each RHS or Runge-Kutta stage.
     """
 
     def __init__(self, ndims: int, nelem, polydeg: int, lo=None, hi=None, mapping: str = "affine", amp: float = 0.0,
                  node_xyz=None, Ja=None, J=None, gamma: float = 1.4, surface: str = "llf",
                  precision: str = "fp64", flux: str = "ranocha", logmean: str = "rcp",
                  precompute_logs: bool = False, nodes: str = "lgl", staging: str = "auto",
-                 launch: str = "overlap", p_ref: float = 0.0):
+                 launch: str = "overlap", p_ref: float = 0.0, part=None):
         mesh = DgMesh()
         mesh.ndims = ndims
         ne = list(nelem) + [1] * (3 - len(nelem))
@@ -190,8 +213,15 @@ class DG:
         opts.surface_flux = {"ec": DG_SURF_EC, "llf": DG_SURF_EC_LLF}[surface]
         opts.precision = {"fp64": DG_FP64, "fp32": DG_FP32}[precision]
         ctx = ctypes.c_void_p()
-        check(dg_init(ctypes.byref(ctx), ctypes.byref(mesh), int(polydeg),
-                      ctypes.byref(met) if met is not None else None, ctypes.byref(opts)), "dg_init")
+        if part is None:
+            check(dg_init(ctypes.byref(ctx), ctypes.byref(mesh), int(polydeg),
+                          ctypes.byref(met) if met is not None else None, ctypes.byref(opts)), "dg_init")
+        else:
+            if met is not None:
+                raise ValueError("a partitioned context computes its own metric terms")
+            dp = DgPart(int(part[0]), int(part[1]))
+            check(dg_init_part(ctypes.byref(ctx), ctypes.byref(mesh), int(polydeg), ctypes.byref(opts),
+                               ctypes.byref(dp)), "dg_init_part")
         self.ctx = ctx
         info = DgInfo()
         check(dg_get_info(ctx, ctypes.byref(info)), "dg_get_info")
@@ -200,6 +230,12 @@ class DG:
         self.ndofs, self.state_len = info.ndofs, info.state_len
         self.shape = (self.nelem_total, self.nvar, self.nodes_per_elem)
         self.precision = precision
+        self.part = None
+        if part is not None:
+            pi = DgPartInfo()
+            check(dg_part_get_info(ctx, ctypes.byref(pi)), "dg_part_get_info")
+            self.part = pi
+            self.ghost_elems, self.halo_len = pi.ghost_elems, pi.halo_len
         import torch
         self.device = torch.device("cuda", torch.cuda.current_device())
 
@@ -242,6 +278,40 @@ class DG:
         check(dg_step(self.ctx, self._state(u, "u"), ctypes.c_void_p(scratch.data_ptr()), 0.0, float(dt), int(scheme),
                       _stream_handle(stream)), "dg_step")
         return u
+
+    def step_stage(self, u, scratch, dt: float, scheme: int, stage: int, stream=None):
+        """Stage `stage` of dg_step's scheme (dg_step_stage); it reads u or scratch[0] (stage_input)."""
+        nreg = 2 if scheme == DG_RK4_CLASSIC else 1
+        if scratch.numel() < nreg * self.state_len or scratch.dtype != __import__("torch").float64 or \
+                not scratch.is_contiguous():
+            raise ValueError("scratch must be contiguous float64 with %d elements" % (nreg * self.state_len))
+        check(dg_step_stage(self.ctx, self._state(u, "u"), ctypes.c_void_p(scratch.data_ptr()), 0.0, float(dt),
+                            int(scheme), int(stage), _stream_handle(stream)), "dg_step_stage")
+        return u
+
+    @staticmethod
+    def stage_input(scheme: int, stage: int) -> int:
+        """0: the stage reads u; 1: it reads scratch[0]."""
+        return int(dg_stage_input(int(scheme), int(stage)))
+
+    def halo_buffers(self):
+        """Four float64 device tensors of halo_len values: send_lo, send_hi, recv_lo, recv_hi."""
+        import torch
+        return [torch.empty(self.halo_len, dtype=torch.float64, device=self.device) for _ in range(4)]
+
+    def pack(self, state, send_lo, send_hi, stream=None):
+        check(dg_part_pack(self.ctx, self._state(state, "state"), ctypes.c_void_p(send_lo.data_ptr()),
+                           ctypes.c_void_p(send_hi.data_ptr()), _stream_handle(stream)), "dg_part_pack")
+
+    def unpack(self, state, recv_lo, recv_hi, stream=None):
+        check(dg_part_unpack(self.ctx, self._state(state, "state"), ctypes.c_void_p(recv_lo.data_ptr()),
+                             ctypes.c_void_p(recv_hi.data_ptr()), _stream_handle(stream)), "dg_part_unpack")
+
+    def conserved_totals(self, q, stream=None) -> np.ndarray:
+        out = np.zeros(self.nvar)
+        check(dg_conserved_totals(self.ctx, self._state(q, "q"), _dptr(out), _stream_handle(stream)),
+              "dg_conserved_totals")
+        return out
 
     def vjp(self, u, gbar, ubar=None, stream=None):
         """ubar = (d RHS/du)^T gbar (dg_vjp)."""
