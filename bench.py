@@ -9,8 +9,10 @@ low-storage RK4 (4 RHS evaluations + 4 fused stage updates); PID = step time / (
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-For N > 1 launch with torchrun: every rank advances its own independent copy of the workload (weak
-scaling, no data-path collective); the step time is the max over ranks.
+For N > 1 launch with torchrun: the mesh grows with N along its last direction (N x 16 element layers, periodic)
+and is cut into N slabs of 16^3 elements, one per rank (weak scaling); every Runge-Kutta stage packs the slab's two
+boundary face planes, exchanges them with the neighbouring ranks over NCCL and unpacks them into the ghost layer
+before the stage's kernels. The step time is the max over ranks.
 --impl reference times the CPU oracle (plain C, FP64, one core) on a bounded element sample of the same
 workload, one oracle RHS evaluation per step.
 """
@@ -68,6 +70,8 @@ def parse_args(argv=None):
     ap.add_argument("--extras", default="", help="comma-separated sub-benchmarks to run before the contract line "
                     "(%s, or all); each prints its own line" % ",".join(EXTRAS))
     ap.add_argument("--details", default="", help="also write every result of the run to this JSON file")
+    ap.add_argument("--slabs", action="store_true", help="run the partitioned path (slabs with halo exchanges) also "
+                    "at N = 1, as one slab that is its own neighbour")
     return ap.parse_args(argv)
 
 
@@ -312,6 +316,24 @@ def make_state(ctx):
     return inputs.taylor_green(ctx.node_coords(), mach=MACH)
 
 
+def make_case(nelem, precision, rank, world, slabs=False, **kw):
+    """The context of one rank and a function doing one RK4 step on it: the whole mesh at N = 1; at N > 1 the
+    rank's slab of a mesh of nelem[2] x N layers on [-pi, (2N - 1) pi] along the last direction, stepped stage by
+    stage with a halo exchange before each stage (partition.Slab)."""
+    from paper_2112_10517_gb300 import dg, partition
+    if world == 1 and not slabs:
+        ctx = dg.DG(3, nelem, POLYDEG, lo=[-math.pi] * 3, hi=[math.pi] * 3, mapping="sine", amp=AMP, surface="llf",
+                    precision=precision, **kw)
+        return ctx, (lambda u, dt, scratch, stream: ctx.step(u, dt, dg.DG_RK4_CLASSIC, scratch=scratch,
+                                                             stream=stream))
+    glob = [nelem[0], nelem[1], nelem[2] * world]
+    b, e = partition.slab_plan(glob[2], world)[rank]
+    ctx = dg.DG(3, glob, POLYDEG, lo=[-math.pi] * 3, hi=[math.pi, math.pi, (2 * world - 1) * math.pi],
+                mapping="sine", amp=AMP, surface="llf", precision=precision, part=(b, e), **kw)
+    slab = partition.Slab(ctx, rank, world)
+    return ctx, (lambda u, dt, scratch, stream: slab.step(u, scratch, dt, dg.DG_RK4_CLASSIC))
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -326,7 +348,6 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    lo, hi = [-math.pi] * 3, [math.pi] * 3
     only = [x for x in args.only.split(",") if x]
     peaks_alu = alu_peaks() if rank == 0 and not only else {}
     results = {}
@@ -335,14 +356,15 @@ def run_ours(args, rank, world, local_rank):
     if only:
         runs = [(lab, ne, pr, False) for lab, ne, pr, _ in runs if lab in only]
     for label, nelem, precision, main in runs:
-        ctx = dg.DG(3, nelem, POLYDEG, lo=lo, hi=hi, mapping="sine", amp=AMP, surface="llf", precision=precision)
+        ctx, step = make_case(nelem, precision, rank, world, slabs=args.slabs)
+        slab_path = world > 1 or args.slabs
         u0 = make_state(ctx)
         u = torch.from_numpy(u0).to(dev)
         scratch = torch.empty((2,) + ctx.shape, dtype=torch.float64, device=dev)
         # time step: CFL 0.5 on the smallest node spacing (TGV speed |v| + c <= 1 + 1/M)
         dt = 0.5 * (2 * math.pi / nelem[0]) / (POLYDEG + 1) ** 2 / (1.0 + 1.0 / MACH)
         for _ in range(args.warmup):
-            ctx.step(u, dt, dg.DG_RK4_CLASSIC, scratch=scratch)
+            step(u, dt, scratch, stream)
         torch.cuda.synchronize()
         if ctx.check_status() != dg.DG_OK:
             raise RuntimeError("non-physical state during warm-up")
@@ -362,7 +384,7 @@ def run_ours(args, rank, world, local_rank):
         for k in range(args.steps):
             flush.zero_()  # evict L2 (larger than the 126 MB L2) between timed steps
             starts[k].record(stream)
-            ctx.step(u, dt, dg.DG_RK4_CLASSIC, scratch=scratch)
+            step(u, dt, scratch, stream)
             ends[k].record(stream)
         torch.cuda.synchronize()
         launches = ctx.launch_count() - launches0
@@ -378,7 +400,7 @@ def run_ours(args, rank, world, local_rank):
         ctx.profile(True, kernels=[dg.KERNEL_INTERFACE])
         for k in range(args.steps):
             flush.zero_()
-            ctx.step(u, dt, dg.DG_RK4_CLASSIC, scratch=scratch)
+            step(u, dt, scratch, stream)
         torch.cuda.synchronize()
         ifc_ms, ifc_n = ctx.profile_read(dg.KERNEL_INTERFACE)
         ctx.profile(False)
@@ -386,27 +408,30 @@ def run_ours(args, rank, world, local_rank):
         for k in range(args.steps):
             flush.zero_()
             starts[k].record(stream)
-            ctx.step(u, dt, dg.DG_RK4_CLASSIC, scratch=scratch)
+            step(u, dt, scratch, stream)
             ends[k].record(stream)
         torch.cuda.synchronize()
         nms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps, dev)
         # the same step captured once in a CUDA graph (8 kernels) and replayed per step: the launch gaps go away
-        # (the library neither allocates nor synchronizes in dg_step); timed separately, same L2 flushes
-        side = torch.cuda.Stream(device=dev)
-        side.wait_stream(stream)
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph, stream=side):
-            ctx.step(u, dt, dg.DG_RK4_CLASSIC, scratch=scratch, stream=side)
-        for _ in range(2):
-            graph.replay()
-        torch.cuda.synchronize()
-        for k in range(args.steps):
-            flush.zero_()
-            starts[k].record(stream)
-            graph.replay()
-            ends[k].record(stream)
-        torch.cuda.synchronize()
-        gms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps, dev)
+        # (the library neither allocates nor synchronizes in dg_step); timed separately, same L2 flushes. (One GPU:
+        # a slab's step has halo exchanges between its stages.)
+        gms = None
+        if not slab_path:
+            side = torch.cuda.Stream(device=dev)
+            side.wait_stream(stream)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=side):
+                step(u, dt, scratch, side)
+            for _ in range(2):
+                graph.replay()
+            torch.cuda.synchronize()
+            for k in range(args.steps):
+                flush.zero_()
+                starts[k].record(stream)
+                graph.replay()
+                ends[k].record(stream)
+            torch.cuda.synchronize()
+            gms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
         status = ctx.check_status()
         if status != dg.DG_OK:
             raise RuntimeError("non-physical state during the timed steps")
@@ -417,21 +442,30 @@ def run_ours(args, rank, world, local_rank):
                "launches": launches, "clocks": clk,
                "volume_ms_avg": vol_avg_s * 1e3, "interface_ms_avg": ifc_ms / max(ifc_n, 1),
                "volume_share_of_step": vol_avg_s * 1e3 * STAGES / ms if ms > 0 else None,
-               "graph_ms_per_step": gms, "graph_pid_ns": whole_job_pid(gms, ndofs, world),
+               "graph_ms_per_step": gms, "graph_pid_ns": whole_job_pid(gms, ndofs, world) if gms else None,
                "noprof_pid_ns": whole_job_pid(nms, ndofs, world)}
         # e2e: the same step through the C ABI with the state in pinned host memory (dg_step_host: host->device copy,
         # the step, device->host copy of the new state, all inside the timed region)
+        # (a slab at N > 1: the same copies around the slab's step, through the partition module's Slab)
         if main:
             u_host = torch.from_numpy(u0).pin_memory()
             e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
             e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+
+            def host_step():
+                if not slab_path:
+                    ctx.step_host(u_host, dt, dg.DG_RK4_CLASSIC, stream=stream)
+                else:
+                    u.copy_(u_host, non_blocking=True)
+                    step(u, dt, scratch, stream)
+                    u_host.copy_(u, non_blocking=True)
             for k in range(args.warmup):
-                ctx.step_host(u_host, dt, dg.DG_RK4_CLASSIC, stream=stream)
+                host_step()
             torch.cuda.synchronize()
             for k in range(args.steps):
                 flush.zero_()
                 e0[k].record(stream)
-                ctx.step_host(u_host, dt, dg.DG_RK4_CLASSIC, stream=stream)
+                host_step()
                 e1[k].record(stream)
             torch.cuda.synchronize()
             ems = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / args.steps, dev)
@@ -1028,7 +1062,7 @@ def contract_line(args, world: int, results: dict, cpu) -> dict:
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sig(r64["ms_per_step"]),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_SHORT, "l2": "flushed each step",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "slabs+halo" if world > 1 or args.slabs else "single GPU"},
         "roofline": {"bound": rf["bound"], "achieved": sig(rf["achieved"]), "peak": sig(rf["peak"]),
                      "unit": rf["unit"], "frac": sig(rf["frac"], 3), "traffic": sig(rf["traffic"]),
                      "peak_src": rf["peak_src"]},
@@ -1102,7 +1136,7 @@ def main(argv=None):
                 raise SystemExit("unknown --extras entry %r (choose from %s)" % (name, ", ".join(EXTRAS)))
             emit(name, runners[name](args, dev), details)
         cpu = None
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and world == 1:  # the oracle baseline: rank 0 at N = 1 only
             pid_cpu, reps, nd = oracle_pid(10.0)
             cpu = {"value": pid_cpu, "unit": "ns/DOF/RHS", "cores": 1, "kind": "oracle", "reps": reps,
                    "sample": "%d oracle RHS evaluations of the full 16^3 p=3 mesh (%d DOF each), 1 core" % (reps, nd)}
