@@ -329,9 +329,11 @@ __device__ __forceinline__ bool node_quantities_ir(const U* uc, T ir, T gm1, T t
 }
 
 // From the FP64 state; sh (FP32 mode) the reference pressure's split energy and pp0 (all zero: none).
+// beta: q[PG] holds beta = rho/p instead of pg (the volume terms of Ranocha's flux, ranocha_flux8 with BETA).
 template <int ND, typename T>
 __device__ __forceinline__ bool node_quantities(const double* uc, T gm1, T two_over_gm1, T* q, T* ir_out = nullptr,
-                                                float sh_eh = 0.0f, float sh_el = 0.0f, float sh_pp = 0.0f) {
+                                                float sh_eh = 0.0f, float sh_el = 0.0f, float sh_pp = 0.0f,
+                                                bool beta = false) {
   const T rho = to_flux<T>(uc[0]);
   const T ir = Num<T>::rcp(rho);
   if (ir_out) *ir_out = ir;  // 1/rho, for callers that need it again (the LLF wave speed)
@@ -347,7 +349,7 @@ __device__ __forceinline__ bool node_quantities(const double* uc, T gm1, T two_o
   const T pt = sizeof(T) == 8 ? p : p + T(0.5) * T(sh_pp);  // the pressure itself (no shift: p)
   q[0] = rho;
   q[NodeQ<ND>::PP] = p + p;
-  q[NodeQ<ND>::PG] = pt * two_over_gm1;
+  q[NodeQ<ND>::PG] = beta ? rho * Num<T>::rcp(pt) : pt * two_over_gm1;
   return Num<T>::pos(rho) && Num<T>::pos(pt);
 }
 
@@ -460,10 +462,17 @@ __device__ __forceinline__ T unshift_pp(T pp, T pp0) {
     return pp + pp0;
 }
 
-template <int ND, typename T, int LM = LM_SHARED_RCP, bool HALF0 = false>
+// BETA (the volume terms, default log mean): the nodes' q[PG] hold beta = rho/p, the inverse mean is taken of beta
+// directly, Li = 1/{{beta}}_log, and the energy flux's 1/({{rho/p}}_log (gamma-1)) term is c2 Li with
+// c2 = 2/(gamma-1) (pg_a pp_b / {{rho_a pp_b, rho_b pp_a}}_log = 2/((gamma-1) {{beta}}_log by the homogeneity of the
+// mean): the two products rho_a pp_b, rho_b pp_a and one product of the energy flux per pair become one reciprocal
+// per node.
+template <int ND, typename T, int LM = LM_SHARED_RCP, bool HALF0 = false, bool BETA = false>
 __device__ __forceinline__ void ranocha_flux8(const T* a, const T* b, const T* n2, T* F,
-                                              const LogRef<T>& lg = LogRef<T>{nullptr, nullptr, 0}, T pp0 = T(0)) {
+                                              const LogRef<T>& lg = LogRef<T>{nullptr, nullptr, 0}, T pp0 = T(0),
+                                              T c2 = T(0)) {
   using Q = NodeQ<ND>;
+  static_assert(!BETA || LM == LM_SHARED_RCP, "the beta form serves the default log mean");
   T A = a[1] * n2[0], B = b[1] * n2[0], vv = a[1] * b[1];
 #pragma unroll
   for (int j = 1; j < ND; ++j) {
@@ -473,13 +482,19 @@ __device__ __forceinline__ void ranocha_flux8(const T* a, const T* b, const T* n
   }
   const T ppa = unshift_pp(a[Q::PP], pp0), ppb = unshift_pp(b[Q::PP], pp0);
   T L, Li;
-  ranocha_means<ND, T, LM>(a, b, ppa, ppb, L, Li, lg);
+  if constexpr (BETA)
+    log_means<T>(a[Q::RHO], b[Q::RHO], a[Q::PG], b[Q::PG], L, Li);
+  else
+    ranocha_means<ND, T, LM>(a, b, ppa, ppb, L, Li, lg);
   const T q = L * (A + B);
   const T ps = a[Q::PP] + b[Q::PP];
   F[0] = HALF0 ? q : q + q;
 #pragma unroll
   for (int j = 0; j < ND; ++j) F[1 + j] = q * (a[1 + j] + b[1 + j]) + ps * n2[j];
-  F[ND + 1] = q * (vv + a[Q::PG] * ppb * Li) + (ppa * B + ppb * A);
+  if constexpr (BETA)
+    F[ND + 1] = q * (vv + c2 * Li) + (ppa * B + ppb * A);
+  else
+    F[ND + 1] = q * (vv + a[Q::PG] * ppb * Li) + (ppa * B + ppb * A);
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -516,9 +531,10 @@ __device__ __forceinline__ void shima_flux8(const T* a, const T* b, const T* n2,
 // has the single component n2n = 2 Ja^n_n along axis n, so v.n2 is one product and the pressure acts on one
 // momentum component (van, vbn: the velocity components along n).
 // ---------------------------------------------------------------------------------------------------
-template <int ND, typename T, int FLUX, int LM = LM_SHARED_RCP, bool HALF0 = false>
+template <int ND, typename T, int FLUX, int LM = LM_SHARED_RCP, bool HALF0 = false, bool BETA = false>
 __device__ __forceinline__ void pair_flux8_cart(const T* a, const T* b, T van, T vbn, T n2n, int n, T* F,
-                                                const LogRef<T>& lg = LogRef<T>{nullptr, nullptr, 0}, T pp0 = T(0)) {
+                                                const LogRef<T>& lg = LogRef<T>{nullptr, nullptr, 0}, T pp0 = T(0),
+                                                T c2 = T(0)) {
   using Q = NodeQ<ND>;
   const T A = van * n2n, B = vbn * n2n;
   T vv = a[1] * b[1];
@@ -529,11 +545,17 @@ __device__ __forceinline__ void pair_flux8_cart(const T* a, const T* b, T van, T
   T qv, e;
   if (FLUX == 0) {
     T L, Li;
-    ranocha_means<ND, T, LM>(a, b, ppa, ppb, L, Li, lg);
+    if constexpr (BETA)
+      log_means<T>(a[Q::RHO], b[Q::RHO], a[Q::PG], b[Q::PG], L, Li);
+    else
+      ranocha_means<ND, T, LM>(a, b, ppa, ppb, L, Li, lg);
     const T q = L * (A + B);
     F[0] = HALF0 ? q : q + q;
     qv = q;
-    e = q * (vv + a[Q::PG] * ppb * Li);
+    if constexpr (BETA)
+      e = q * (vv + c2 * Li);
+    else
+      e = q * (vv + a[Q::PG] * ppb * Li);
   } else {
     const T AB = A + B;
     const T q = (a[Q::RHO] + b[Q::RHO]) * AB;
@@ -546,11 +568,12 @@ __device__ __forceinline__ void pair_flux8_cart(const T* a, const T* b, T van, T
   F[ND + 1] = e + (ppa * B + ppb * A);
 }
 
-template <int ND, typename T, int FLUX, int LM = LM_SHARED_RCP, bool HALF0 = false>
+template <int ND, typename T, int FLUX, int LM = LM_SHARED_RCP, bool HALF0 = false, bool BETA = false>
 __device__ __forceinline__ void pair_flux8(const T* a, const T* b, const T* n2, T* F,
-                                           const LogRef<T>& lg = LogRef<T>{nullptr, nullptr, 0}, T pp0 = T(0)) {
+                                           const LogRef<T>& lg = LogRef<T>{nullptr, nullptr, 0}, T pp0 = T(0),
+                                           T c2 = T(0)) {
   if (FLUX == 0)
-    ranocha_flux8<ND, T, LM, HALF0>(a, b, n2, F, lg, pp0);
+    ranocha_flux8<ND, T, LM, HALF0, BETA>(a, b, n2, F, lg, pp0, c2);
   else
     shima_flux8<ND, T, HALF0>(a, b, n2, F, pp0);
 }

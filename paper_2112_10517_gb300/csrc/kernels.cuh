@@ -339,10 +339,15 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // point; the surface term then starts the end nodes' sums (+fu at node N-1, -fl at node 0) instead of being added
 // in the epilogue.
 // pp0: 2 p_ref of the FP32 mode's reference pressure (the node quantities' pp is shifted by it), else 0.
+// Ranocha's flux with the default log mean takes its beta form in FP64 (the node quantities' PG slot holds rho/p;
+// c2 = 2/(gamma-1)): three FP64 products per pair less for one reciprocal per node, -3 % of the FP64 volume kernel.
+// FP32 keeps pg (its FP32 pipe is not the bound, and the reciprocal lengthens phase A: +1.8 % at 16^3); so do
+// Shima's flux and the log-mean variants.
 template <int ND, int N, typename T, int FLUX, bool CART, int LM = LM_SHARED_RCP>
 __device__ __forceinline__ void line_pairs(const T* sp, const T* sj, const T* sl, int st, int n, T n2n,
                                            const OpTable<N, T>& op, T* sa, const T* fu = nullptr,
-                                           const T* fl = nullptr, T pp0 = T(0)) {
+                                           const T* fl = nullptr, T pp0 = T(0), T c2 = T(0)) {
+  constexpr bool kBeta = FLUX == 0 && LM == LM_SHARED_RCP && sizeof(T) == 8;
   using G = Geo<ND, N>;
   constexpr int NQ = NodeQ<ND>::NQ;
   T acc[N][G::NV];
@@ -375,12 +380,13 @@ __device__ __forceinline__ void line_pairs(const T* sp, const T* sj, const T* sl
       for (int c = 0; c < NQ; ++c) b[c] = sp[c * G::NDOF + k * st];
       const LogRef<T> lg{sl + i * st, sl + k * st, G::NDOF};
       if (CART) {
-        pair_flux8_cart<ND, T, FLUX, LM, true>(a, b, va_n, sp[(1 + n) * G::NDOF + k * st], n2n, n, f, lg, pp0);
+        pair_flux8_cart<ND, T, FLUX, LM, true, kBeta>(a, b, va_n, sp[(1 + n) * G::NDOF + k * st], n2n, n, f, lg,
+                                                       pp0, c2);
       } else {
         T n2[ND];
 #pragma unroll
         for (int j = 0; j < ND; ++j) n2[j] = ja_i[j] + sj[j * G::NDOF + k * st];
-        pair_flux8<ND, T, FLUX, LM, true>(a, b, n2, f, lg, pp0);
+        pair_flux8<ND, T, FLUX, LM, true, kBeta>(a, b, n2, f, lg, pp0, c2);
       }
       const T dik = op.Dt8[i * N + k], dki = op.Dt8[k * N + i];
       // f[0] is the halved mass flux: 2 dik (f[0]) equals dik (2 f[0]) exactly
@@ -449,7 +455,8 @@ __device__ __forceinline__ void volume_tile(const double* u, const T* __restrict
 #pragma unroll
     for (int c = 0; c < G::NV; ++c) uc[c] = ue[c * G::NDOF];
     T q[NQ];
-    ok &= node_quantities<ND, T>(uc, gm1, T(2) / gm1, q, nullptr, var.sh_eh, var.sh_el, var.sh_pp);
+    ok &= node_quantities<ND, T>(uc, gm1, T(2) / gm1, q, nullptr, var.sh_eh, var.sh_el, var.sh_pp,
+                                 sizeof(T) == 8 && LMK == LM_SHARED_RCP && var.flux == 0);  // line_pairs' kBeta
 #pragma unroll
     for (int c = 0; c < NQ; ++c) s_prim[(el * NQ + c) * G::NDOF + i] = q[c];
     if constexpr (LMK == LM_PRELOG) {  // the element's range of rho and w = pp/rho (positive floats order as integers)
@@ -500,10 +507,10 @@ __device__ __forceinline__ void volume_tile(const double* u, const T* __restrict
     T* sa = s_acc + (el * ND + n) * G::NV * G::NDOF + base;
     const T n2n = T(2) * to_flux<T>(cart_jn(var, n));
     if constexpr (LMK == LM_SHARED_RCP) {
-      const T pp0 = T(var.sh_pp);
+      const T pp0 = T(var.sh_pp), c2 = T(2) / gm1;
       switch (var.flux * 2 + var.cart) {
-        case 0: line_pairs<ND, N, T, 0, false>(sp, sj, sl, st, n, n2n, op, sa, nullptr, nullptr, pp0); break;
-        case 1: line_pairs<ND, N, T, 0, true>(sp, sj, sl, st, n, n2n, op, sa, nullptr, nullptr, pp0); break;
+        case 0: line_pairs<ND, N, T, 0, false>(sp, sj, sl, st, n, n2n, op, sa, nullptr, nullptr, pp0, c2); break;
+        case 1: line_pairs<ND, N, T, 0, true>(sp, sj, sl, st, n, n2n, op, sa, nullptr, nullptr, pp0, c2); break;
         case 2: line_pairs<ND, N, T, 1, false>(sp, sj, sl, st, n, n2n, op, sa, nullptr, nullptr, pp0); break;
         default: line_pairs<ND, N, T, 1, true>(sp, sj, sl, st, n, n2n, op, sa, nullptr, nullptr, pp0); break;
       }

@@ -328,7 +328,8 @@ __device__ __forceinline__ void pipe_tiles(const Src& src, const OpTable<N, T>& 
 #pragma unroll
       for (int c = 0; c < G::NV; ++c) uc[c] = s_in[(el * G::NV + c) * G::NDOF + i];
       T q[NQ];
-      ok &= node_quantities<ND, T>(uc, gm1, T(2) / gm1, q, nullptr, var.sh_eh, var.sh_el, var.sh_pp);
+      ok &= node_quantities<ND, T>(uc, gm1, T(2) / gm1, q, nullptr, var.sh_eh, var.sh_el, var.sh_pp,
+                                   sizeof(T) == 8 && var.flux == 0);  // beta = rho/p as line_pairs' kBeta
 #pragma unroll
       for (int c = 0; c < NQ; ++c) s_prim[(el * NQ + c) * G::NDOF + i] = q[c];
     }
@@ -360,10 +361,10 @@ __device__ __forceinline__ void pipe_tiles(const Src& src, const OpTable<N, T>& 
       const T* fu = s_fc + ((1 * ND + n) * EPB + el) * kFaceT + l;
       const T* fl = s_fc + ((0 * ND + n) * EPB + el) * kFaceT + l;
       const T n2n = T(2) * to_flux<T>(cart_jn(var, n));
-      const T pp0 = T(var.sh_pp);
+      const T pp0 = T(var.sh_pp), c2 = T(2) / gm1;
       switch (var.flux * 2 + var.cart) {
-        case 0: line_pairs<ND, N, T, 0, false>(sp, sj, nullptr, st, n, n2n, op, sa, fu, fl, pp0); break;
-        case 1: line_pairs<ND, N, T, 0, true>(sp, sj, nullptr, st, n, n2n, op, sa, fu, fl, pp0); break;
+        case 0: line_pairs<ND, N, T, 0, false>(sp, sj, nullptr, st, n, n2n, op, sa, fu, fl, pp0, c2); break;
+        case 1: line_pairs<ND, N, T, 0, true>(sp, sj, nullptr, st, n, n2n, op, sa, fu, fl, pp0, c2); break;
         case 2: line_pairs<ND, N, T, 1, false>(sp, sj, nullptr, st, n, n2n, op, sa, fu, fl, pp0); break;
         default: line_pairs<ND, N, T, 1, true>(sp, sj, nullptr, st, n, n2n, op, sa, fu, fl, pp0); break;
       }
