@@ -111,6 +111,7 @@ __device__ __forceinline__ Variant general_variant(int lm = LM_SHARED_RCP) {
   v.invJ = 0.0;
   v.sh_eh = v.sh_el = v.sh_pp = 0.0f;  // batches take no reference pressure
   v.ghost = 0;                         // nor partitioned contexts
+  v.fgeo = nullptr;                    // the interface kernel forms the geometry from the instances' metric terms
   return v;
 }
 

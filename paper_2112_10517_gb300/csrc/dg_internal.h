@@ -102,6 +102,10 @@ struct Variant {
   // elements [ghost, E) only; the interface kernel computes only the last direction's faces of ghost elements (the
   // partition's lower boundary). 0: an ordinary context.
   int ghost;
+  // FP64, curvilinear: per interface node, the lower element's metric vector scaled for the lifted flux
+  // (m2 = p(p+1)/8 Ja^n at the face node) and the LLF wave speed's geometric factor gamma |m2|^2 / 2, as
+  // [E][ND][4][NL] (computed once at dg_init); nullptr: the interface kernel forms them from the metric terms.
+  const double* fgeo;
 };
 
 // RHS kernels. Each returns the launch error. Ja is FP64 for precision DG_FP64 and FP32 for DG_FP32; the face
@@ -186,6 +190,7 @@ struct dg_ctx {
   int part_dir, part_begin, part_end;
   long long layer;       // elements per layer (the ghost layer and each halo plane's element count)
   long long owned_elems;  // elements computed (E minus the ghost layer)
+  double* d_fgeo;  // interface geometry (Variant::fgeo; FP64 curvilinear contexts)
   double* d_red;   // entropy-rate partials + result
   int* d_flag;     // non-physical-state flag
   cudaStream_t last_stream;

@@ -209,6 +209,7 @@ void release(dg_ctx* c) {
   cudaFree(c->d_gface);
   cudaFree(c->d_hstage);
   cudaFree(c->d_red);
+  cudaFree(c->d_fgeo);
   cudaFree(c->d_flag);
   if (c->prof_ev) {
     for (int i = 0; i < 2 * c->prof_cap; ++i) cudaEventDestroy(c->prof_ev[i]);
@@ -503,6 +504,32 @@ dg_status init_ctx(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metr
   if (ce == cudaSuccess) ce = cudaMemcpy(c->d_invJ, invJ.data(), nj * sizeof(double), cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) ce = cudaMemcpy(c->d_JW, JW.data(), nj * sizeof(double), cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) ce = cudaMemset(c->d_flag, 0, sizeof(int));
+  // interface geometry of FP64 curvilinear contexts: per interface node (element e, direction n, face node l) the
+  // lower element's metric vector at its face node scaled by p(p+1)/8 (the lifted flux's factor: 2 x N(N-1)/16) and
+  // gamma |m2|^2 / 2, the LLF wave speed's geometric factor (Variant::fgeo, [E][nd][4][NL])
+  if (ce == cudaSuccess && c->precision == DG_FP64 && !c->var.cart && !gauss) {
+    const int NL = Nd / N;
+    std::vector<double> fg((size_t)E * nd * 4 * NL, 0.0);
+    const double sc = N * (N - 1) / 8.0;
+    for (long long e = 0; e < E; ++e)
+      for (int n = 0; n < nd; ++n) {
+        const int st = ipow(N, n);
+        for (int l = 0; l < NL; ++l) {
+          const int node = l % st + (N - 1) * st + (l / st) * st * N;
+          double mm = 0.0;
+          double* g = &fg[(((size_t)e * nd + n) * 4) * NL + l];
+          for (int j = 0; j < nd; ++j) {
+            const double m2 = c->h_Ja[(((size_t)e * nd + n) * nd + j) * Nd + node] * sc;
+            g[(size_t)j * NL] = m2;
+            mm += m2 * m2;
+          }
+          g[(size_t)3 * NL] = 0.5 * opts->gamma * mm;
+        }
+      }
+    ce = dev_alloc(&c->d_fgeo, fg.size());
+    if (ce == cudaSuccess) ce = cudaMemcpy(c->d_fgeo, fg.data(), fg.size() * sizeof(double), cudaMemcpyHostToDevice);
+    c->var.fgeo = c->d_fgeo;
+  }
   if (ce == cudaSuccess && c->precision == DG_FP32) {
     std::vector<float> ja32(nja);
     for (size_t i = 0; i < nja; ++i) ja32[i] = (float)c->h_Ja[i];

@@ -126,11 +126,20 @@ __device__ __forceinline__ void interface_node(const double* __restrict__ u, con
   const int nodeR = lo + hi * st * N;
   // the pair flux takes 2 m and returns 8 f: with 2 m scaled by lift8 = N(N-1)/16 the result is f / w_0
   constexpr double kLift8 = N * (N - 1) / 16.0;
-  T m[ND], m2[ND];
+  T m[ND], m2[ND], gm2 = T(0);
+  // FP64 curvilinear contexts: m2 and gamma |m2|^2 / 2 precomputed per interface node (Variant::fgeo)
+  const bool pre = sizeof(T) == 8 && var.fgeo != nullptr;
   const T jn = var.cart ? to_flux<T>(cart_jn(var, n)) : T(0);  // (integer-pipe conversion in FP32 mode)
+  if (pre) {
+    const double* g = var.fgeo + (size_t)t * 4 * G::NL + fn;  // [E][ND][4][NL], t = e ND + n
 #pragma unroll
-  for (int j = 0; j < ND; ++j)  // the metric terms are written once, at set-up: read before the wait
-    m[j] = var.cart ? (j == n ? jn : T(0)) : Ja[(((size_t)e * ND + n) * ND + j) * G::NDOF + nodeL];
+    for (int j = 0; j < ND; ++j) m2[j] = (T)g[j * G::NL];
+    gm2 = (T)g[3 * G::NL];
+  } else {
+#pragma unroll
+    for (int j = 0; j < ND; ++j)  // the metric terms are written once, at set-up: read before the wait
+      m[j] = var.cart ? (j == n ? jn : T(0)) : Ja[(((size_t)e * ND + n) * ND + j) * G::NDOF + nodeL];
+  }
   pdl_wait();  // the state comes from the kernel before (a stage update)
   double uL[G::NV], uR[G::NV];
 #pragma unroll
@@ -138,8 +147,10 @@ __device__ __forceinline__ void interface_node(const double* __restrict__ u, con
     uL[c] = u[((size_t)e * G::NV + c) * G::NDOF + nodeL];
     uR[c] = u[((size_t)eR * G::NV + c) * G::NDOF + nodeR];
   }
+  if (!pre) {
 #pragma unroll
-  for (int j = 0; j < ND; ++j) m2[j] = m[j] * T(2.0 * kLift8);
+    for (int j = 0; j < ND; ++j) m2[j] = m[j] * T(2.0 * kLift8);
+  }
   const T gm1 = gamma - T(1);
   // the states in the flux precision, converted once (FP32 mode: also the LLF jump below); with a reference
   // pressure (FP32 mode) the energies relative to that of p_ref, so that their jump, and the pressure terms of the
@@ -167,15 +178,30 @@ __device__ __forceinline__ void interface_node(const double* __restrict__ u, con
   if (!ok) atomicOr(flag, 1);
   pair_flux8<ND, T, FLUX>(qL, qR, m2, f, LogRef<T>{nullptr, nullptr, 0}, pp0);  // f(u_L, u_R, m) / w_0
   if (LLF) {
-    T mm = m[0] * m[0], vnL = qL[1] * m[0], vnR = qR[1] * m[0];
+    // with the precomputed geometry the speeds come out scaled like m2 (by p(p+1)/8), which the last factor undoes
+    T vnL, vnR, hgm;
+    if (pre) {
+      vnL = qL[1] * m2[0];
+      vnR = qR[1] * m2[0];
 #pragma unroll
-    for (int j = 1; j < ND; ++j) {
-      mm += m[j] * m[j];
-      vnL += qL[1 + j] * m[j];
-      vnR += qR[1 + j] * m[j];
+      for (int j = 1; j < ND; ++j) {
+        vnL += qL[1 + j] * m2[j];
+        vnR += qR[1 + j] * m2[j];
+      }
+      hgm = gm2;
+    } else {
+      T mm = m[0] * m[0];
+      vnL = qL[1] * m[0];
+      vnR = qR[1] * m[0];
+#pragma unroll
+      for (int j = 1; j < ND; ++j) {
+        mm += m[j] * m[j];
+        vnL += qL[1 + j] * m[j];
+        vnR += qR[1 + j] * m[j];
+      }
+      hgm = T(0.5) * gamma * mm;
     }
     // c |m| = sqrt(gamma p |m|^2 / rho) with p = pp/2: one root per side (FP64: to about 46 bits, sqrt_wave_f64)
-    const T hgm = T(0.5) * gamma * mm;
     const T aL = hgm * unshift_pp(qL[NodeQ<ND>::PP], pp0) * irL, aR = hgm * unshift_pp(qR[NodeQ<ND>::PP], pp0) * irR;
     T cL, cR;
     if constexpr (sizeof(T) == 8) {
@@ -187,7 +213,8 @@ __device__ __forceinline__ void interface_node(const double* __restrict__ u, con
     }
     const T lamL = Num<T>::abs(vnL) + cL;
     const T lamR = Num<T>::abs(vnR) + cR;
-    const T lam4 = T(4.0 * kLift8) * Num<T>::maxnn(lamL, lamR);  // (lambda / 2) / w_0
+    const T lmax = Num<T>::maxnn(lamL, lamR);
+    const T lam4 = pre ? lmax + lmax : T(4.0 * kLift8) * lmax;  // (lambda / 2) / w_0
 #pragma unroll
     for (int c = 0; c < G::NV; ++c) {
       // FP64: the jump in FP64; FP32 mode: both states rounded to FP32 first (no FP64 arithmetic)
