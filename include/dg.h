@@ -192,10 +192,12 @@ dg_status dg_rhs(dg_ctx* ctx, const double* u, double* du, double t, dg_stream_t
 dg_status dg_step(dg_ctx* ctx, double* u, double* scratch, double t, double dt, int scheme, dg_stream_t stream);
 
 /* The same with the state in host memory: queue on `stream` the host->device copy of u_host, dg_step (or dg_rhs)
-   on device copies owned by the context, and the device->host copy of the result (the new state into u_host, or
-   du into du_host). Pinned host memory makes the copies asynchronous; the caller synchronizes the stream before
-   reading the result. The first call allocates three state arrays of device memory held by the context until
-   dg_free. Errors as dg_step / dg_rhs. */
+   on device copies owned by the context, and the result into host memory (the new state into u_host, or du into
+   du_host). When the result buffer is page-locked (cudaHostAlloc / cudaHostRegister, torch pin_memory), the last
+   kernel writes the result straight into it through its device address, over the CPU-GPU link while it computes,
+   and no device->host copy follows; otherwise a device->host copy does. Pinned host memory also makes the
+   host->device copy asynchronous. The caller synchronizes the stream before reading the result. The first call
+   allocates three state arrays of device memory held by the context until dg_free. Errors as dg_step / dg_rhs. */
 dg_status dg_step_host(dg_ctx* ctx, double* u_host, double t, double dt, int scheme, dg_stream_t stream);
 dg_status dg_rhs_host(dg_ctx* ctx, const double* u_host, double* du_host, double t, dg_stream_t stream);
 

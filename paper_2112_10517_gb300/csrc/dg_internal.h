@@ -74,6 +74,8 @@ struct Epilogue {
   double* u;       // RK4: solution at the start of the step (updated at the last stage); CK45: the state
   double* y;       // RK4: next stage state; CK45: the K register
   double* acc;     // RK4: accumulated sum of b_s dt k_s
+  double* uw;      // where the stage writes the updated state: u, or (dg_step_host's last stage) the device address
+                   // of the caller's pinned host buffer, which then receives the new state as it is computed
 };
 
 // Runtime variant of the RHS kernels (uniform over a launch): the two-point flux and the Cartesian

@@ -667,14 +667,17 @@ dg_status check_step_args(const dg_ctx* c, const double* u, const double* scratc
 }
 
 // Stage `st` of the scheme: the interface fluxes of the stage state, then the volume term whose epilogue applies
-// the stage update (no du round trip, no update kernel).
-dg_status run_stage(dg_ctx* c, double* u, double* scratch, double dt, int scheme, int st, cudaStream_t s) {
+// the stage update (no du round trip, no update kernel). uw (optional): where the stage writes the updated state
+// instead of u (dg_step_host's last stage: the caller's pinned host buffer).
+dg_status run_stage(dg_ctx* c, double* u, double* scratch, double dt, int scheme, int st, cudaStream_t s,
+                    double* uw = nullptr) {
   const size_t n = (size_t)c->state_len;
   const void* ja = c->precision == DG_FP32 ? (const void*)c->d_Ja32 : (const void*)c->d_Ja;
   dgk::Epilogue epi{};
   epi.mode = scheme == DG_RK4_CLASSIC ? dgk::EPI_RK4 : dgk::EPI_CK45;
   epi.dt = dt;
   epi.u = u;
+  epi.uw = uw ? uw : u;
   epi.y = scratch;
   epi.acc = scheme == DG_RK4_CLASSIC ? scratch + n : nullptr;
   // stage state: RK4 evaluates u, then y; CK45 evaluates u (updated in place)
@@ -732,7 +735,19 @@ static dg_status ensure_host_staging(dg_ctx* c) {
   return cuda_status(dev_alloc(&c->d_hstage, (size_t)c->state_len * 3));
 }
 
+// The device address of pinned host memory (nullptr for pageable memory): a kernel can then write results into the
+// caller's host buffer as it computes them (over the CPU-GPU link, overlapped with the computation).
+static double* mapped_host(void* p) {
+  void* d = nullptr;
+  if (cudaHostGetDevicePointer(&d, p, 0) != cudaSuccess) {
+    cudaGetLastError();  // not page-locked: clear the (non-sticky) error and copy instead
+    return nullptr;
+  }
+  return static_cast<double*>(d);
+}
+
 dg_status dg_step_host(dg_ctx* c, double* u_host, double t, double dt, int scheme, dg_stream_t stream) {
+  (void)t;
   if (!c || !u_host) return DG_ERR_ARG;
   if (c->layer) return DG_ERR_UNSUPPORTED;
   dg_status st = ensure_host_staging(c);
@@ -740,10 +755,19 @@ dg_status dg_step_host(dg_ctx* c, double* u_host, double t, double dt, int schem
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = (size_t)c->state_len * sizeof(double);
   double* u = c->d_hstage;
+  st = check_step_args(c, u, u + c->state_len, dt, scheme);
+  if (st != DG_OK) return st;
+  // pinned u_host: the last stage's volume kernel writes the new state straight into it (no device-to-host copy)
+  double* out = mapped_host(u_host);
   cudaError_t e = cudaMemcpyAsync(u, u_host, bytes, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_status(e);
-  st = dg_step(c, u, u + c->state_len, t, dt, scheme, stream);
-  if (st != DG_OK) return st;
+  c->last_stream = s;
+  const int stages = scheme == DG_RK4_CLASSIC ? 4 : 5;
+  for (int k = 0; k < stages; ++k) {
+    st = run_stage(c, u, u + c->state_len, dt, scheme, k, s, k == stages - 1 ? out : nullptr);
+    if (st != DG_OK) return st;
+  }
+  if (out) return DG_OK;
   return cuda_status(cudaMemcpyAsync(u_host, u, bytes, cudaMemcpyDeviceToHost, s));
 }
 
@@ -755,11 +779,14 @@ dg_status dg_rhs_host(dg_ctx* c, const double* u_host, double* du_host, double t
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = (size_t)c->state_len * sizeof(double);
   double* u = c->d_hstage;
-  double* du = u + c->state_len;
+  // pinned du_host: the volume kernel stores du straight into it (no device-to-host copy)
+  double* out = mapped_host(du_host);
+  double* du = out ? out : u + c->state_len;
   cudaError_t e = cudaMemcpyAsync(u, u_host, bytes, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_status(e);
   st = dg_rhs(c, u, du, t, stream);
   if (st != DG_OK) return st;
+  if (out) return DG_OK;
   return cuda_status(cudaMemcpyAsync(du_host, du, bytes, cudaMemcpyDeviceToHost, s));
 }
 

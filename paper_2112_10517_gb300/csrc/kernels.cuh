@@ -271,12 +271,12 @@ __device__ __forceinline__ void stage_update(const Epilogue& epi, size_t o, doub
       epi.acc[o] = yo + epi.ca * k;
       epi.y[o] = uo + epi.cy * k;
     } else {
-      epi.u[o] = uo + yo + epi.ca * k;
+      epi.uw[o] = uo + yo + epi.ca * k;
     }
   } else {
     const double kk = (epi.stage == 0 ? 0.0 : epi.a * yo) + epi.dt * k;
     epi.y[o] = kk;
-    epi.u[o] = uo + epi.b * kk;
+    epi.uw[o] = uo + epi.b * kk;
   }
 }
 
@@ -305,12 +305,12 @@ __device__ __forceinline__ void stage_update_w(const Epilogue& epi, size_t o, do
       epi.acc[o] = yo + w1 * tot;
       epi.y[o] = uo + w2 * tot;
     } else {
-      epi.u[o] = uo + yo + w1 * tot;
+      epi.uw[o] = uo + yo + w1 * tot;
     }
   } else {
     const double kk = (epi.stage == 0 ? 0.0 : epi.a * yo) + w1 * tot;
     epi.y[o] = kk;
-    epi.u[o] = uo + epi.b * kk;
+    epi.uw[o] = uo + epi.b * kk;
   }
 }
 

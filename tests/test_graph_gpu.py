@@ -136,6 +136,28 @@ def test_host_buffer_entry_points_match_device_calls(dgmod):
         ctx.rhs_host(ud, duh)  # a device tensor is not a host state
 
 
+@pytest.mark.parametrize("scheme", [0, 1])
+@pytest.mark.parametrize("precision,nelem,staging", [("fp64", [16, 16, 16], "auto"), ("fp32", [16, 16, 16], "auto"),
+                                                     ("fp64", [3, 4, 3], "direct")])
+def test_host_step_writes_the_result_into_pinned_memory(dgmod, scheme, precision, nelem, staging):
+    # a pinned result buffer receives the last stage's state from the volume kernel itself (through its device
+    # address); a pageable one by a copy: both equal dg_step on the device bit for bit, both schemes, both kernels
+    import torch
+    sc = Scenario(3, nelem, 3, mapping="sine", ic="tgv", llf=True)
+    ctx = dgmod.DG(precision=precision, staging=staging, **sc.dg_kwargs())
+    ud = torch.from_numpy(sc.u).cuda()
+    pinned = torch.from_numpy(sc.u.copy()).pin_memory()
+    pageable = torch.from_numpy(sc.u.copy())
+    for _ in range(2):
+        ctx.step(ud, 1e-3, scheme)
+        ctx.step_host(pinned, 1e-3, scheme)
+        ctx.step_host(pageable, 1e-3, scheme)
+        torch.cuda.synchronize()
+    ref = ud.cpu()
+    assert torch.equal(pinned, ref) and torch.equal(pageable, ref)
+    assert ctx.check_status() == dgmod.DG_OK
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("staging,p,nelem", [("pipelined", 3, [16, 16, 16]), ("direct", 3, [4, 3, 5]),
                                              ("pipelined", 2, [9, 8, 10])])
