@@ -165,7 +165,7 @@ __device__ __forceinline__ void interface_node(const double* __restrict__ u, con
   uRt[G::NV - 1] = energy_rel<T>(uR[G::NV - 1], var.sh_eh, var.sh_el);
   const T pp0 = T(var.sh_pp);  // 2 p_ref (FP32 mode), else 0
   T qL[NodeQ<ND>::NQ], qR[NodeQ<ND>::NQ], f[G::NV], irL, irR;
-  if constexpr (sizeof(T) == 8) {  // one Newton reciprocal for both densities: 1/rho_L = rho_R R, R = 1/(rho_L rho_R)
+  if constexpr (sizeof(T) == 8) {  // one reciprocal for both densities: 1/rho_L = rho_R R, R = 1/(rho_L rho_R)
     const T R = Num<T>::rcp(uLt[0] * uRt[0]);
     irL = uRt[0] * R;
     irR = uLt[0] * R;
