@@ -360,7 +360,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // stage update the kernel writes arrays that alias its input u (the CTA has read its own elements before the
 // barrier; no other CTA reads them).
 // The pairs i < k of one line (Sec. 2.2): sp/sj point at the line's first node in the node-quantity and metric
-// arrays (stride st), sa at its accumulator slots; each pair's flux is evaluated once and added to both nodes.
+// arrays (stride st), sa at its accumulator slots (node k at so[k] = k st from sp and sa); each pair's flux is
+// evaluated once and added to both nodes.
 // With LM == LM_PRELOG, sl points at the line's first node in the per-node logarithm array [2][NDOF].
 // fu, fl (optional): the lifted interface fluxes (f* / w_0, component stride NL) of the line's upper and lower face
 // point; the surface term then starts the end nodes' sums (+fu at node N-1, -fl at node 0) instead of being added
@@ -371,7 +372,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // FP32 keeps pg (its FP32 pipe is not the bound, and the reciprocal lengthens phase A: +1.8 % at 16^3); so do
 // Shima's flux and the log-mean variants.
 template <int ND, int N, typename T, int FLUX, bool CART, int LM = LM_SHARED_RCP>
-__device__ __forceinline__ void line_pairs(const T* sp, const T* sj, const T* sl, int st, int n, T n2n,
+__device__ __forceinline__ void line_pairs(const T* sp, const int (&so)[N], const T* sj, const T* sl, int st, int n, T n2n,
                                            const OpTable<N, T>& op, T* sa, const T* fu = nullptr,
                                            const T* fl = nullptr, T pp0 = T(0), T c2 = T(0)) {
   constexpr bool kBeta = FLUX == 0 && LM == LM_SHARED_RCP && sizeof(T) == 8;
@@ -393,9 +394,9 @@ __device__ __forceinline__ void line_pairs(const T* sp, const T* sj, const T* sl
   for (int i = 0; i < N - 1; ++i) {
     T a[NQ], ja_i[ND], va_n = T(0);
 #pragma unroll
-    for (int c = 0; c < NQ; ++c) a[c] = sp[c * G::NDOF + i * st];
+    for (int c = 0; c < NQ; ++c) a[c] = sp[c * G::NDOF + so[i]];
     if (CART) {
-      va_n = sp[(1 + n) * G::NDOF + i * st];
+      va_n = sp[(1 + n) * G::NDOF + so[i]];
     } else {
 #pragma unroll
       for (int j = 0; j < ND; ++j) ja_i[j] = sj[j * G::NDOF + i * st];
@@ -404,10 +405,10 @@ __device__ __forceinline__ void line_pairs(const T* sp, const T* sj, const T* sl
     for (int k = i + 1; k < N; ++k) {
       T b[NQ], f[G::NV];
 #pragma unroll
-      for (int c = 0; c < NQ; ++c) b[c] = sp[c * G::NDOF + k * st];
+      for (int c = 0; c < NQ; ++c) b[c] = sp[c * G::NDOF + so[k]];
       const LogRef<T> lg{sl + i * st, sl + k * st, G::NDOF};
       if (CART) {
-        pair_flux8_cart<ND, T, FLUX, LM, true, kBeta>(a, b, va_n, sp[(1 + n) * G::NDOF + k * st], n2n, n, f, lg,
+        pair_flux8_cart<ND, T, FLUX, LM, true, kBeta>(a, b, va_n, sp[(1 + n) * G::NDOF + so[k]], n2n, n, f, lg,
                                                        pp0, c2);
       } else {
         T n2[ND];
@@ -429,7 +430,7 @@ __device__ __forceinline__ void line_pairs(const T* sp, const T* sj, const T* sl
 #pragma unroll
   for (int i = 0; i < N; ++i)
 #pragma unroll
-    for (int c = 0; c < G::NV; ++c) sa[c * G::NDOF + i * st] = acc[i][c];
+    for (int c = 0; c < G::NV; ++c) sa[c * G::NDOF + so[i]] = acc[i][c];
 }
 
 // One tile of EPB elements starting at element e0, computed by the kThreads threads of a CTA (kThreads >=
@@ -532,22 +533,25 @@ __device__ __forceinline__ void volume_tile(const double* u, const T* __restrict
     const T* sj = s_ja + (el * ND + n) * ND * G::NDOF + base;
     const T* sl = s_log + el * 2 * G::NDOF + base;
     T* sa = s_acc + (el * ND + n) * G::NV * G::NDOF + base;
+    int so[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) so[k] = k * st;
     const T n2n = T(2) * to_flux<T>(cart_jn(var, n));
     if constexpr (LMK == LM_SHARED_RCP) {
       const T pp0 = T(var.sh_pp), c2 = T(2) / gm1;
       switch (var.flux * 2 + var.cart) {
-        case 0: line_pairs<ND, N, T, 0, false>(sp, sj, sl, st, n, n2n, op, sa, nullptr, nullptr, pp0, c2); break;
-        case 1: line_pairs<ND, N, T, 0, true>(sp, sj, sl, st, n, n2n, op, sa, nullptr, nullptr, pp0, c2); break;
-        case 2: line_pairs<ND, N, T, 1, false>(sp, sj, sl, st, n, n2n, op, sa, nullptr, nullptr, pp0); break;
-        default: line_pairs<ND, N, T, 1, true>(sp, sj, sl, st, n, n2n, op, sa, nullptr, nullptr, pp0); break;
+        case 0: line_pairs<ND, N, T, 0, false>(sp, so, sj, sl, st, n, n2n, op, sa, nullptr, nullptr, pp0, c2); break;
+        case 1: line_pairs<ND, N, T, 0, true>(sp, so, sj, sl, st, n, n2n, op, sa, nullptr, nullptr, pp0, c2); break;
+        case 2: line_pairs<ND, N, T, 1, false>(sp, so, sj, sl, st, n, n2n, op, sa, nullptr, nullptr, pp0); break;
+        default: line_pairs<ND, N, T, 1, true>(sp, so, sj, sl, st, n, n2n, op, sa, nullptr, nullptr, pp0); break;
       }
     } else if constexpr (LMK == LM_PRELOG) {
       if (var.cart)
-        line_pairs<ND, N, T, 0, true, LM_PRELOG>(sp, sj, sl, st, n, n2n, op, sa);
+        line_pairs<ND, N, T, 0, true, LM_PRELOG>(sp, so, sj, sl, st, n, n2n, op, sa);
       else
-        line_pairs<ND, N, T, 0, false, LM_PRELOG>(sp, sj, sl, st, n, n2n, op, sa);
+        line_pairs<ND, N, T, 0, false, LM_PRELOG>(sp, so, sj, sl, st, n, n2n, op, sa);
     } else {
-      line_pairs<ND, N, T, 0, false, LMK>(sp, sj, sl, st, n, n2n, op, sa);
+      line_pairs<ND, N, T, 0, false, LMK>(sp, so, sj, sl, st, n, n2n, op, sa);
     }
   }
   __syncthreads();

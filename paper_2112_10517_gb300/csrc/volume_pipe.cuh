@@ -86,8 +86,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
 //                                                                                  mbarrier 1
 //   IJ [EPB][NDOF] f64 (1/J; not on Cartesian meshes), EU, EY [EPB][NV][NDOF] f64
 //   (fused stage update: u, and acc (RK4) / K (CK45) after stage 0)              mbarrier 2
-// then the tile scratch, node quantities [EPB][NQ][NDOF] T and per-direction sums [EPB][ND][NV][NDOF] T, then the
-// three mbarriers. Each region starts on a 16-byte boundary (for even N every element block is a multiple of 16
+// then the tile scratch, node quantities [EPB][NQ][NDOF] T and per-direction sums [EPB][ND][NV][NDOF] T (each
+// element's block followed by kElemPad bytes), then the three mbarriers. Each region starts on a 16-byte boundary (for even N every element block is a multiple of 16
 // bytes already).
 template <int ND, int N, typename T>
 struct PipeSmem {
@@ -98,8 +98,12 @@ struct PipeSmem {
   static constexpr size_t kJa = (size_t)ND * ND * G::NDOF * sizeof(T);
   static constexpr size_t kInvJ = (size_t)G::NDOF * sizeof(double);
   static constexpr size_t kFace = (size_t)G::NV * G::NL * sizeof(T);  // one face of one element
-  static constexpr size_t kPrim = (size_t)NodeQ<ND>::NQ * G::NDOF * sizeof(T);
-  static constexpr size_t kAcc = (size_t)ND * G::NV * G::NDOF * sizeof(T);
+  // 5 words between the scratch blocks of consecutive elements (4-byte T, ND = 3, N = 4): a phase-B warp holds
+  // lines of one direction for two elements, and the pad moves the second element's plane onto other banks
+  static constexpr size_t kElemPad = (ND == 3 && N == 4 && sizeof(T) == 4) ? 20 : 0;
+  static constexpr size_t kPrim = (size_t)NodeQ<ND>::NQ * G::NDOF * sizeof(T) + kElemPad;
+  static constexpr size_t kAcc = (size_t)ND * G::NV * G::NDOF * sizeof(T) + kElemPad;
+  static constexpr int kPrimT = (int)(kPrim / sizeof(T)), kAccT = (int)(kAcc / sizeof(T));  // element strides
   // byte offsets of the regions for EPB elements
   __host__ __device__ static constexpr size_t off_ja(int epb) { return r16((size_t)epb * kIn); }
   __host__ __device__ static constexpr size_t off_ij(int epb) { return off_ja(epb) + r16((size_t)epb * kJa); }
@@ -331,7 +335,7 @@ __device__ __forceinline__ void pipe_tiles(const Src& src, const OpTable<N, T>& 
       ok &= node_quantities<ND, T>(uc, gm1, T(2) / gm1, q, nullptr, var.sh_eh, var.sh_el, var.sh_pp,
                                    sizeof(T) == 8 && var.flux == 0);  // beta = rho/p as line_pairs' kBeta
 #pragma unroll
-      for (int c = 0; c < NQ; ++c) s_prim[(el * NQ + c) * G::NDOF + i] = q[c];
+      for (int c = 0; c < NQ; ++c) s_prim[el * S::kPrimT + c * G::NDOF + i] = q[c];
     }
     if (!ok) atomicOr(flag, FLAG_NONPHYSICAL);
     if (tid == 0) s_ok[1] = mbar_wait_bounded(&bars[1], par) ? 1 : 0;
@@ -351,22 +355,26 @@ __device__ __forceinline__ void pipe_tiles(const Src& src, const OpTable<N, T>& 
 
     // ---- B: the pairs i < k of each line, as in volume_tile; the end nodes' sums start from the lifted fluxes of
     // the line's two face points (face node l of the faces normal to n)
-    if (tid < nel * G::TPE) {
-      const int el = tid / G::TPE, r = tid - el * G::TPE;
-      const int n = r / G::NL, l = r - n * G::NL;
+    // direction-major threads: n = tid / (EPB NL), then the element, then the line
+    const int n = tid / (EPB * G::NL), r = tid - n * (EPB * G::NL);
+    const int el = r / G::NL, l = r - el * G::NL;
+    if (el < nel) {
       const int st = G::stride(n), lb = G::line_base(n, l);
-      const T* sp = s_prim + el * NQ * G::NDOF + lb;
+      int so[N];
+#pragma unroll
+      for (int k = 0; k < N; ++k) so[k] = k * st;
+      const T* sp = s_prim + el * S::kPrimT + lb;
       const T* sj = s_ja + (el * ND + n) * ND * G::NDOF + lb;
-      T* sa = s_acc + (el * ND + n) * G::NV * G::NDOF + lb;
+      T* sa = s_acc + el * S::kAccT + n * G::NV * G::NDOF + lb;
       const T* fu = s_fc + ((1 * ND + n) * EPB + el) * kFaceT + l;
       const T* fl = s_fc + ((0 * ND + n) * EPB + el) * kFaceT + l;
       const T n2n = T(2) * to_flux<T>(cart_jn(var, n));
       const T pp0 = T(var.sh_pp), c2 = T(2) / gm1;
       switch (var.flux * 2 + var.cart) {
-        case 0: line_pairs<ND, N, T, 0, false>(sp, sj, nullptr, st, n, n2n, op, sa, fu, fl, pp0, c2); break;
-        case 1: line_pairs<ND, N, T, 0, true>(sp, sj, nullptr, st, n, n2n, op, sa, fu, fl, pp0, c2); break;
-        case 2: line_pairs<ND, N, T, 1, false>(sp, sj, nullptr, st, n, n2n, op, sa, fu, fl, pp0); break;
-        default: line_pairs<ND, N, T, 1, true>(sp, sj, nullptr, st, n, n2n, op, sa, fu, fl, pp0); break;
+        case 0: line_pairs<ND, N, T, 0, false>(sp, so, sj, nullptr, st, n, n2n, op, sa, fu, fl, pp0, c2); break;
+        case 1: line_pairs<ND, N, T, 0, true>(sp, so, sj, nullptr, st, n, n2n, op, sa, fu, fl, pp0, c2); break;
+        case 2: line_pairs<ND, N, T, 1, false>(sp, so, sj, nullptr, st, n, n2n, op, sa, fu, fl, pp0); break;
+        default: line_pairs<ND, N, T, 1, true>(sp, so, sj, nullptr, st, n, n2n, op, sa, fu, fl, pp0); break;
       }
     }
     if (tid == 0) s_ok[2] = mbar_wait_bounded(&bars[2], par) ? 1 : 0;
@@ -389,7 +397,7 @@ __device__ __forceinline__ void pipe_tiles(const Src& src, const OpTable<N, T>& 
       for (int c = 0; c < G::NV; ++c) {
         T s = T(0);
 #pragma unroll
-        for (int n = 0; n < ND; ++n) s += s_acc[((el * ND + n) * G::NV + c) * G::NDOF + i];
+        for (int n = 0; n < ND; ++n) s += s_acc[el * S::kAccT + (n * G::NV + c) * G::NDOF + i];
         tot[c] = s;
       }
       const double ij = var.cart ? var.invJ : s_ij[el * G::NDOF + i];
