@@ -122,7 +122,9 @@ typedef struct dg_metrics {
                            tile's copies are not overlapped), except DG_FP32 at polydeg 2 (measured slower); else
                            as DG_STAGING_DIRECT.
      DG_STAGING_DIRECT     one CTA per tile, loads issued by its threads.
-   All compute the same values (the same arithmetic in the same order). A pipelined kernel whose wait for its own
+   All evaluate the same terms; the pipelined kernel starts each line's sums from the lifted interface fluxes and
+   the direct one adds them after the sums, so the two agree to rounding (the parity bounds), and DG_STAGING_AUTO
+   gives bit for bit the result of the kernel it selects. A pipelined kernel whose wait for its own
    copies runs out (bounded; it cannot under normal operation) skips the rest of its tiles and raises the flag that
    dg_check_status reports as DG_ERR_TIMEOUT.
    launch: how dg_rhs / dg_step queue the interface kernel and the pipelined volume kernel.

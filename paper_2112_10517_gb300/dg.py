@@ -164,7 +164,8 @@ class DG:
     Sec. 6; affine meshes, FP64, Ranocha's flux).
     staging: "pipelined" (the volume kernel copies tiles with asynchronous copies that overlap computation),
     "direct" (one CTA per tile, loads by its threads) or "auto" (pipelined on meshes with enough tiles per CTA,
-    except FP32 at p = 2); the same values either way.
+    except FP32 at p = 2); the same terms, added in another order (the surface term starts the pipelined kernel's
+    line sums and follows the direct kernel's), so the two agree to rounding.
     launch: "overlap" (each interface and pipelined volume kernel is scheduled ahead and starts as the kernel
     before it ends, waiting for its writes before reading them) or "serial" (ordinary launches); the same values.
     p_ref: FP32 mode only, a reference pressure (0: none) on which the momentum equations' pressure terms are

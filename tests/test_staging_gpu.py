@@ -1,9 +1,9 @@
 """The two ways the volume kernel stages an element tile (dg_opts.staging): asynchronous copies into shared memory
 that overlap the computation of a persistent CTA's tiles (DG_STAGING_PIPELINED: bulk copies for even node counts
 per line, per-thread cp.async for odd ones), and direct loads by one CTA per tile (DG_STAGING_DIRECT);
-DG_STAGING_AUTO picks the first on meshes with enough tiles per CTA. The pipelined kernel evaluates the same arithmetic in the same order, so it
-must meet the FP32 parity bound against the oracle (4e-6 of the term magnitude) and agree with the direct kernel
-to rounding; the cases cover ragged last tiles, lower-neighbour faces that wrap around the periodic mesh (copied
+DG_STAGING_AUTO picks the first on meshes with enough tiles per CTA. The pipelined kernel evaluates the same terms
+(the lifted surface term starts its line sums, where the direct kernel adds it after them), so it must meet the
+FP32 parity bound against the oracle (4e-6 of the term magnitude) and agree with the direct kernel to rounding; the cases cover ragged last tiles, lower-neighbour faces that wrap around the periodic mesh (copied
 element by element), tiles that are smaller than the grid and grids that loop over a tile count several times
 (both stage buffers reused twice), 2D and 3D, Cartesian and curvilinear meshes, both two-point fluxes, the fused
 RK4 and CK45 stage updates, and state arrays that are only 8-byte aligned (the launcher then falls back to direct
