@@ -354,7 +354,7 @@ def run_ours(args, rank, world, local_rank):
     runs = [("fp64_16", NELEM, "fp64", True), ("fp32_16", NELEM, "fp32", False),
             ("fp64_32", NELEM_LARGE, "fp64", False), ("fp32_32", NELEM_LARGE, "fp32", False)]
     if only:
-        runs = [(lab, ne, pr, False) for lab, ne, pr, _ in runs if lab in only]
+        runs = [(lab, ne, pr, main) for lab, ne, pr, main in runs if lab in only]
     for label, nelem, precision, main in runs:
         ctx, step = make_case(nelem, precision, rank, world, slabs=args.slabs)
         slab_path = world > 1 or args.slabs
@@ -1121,7 +1121,8 @@ def main(argv=None):
         for label, res in results.items():
             print(json.dumps({"configuration": label, "pid_ns": res["pid_ns"], "noprof_pid_ns": res["noprof_pid_ns"],
                               "graph_pid_ns": res["graph_pid_ns"], "ms_per_step": res["ms_per_step"],
-                              "volume_ms": res["volume_ms_avg"], "interface_ms": res["interface_ms_avg"]}),
+                              "volume_ms": res["volume_ms_avg"], "interface_ms": res["interface_ms_avg"],
+                              "e2e_pid_ns": res.get("e2e_pid_ns")}),
                   flush=True)
         for name in args.only.split(","):
             if name in runners:

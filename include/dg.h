@@ -198,8 +198,12 @@ dg_status dg_step(dg_ctx* ctx, double* u, double* scratch, double t, double dt, 
    du_host). When the result buffer is page-locked (cudaHostAlloc / cudaHostRegister, torch pin_memory), the last
    kernel writes the result straight into it through its device address, over the CPU-GPU link while it computes,
    and no device->host copy follows; otherwise a device->host copy does. Pinned host memory also makes the
-   host->device copy asynchronous. The caller synchronizes the stream before reading the result. The first call
-   allocates three state arrays of device memory held by the context until dg_free. Errors as dg_step / dg_rhs. */
+   host->device copy asynchronous. LGL meshes with at least 4 element layers along the last direction get the
+   state in 2 chunks of layers on a copy stream of the context (after the work queued on `stream` before the call),
+   and the first interface fluxes per chunk on `stream` as soon as the chunk (and the next layer) is there, so the
+   second chunk's copy overlaps the first chunk's fluxes; `stream` then waits for the copies. The caller
+   synchronizes the stream before reading the result. The first call allocates three state arrays of device memory
+   and the copy stream held by the context until dg_free. Errors as dg_step / dg_rhs. */
 dg_status dg_step_host(dg_ctx* ctx, double* u_host, double t, double dt, int scheme, dg_stream_t stream);
 dg_status dg_rhs_host(dg_ctx* ctx, const double* u_host, double* du_host, double t, dg_stream_t stream);
 

@@ -112,6 +112,7 @@ __device__ __forceinline__ Variant general_variant(int lm = LM_SHARED_RCP) {
   v.sh_eh = v.sh_el = v.sh_pp = 0.0f;  // batches take no reference pressure
   v.ghost = 0;                         // nor partitioned contexts
   v.fgeo = nullptr;                    // the interface kernel forms the geometry from the instances' metric terms
+  v.if_e0 = v.if_e1 = 0;
   return v;
 }
 

@@ -108,7 +108,15 @@ struct Variant {
   // (m2 = p(p+1)/8 Ja^n at the face node) and the LLF wave speed's geometric factor gamma |m2|^2 / 2, as
   // [E][ND][4][NL] (computed once at dg_init); nullptr: the interface kernel forms them from the metric terms.
   const double* fgeo;
+  // The interface kernel's elements: the faces of elements [if_e0, if_e1) (if_e1 = 0: all; dg_step_host's first
+  // interface fluxes, computed per chunk of the state as it arrives from the host).
+  int if_e0, if_e1;
 };
+
+// Chunks of element layers in which dg_step_host / dg_rhs_host bring the state to the device (measured on the
+// 16^3 FP64 step through dg_step_host, e2e ns/DOF: 1 chunk 0.840, 2 0.827, 3 0.830, 4 0.833, 8 0.850: each
+// further chunk adds an interface launch that waits for its copy and so cannot be scheduled ahead).
+enum { kUploadChunks = 2 };
 
 // RHS kernels. Each returns the launch error. Ja is FP64 for precision DG_FP64 and FP32 for DG_FP32; the face
 // buffer holds the same type.
@@ -188,6 +196,8 @@ struct dg_ctx {
   double* d_fadj;  // dg_vjp: face adjoint contributions [nd][E][2][nv][N^(nd-1)] (allocated at the first dg_vjp)
   double* d_gface;  // Gauss collocation: projected face states [nd][E][2][nv][N^(nd-1)]
   double* d_hstage;  // dg_step_host / dg_rhs_host: device copies of the host state (3 state arrays, first call)
+  cudaStream_t up_stream;                       // ... and their copy stream and events (first call)
+  cudaEvent_t up_ev[1 + dgk::kUploadChunks];
   // partitioned context (dg_init_part): ghost layer of `layer` elements first, then `owned` layers; 0 otherwise
   int part_dir, part_begin, part_end;
   long long layer;       // elements per layer (the ghost layer and each halo plane's element count)

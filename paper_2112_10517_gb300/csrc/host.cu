@@ -208,6 +208,10 @@ void release(dg_ctx* c) {
   cudaFree(c->d_fadj);
   cudaFree(c->d_gface);
   cudaFree(c->d_hstage);
+  if (c->up_stream) {
+    cudaStreamDestroy(c->up_stream);
+    for (int k = 0; k <= dgk::kUploadChunks; ++k) cudaEventDestroy(c->up_ev[k]);
+  }
   cudaFree(c->d_red);
   cudaFree(c->d_fgeo);
   cudaFree(c->d_flag);
@@ -625,6 +629,32 @@ dg_status dg_conserved_totals(dg_ctx* c, const double* q, double* out_host, dg_s
 
 void dg_free(dg_ctx* ctx) { release(ctx); }
 
+}  // extern "C"
+
+namespace {
+// The interface kernel (unless interface_done: already queued, per chunk, by upload_interface) and the volume
+// kernel storing du, on stream s.
+dg_status rhs_kernels(dg_ctx* c, const double* u, double* du, cudaStream_t s, bool interface_done) {
+  int slot;
+  const void* ja = c->precision == DG_FP32 ? (const void*)c->d_Ja32 : (const void*)c->d_Ja;
+  cudaError_t e = cudaSuccess;
+  if (!interface_done) {
+    dgk::prof_begin(c, dgk::KID_INTERFACE, s, &slot);
+    e = dgk::launch_interface(c->nd, c->p, c->precision, c->surface_flux == DG_SURF_EC_LLF, c->md, u, ja, c->d_face,
+                              c->gamma, c->d_flag, s, &c->var);
+    dgk::prof_end(c, s, slot);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  dgk::prof_begin(c, dgk::KID_VOLUME, s, &slot);
+  e = dgk::launch_volume(c->nd, c->p, c->precision, c->md, u, ja, c->d_invJ, c->d_face, du, c->gamma, c->d_flag, s,
+                         nullptr, &c->var);
+  dgk::prof_end(c, s, slot);
+  return cuda_status(e);
+}
+}  // namespace
+
+extern "C" {
+
 dg_status dg_rhs(dg_ctx* c, const double* u, double* du, double t, dg_stream_t stream) {
   (void)t;
   if (!c || !u || !du) return DG_ERR_ARG;
@@ -635,18 +665,7 @@ dg_status dg_rhs(dg_ctx* c, const double* u, double* du, double t, dg_stream_t s
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;
   if (c->nodes == DG_NODES_GAUSS) return gauss_rhs(c, u, du, nullptr, s);
-  int slot;
-  dgk::prof_begin(c, dgk::KID_INTERFACE, s, &slot);
-  const void* ja = c->precision == DG_FP32 ? (const void*)c->d_Ja32 : (const void*)c->d_Ja;
-  cudaError_t e = dgk::launch_interface(c->nd, c->p, c->precision, c->surface_flux == DG_SURF_EC_LLF, c->md, u, ja,
-                                        c->d_face, c->gamma, c->d_flag, s, &c->var);
-  dgk::prof_end(c, s, slot);
-  if (e != cudaSuccess) return cuda_status(e);
-  dgk::prof_begin(c, dgk::KID_VOLUME, s, &slot);
-  e = dgk::launch_volume(c->nd, c->p, c->precision, c->md, u, ja, c->d_invJ, c->d_face, du, c->gamma, c->d_flag, s,
-                         nullptr, &c->var);
-  dgk::prof_end(c, s, slot);
-  return cuda_status(e);
+  return rhs_kernels(c, u, du, s, false);
 }
 
 }  // extern "C"
@@ -670,7 +689,7 @@ dg_status check_step_args(const dg_ctx* c, const double* u, const double* scratc
 // the stage update (no du round trip, no update kernel). uw (optional): where the stage writes the updated state
 // instead of u (dg_step_host's last stage: the caller's pinned host buffer).
 dg_status run_stage(dg_ctx* c, double* u, double* scratch, double dt, int scheme, int st, cudaStream_t s,
-                    double* uw = nullptr) {
+                    double* uw = nullptr, bool interface_done = false) {
   const size_t n = (size_t)c->state_len;
   const void* ja = c->precision == DG_FP32 ? (const void*)c->d_Ja32 : (const void*)c->d_Ja;
   dgk::Epilogue epi{};
@@ -688,11 +707,14 @@ dg_status run_stage(dg_ctx* c, double* u, double* scratch, double dt, int scheme
   epi.cy = st == 2 ? dt : 0.5 * dt;
   if (c->nodes == DG_NODES_GAUSS) return gauss_rhs(c, in, nullptr, &epi, s);
   int slot;
-  dgk::prof_begin(c, dgk::KID_INTERFACE, s, &slot);
-  cudaError_t e = dgk::launch_interface(c->nd, c->p, c->precision, c->surface_flux == DG_SURF_EC_LLF, c->md, in,
-                                        ja, c->d_face, c->gamma, c->d_flag, s, &c->var);
-  dgk::prof_end(c, s, slot);
-  if (e != cudaSuccess) return cuda_status(e);
+  cudaError_t e = cudaSuccess;
+  if (!interface_done) {  // (dg_step_host's first stage: queued per chunk of the state by upload_interface)
+    dgk::prof_begin(c, dgk::KID_INTERFACE, s, &slot);
+    e = dgk::launch_interface(c->nd, c->p, c->precision, c->surface_flux == DG_SURF_EC_LLF, c->md, in, ja,
+                              c->d_face, c->gamma, c->d_flag, s, &c->var);
+    dgk::prof_end(c, s, slot);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
   dgk::prof_begin(c, dgk::KID_VOLUME, s, &slot);
   e = dgk::launch_volume(c->nd, c->p, c->precision, c->md, in, ja, c->d_invJ, c->d_face, nullptr, c->gamma,
                          c->d_flag, s, &epi, &c->var);
@@ -731,8 +753,72 @@ dg_status dg_step_stage(dg_ctx* c, double* u, double* scratch, double t, double 
 
 // Device staging of dg_step_host / dg_rhs_host: three state arrays, allocated at the first call.
 static dg_status ensure_host_staging(dg_ctx* c) {
-  if (c->d_hstage) return DG_OK;
-  return cuda_status(dev_alloc(&c->d_hstage, (size_t)c->state_len * 3));
+  if (!c->d_hstage) {
+    const dg_status st = cuda_status(dev_alloc(&c->d_hstage, (size_t)c->state_len * 3));
+    if (st != DG_OK) return st;
+  }
+  if (c->up_stream) return DG_OK;
+  cudaEvent_t ev[1 + dgk::kUploadChunks];
+  int made = 0;
+  cudaError_t e = cudaSuccess;
+  for (; made <= dgk::kUploadChunks; ++made)
+    if ((e = cudaEventCreateWithFlags(&ev[made], cudaEventDisableTiming)) != cudaSuccess) break;
+  cudaStream_t us = nullptr;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&us, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
+    return cuda_status(e);
+  }
+  for (int k = 0; k <= dgk::kUploadChunks; ++k) c->up_ev[k] = ev[k];
+  c->up_stream = us;
+  return DG_OK;
+}
+
+// Brings the host state u_host into u (device) for dg_step_host / dg_rhs_host. On LGL meshes with at least two
+// element layers per chunk along the last direction, the copy runs in kUploadChunks (2) chunks of layers on the
+// context's copy stream, and the interface kernel of u is queued on s per chunk: the faces of the elements whose
+// upper neighbours have all arrived (each face flux reads an element and its upper neighbour; the last layer's
+// upper neighbour across the periodic boundary is the first chunk's), so that the copy of each chunk overlaps the
+// interface fluxes of the one before. *interface_done tells the caller that the interface fluxes of u are queued.
+// Otherwise one copy on s.
+static dg_status upload_interface(dg_ctx* c, double* u, const double* u_host, cudaStream_t s, bool* interface_done) {
+  *interface_done = false;
+  const long long nlayer = c->nd == 3 ? c->md.n3 : c->md.n2;
+  const long long per_layer = (long long)c->md.E / nlayer;  // elements per layer along the last direction
+  const size_t per_elem = (size_t)c->nv * c->Nd;          // doubles per element
+  constexpr int K = dgk::kUploadChunks;
+  if (c->nodes == DG_NODES_GAUSS || nlayer < 2 * K)
+    return cuda_status(cudaMemcpyAsync(u, u_host, (size_t)c->state_len * sizeof(double), cudaMemcpyHostToDevice, s));
+  // the copies may start once the work queued on s before this call (which may read u) is done
+  cudaError_t e = cudaEventRecord(c->up_ev[0], s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->up_stream, c->up_ev[0], 0);
+  for (int k = 0; k < K && e == cudaSuccess; ++k) {
+    const long long z0 = k * nlayer / K, z1 = (k + 1) * nlayer / K;
+    const size_t off = (size_t)(z0 * per_layer) * per_elem;
+    e = cudaMemcpyAsync(u + off, u_host + off, (size_t)((z1 - z0) * per_layer) * per_elem * sizeof(double),
+                        cudaMemcpyHostToDevice, c->up_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->up_ev[1 + k], c->up_stream);
+  }
+  if (e != cudaSuccess) return cuda_status(e);
+  const void* ja = c->precision == DG_FP32 ? (const void*)c->d_Ja32 : (const void*)c->d_Ja;
+  for (int k = 0; k < K; ++k) {
+    // chunk k holds layers [z_k, z_k+1): the elements of layers [z_k - 1, z_k+1 - 1) have all their upper
+    // neighbours in chunks 0..k (the first part starts at layer 0, the last one ends at the last layer)
+    const long long zk = k * nlayer / K, zn = (k + 1) * nlayer / K;
+    dgk::Variant v = c->var;
+    v.if_e0 = (int)(k == 0 ? 0 : (zk - 1) * per_layer);
+    v.if_e1 = (int)(k == K - 1 ? c->md.E : (zn - 1) * per_layer);
+    e = cudaStreamWaitEvent(s, c->up_ev[1 + k], 0);
+    if (e != cudaSuccess) return cuda_status(e);
+    int slot;
+    dgk::prof_begin(c, dgk::KID_INTERFACE, s, &slot);
+    e = dgk::launch_interface(c->nd, c->p, c->precision, c->surface_flux == DG_SURF_EC_LLF, c->md, u, ja, c->d_face,
+                              c->gamma, c->d_flag, s, &v);
+    dgk::prof_end(c, s, slot);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  *interface_done = true;
+  return DG_OK;
 }
 
 // The device address of pinned host memory (nullptr for pageable memory): a kernel can then write results into the
@@ -759,12 +845,13 @@ dg_status dg_step_host(dg_ctx* c, double* u_host, double t, double dt, int schem
   if (st != DG_OK) return st;
   // pinned u_host: the last stage's volume kernel writes the new state straight into it (no device-to-host copy)
   double* out = mapped_host(u_host);
-  cudaError_t e = cudaMemcpyAsync(u, u_host, bytes, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return cuda_status(e);
   c->last_stream = s;
+  bool if_done = false;
+  st = upload_interface(c, u, u_host, s, &if_done);  // the first stage's input is u
+  if (st != DG_OK) return st;
   const int stages = scheme == DG_RK4_CLASSIC ? 4 : 5;
   for (int k = 0; k < stages; ++k) {
-    st = run_stage(c, u, u + c->state_len, dt, scheme, k, s, k == stages - 1 ? out : nullptr);
+    st = run_stage(c, u, u + c->state_len, dt, scheme, k, s, k == stages - 1 ? out : nullptr, k == 0 && if_done);
     if (st != DG_OK) return st;
   }
   if (out) return DG_OK;
@@ -782,9 +869,11 @@ dg_status dg_rhs_host(dg_ctx* c, const double* u_host, double* du_host, double t
   // pinned du_host: the volume kernel stores du straight into it (no device-to-host copy)
   double* out = mapped_host(du_host);
   double* du = out ? out : u + c->state_len;
-  cudaError_t e = cudaMemcpyAsync(u, u_host, bytes, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return cuda_status(e);
-  st = dg_rhs(c, u, du, t, stream);
+  c->last_stream = s;
+  bool if_done = false;
+  st = upload_interface(c, u, u_host, s, &if_done);
+  if (st != DG_OK) return st;
+  st = if_done ? rhs_kernels(c, u, du, s, true) : dg_rhs(c, u, du, t, stream);
   if (st != DG_OK) return st;
   if (out) return DG_OK;
   return cuda_status(cudaMemcpyAsync(du_host, du, bytes, cudaMemcpyDeviceToHost, s));

@@ -191,3 +191,36 @@ def test_overlapped_launches_equal_serial_launches(dgmod, precision, staging, p,
         np.testing.assert_array_equal(a, b)
     np.testing.assert_array_equal(res["overlap"][0], res["overlap"][2])
     np.testing.assert_array_equal(res["overlap"][1], res["overlap"][3])
+
+
+@pytest.mark.parametrize("nd,nelem,chunked", [(3, [4, 3, 9], True), (3, [3, 2, 4], True), (2, [5, 11], True),
+                                             (3, [2, 3, 3], False)])
+def test_host_entry_points_upload_the_state_in_chunks(dgmod, nd, nelem, chunked):
+    # with at least 4 element layers along the last direction the host state arrives in 2 chunks of layers on a
+    # copy stream, and the first interface fluxes are computed per chunk as it arrives (2 interface launches
+    # instead of 1): bit for bit the device calls' results, for uneven chunks (9 layers), two layers per chunk
+    # (4), 2D, and 3 layers (one copy); pinned and pageable host memory
+    import torch
+    sc = Scenario(nd, nelem, 3, mapping="sine", ic="smooth", llf=True, seed=730)
+    ctx = dgmod.DG(**sc.dg_kwargs())
+    ud = torch.from_numpy(sc.u).cuda()
+    du_dev = ctx.rhs(ud).cpu()
+    for pin in (True, False):
+        uh = torch.from_numpy(sc.u.copy())
+        duh = torch.empty_like(uh)
+        if pin:
+            uh, duh = uh.pin_memory(), duh.pin_memory()
+        n0 = ctx.launch_count()
+        ctx.rhs_host(uh, duh)
+        torch.cuda.synchronize()
+        assert ctx.launch_count() - n0 == (3 if chunked else 2)
+        assert torch.equal(duh, du_dev)
+    for scheme in (0, 1):
+        ud = torch.from_numpy(sc.u).cuda()
+        uh = torch.from_numpy(sc.u.copy()).pin_memory()
+        for _ in range(2):
+            ctx.step(ud, 1e-3, scheme)
+            ctx.step_host(uh, 1e-3, scheme)
+        torch.cuda.synchronize()
+        assert torch.equal(uh, ud.cpu()), scheme
+    assert ctx.check_status() == dgmod.DG_OK
