@@ -193,18 +193,23 @@ def test_overlapped_launches_equal_serial_launches(dgmod, precision, staging, p,
     np.testing.assert_array_equal(res["overlap"][1], res["overlap"][3])
 
 
-@pytest.mark.parametrize("nd,nelem,chunked", [(3, [4, 3, 9], True), (3, [3, 2, 4], True), (2, [5, 11], True),
-                                             (3, [2, 3, 3], False)])
-def test_host_entry_points_upload_the_state_in_chunks(dgmod, nd, nelem, chunked):
+@pytest.mark.parametrize("nd,nelem,chunked,extra", [(3, [4, 3, 9], True, {}), (3, [3, 2, 4], True, {}),
+                                                   (2, [5, 11], True, {}), (3, [2, 3, 3], False, {}),
+                                                   (3, [3, 2, 8], True, {"precision": "fp32"}),
+                                                   (3, [2, 2, 8], False, {"nodes": "gauss", "mapping": "affine"})])
+def test_host_entry_points_upload_the_state_in_chunks(dgmod, nd, nelem, chunked, extra):
     # with at least 4 element layers along the last direction the host state arrives in 2 chunks of layers on a
     # copy stream, and the first interface fluxes are computed per chunk as it arrives (2 interface launches
     # instead of 1): bit for bit the device calls' results, for uneven chunks (9 layers), two layers per chunk
-    # (4), 2D, and 3 layers (one copy); pinned and pageable host memory
+    # (4), 2D, FP32, and one copy for 3 layers and for Gauss collocation; pinned and pageable host memory
     import torch
-    sc = Scenario(nd, nelem, 3, mapping="sine", ic="smooth", llf=True, seed=730)
-    ctx = dgmod.DG(**sc.dg_kwargs())
+    extra = dict(extra)
+    sc = Scenario(nd, nelem, 3, mapping=extra.pop("mapping", "sine"), ic="smooth", llf=True, seed=730)
+    ctx = dgmod.DG(**sc.dg_kwargs(), **extra)
     ud = torch.from_numpy(sc.u).cuda()
+    n0 = ctx.launch_count()
     du_dev = ctx.rhs(ud).cpu()
+    base = ctx.launch_count() - n0  # the device call's kernels; chunked: one interface launch more
     for pin in (True, False):
         uh = torch.from_numpy(sc.u.copy())
         duh = torch.empty_like(uh)
@@ -213,7 +218,7 @@ def test_host_entry_points_upload_the_state_in_chunks(dgmod, nd, nelem, chunked)
         n0 = ctx.launch_count()
         ctx.rhs_host(uh, duh)
         torch.cuda.synchronize()
-        assert ctx.launch_count() - n0 == (3 if chunked else 2)
+        assert ctx.launch_count() - n0 == base + (1 if chunked else 0)
         assert torch.equal(duh, du_dev)
     for scheme in (0, 1):
         ud = torch.from_numpy(sc.u).cuda()
