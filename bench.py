@@ -1005,6 +1005,12 @@ def oracle_pid_all_cores(reps: int = 8):
     return max(times) / (reps * u.shape[0] * u.shape[2]) * 1e9, cores
 
 
+def arm_config(args, world):
+    """The contract line's config, the same on both arms (the reference arm's sample is in its cpu_baseline)."""
+    return {"workload": WORKLOAD_SHORT, "l2": "flushed each step",
+            "parallelism": "slabs+halo" if world > 1 or args.slabs else "single GPU"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -1031,9 +1037,10 @@ def run_reference(args, rank, world):
     line = {"metric": METRIC, "value": pid, "unit": "ns/DOF/RHS", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "sample": "elements 1536-2047 (512 of 4096)", "l2": "n/a (CPU)"},
+            "config": arm_config(args, world),
             "cpu_baseline": {"value": pid, "unit": "ns/DOF/RHS", "cores": 1, "kind": "oracle",
-                             "sample": "one oracle RHS evaluation per step on 512 of the 4096 elements"},
+                             "sample": "one oracle RHS evaluation per step on elements 1536-2047 (512 of the "
+                                       "4096) of the 16^3 Taylor-Green mesh (%s)" % WORKLOAD},
             "e2e": {"value": pid, "unit": "ns/DOF/RHS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -1062,8 +1069,7 @@ def contract_line(args, world: int, results: dict, cpu) -> dict:
         "metric": METRIC, "value": sig(r64["pid_ns"]), "value_std": sig(r64["pid_std_ns"], 2), "unit": "ns/DOF/RHS",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sig(r64["ms_per_step"]),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_SHORT, "l2": "flushed each step",
-                   "parallelism": "slabs+halo" if world > 1 or args.slabs else "single GPU"},
+        "config": arm_config(args, world),
         "roofline": {"bound": rf["bound"], "achieved": sig(rf["achieved"]), "peak": sig(rf["peak"]),
                      "unit": rf["unit"], "frac": sig(rf["frac"], 3), "traffic": sig(rf["traffic"]),
                      "peak_src": rf["peak_src"]},
