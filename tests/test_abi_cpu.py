@@ -108,3 +108,33 @@ def test_noalloc_rejects_misaligned_arrays_before_any_device_call(built):
     assert call(dg.DG_FP32, ja32 + 2, flag) == dg.DG_ERR_ARG  # FP32 metric terms 2 bytes off
     assert call(dg.DG_FP64, ja64, flag + 2) == dg.DG_ERR_ARG  # the int flag 2 bytes off
     assert call(dg.DG_FP64, ja64, flag, uu=u + 4) == dg.DG_ERR_ARG  # the state 4 bytes off
+
+
+def test_mesh_size_limits_are_rejected_before_any_device_call(built):
+    # the kernels index nodes with 32-bit offsets: E * (p+1)^nd * (nd+2) must stay below 2^31 (DG_ERR_UNSUPPORTED),
+    # and every direction holds at most 2^20 elements (DG_ERR_ARG); both checks come before any device call
+    from paper_2112_10517_gb300 import dg
+    ctx = ctypes.c_void_p()
+    opts = dg.DgOpts()
+    opts.gamma = 1.4
+
+    def init(nelem, p, part=None):
+        mesh = dg.DgMesh()
+        mesh.ndims = len(nelem)
+        for i, n in enumerate(nelem):
+            mesh.nelem[i], mesh.lo[i], mesh.hi[i] = n, -1.0, 1.0
+        if part is None:
+            return dg.dg_init(ctypes.byref(ctx), ctypes.byref(mesh), p, None, ctypes.byref(opts))
+        pa = dg.DgPart()
+        pa.begin, pa.end = part
+        return dg.dg_init_part(ctypes.byref(ctx), ctypes.byref(mesh), p, None, ctypes.byref(opts), ctypes.byref(pa))
+
+    assert 189 ** 3 * 64 * 5 > 2 ** 31 - 1 > 188 ** 3 * 64 * 5
+    assert init([189, 189, 189], 3) == dg.DG_ERR_UNSUPPORTED
+    assert 128 ** 3 * 512 * 5 > 2 ** 31 - 1
+    assert init([128, 128, 128], 7) == dg.DG_ERR_UNSUPPORTED
+    assert init([1 << 21, 1], 1) == dg.DG_ERR_ARG                # more than 2^20 elements along x
+    # a slab counts its own layers plus the ghost layer: 2 + 1 layers of 1024 x 1024 at p = 1 (8 x 5 values)
+    assert 3 * 1024 * 1024 * 8 * 5 > 2 ** 31 - 1
+    assert init([1024, 1024, 4], 1, part=(0, 2)) == dg.DG_ERR_UNSUPPORTED
+    assert not ctx.value
