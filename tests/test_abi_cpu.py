@@ -127,14 +127,16 @@ def test_mesh_size_limits_are_rejected_before_any_device_call(built):
             return dg.dg_init(ctypes.byref(ctx), ctypes.byref(mesh), p, None, ctypes.byref(opts))
         pa = dg.DgPart()
         pa.begin, pa.end = part
-        return dg.dg_init_part(ctypes.byref(ctx), ctypes.byref(mesh), p, None, ctypes.byref(opts), ctypes.byref(pa))
+        return dg.dg_init_part(ctypes.byref(ctx), ctypes.byref(mesh), p, ctypes.byref(opts), ctypes.byref(pa))
 
     assert 189 ** 3 * 64 * 5 > 2 ** 31 - 1 > 188 ** 3 * 64 * 5
     assert init([189, 189, 189], 3) == dg.DG_ERR_UNSUPPORTED
     assert 128 ** 3 * 512 * 5 > 2 ** 31 - 1
     assert init([128, 128, 128], 7) == dg.DG_ERR_UNSUPPORTED
     assert init([1 << 21, 1], 1) == dg.DG_ERR_ARG                # more than 2^20 elements along x
-    # a slab counts its own layers plus the ghost layer: 2 + 1 layers of 1024 x 1024 at p = 1 (8 x 5 values)
-    assert 3 * 1024 * 1024 * 8 * 5 > 2 ** 31 - 1
-    assert init([1024, 1024, 4], 1, part=(0, 2)) == dg.DG_ERR_UNSUPPORTED
+    # a slab counts its own layers plus the ghost layer: 2 own layers of 1536 x 1536 elements at p = 3 would fit,
+    # with the ghost layer they do not
+    layer = 1536 * 1536 * 64 * 5
+    assert 2 * layer <= 2 ** 31 - 1 < 3 * layer
+    assert init([1536, 1536, 4], 3, part=(0, 2)) == dg.DG_ERR_UNSUPPORTED
     assert not ctx.value
