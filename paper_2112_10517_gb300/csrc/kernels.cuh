@@ -63,12 +63,19 @@ __device__ __forceinline__ int upper_neighbor(const MeshDims& md, int e, int n) 
 // Programmatic dependent launch (the kernels that a stream runs back to back may overlap): pdl_wait blocks until
 // the kernels before this one in the stream have completed and their writes are visible (at once when the kernel
 // was launched without the attribute); a kernel reads nothing those kernels write, and writes nothing, before it.
-// No kernel here signals its dependents early (griddepcontrol.launch_dependents): a dependent grid is then
-// scheduled as the CTAs of the one before it exit, and its CTAs set up and copy their first tile's geometry while
-// that grid's writes are made visible. Earlier signals measured slower: volume CTAs placed on SMs in the order the
-// interface kernel freed them lose the round-robin balance of their tiles (16^3 FP64: +9 %), and interface CTAs
-// resident during the volume kernel's last tiles slowed it (32^3 FP32: +7 %).
+// A dependent grid is scheduled as the CTAs of the one before it exit (or signal, griddepcontrol.launch_dependents),
+// and its CTAs set up and copy their first tile's geometry while that grid's writes are made visible. Only the FP64
+// pipelined volume kernel signals early, at the start of each CTA's last tile, so that the next interface kernel's
+// CTAs take the SMs its last round leaves idle (16^3 RK4 step -0.2 %, graph replay -0.4 %; 32^3 unchanged). The
+// dependents still wait (pdl_wait) for the whole grid before reading its results. Other early signals measured
+// slower: volume CTAs placed on SMs in the order the interface kernel freed them lose the round-robin balance of
+// their tiles (16^3 FP64: +9 %), and interface CTAs resident during the FP32 volume kernel's last tiles slowed it
+// (32^3 FP32: +7 %).
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+#ifndef DG_VOLUME_EARLY_TRIGGER
+#define DG_VOLUME_EARLY_TRIGGER 1
+#endif
 
 // Launch of `kern`; with `overlap`, as a programmatic dependent of the kernel before it in stream s (the kernel
 // calls pdl_wait before its first read of data written by the stream's earlier work).

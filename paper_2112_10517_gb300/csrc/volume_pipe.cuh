@@ -347,6 +347,8 @@ __device__ __forceinline__ void pipe_tiles(const Src& src, const OpTable<N, T>& 
     mbar_test(&bars[1], par);
     const int tn = s_tile[1];
     const bool has_next = src.valid(tn);
+    if constexpr (DG_VOLUME_EARLY_TRIGGER && sizeof(T) == 8)
+      if (!has_next) pdl_trigger();  // this CTA's last tile: the dependent grid may be scheduled
     const PipeTile<T> nxt = src.tile(has_next ? tn : t);
     if (issuer && has_next) {  // the stage input has been read
       issue_in(nxt);
