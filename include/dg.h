@@ -283,6 +283,9 @@ const char* dg_status_string(dg_status s);
  *      transport: NCCL send/recv, peer copies, or, for a slab that is its own neighbour, local copies);
  *   3. dg_part_unpack(ctx, state, recv_lo, recv_hi) writes them into the ghost layer of `state`;
  *   4. dg_rhs(ctx, state, du) or dg_step_stage(ctx, u, scratch, ..., stage).
+ * A stage can also overlap the transport of step 2 (Sec. 2.4: only the faces at the slab's ends read the ghost
+ * layer): dg_stage_interface(..., DG_REGION_INTERIOR) between steps 1 and 3, then after step 3
+ * dg_stage_interface(..., DG_REGION_BOUNDARY) and dg_stage_volume; the three together are dg_step_stage.
  * Each call queues on `stream` and synchronizes nothing. The result equals, bit for bit, the same elements of the
  * global context's result when both use the same volume-kernel staging. dg_step, dg_step_host, dg_rhs_host,
  * dg_vjp and dg_batch_* return DG_ERR_UNSUPPORTED for a partitioned context (they cannot exchange halos between
@@ -316,6 +319,19 @@ dg_status dg_part_unpack(dg_ctx* ctx, double* state, const double* recv_lo, cons
 dg_status dg_step_stage(dg_ctx* ctx, double* u, double* scratch, double t, double dt, int scheme, int stage,
                         dg_stream_t stream);
 int dg_stage_input(int scheme, int stage); /* 0: u, 1: scratch, -1: invalid scheme or stage */
+
+/* dg_step_stage in parts, for a partitioned context that overlaps its halo transport with computation (Sec. 2.4):
+   dg_stage_interface computes the interface fluxes of the stage's input state (dg_stage_input) for the faces of a
+   region of the slab: DG_REGION_INTERIOR, the faces of the own layers except the last, which read no ghost-layer
+   data (queue it before the ghost layer is unpacked); DG_REGION_BOUNDARY, the rest (the last own layer's faces and
+   the faces of the ghost layer, whose two planes must then hold the neighbours' data). dg_stage_volume then runs
+   the stage's volume kernel and update. Interior, boundary, volume in this order on one stream equal
+   dg_step_stage bit for bit. Arguments as dg_step_stage; DG_ERR_ARG for an ordinary context or another region. */
+enum { DG_REGION_INTERIOR = 0, DG_REGION_BOUNDARY = 1 };
+dg_status dg_stage_interface(dg_ctx* ctx, double* u, double* scratch, int scheme, int stage, int region,
+                             dg_stream_t stream);
+dg_status dg_stage_volume(dg_ctx* ctx, double* u, double* scratch, double t, double dt, int scheme, int stage,
+                          dg_stream_t stream);
 
 /* Conserved totals sum_e sum_i J_i W_i q_i per variable (Sec. 2: discrete conservation; q a device state array, W
    the tensor LGL weights), FP64 in a fixed order, into out_host[nvar]; the slab's own elements for a partitioned

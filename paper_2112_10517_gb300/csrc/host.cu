@@ -751,6 +751,52 @@ dg_status dg_step_stage(dg_ctx* c, double* u, double* scratch, double t, double 
   return run_stage(c, u, scratch, dt, scheme, stage, s);
 }
 
+dg_status dg_stage_interface(dg_ctx* c, double* u, double* scratch, int scheme, int stage, int region,
+                             dg_stream_t stream) {
+  dg_status st = check_step_args(c, u, scratch, 0.0, scheme);
+  if (st != DG_OK) return st;
+  if (!c->layer || dg_stage_input(scheme, stage) < 0) return DG_ERR_ARG;
+  if (region != DG_REGION_INTERIOR && region != DG_REGION_BOUNDARY) return DG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  const double* in = dg_stage_input(scheme, stage) == 1 ? scratch : u;
+  const void* ja = c->precision == DG_FP32 ? (const void*)c->d_Ja32 : (const void*)c->d_Ja;
+  const long long E = c->md.E, layer = c->layer;
+  // elements [layer, E - layer): the own layers but the last, whose faces read only own layers; the rest: the
+  // ghost layer [0, layer) (its faces along the cut only, the kernel's ghost rule) and the last own layer
+  long long ranges[2][2] = {{layer, E - layer}, {0, 0}};
+  int nr = 1;
+  if (region == DG_REGION_BOUNDARY) {
+    ranges[0][0] = 0, ranges[0][1] = layer;
+    ranges[1][0] = E - layer, ranges[1][1] = E;
+    nr = 2;
+  }
+  for (int r = 0; r < nr; ++r) {
+    if (ranges[r][1] <= ranges[r][0]) continue;  // a slab of one own layer has no interior faces
+    dgk::Variant v = c->var;
+    v.if_e0 = (int)ranges[r][0];
+    v.if_e1 = (int)ranges[r][1];
+    int slot;
+    dgk::prof_begin(c, dgk::KID_INTERFACE, s, &slot);
+    const cudaError_t e = dgk::launch_interface(c->nd, c->p, c->precision, c->surface_flux == DG_SURF_EC_LLF, c->md,
+                                                in, ja, c->d_face, c->gamma, c->d_flag, s, &v);
+    dgk::prof_end(c, s, slot);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return DG_OK;
+}
+
+dg_status dg_stage_volume(dg_ctx* c, double* u, double* scratch, double t, double dt, int scheme, int stage,
+                          dg_stream_t stream) {
+  (void)t;
+  const dg_status st = check_step_args(c, u, scratch, dt, scheme);
+  if (st != DG_OK) return st;
+  if (!c->layer || dg_stage_input(scheme, stage) < 0) return DG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  return run_stage(c, u, scratch, dt, scheme, stage, s, nullptr, true);
+}
+
 // Device staging of dg_step_host / dg_rhs_host: three state arrays, allocated at the first call.
 static dg_status ensure_host_staging(dg_ctx* c) {
   if (!c->d_hstage) {

@@ -37,6 +37,7 @@ DG_LAUNCH_OVERLAP, DG_LAUNCH_SERIAL = 0, 1
 STAGINGS = {"auto": DG_STAGING_AUTO, "direct": DG_STAGING_DIRECT, "pipelined": DG_STAGING_PIPELINED}
 LAUNCHES = {"overlap": DG_LAUNCH_OVERLAP, "serial": DG_LAUNCH_SERIAL}
 DG_RK4_CLASSIC, DG_LSRK45_CK = 0, 1
+DG_REGION_INTERIOR, DG_REGION_BOUNDARY = 0, 1
 KERNEL_VOLUME, KERNEL_INTERFACE, KERNEL_PROJECT = 0, 1, 2
 
 EXPORTED = ["dg_init", "dg_rhs", "dg_step", "dg_entropy_rate", "dg_check_status", "dg_get_info",
@@ -45,7 +46,7 @@ EXPORTED = ["dg_init", "dg_rhs", "dg_step", "dg_entropy_rate", "dg_check_status"
             "dg_batch_autotune", "dg_batch_set_tuning", "dg_batch_free", "dg_vjp", "dg_selftest_wait_timeout",
             "dg_profile_enable_kernels", "dg_profile_enable_sampled", "dg_step_host", "dg_rhs_host",
             "dg_init_part", "dg_part_get_info", "dg_part_pack", "dg_part_unpack", "dg_step_stage", "dg_stage_input",
-            "dg_conserved_totals"]
+            "dg_conserved_totals", "dg_stage_interface", "dg_stage_volume"]
 
 
 class DgMesh(ctypes.Structure):
@@ -119,6 +120,9 @@ _sig = {
     "dg_step_stage": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                      _vp]),
     "dg_stage_input": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
+    "dg_stage_interface": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]),
+    "dg_stage_volume": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                       _vp]),
     "dg_conserved_totals": (ctypes.c_int, [_vp, _vp, _dp, _vp]),
     "dg_selftest_wait_timeout": (ctypes.c_int, [_vp, _vp]),
 }
@@ -288,6 +292,25 @@ class DG:
             raise ValueError("scratch must be contiguous float64 with %d elements" % (nreg * self.state_len))
         check(dg_step_stage(self.ctx, self._state(u, "u"), ctypes.c_void_p(scratch.data_ptr()), 0.0, float(dt),
                             int(scheme), int(stage), _stream_handle(stream)), "dg_step_stage")
+        return u
+
+    def _scratch(self, scratch, scheme):
+        nreg = 2 if scheme == DG_RK4_CLASSIC else 1
+        if scratch.numel() < nreg * self.state_len or scratch.dtype != __import__("torch").float64 or \
+                not scratch.is_contiguous():
+            raise ValueError("scratch must be contiguous float64 with %d elements" % (nreg * self.state_len))
+        return ctypes.c_void_p(scratch.data_ptr())
+
+    def stage_interface(self, u, scratch, scheme: int, stage: int, region: int, stream=None):
+        """The interface fluxes of stage `stage`'s input for DG_REGION_INTERIOR (faces that read no ghost-layer data)
+        or DG_REGION_BOUNDARY (the rest) of a slab (dg_stage_interface)."""
+        check(dg_stage_interface(self.ctx, self._state(u, "u"), self._scratch(scratch, scheme), int(scheme),
+                                 int(stage), int(region), _stream_handle(stream)), "dg_stage_interface")
+
+    def stage_volume(self, u, scratch, dt: float, scheme: int, stage: int, stream=None):
+        """The volume kernel and update of stage `stage` after both regions' interface fluxes (dg_stage_volume)."""
+        check(dg_stage_volume(self.ctx, self._state(u, "u"), self._scratch(scratch, scheme), 0.0, float(dt),
+                              int(scheme), int(stage), _stream_handle(stream)), "dg_stage_volume")
         return u
 
     @staticmethod

@@ -35,21 +35,34 @@ def neighbors(rank: int, world: int):
 TAG_DOWN, TAG_UP = 7, 8
 
 
-def exchange(send_lo, send_hi, recv_lo, recv_hi, rank: int, world: int, group=None):
-    """send_lo -> the lower neighbour's recv_hi, send_hi -> the upper neighbour's recv_lo (blocking until the
-    receives are complete on the current stream for NCCL, on the host for gloo). One rank: local copies."""
+def exchange_start(send_lo, send_hi, recv_lo, recv_hi, rank: int, world: int, group=None):
+    """Queues send_lo -> the lower neighbour's recv_hi and send_hi -> the upper neighbour's recv_lo, and returns the
+    requests that exchange_finish waits for. NCCL runs the transfers on its own stream after the work queued so far
+    on the current stream (the pack), so that work queued on the current stream before exchange_finish overlaps
+    them. One rank: local copies on the current stream, no requests."""
     if world == 1:
         recv_lo.copy_(send_hi)
         recv_hi.copy_(send_lo)
-        return
+        return []
     import torch.distributed as dist
     lower, upper = neighbors(rank, world)
     ops = [dist.P2POp(dist.isend, send_lo, lower, group, TAG_DOWN),
            dist.P2POp(dist.irecv, recv_hi, upper, group, TAG_DOWN),
            dist.P2POp(dist.isend, send_hi, upper, group, TAG_UP),
            dist.P2POp(dist.irecv, recv_lo, lower, group, TAG_UP)]
-    for req in dist.batch_isend_irecv(ops):
+    return dist.batch_isend_irecv(ops)
+
+
+def exchange_finish(pending):
+    """Waits for exchange_start's requests (NCCL: the current stream waits for the transfers; gloo: the host)."""
+    for req in pending or ():
         req.wait()
+
+
+def exchange(send_lo, send_hi, recv_lo, recv_hi, rank: int, world: int, group=None):
+    """exchange_start and exchange_finish: the receives are complete on the current stream (NCCL) or on the host
+    (gloo) when it returns."""
+    exchange_finish(exchange_start(send_lo, send_hi, recv_lo, recv_hi, rank, world, group))
 
 
 def exchange_local(bufs):
@@ -73,21 +86,24 @@ def allreduce_sum(values, device, group=None):
 
 
 class Slab:
-    """One rank's slab: a partitioned context (dg.DG with part=...) and its four halo buffers. rhs() and step() run
-    pack -> exchange -> unpack -> compute on each state the library reads; `exchange_fn(send_lo, send_hi, recv_lo,
-    recv_hi)` moves the planes (default: exchange() over torch.distributed with this rank's neighbours)."""
+    """One rank's slab: a partitioned context (dg.DG with part=...) and its four halo buffers. rhs() runs pack ->
+    exchange -> unpack -> RHS; step() runs, per stage, pack -> exchange start -> the interior faces' fluxes (which
+    read no ghost-layer data, so they overlap the transfers) -> exchange finish -> unpack -> the boundary faces'
+    fluxes -> volume and update. `exchange_fn(send_lo, send_hi, recv_lo, recv_hi)` queues the plane transfers and
+    returns what exchange_finish waits for (default: exchange_start over torch.distributed with this rank's
+    neighbours; a blocking transport may return None)."""
 
     def __init__(self, ctx, rank: int = 0, world: int = 1, group=None, exchange_fn=None):
         if ctx.part is None:
             raise ValueError("Slab needs a partitioned context (dg.DG(..., part=(begin, end)))")
         self.ctx, self.rank, self.world, self.group = ctx, rank, world, group
         self.bufs = ctx.halo_buffers()
-        self.exchange_fn = exchange_fn or (lambda a, b, c, d: exchange(a, b, c, d, rank, world, group))
+        self.exchange_fn = exchange_fn or (lambda a, b, c, d: exchange_start(a, b, c, d, rank, world, group))
 
     def halo(self, state, stream=None):
         send_lo, send_hi, recv_lo, recv_hi = self.bufs
         self.ctx.pack(state, send_lo, send_hi, stream=stream)
-        self.exchange_fn(send_lo, send_hi, recv_lo, recv_hi)
+        exchange_finish(self.exchange_fn(send_lo, send_hi, recv_lo, recv_hi))
         self.ctx.unpack(state, recv_lo, recv_hi, stream=stream)
 
     def rhs(self, u, du=None):
@@ -97,7 +113,14 @@ class Slab:
     def step(self, u, scratch, dt: float, scheme: int):
         from . import dg
         stages = 4 if scheme == dg.DG_RK4_CLASSIC else 5
+        send_lo, send_hi, recv_lo, recv_hi = self.bufs
         for st in range(stages):
-            self.halo(u if dg.DG.stage_input(scheme, st) == 0 else scratch[0])
-            self.ctx.step_stage(u, scratch, dt, scheme, st)
+            state = u if dg.DG.stage_input(scheme, st) == 0 else scratch[0]
+            self.ctx.pack(state, send_lo, send_hi)
+            pending = self.exchange_fn(send_lo, send_hi, recv_lo, recv_hi)
+            self.ctx.stage_interface(u, scratch, scheme, st, dg.DG_REGION_INTERIOR)  # overlaps the transfers
+            exchange_finish(pending)
+            self.ctx.unpack(state, recv_lo, recv_hi)
+            self.ctx.stage_interface(u, scratch, scheme, st, dg.DG_REGION_BOUNDARY)
+            self.ctx.stage_volume(u, scratch, dt, scheme, st)
         return u

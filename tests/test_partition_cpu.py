@@ -128,7 +128,10 @@ class FakeSlabContext:
     def unpack(self, state, a, b, stream=None):
         self.calls.append(("unpack", id(state)))
 
-    def step_stage(self, u, scratch, dt, scheme, st):
+    def stage_interface(self, u, scratch, scheme, st, region):
+        self.calls.append(("iface", st, region))
+
+    def stage_volume(self, u, scratch, dt, scheme, st):
         self.calls.append(("stage", st))
 
     def rhs(self, u, du=None):
@@ -139,24 +142,38 @@ def test_slab_exchanges_each_stage_input_before_the_stage(monkeypatch):
     # RK4 reads u at stage 0 and the stage state scratch[0] at stages 1-3; CK(5,4) reads u at every stage
     import types
     import sys
-    fake_dg = types.SimpleNamespace(DG_RK4_CLASSIC=0, DG=types.SimpleNamespace(
-        stage_input=lambda scheme, st: 1 if scheme == 0 and st > 0 else 0))
+    fake_dg = types.SimpleNamespace(DG_RK4_CLASSIC=0, DG_REGION_INTERIOR=0, DG_REGION_BOUNDARY=1,
+                                    DG=types.SimpleNamespace(stage_input=lambda scheme, st: 1 if scheme == 0 and st > 0
+                                                             else 0))
     monkeypatch.setitem(sys.modules, "paper_2112_10517_gb300.dg", fake_dg)
     monkeypatch.setattr(sys.modules["paper_2112_10517_gb300"], "dg", fake_dg, raising=False)
     ctx = FakeSlabContext()
     moved = []
-    slab = partition.Slab(ctx, exchange_fn=lambda *bufs: moved.append(len(bufs)))
+
+    class Pending:  # a transfer in flight: its wait is recorded among the context's calls
+        def wait(self):
+            ctx.calls.append(("finish",))
+
+    def transport(*bufs):
+        moved.append(len(bufs))
+        ctx.calls.append(("start",))
+        return [Pending()]
+    slab = partition.Slab(ctx, exchange_fn=transport)
     u, scratch = torch.zeros(3), torch.zeros(2, 3)
     slab.step(u, scratch, 0.1, 0)
     y = id(scratch[0])
     kinds = [c[0] for c in ctx.calls]
-    assert kinds == ["pack", "unpack", "stage"] * 4 and moved == [4] * 4
+    # per stage: the interior faces between the start and the finish of the transfers, the boundary faces after
+    # the unpack, then the volume kernel
+    assert kinds == ["pack", "start", "iface", "finish", "unpack", "iface", "stage"] * 4 and moved == [4] * 4
+    assert [c[2] for c in ctx.calls if c[0] == "iface"] == [0, 1] * 4
     assert [c[1] for c in ctx.calls if c[0] == "stage"] == [0, 1, 2, 3]
-    assert ctx.calls[0][1] == id(u) and ctx.calls[3][1] != id(u)
+    packs = [c[1] for c in ctx.calls if c[0] == "pack"]
+    assert packs[0] == id(u) and packs[1] != id(u)
     ctx.calls.clear()
     slab.step(u, scratch[:1], 0.1, 1)
     assert [c[1] for c in ctx.calls if c[0] == "pack"] == [id(u)] * 5
     ctx.calls.clear()
     slab.rhs(u)
-    assert [c[0] for c in ctx.calls] == ["pack", "unpack", "rhs"]
+    assert [c[0] for c in ctx.calls] == ["pack", "start", "finish", "unpack", "rhs"]
     del y

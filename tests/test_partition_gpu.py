@@ -178,3 +178,56 @@ def test_partition_arguments(dgmod):
     import ctypes
     info = dgmod.DgPartInfo()
     assert dgmod.dg_part_get_info(whole.ctx, ctypes.byref(info)) == dgmod.DG_ERR_ARG
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+@pytest.mark.parametrize("precision,nelem,nslabs", [("fp64", [3, 2, 6], 3), ("fp32", [3, 2, 6], 2),
+                                                   ("fp64", [2, 3, 4], 4)])
+def test_slab_stages_overlapping_the_exchange_equal_whole_mesh(dgmod, scheme, precision, nelem, nslabs):
+    # per stage: pack, the interior faces' fluxes (no ghost-layer data: they may overlap the transfers), exchange,
+    # unpack, the boundary faces' fluxes, volume; slabs of 2 own layers and of 1 (no interior faces); bit for bit
+    # the whole mesh's steps; then the same through partition.Slab on a single slab (its own neighbour)
+    import torch
+    from paper_2112_10517_gb300 import partition
+    sc = Scenario(3, nelem, 3, mapping="sine", ic="smooth", llf=True, seed=84)
+    whole, slabs, layer = make_slabs(dgmod, sc, nslabs, precision=precision)
+    uw = torch.from_numpy(sc.u).cuda()
+    nreg = 2 if scheme == 0 else 1
+    dt = 0.01
+    scr = [torch.full((nreg,) + s[0].shape, float("nan"), dtype=torch.float64, device="cuda") for s in slabs]
+    stages = 4 if scheme == 0 else 5
+    for _ in range(2):
+        whole.step(uw, dt, scheme)
+        for st in range(stages):
+            ins = [s[1] if dgmod.DG.stage_input(scheme, st) == 0 else scr[k][0] for k, s in enumerate(slabs)]
+            for (ctx, _, bufs, _), state in zip(slabs, ins):
+                ctx.pack(state, bufs[0], bufs[1])
+            for k, s in enumerate(slabs):
+                s[0].stage_interface(s[1], scr[k], scheme, st, dgmod.DG_REGION_INTERIOR)
+            partition.exchange_local([s[2] for s in slabs])
+            for (ctx, _, bufs, _), state in zip(slabs, ins):
+                ctx.unpack(state, bufs[2], bufs[3])
+            for k, s in enumerate(slabs):
+                s[0].stage_interface(s[1], scr[k], scheme, st, dgmod.DG_REGION_BOUNDARY)
+                s[0].stage_volume(s[1], scr[k], dt, scheme, st)
+    ref = uw.cpu().numpy()
+    for ctx, u, _, (b, e) in slabs:
+        assert ctx.check_status() == dgmod.DG_OK
+        np.testing.assert_array_equal(u.cpu().numpy()[layer:], ref[b * layer:e * layer])
+    # one slab of the whole mesh through partition.Slab (default transport: local copies)
+    one = dgmod.DG(**sc.dg_kwargs(), part=(0, nelem[-1]), precision=precision)
+    u1 = torch.full(one.shape, float("nan"), dtype=torch.float64, device="cuda")
+    u1[layer:] = torch.from_numpy(sc.u).cuda()
+    s1 = torch.full((nreg,) + one.shape, float("nan"), dtype=torch.float64, device="cuda")
+    slab = partition.Slab(one)
+    for _ in range(2):
+        slab.step(u1, s1, dt, scheme)
+    np.testing.assert_array_equal(u1.cpu().numpy()[layer:], ref)
+    # an ordinary context has no regions; an unknown region is an argument error
+    with pytest.raises(dgmod.DGError) as ei:
+        whole.stage_interface(uw, torch.zeros((nreg,) + whole.shape, dtype=torch.float64, device="cuda"), scheme, 0,
+                              dgmod.DG_REGION_INTERIOR)
+    assert ei.value.status == dgmod.DG_ERR_ARG
+    with pytest.raises(dgmod.DGError) as ei:
+        one.stage_interface(u1, s1, scheme, 0, 2)
+    assert ei.value.status == dgmod.DG_ERR_ARG
