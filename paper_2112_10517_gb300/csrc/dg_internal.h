@@ -109,7 +109,8 @@ struct Variant {
   // [E][ND][4][NL] (computed once at dg_init); nullptr: the interface kernel forms them from the metric terms.
   const double* fgeo;
   // The interface kernel's elements: the faces of elements [if_e0, if_e1) (if_e1 = 0: all; dg_step_host's first
-  // interface fluxes, computed per chunk of the state as it arrives from the host).
+  // interface fluxes, computed per chunk of the state as it arrives from the host). if_e1 may exceed E: the range
+  // then wraps around to element 0 (a slab's boundary faces: its last own layer and its ghost layer).
   int if_e0, if_e1;
 };
 
@@ -137,9 +138,10 @@ cudaError_t launch_totals(int nd, int p, long long nelem, const double* q, const
 // Halo planes of a partitioned context (see misc.cu): pack copies the owned boundary planes of state u into
 // send_lo/send_hi; unpack copies recv_lo/recv_hi into the ghost layer's two planes. layer: elements per layer;
 // first_owned, last_owned: the first elements of the first and last owned layers.
+// overlap: launched as a programmatic dependent of the kernel before it in s (dg_opts.launch).
 cudaError_t launch_halo(int nd, int p, int layer, long long first_owned, long long last_owned, double* u,
                         const double* recv_lo, const double* recv_hi, double* send_lo, double* send_hi, bool pack,
-                        cudaStream_t s);
+                        bool overlap, cudaStream_t s);
 // One CTA whose bounded mbarrier wait runs out and sets FLAG_WAIT_TIMEOUT in *flag (dg_selftest_wait_timeout).
 cudaError_t launch_wait_probe(int* flag, cudaStream_t s);
 void ck45_coefficients(int stage, double* a, double* b);

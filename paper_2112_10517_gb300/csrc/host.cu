@@ -590,7 +590,7 @@ dg_status dg_part_pack(dg_ctx* c, const double* state, double* send_lo, double* 
   c->last_stream = s;
   c->launches += 1;
   return cuda_status(dgk::launch_halo(c->nd, c->p, (int)c->layer, c->layer, c->E - c->layer, const_cast<double*>(state),
-                                      nullptr, nullptr, send_lo, send_hi, true, s));
+                                      nullptr, nullptr, send_lo, send_hi, true, c->var.overlap != 0, s));
 }
 
 dg_status dg_part_unpack(dg_ctx* c, double* state, const double* recv_lo, const double* recv_hi, dg_stream_t stream) {
@@ -599,7 +599,7 @@ dg_status dg_part_unpack(dg_ctx* c, double* state, const double* recv_lo, const 
   c->last_stream = s;
   c->launches += 1;
   return cuda_status(dgk::launch_halo(c->nd, c->p, (int)c->layer, c->layer, c->E - c->layer, state, recv_lo, recv_hi,
-                                      nullptr, nullptr, false, s));
+                                      nullptr, nullptr, false, c->var.overlap != 0, s));
 }
 
 int dg_stage_input(int scheme, int stage) {
@@ -762,28 +762,21 @@ dg_status dg_stage_interface(dg_ctx* c, double* u, double* scratch, int scheme, 
   const double* in = dg_stage_input(scheme, stage) == 1 ? scratch : u;
   const void* ja = c->precision == DG_FP32 ? (const void*)c->d_Ja32 : (const void*)c->d_Ja;
   const long long E = c->md.E, layer = c->layer;
-  // elements [layer, E - layer): the own layers but the last, whose faces read only own layers; the rest: the
-  // ghost layer [0, layer) (its faces along the cut only, the kernel's ghost rule) and the last own layer
-  long long ranges[2][2] = {{layer, E - layer}, {0, 0}};
-  int nr = 1;
-  if (region == DG_REGION_BOUNDARY) {
-    ranges[0][0] = 0, ranges[0][1] = layer;
-    ranges[1][0] = E - layer, ranges[1][1] = E;
-    nr = 2;
-  }
-  for (int r = 0; r < nr; ++r) {
-    if (ranges[r][1] <= ranges[r][0]) continue;  // a slab of one own layer has no interior faces
-    dgk::Variant v = c->var;
-    v.if_e0 = (int)ranges[r][0];
-    v.if_e1 = (int)ranges[r][1];
-    int slot;
-    dgk::prof_begin(c, dgk::KID_INTERFACE, s, &slot);
-    const cudaError_t e = dgk::launch_interface(c->nd, c->p, c->precision, c->surface_flux == DG_SURF_EC_LLF, c->md,
-                                                in, ja, c->d_face, c->gamma, c->d_flag, s, &v);
-    dgk::prof_end(c, s, slot);
-    if (e != cudaSuccess) return cuda_status(e);
-  }
-  return DG_OK;
+  // elements [layer, E - layer): the own layers but the last, whose faces read only own layers; the rest, one
+  // range wrapping around: the last own layer [E - layer, E) and the ghost layer [0, layer) (its faces along the
+  // cut only, the kernel's ghost rule)
+  const long long e0 = region == DG_REGION_INTERIOR ? layer : E - layer;
+  const long long e1 = region == DG_REGION_INTERIOR ? E - layer : E + layer;
+  if (e1 <= e0) return DG_OK;  // a slab of one own layer has no interior faces
+  dgk::Variant v = c->var;
+  v.if_e0 = (int)e0;
+  v.if_e1 = (int)e1;
+  int slot;
+  dgk::prof_begin(c, dgk::KID_INTERFACE, s, &slot);
+  const cudaError_t e = dgk::launch_interface(c->nd, c->p, c->precision, c->surface_flux == DG_SURF_EC_LLF, c->md,
+                                              in, ja, c->d_face, c->gamma, c->d_flag, s, &v);
+  dgk::prof_end(c, s, slot);
+  return cuda_status(e);
 }
 
 dg_status dg_stage_volume(dg_ctx* c, double* u, double* scratch, double t, double dt, int scheme, int stage,

@@ -238,10 +238,13 @@ template <int ND, int N, typename T, bool LLF>
 __global__ void __launch_bounds__(256) interface_kernel(const double* __restrict__ u, const T* __restrict__ Ja,
                                                         T* __restrict__ face, MeshDims md, T gamma, int* flag,
                                                         Variant var) {
-  // the faces of elements [if_e0, if_e1) (all when if_e1 = 0); ND E NL < 2^31 (checked at dg_init)
+  // the faces of elements [if_e0, if_e1) (all when if_e1 = 0; past E wrapping around to element 0);
+  // ND E NL < 2^31 (checked at dg_init)
+  const long long total = (long long)ND * md.E * Geo<ND, N>::NL;
   const long long end = (long long)ND * (var.if_e1 > 0 ? var.if_e1 : md.E) * Geo<ND, N>::NL;
-  const long long idx = (long long)ND * var.if_e0 * Geo<ND, N>::NL + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long idx = (long long)ND * var.if_e0 * Geo<ND, N>::NL + (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= end) return;
+  if (idx >= total) idx -= total;
   if (var.ghost) {  // a partition's ghost layer: only its faces along the last direction (the lower boundary)
     const int t = (int)(idx / Geo<ND, N>::NL);
     if (t / ND < var.ghost && t % ND != ND - 1) return;

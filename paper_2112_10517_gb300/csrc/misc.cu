@@ -163,6 +163,7 @@ __global__ void halo_kernel(double* u, const double* recv_lo, const double* recv
                             long long last_owned, int pack) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long count = (long long)layer * nv * nl;
+  pdl_wait();  // the state comes from the kernel before (a stage update), the ghost layer is read after this one
   if (g >= count) return;
   const int fn = (int)(g % nl);
   const long long t = g / nl;
@@ -182,15 +183,16 @@ __global__ void halo_kernel(double* u, const double* recv_lo, const double* recv
 
 cudaError_t launch_halo(int nd, int p, int layer, long long first_owned, long long last_owned, double* u,
                         const double* recv_lo, const double* recv_hi, double* send_lo, double* send_hi, bool pack,
-                        cudaStream_t s) {
+                        bool overlap, cudaStream_t s) {
   const int N = p + 1, nv = nd + 2;
   const int nl = nd == 3 ? N * N : N;
   const long long count = (long long)layer * nv * nl;
   if (count <= 0) return cudaSuccess;
   const int threads = 256;
-  halo_kernel<<<(unsigned)((count + threads - 1) / threads), threads, 0, s>>>(
-      u, recv_lo, recv_hi, send_lo, send_hi, layer, nv, nl, nl * N, first_owned, last_owned, pack ? 1 : 0);
-  return cudaGetLastError();
+  const cudaError_t e = launch_kernel(halo_kernel, dim3((unsigned)((count + threads - 1) / threads)), dim3(threads), 0,
+                                      s, overlap, u, recv_lo, recv_hi, send_lo, send_hi, layer, nv, nl, nl * N,
+                                      first_owned, last_owned, pack ? 1 : 0);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_totals(int nd, int p, long long nelem, const double* q, const double* JW, double* partial,
