@@ -16,6 +16,7 @@ cudaError_t launch_interface_t(int llf, MeshDims md, const double* u, const T* J
   const int threads = 128;
   const long long blocks = (total + threads - 1) / threads;
   auto kern = llf ? interface_kernel<ND, N, T, true> : interface_kernel<ND, N, T, false>;
+  if constexpr (sizeof(T) == 4) kern = llf ? interface_kernel_f32<ND, N, true> : interface_kernel_f32<ND, N, false>;
   const cudaError_t e = launch_kernel(kern, dim3((unsigned)blocks), dim3(threads), 0, s, var.overlap != 0, u, Ja, face,
                                       md, (T)gamma, flag, var);
   return e != cudaSuccess ? e : cudaGetLastError();

@@ -234,10 +234,11 @@ __device__ __forceinline__ void interface_node(const double* __restrict__ u, con
   for (int c = 0; c < G::NV; ++c) fo[c * G::NL] = f[c];
 }
 
+// The interface kernel's body: one face node per thread (see interface_node); kernels below by precision.
 template <int ND, int N, typename T, bool LLF>
-__global__ void __launch_bounds__(256) interface_kernel(const double* __restrict__ u, const T* __restrict__ Ja,
-                                                        T* __restrict__ face, MeshDims md, T gamma, int* flag,
-                                                        Variant var) {
+__device__ __forceinline__ void interface_items(const double* __restrict__ u, const T* __restrict__ Ja,
+                                                T* __restrict__ face, const MeshDims& md, T gamma, int* flag,
+                                                const Variant& var) {
   // the faces of elements [if_e0, if_e1) (all when if_e1 = 0; past E wrapping around to element 0);
   // ND E NL < 2^31 (checked at dg_init)
   const long long total = (long long)ND * md.E * Geo<ND, N>::NL;
@@ -253,6 +254,26 @@ __global__ void __launch_bounds__(256) interface_kernel(const double* __restrict
     interface_node<ND, N, T, LLF, 0>(u, Ja, face, md, gamma, flag, (int)idx, var);
   else
     interface_node<ND, N, T, LLF, 1>(u, Ja, face, md, gamma, flag, (int)idx, var);
+}
+
+template <int ND, int N, typename T, bool LLF>
+__global__ void __launch_bounds__(256) interface_kernel(const double* __restrict__ u, const T* __restrict__ Ja,
+                                                        T* __restrict__ face, MeshDims md, T gamma, int* flag,
+                                                        Variant var) {
+  interface_items<ND, N, T, LLF>(u, Ja, face, md, gamma, flag, var);
+}
+
+// FP32: at most 40 registers (6 CTAs of 256 threads): 12 of the launcher's 128-thread CTAs fit per SM instead of
+// 10 at 50 registers, for the memory-latency-bound kernel (32^3 launch 38.5 -> 37.8 us; 16^3 unchanged at 10.5 us,
+// where the launch's fixed latency dominates)
+#ifndef DG_INTERFACE_F32_MIN_BLOCKS
+#define DG_INTERFACE_F32_MIN_BLOCKS 6
+#endif
+template <int ND, int N, bool LLF>
+__global__ void __launch_bounds__(256, DG_INTERFACE_F32_MIN_BLOCKS)
+    interface_kernel_f32(const double* __restrict__ u, const float* __restrict__ Ja, float* __restrict__ face,
+                         MeshDims md, float gamma, int* flag, Variant var) {
+  interface_items<ND, N, float, LLF>(u, Ja, face, md, gamma, flag, var);
 }
 
 // ---------------------------------------------------------------------------------------------------
