@@ -95,7 +95,8 @@ typedef struct dg_metrics {
    the inverse logarithmic mean of rho/p (Sec. 3.1, Algorithms 2 and 3; Sec. 7.2), for ablation studies. All
    variants compute the same means up to rounding; the default (both 0) is the fastest on this hardware.
      logmean = DG_LOGMEAN_SHARED_RCP  no division: one reciprocal serves both means' u and the inverse
-                                      mean's series; the mean's series in the polynomial 1/log form;
+                                      mean's series; the mean's series in the polynomial 1/log form; in FP64
+                                      the series continued to u^7 for 1e-4 <= u < 1e-2 instead of logarithms;
                DG_LOGMEAN_ALG         Algorithms 2 and 3 as stated (divisions, log of the ratio per pair);
                DG_LOGMEAN_ALG_POLY    the same with the polynomial 1/log form of the mean's series branch.
      precompute_logs = 1              logarithms of density and rho/p once per node instead of once per pair
