@@ -315,10 +315,12 @@ __device__ __forceinline__ double wide_Li_f64(double r, double u) {
 // Series branches: L = s1 (1/2 - u/6 - 2u^2/45 - 22u^3/945), the polynomial form of 1/log of Sec. 3.1
 // (a multiplication instead of a division), and Li = (2 + 2u/3 + 2u^2/5 + 2u^3/7)/s2 (Algorithm 3); the innermost
 // coefficients (of u^2) in FP32 for FP64 means (series_inner).
-// FP64 between u = 1e-4 and 1e-2: the same series to u^7 (wide_L_f64, wide_Li_f64).
+// WIDE (FP64): between u = 1e-4 and 1e-2 the same series to u^7 (wide_L_f64, wide_Li_f64). The volume terms' beta
+// form takes it; the product form (the interface kernel, which it measured 2 % slower on the Taylor-Green vortex,
+// whose pairs never need it) keeps the paper's two branches.
 // Log branches: L = (b - a)/log(b/a), Li = log(b/a)/(b - a), as in Algorithms 2 and 3.
 // ---------------------------------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool WIDE = true>
 __device__ __forceinline__ void log_means(T a1, T b1, T a2, T b2, T& L, T& Li) {
   const T s1 = a1 + b1, d1 = b1 - a1;
   const T s2 = a2 + b2, d2 = b2 - a2;
@@ -328,13 +330,13 @@ __device__ __forceinline__ void log_means(T a1, T b1, T a2, T b2, T& L, T& Li) {
   const T u1 = f1 * f1, u2 = f2 * f2;
   if (Num<T>::series(u1))
     L = s1 * (T(0.5) + u1 * (T(-1.0 / 6.0) + u1 * series_inner<T>(u1, float(-2.0 / 45.0), float(-22.0 / 945.0))));
-  else if (wide_series<T>(u1))
+  else if (WIDE && wide_series<T>(u1))
     L = wide_L<T>(s1, u1);
   else
     L = d1 / Num<T>::log(b1 / a1);
   if (Num<T>::series(u2))
     Li = r2 * (T(2.0) + u2 * (T(2.0 / 3.0) + u2 * series_inner<T>(u2, float(2.0 / 5.0), float(2.0 / 7.0))));
-  else if (wide_series<T>(u2))
+  else if (WIDE && wide_series<T>(u2))
     Li = wide_Li<T>(r2, u2);
   else
     Li = Num<T>::log(b2 / a2) / d2;
@@ -485,7 +487,7 @@ __device__ __forceinline__ void ranocha_means(const T* a, const T* b, T ppa, T p
   else if constexpr (LM == LM_ALG || LM == LM_ALG_POLY)
     log_means_alg<T, LM>(a[Q::RHO], b[Q::RHO], a2, b2, L, Li);
   else
-    log_means<T>(a[Q::RHO], b[Q::RHO], a2, b2, L, Li);
+    log_means<T, false>(a[Q::RHO], b[Q::RHO], a2, b2, L, Li);
 }
 
 // ---------------------------------------------------------------------------------------------------
