@@ -113,6 +113,7 @@ __device__ __forceinline__ Variant general_variant(int lm = LM_SHARED_RCP) {
   v.ghost = 0;                         // nor partitioned contexts
   v.fgeo = nullptr;                    // the interface kernel forms the geometry from the instances' metric terms
   v.if_e0 = v.if_e1 = 0;
+  v.tiles = nullptr;
   return v;
 }
 
@@ -188,8 +189,9 @@ struct BatchTileSource {
     const BatchTile bt = tiles[t];
     const BatchInst& in = insts[bt.inst];
     return PipeTile<T>{in.u, static_cast<const T*>(in.Ja), in.invJ, static_cast<const T*>(in.face), in.du,
-                       in.flag, in.md, bt.e0};
+                       in.flag, in.md, bt.e0, 1 << 30};  // bounded by the kernel's tile size and the instance's end
   }
+  __device__ __forceinline__ void finish() const {}  // the counter is reset before each launch
 };
 
 // The pipelined batch kernel of degree N at a CTA size: the tile of the direct kernel (elements per tile of the

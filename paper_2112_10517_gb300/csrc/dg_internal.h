@@ -112,6 +112,9 @@ struct Variant {
   // interface fluxes, computed per chunk of the state as it arrives from the host). if_e1 may exceed E: the range
   // then wraps around to element 0 (a slab's boundary faces: its last own layer and its ghost layer).
   int if_e0, if_e1;
+  // The pipelined volume kernel's tile counter and its count of finished CTAs (both zero between launches; the
+  // last CTA of a launch resets them); nullptr: tiles round-robin over the grid.
+  int* tiles;
 };
 
 // Chunks of element layers in which dg_step_host / dg_rhs_host bring the state to the device (measured on the
@@ -207,6 +210,7 @@ struct dg_ctx {
   double* d_fgeo;  // interface geometry (Variant::fgeo; FP64 curvilinear contexts)
   double* d_red;   // entropy-rate partials + result
   int* d_flag;     // non-physical-state flag
+  int* d_tiles;    // the pipelined volume kernel's tile counters (Variant::tiles)
   cudaStream_t last_stream;
   // profiling
   int prof_on;

@@ -215,6 +215,7 @@ void release(dg_ctx* c) {
   cudaFree(c->d_red);
   cudaFree(c->d_fgeo);
   cudaFree(c->d_flag);
+  cudaFree(c->d_tiles);
   if (c->prof_ev) {
     for (int i = 0; i < 2 * c->prof_cap; ++i) cudaEventDestroy(c->prof_ev[i]);
     free(c->prof_ev);
@@ -502,12 +503,15 @@ dg_status init_ctx(dg_ctx** out, const dg_mesh* mesh, int polydeg, const dg_metr
   // reduction scratch: entropy-rate pairs or conserved totals (nvar per block), then the result
   if (ce == cudaSuccess) ce = dev_alloc(&c->d_red, (size_t)(nv + 2) * dgk::entropy_rate_blocks() + nv + 2);
   if (ce == cudaSuccess) ce = dev_alloc(&c->d_flag, 1);
+  if (ce == cudaSuccess) ce = dev_alloc(&c->d_tiles, 2);
   if (ce == cudaSuccess && c->precision == DG_FP32) ce = dev_alloc(&c->d_Ja32, nja);
   if (ce == cudaSuccess && gauss) ce = dev_alloc(&c->d_gface, 2 * nface);
   if (ce == cudaSuccess) ce = cudaMemcpy(c->d_Ja, c->h_Ja, nja * sizeof(double), cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) ce = cudaMemcpy(c->d_invJ, invJ.data(), nj * sizeof(double), cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) ce = cudaMemcpy(c->d_JW, JW.data(), nj * sizeof(double), cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) ce = cudaMemset(c->d_flag, 0, sizeof(int));
+  if (ce == cudaSuccess) ce = cudaMemset(c->d_tiles, 0, 2 * sizeof(int));
+  c->var.tiles = c->d_tiles;
   // interface geometry of FP64 curvilinear contexts: per interface node (element e, direction n, face node l) the
   // lower element's metric vector at its face node scaled by p(p+1)/8 (the lifted flux's factor: 2 x N(N-1)/16) and
   // gamma |m2|^2 / 2, the LLF wave speed's geometric factor (Variant::fgeo, [E][nd][4][NL])

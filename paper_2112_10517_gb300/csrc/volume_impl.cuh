@@ -40,6 +40,17 @@ constexpr int elems_per_block() {
 #ifndef DG_VOLUME_PIPE_MIN_TILES_PER_CTA
 #define DG_VOLUME_PIPE_MIN_TILES_PER_CTA 2
 #endif
+// Tiles from a counter in the pipelined volume kernel (MeshTileSource), per precision. Measured on dg_rhs, p = 3,
+// 16 x 16 x k elements (volume kernel, us, round-robin -> counter): FP64 k = 12: 138.6 -> 131.0, 16: 159.9 -> 163.7,
+// 17: 182.2 -> 174.0, 19: 182.3 -> 185.8, 20: 202.8 -> 195.7, 32: 313.3 -> 305.3, where the launcher's prediction
+// picks the faster in each of the ten sizes measured; FP32 (half tiles of one element) 16: 18.5 -> 22.6, 32:
+// 28.8 -> 33.0, slower at every size but k = 12: FP32 keeps round-robin.
+#ifndef DG_VOLUME_DYNAMIC_TILES_F64
+#define DG_VOLUME_DYNAMIC_TILES_F64 1
+#endif
+#ifndef DG_VOLUME_DYNAMIC_TILES
+#define DG_VOLUME_DYNAMIC_TILES 0
+#endif
 
 template <int N, typename T>
 OpTable<N, T> op_table() {
@@ -78,10 +89,11 @@ cudaError_t launch_volume_pipe(MeshDims md, const double* u, const T* Ja, const 
         if (!ok) return cudaErrorNotSupported;
       }
       auto kern = volume_pipe_kernel<ND, N, T, EPB, EPI>;
-      // resident CTAs on the device (occupancy x SMs), computed once per device together with the opt-in
+      // occupancy and SM count of the device (resident CTAs: their product), computed once per device together
+      // with the opt-in
       static PerDeviceCache cache;
-      long long ctas = 0;
-      cudaError_t ce = per_device(cache, &ctas, [&](long long* v) {
+      long long occ_sms = 0;
+      cudaError_t ce = per_device(cache, &occ_sms, [&](long long* v) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int dev = 0, sms = 0, occ = 0;
@@ -90,10 +102,12 @@ cudaError_t launch_volume_pipe(MeshDims md, const double* u, const T* Ja, const 
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, EPB * TPE, smem)) != cudaSuccess)
           return e;
         if (occ < 1) return cudaErrorNotSupported;
-        *v = (long long)occ * sms;
+        *v = ((long long)occ << 32) | (long long)sms;
         return cudaSuccess;
       });
       if (ce != cudaSuccess) return ce;
+      const int sms = (int)(occ_sms & 0xFFFFFFFF);
+      const long long ctas = (occ_sms >> 32) * sms;
       const int ntiles = (md.E - var.ghost + EPB - 1) / EPB;  // from element var.ghost on
       // auto: enough tiles per CTA, and not FP32 at p = 2 (3 elements of 27 threads per CTA, each thread issuing
       // many small copies: measured 25 % slower than the per-tile kernel; every other degree and precision gains)
@@ -101,8 +115,29 @@ cudaError_t launch_volume_pipe(MeshDims md, const double* u, const T* Ja, const 
       if (var.pipe == 1 && (!kAutoOk || (long long)ntiles < (long long)DG_VOLUME_PIPE_MIN_TILES_PER_CTA * ctas))
         return cudaErrorNotSupported;
       const int grid = ntiles < ctas ? ntiles : (int)ctas;
+      // Tiles from the context's counter with the last round in half tiles (MeshTileSource), where every CTA has at
+      // least two full tiles and that schedule is predicted to finish sooner; otherwise round-robin. The kernel
+      // ends when its busiest SM does: round-robin gives an SM up to ceil(tiles / SMs) full tiles, the counter
+      // balances the SMs to about a half tile, ceil(half tiles / SMs). Each schedule's efficiency is its mean
+      // load per SM over that maximum; the counter is taken where it is higher by more than its own cost (the
+      // atomic fetches, the half tiles' barriers: about 1 %).
+      const int elems = md.E - var.ghost;
+      int nt = ntiles, nfull = ntiles;
+      int* dyn = nullptr;
+      constexpr bool kDyn = sizeof(T) == 8 ? DG_VOLUME_DYNAMIC_TILES_F64 : DG_VOLUME_DYNAMIC_TILES;
+      if (kDyn && EPB >= 2 && var.tiles && elems / EPB >= 2 * grid) {
+        constexpr int half = EPB / 2;
+        const int halves = (elems + half - 1) / half;
+        const double eff_rr = (double)ntiles / ((double)sms * ((ntiles + sms - 1) / sms));
+        const double eff_dyn = (double)halves / ((double)sms * ((halves + sms - 1) / sms));
+        if (eff_dyn > eff_rr + 0.01) {
+          nfull = elems / EPB - grid;
+          nt = nfull + (elems - nfull * EPB + half - 1) / half;
+          dyn = var.tiles;
+        }
+      }
       const cudaError_t e = launch_kernel(kern, dim3(grid), dim3(EPB * TPE), smem, s, var.overlap != 0, u, Ja, invJ,
-                                          face, du, md, op_table<N, T>(), (T)gamma, flag, epi, var, ntiles);
+                                          face, du, md, op_table<N, T>(), (T)gamma, flag, epi, var, nt, nfull, dyn);
       return e != cudaSuccess ? e : cudaGetLastError();
     }
   }

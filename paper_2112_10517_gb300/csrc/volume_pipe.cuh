@@ -158,22 +158,47 @@ struct PipeTile {
   int* flag;          // the mesh's status flag
   MeshDims md;
   int e0;
+  int nel;  // elements in the tile (at most EPB; the mesh's last tile may hold fewer still)
 };
 
-// The tiles of one mesh, round-robin over the persistent grid: t = blockIdx.x, blockIdx.x + gridDim.x, ...
-// (first and next are called by thread 0, which passes the index on through shared memory). Tile t starts at element
-// mesh.e0 + t EPB (mesh.e0: the first element computed, past a partition's ghost layer).
+// The tiles of one mesh (first and next are called by thread 0, which passes the index on through shared memory).
+// Tiles t < nfull hold EPB elements from element mesh.e0 + t EPB (mesh.e0: the first element computed, past a
+// partition's ghost layer), the tiles after them EPB/2 elements each (the mesh's last round).
+// dyn == nullptr: round-robin over the persistent grid, t = blockIdx.x, blockIdx.x + gridDim.x, ...
+// dyn != nullptr: each CTA's first tile is blockIdx.x, the following ones are taken from the counter dyn[0] (one
+// tile ahead), so that SMs whose CTAs finish early take more tiles; with the half-size tiles of the last round the
+// SMs finish within about a half tile of one another. The round-robin grid instead finishes with whole tiles on some
+// SMs only (the time of ceil(tiles / SM) rounds). The last CTA to finish resets dyn[0] and its count dyn[1].
 template <typename T, int EPB>
 struct MeshTileSource {
+  static constexpr int kHalf = EPB / 2 > 0 ? EPB / 2 : 1;
   PipeTile<T> mesh;
   int ntiles;
+  int nfull;
+  int* dyn;
   __device__ __forceinline__ int first() const { return blockIdx.x; }
-  __device__ __forceinline__ int next(int t) const { return t + gridDim.x; }
+  __device__ __forceinline__ int next(int t) const { return dyn ? (int)gridDim.x + atomicAdd(dyn, 1) : t + gridDim.x; }
   __device__ __forceinline__ bool valid(int t) const { return t < ntiles; }
   __device__ __forceinline__ PipeTile<T> tile(int t) const {
     PipeTile<T> r = mesh;
-    r.e0 = mesh.e0 + t * EPB;
+    if (t < nfull) {
+      r.e0 = mesh.e0 + t * EPB;
+      r.nel = EPB;
+    } else {
+      r.e0 = mesh.e0 + nfull * EPB + (t - nfull) * kHalf;
+      r.nel = kHalf;
+    }
     return r;
+  }
+  // by thread 0 of each CTA after its last fetch: the counter's fetches are ordered before the count of finished
+  // CTAs, so the last CTA resets the counter after every fetch of this launch
+  __device__ __forceinline__ void finish() const {
+    if (!dyn) return;
+    __threadfence();
+    if (atomicAdd(dyn + 1, 1) == (int)gridDim.x - 1) {
+      atomicExch(dyn, 0);
+      atomicExch(dyn + 1, 0);
+    }
   }
 };
 
@@ -225,8 +250,9 @@ __device__ __forceinline__ void pipe_tiles(const Src& src, const OpTable<N, T>& 
       }
     }
   };
+  auto tile_nel = [](const PipeTile<T>& tt) { return min(min(EPB, tt.nel), tt.md.E - tt.e0); };
   auto issue_in = [=](const PipeTile<T>& tt) {
-    const int e0 = tt.e0, nel = min(EPB, tt.md.E - e0);
+    const int e0 = tt.e0, nel = tile_nel(tt);
     if constexpr (S::kBulk) mbar_expect_tx(&bars[0], (unsigned)(nel * S::kIn));
     copy(s_in, tt.in + (size_t)e0 * G::NV * G::NDOF, nel * G::NV * G::NDOF, &bars[0]);
     if constexpr (!S::kBulk) cp_async_arrive(&bars[0]);
@@ -234,13 +260,13 @@ __device__ __forceinline__ void pipe_tiles(const Src& src, const OpTable<N, T>& 
   // The metric group in two parts: the metric terms (curvilinear meshes; written once, at set-up), with the byte
   // count of the whole group, then the faces' lifted fluxes (written by the interface kernel before this one).
   auto issue_ja_geo = [=](const PipeTile<T>& tt) {
-    const int e0 = tt.e0, nel = min(EPB, tt.md.E - e0);
+    const int e0 = tt.e0, nel = tile_nel(tt);
     if constexpr (S::kBulk)
       mbar_expect_tx(&bars[1], (has_ja ? (unsigned)(nel * S::kJa) : 0u) + 2u * ND * (unsigned)(nel * S::kFace));
     if (has_ja) copy(s_ja, tt.Ja + (size_t)e0 * ND * ND * G::NDOF, nel * ND * ND * G::NDOF, &bars[1]);
   };
   auto issue_ja_dep = [=](const PipeTile<T>& tt) {
-    const int e0 = tt.e0, nel = min(EPB, tt.md.E - e0);
+    const int e0 = tt.e0, nel = tile_nel(tt);
     const MeshDims& md = tt.md;
 #pragma unroll
     for (int n = 0; n < ND; ++n) {
@@ -260,14 +286,14 @@ __device__ __forceinline__ void pipe_tiles(const Src& src, const OpTable<N, T>& 
   // The phase-C group (may be empty), likewise: 1/J (curvilinear meshes) with the group's byte count, then the
   // stage update's operands.
   auto issue_c_geo = [=](const PipeTile<T>& tt) {
-    const int e0 = tt.e0, nel = min(EPB, tt.md.E - e0);
+    const int e0 = tt.e0, nel = tile_nel(tt);
     if constexpr (S::kBulk)
       mbar_expect_tx(&bars[2], (has_ja ? (unsigned)(nel * S::kInvJ) : 0u) + (kFused ? (unsigned)(nel * S::kIn) : 0u) +
                                    (need_y ? (unsigned)(nel * S::kIn) : 0u));
     if (has_ja) copy(s_ij, tt.invJ + (size_t)e0 * G::NDOF, nel * G::NDOF, &bars[2]);
   };
   auto issue_c_dep = [=](const PipeTile<T>& tt) {
-    const int e0 = tt.e0, nel = min(EPB, tt.md.E - e0);
+    const int e0 = tt.e0, nel = tile_nel(tt);
     const int nin = nel * G::NV * G::NDOF;
     const size_t so = (size_t)e0 * G::NV * G::NDOF;
     if (kFused) copy(s_eu, epi.u + so, nin, &bars[2]);
@@ -314,7 +340,7 @@ __device__ __forceinline__ void pipe_tiles(const Src& src, const OpTable<N, T>& 
   for (int k = 0; src.valid(t); ++k) {
     const unsigned par = (unsigned)(k & 1);  // every group is copied once per tile
     const PipeTile<T> cur = src.tile(t);
-    const int e0 = cur.e0, nel = min(EPB, cur.md.E - e0);
+    const int e0 = cur.e0, nel = tile_nel(cur);
     flag = cur.flag;
     if (tid == 0) s_tile[1] = src.next(t);
     if (!s_ok[0]) {  // all threads read the same slot: the whole CTA leaves the loop
@@ -449,14 +475,15 @@ __device__ __forceinline__ void pipe_tiles(const Src& src, const OpTable<N, T>& 
       cp_async_wait_all();
     }
   }
+  if (tid == 0) src.finish();
 }
 
 template <int ND, int N, typename T, int EPB, int EPI>
 __global__ void __launch_bounds__(EPB* Geo<ND, N>::TPE, pipe_min_ctas<ND, N, T, EPB>())
     volume_pipe_kernel(const double* __restrict__ in, const T* __restrict__ Ja, const double* __restrict__ invJ,
                        const T* __restrict__ face, double* du, MeshDims md, OpTable<N, T> op, T gamma, int* flag,
-                       Epilogue epi, Variant var, int ntiles) {
-  const MeshTileSource<T, EPB> src{{in, Ja, invJ, face, du, flag, md, var.ghost}, ntiles};
+                       Epilogue epi, Variant var, int ntiles, int nfull, int* dyn) {
+  const MeshTileSource<T, EPB> src{{in, Ja, invJ, face, du, flag, md, var.ghost, EPB}, ntiles, nfull, dyn};
   pipe_tiles<ND, N, T, EPB, EPI>(src, op, gamma, epi, var);
 }
 
