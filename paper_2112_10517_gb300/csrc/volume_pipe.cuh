@@ -1,5 +1,6 @@
 // Pipelined volume kernel (Eq. fluxdiff-SBP-opDsplit, the same arithmetic as volume_tile):
-// persistent CTAs take element tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...; one thread copies the tiles'
+// persistent CTAs take element tiles round-robin, t = blockIdx.x, blockIdx.x + gridDim.x, ... (or, FP64 where the
+// launcher predicts an earlier end, from a counter with a half-tile last round: MeshTileSource); one thread copies the tiles'
 // data into shared memory with bulk asynchronous copies (cp.async.bulk, the TMA engine), each group of arrays
 // completing on its own mbarrier. A tile runs in three phases -- A: node quantities from the stage input,
 // B: the two-point fluxes along lines, whose sums start from the lifted interface fluxes (metric terms, faces),
