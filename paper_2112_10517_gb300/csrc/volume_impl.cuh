@@ -124,8 +124,11 @@ cudaError_t launch_volume_pipe(MeshDims md, const double* u, const T* Ja, const 
       const int elems = md.E - var.ghost;
       int nt = ntiles, nfull = ntiles;
       int* dyn = nullptr;
-      constexpr bool kDyn = sizeof(T) == 8 ? DG_VOLUME_DYNAMIC_TILES_F64 : DG_VOLUME_DYNAMIC_TILES;
-      if (kDyn && EPB >= 2 && var.tiles && elems / EPB >= 2 * grid) {
+      // (only where a half tile's lines of one direction fill whole warps, as the pair phase assigns threads
+      // direction-major: 3D p = 3 and p = 1; elsewhere its warps would run partly empty)
+      constexpr bool kHalfWarps = EPB % 2 == 0 && (EPB / 2) * Geo<ND, N>::NL % 32 == 0;
+      constexpr bool kDyn = kHalfWarps && (sizeof(T) == 8 ? DG_VOLUME_DYNAMIC_TILES_F64 : DG_VOLUME_DYNAMIC_TILES);
+      if (kDyn && var.tiles && elems / EPB >= 2 * grid) {
         constexpr int half = EPB / 2;
         const int halves = (elems + half - 1) / half;
         const double eff_rr = (double)ntiles / ((double)sms * ((ntiles + sms - 1) / sms));
