@@ -33,7 +33,7 @@ LIBS = {
                 + VOLUME_OBJS,
     "libdgpeaks.so": ["peaks.cu"],
 }
-HEADERS = ["dg_internal.h", "kernels.cuh", "dgmath.cuh", "volume_impl.cuh", "volume_pipe.cuh"]
+HEADERS = ["dg_internal.h", "kernels.cuh", "dgmath.cuh", "volume_impl.cuh", "volume_pipe.cuh", "tile_plan.h"]
 
 
 def _nvcc() -> str:

@@ -115,32 +115,15 @@ cudaError_t launch_volume_pipe(MeshDims md, const double* u, const T* Ja, const 
       if (var.pipe == 1 && (!kAutoOk || (long long)ntiles < (long long)DG_VOLUME_PIPE_MIN_TILES_PER_CTA * ctas))
         return cudaErrorNotSupported;
       const int grid = ntiles < ctas ? ntiles : (int)ctas;
-      // Tiles from the context's counter with the last round in half tiles (MeshTileSource), where every CTA has at
-      // least two full tiles and that schedule is predicted to finish sooner; otherwise round-robin. The kernel
-      // ends when its busiest SM does: round-robin gives an SM up to ceil(tiles / SMs) full tiles, the counter
-      // balances the SMs to about a half tile, ceil(half tiles / SMs). Each schedule's efficiency is its mean
-      // load per SM over that maximum; the counter is taken where it is higher by more than its own cost (the
-      // atomic fetches, the half tiles' barriers: about 1 %).
-      const int elems = md.E - var.ghost;
-      int nt = ntiles, nfull = ntiles;
-      int* dyn = nullptr;
-      // (only where a half tile's lines of one direction fill whole warps, as the pair phase assigns threads
+      // round-robin, or tiles from the context's counter with the last round in half tiles (tile_plan.h), only
+      // where a half tile's lines of one direction fill whole warps (the pair phase assigns threads
       // direction-major: 3D p = 3 and p = 1; elsewhere its warps would run partly empty)
       constexpr bool kHalfWarps = EPB % 2 == 0 && (EPB / 2) * Geo<ND, N>::NL % 32 == 0;
       constexpr bool kDyn = kHalfWarps && (sizeof(T) == 8 ? DG_VOLUME_DYNAMIC_TILES_F64 : DG_VOLUME_DYNAMIC_TILES);
-      if (kDyn && var.tiles && elems / EPB >= 2 * grid) {
-        constexpr int half = EPB / 2;
-        const int halves = (elems + half - 1) / half;
-        const double eff_rr = (double)ntiles / ((double)sms * ((ntiles + sms - 1) / sms));
-        const double eff_dyn = (double)halves / ((double)sms * ((halves + sms - 1) / sms));
-        if (eff_dyn > eff_rr + 0.01) {
-          nfull = elems / EPB - grid;
-          nt = nfull + (elems - nfull * EPB + half - 1) / half;
-          dyn = var.tiles;
-        }
-      }
-      const cudaError_t e = launch_kernel(kern, dim3(grid), dim3(EPB * TPE), smem, s, var.overlap != 0, u, Ja, invJ,
-                                          face, du, md, op_table<N, T>(), (T)gamma, flag, epi, var, nt, nfull, dyn);
+      const TilePlan tp = tile_plan(md.E - var.ghost, EPB, grid, sms, kDyn && var.tiles != nullptr);
+      const cudaError_t e =
+          launch_kernel(kern, dim3(grid), dim3(EPB * TPE), smem, s, var.overlap != 0, u, Ja, invJ, face, du, md,
+                        op_table<N, T>(), (T)gamma, flag, epi, var, tp.ntiles, tp.nfull, tp.counter ? var.tiles : nullptr);
       return e != cudaSuccess ? e : cudaGetLastError();
     }
   }

@@ -19,6 +19,7 @@
 #pragma once
 
 #include "kernels.cuh"
+#include "tile_plan.h"
 
 namespace dgk {
 
@@ -172,7 +173,6 @@ struct PipeTile {
 // SMs only (the time of ceil(tiles / SM) rounds). The last CTA to finish resets dyn[0] and its count dyn[1].
 template <typename T, int EPB>
 struct MeshTileSource {
-  static constexpr int kHalf = EPB / 2 > 0 ? EPB / 2 : 1;
   PipeTile<T> mesh;
   int ntiles;
   int nfull;
@@ -182,13 +182,9 @@ struct MeshTileSource {
   __device__ __forceinline__ bool valid(int t) const { return t < ntiles; }
   __device__ __forceinline__ PipeTile<T> tile(int t) const {
     PipeTile<T> r = mesh;
-    if (t < nfull) {
-      r.e0 = mesh.e0 + t * EPB;
-      r.nel = EPB;
-    } else {
-      r.e0 = mesh.e0 + nfull * EPB + (t - nfull) * kHalf;
-      r.nel = kHalf;
-    }
+    int first;
+    tile_range(nfull, EPB, mesh.md.E - mesh.e0, t, first, r.nel);
+    r.e0 = mesh.e0 + first;
     return r;
   }
   // by thread 0 of each CTA after its last fetch: the counter's fetches are ordered before the count of finished
