@@ -213,12 +213,16 @@ def clock_sampler(local_rank: int, device):
 
 
 # ------------------------------------------------------------------------------------------------------
+# the volume kernel's sources (the launcher and the tile schedule included)
+DIGEST_SOURCES = ("dgmath.cuh", "kernels.cuh", "volume.cu", "volume_impl.cuh", "volume_inst.cu", "volume_pipe.cuh",
+                  "tile_plan.h")
+
+
 def source_digest(root: str = ROOT) -> str:
     """sha256 (first 16 hex digits) of the volume kernel's sources with comments and blank lines removed: it changes
     with the compiled code, not with its comments."""
     h = hashlib.sha256()
-    for f in ("dgmath.cuh", "kernels.cuh", "volume.cu", "volume_impl.cuh", "volume_inst.cu", "volume_pipe.cuh",
-              "tile_plan.h"):
+    for f in DIGEST_SOURCES:
         with open(os.path.join(root, "paper_2112_10517_gb300", "csrc", f)) as fh:
             for line in fh:
                 code = line.split("//", 1)[0].rstrip()

@@ -9,7 +9,7 @@ import time
 
 import bench
 
-CSRC = ("dgmath.cuh", "kernels.cuh", "volume.cu", "volume_impl.cuh", "volume_inst.cu", "volume_pipe.cuh")
+CSRC = bench.DIGEST_SOURCES
 
 
 def copy_tree(tmp_path):
