@@ -125,7 +125,9 @@ typedef struct dg_metrics {
      DG_STAGING_DIRECT     one CTA per tile, loads issued by its threads.
    All evaluate the same terms; the pipelined kernel starts each line's sums from the lifted interface fluxes and
    the direct one adds them after the sums, so the two agree to rounding (the parity bounds), and DG_STAGING_AUTO
-   gives bit for bit the result of the kernel it selects. A pipelined kernel whose wait for its own
+   gives bit for bit the result of the kernel it selects. The order in which the pipelined kernel's CTAs take the
+   tiles (round-robin, or on some DG_FP64 meshes from a counter in the context's workspace, with smaller tiles
+   last) changes no result: each element's arithmetic is the same in any tile. A pipelined kernel whose wait for its own
    copies runs out (bounded; it cannot under normal operation) skips the rest of its tiles and raises the flag that
    dg_check_status reports as DG_ERR_TIMEOUT.
    launch: how dg_rhs / dg_step queue the interface kernel and the pipelined volume kernel.
