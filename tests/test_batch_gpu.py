@@ -1,7 +1,7 @@
 """Batched RHS (dg_batch_*): many meshes of uneven size and degree, one persistent volume launch per degree. Each
 instance's
 du must match dg_rhs on its own context (the same formulas; the compiler may contract multiply-adds differently
-in the two kernels, so agreement is to rounding, judged like the parity tests) and the oracle; the autotuner's
+in the two kernels, so agreement is to rounding, measured like the parity tests) and the oracle; the autotuner's
 choices must not change results beyond rounding."""
 import numpy as np
 import pytest
