@@ -34,6 +34,11 @@ def test_digest_ignores_comments_and_blank_lines_but_not_code(tmp_path):
     assert bench.source_digest(root) == d0
     open(path, "w").write(text + "\nstatic const int a_new_constant = 1;\n")
     assert bench.source_digest(root) != d0
+    open(path, "w").write(text)
+    # the tile schedule decides which tiles the kernel runs: a change to it is a change of the kernel
+    plan = os.path.join(root, "paper_2112_10517_gb300", "csrc", "tile_plan.h")
+    open(plan, "a").write("\nstatic const int changed_plan = 3;\n")
+    assert bench.source_digest(root) != d0
 
 
 def test_committed_traffic_only_for_the_source_it_was_measured_on(tmp_path):
